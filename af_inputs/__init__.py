@@ -1,0 +1,328 @@
+"""Seeded synthetic problem descriptions and initial data.
+
+This module holds problem set-up only -- mesh geometry, initial functions, their cell
+averages by quadrature and their point values -- and none of the numerical method's
+arithmetic. Both the CUDA path's tests/benchmark and the CPU oracle consume the arrays
+it produces, so the two sides always start from identical inputs.
+
+Layout of a 2D state (periodic, row-major [ny][nx], i fastest):
+  ub[j,i] cell average, V[j,i] at (x_{i+1/2}, y_{j+1/2}), X[j,i] at (x_{i+1/2}, y_j),
+  Y[j,i] at (x_i, y_{j+1/2}).  A 1D state is (ub[i], P[i] = u(x_{i+1/2})).
+
+Cell averages use a tensor Gauss-Legendre rule on sub-cells (exact closed forms for
+single Fourier modes); point values are exact evaluations. Disc indicators use the
+strict inequality.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable, List, Sequence, Tuple
+
+import numpy as np
+import torch
+
+
+@dataclasses.dataclass
+class Spec:
+    """Problem description: periodic mesh, flux, diffusion potential, bounds, options.
+
+    flux: ("zero", ()), ("linear", (cx, cy)), ("burgers", (coef,)) for f = coef*u^2 in
+          every direction, ("bl", (g,)) for f1 = u^2/(u^2+(1-u)^2), f2 = f1*(1-g(1-u)^2).
+    diff: ("none", ()), ("const", (k0,)) for a = k0*u,
+          ("pwl", (klo, lo, khi, hi)) for a = klo*min(u-lo,0) + khi*max(u-hi,0),
+          ("pme", (m,)) for a = u^m, ("cubic", (c1, c2, c3)) for a = c1 u + c2 u^2 + c3 u^3.
+    blend: "off", "plain" (smoothness indicator) or "external" (per-cell indicator input).
+    """
+    dim: int
+    nx: int
+    ny: int = 1
+    x0: float = 0.0
+    x1: float = 1.0
+    y0: float = 0.0
+    y1: float = 1.0
+    flux: Tuple[str, Sequence[float]] = ("zero", ())
+    diff: Tuple[str, Sequence[float]] = ("none", ())
+    umin: float = 0.0
+    umax: float = 1.0
+    limiter: bool = True
+    blend: str = "off"
+    gamma: float = 1.0
+    rk: int = 3
+    cfl: float = 0.0          # 0 -> 0.33/d (the paper's experiments)
+    T: float = 0.0
+    name: str = ""
+
+    @property
+    def dx(self) -> float:
+        return (self.x1 - self.x0) / self.nx
+
+    @property
+    def dy(self) -> float:
+        return (self.y1 - self.y0) / self.ny if self.dim == 2 else 1.0
+
+    @property
+    def cells(self) -> int:
+        return self.nx * (self.ny if self.dim == 2 else 1)
+
+    def with_size(self, nx: int, ny: int | None = None) -> "Spec":
+        return dataclasses.replace(self, nx=nx, ny=(ny if ny is not None else (nx if self.dim == 2 else 1)))
+
+
+# ----------------------------------------------------------------------------------
+# quadrature
+
+def _gauss(order: int):
+    x, w = np.polynomial.legendre.leggauss(order)
+    return x, w
+
+
+def cell_average_2d(func: Callable, spec: Spec, sub: int = 4, order: int = 5,
+                    device="cpu", row_chunk: int = 64) -> torch.Tensor:
+    """Cell averages of func(x, y) by a tensor Gauss rule on sub x sub sub-cells."""
+    gx, gw = _gauss(order)
+    # local offsets inside a unit cell [0,1]
+    offs = []
+    wts = []
+    for s in range(sub):
+        for q in range(order):
+            offs.append((s + 0.5 + 0.5 * gx[q]) / sub)
+            wts.append(gw[q] / (2 * sub))
+    offs = torch.tensor(offs, dtype=torch.float64, device=device)
+    wts = torch.tensor(wts, dtype=torch.float64, device=device)
+    nx, ny = spec.nx, spec.ny
+    dx, dy = spec.dx, spec.dy
+    out = torch.empty((ny, nx), dtype=torch.float64, device=device)
+    xs = spec.x0 + (torch.arange(nx, dtype=torch.float64, device=device)[:, None] + offs[None, :]) * dx
+    for j0 in range(0, ny, row_chunk):
+        j1 = min(ny, j0 + row_chunk)
+        ys = spec.y0 + (torch.arange(j0, j1, dtype=torch.float64, device=device)[:, None] + offs[None, :]) * dy
+        # shape (rows, qy, nx, qx)
+        Xg = xs[None, None, :, :]
+        Yg = ys[:, :, None, None]
+        vals = func(Xg, Yg)
+        avg = torch.einsum("rqnp,q,p->rn", vals, wts, wts)
+        out[j0:j1] = avg
+    return out
+
+
+def cell_average_1d(func: Callable, spec: Spec, sub: int = 4, order: int = 5, device="cpu") -> torch.Tensor:
+    gx, gw = _gauss(order)
+    offs, wts = [], []
+    for s in range(sub):
+        for q in range(order):
+            offs.append((s + 0.5 + 0.5 * gx[q]) / sub)
+            wts.append(gw[q] / (2 * sub))
+    offs = torch.tensor(offs, dtype=torch.float64, device=device)
+    wts = torch.tensor(wts, dtype=torch.float64, device=device)
+    xs = spec.x0 + (torch.arange(spec.nx, dtype=torch.float64, device=device)[:, None] + offs[None, :]) * spec.dx
+    return (func(xs) * wts[None, :]).sum(dim=1)
+
+
+def points_2d(func: Callable, spec: Spec, device="cpu"):
+    """Exact point values (V, X, Y) of func(x, y)."""
+    i = torch.arange(spec.nx, dtype=torch.float64, device=device)
+    j = torch.arange(spec.ny, dtype=torch.float64, device=device)
+    xc = spec.x0 + (i + 0.5) * spec.dx   # x_i
+    xf = spec.x0 + (i + 1.0) * spec.dx   # x_{i+1/2}
+    yc = spec.y0 + (j + 0.5) * spec.dy
+    yf = spec.y0 + (j + 1.0) * spec.dy
+    V = func(xf[None, :], yf[:, None])
+    X = func(xf[None, :], yc[:, None])
+    Y = func(xc[None, :], yf[:, None])
+    return V, X, Y
+
+
+def points_1d(func: Callable, spec: Spec, device="cpu"):
+    i = torch.arange(spec.nx, dtype=torch.float64, device=device)
+    return func(spec.x0 + (i + 1.0) * spec.dx)
+
+
+def state_2d(func: Callable, spec: Spec, device="cpu", sub: int = 4, order: int = 5) -> List[torch.Tensor]:
+    ub = cell_average_2d(func, spec, sub=sub, order=order, device=device)
+    V, X, Y = points_2d(func, spec, device=device)
+    return [ub.contiguous(), V.contiguous(), X.contiguous(), Y.contiguous()]
+
+
+# ----------------------------------------------------------------------------------
+# initial functions
+
+def sine_1d_state(spec: Spec, device="cpu"):
+    """u0 = sin(x): closed-form cell averages (2/dx) sin(dx/2) sin(x_i)."""
+    i = torch.arange(spec.nx, dtype=torch.float64, device=device)
+    xc = spec.x0 + (i + 0.5) * spec.dx
+    ub = (2.0 / spec.dx) * math.sin(spec.dx / 2) * torch.sin(xc)
+    P = torch.sin(spec.x0 + (i + 1.0) * spec.dx)
+    return [ub, P]
+
+
+def mode_1d_state(spec: Spec, k: float, shift: float = 1.0, amp: float = 1.0, device="cpu"):
+    """u0 = shift + amp*sin(k x) with closed-form cell averages."""
+    i = torch.arange(spec.nx, dtype=torch.float64, device=device)
+    xc = spec.x0 + (i + 0.5) * spec.dx
+    fac = math.sin(k * spec.dx / 2) / (k * spec.dx / 2)
+    ub = shift + amp * fac * torch.sin(k * xc)
+    P = shift + amp * torch.sin(k * (spec.x0 + (i + 1.0) * spec.dx))
+    return [ub, P]
+
+
+def mode_2d_state(spec: Spec, k: float, shift: float = 1.0, amp: float = 1.0, device="cpu"):
+    """u0 = shift + amp*sin(k (x + y)) (Example 6.1 in 2D) with closed-form averages."""
+    i = torch.arange(spec.nx, dtype=torch.float64, device=device)
+    j = torch.arange(spec.ny, dtype=torch.float64, device=device)
+    xc = spec.x0 + (i + 0.5) * spec.dx
+    yc = spec.y0 + (j + 0.5) * spec.dy
+    fx = math.sin(k * spec.dx / 2) / (k * spec.dx / 2)
+    fy = math.sin(k * spec.dy / 2) / (k * spec.dy / 2)
+    ub = shift + amp * fx * fy * torch.sin(k * (xc[None, :] + yc[:, None]))
+    f = lambda x, y: shift + amp * torch.sin(k * (x + y))
+    V, X, Y = points_2d(f, spec, device=device)
+    return [ub.contiguous(), V.contiguous(), X.contiguous(), Y.contiguous()]
+
+
+def discs_fn(x, y):
+    """+1 on the disc r<0.35 about (-0.5,-0.5), -1 on the disc r<0.35 about (0.5,0.5)."""
+    r1 = (x + 0.5) ** 2 + (y + 0.5) ** 2
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
+    return (r1 < 0.35 ** 2).to(torch.float64) - (r2 < 0.35 ** 2).to(torch.float64)
+
+
+def barenblatt(x, y, t: float, m: int = 2, d: int = 2):
+    """Barenblatt profile B_m(x, t) (Example 6.3)."""
+    alpha = 1.0 / (m - 1 + 2.0 / d)
+    r2 = x * x + y * y
+    core = 1.0 - alpha * (m - 1) / (2.0 * d * m) * r2 / (t ** (2 * alpha / d))
+    return t ** (-alpha) * torch.clamp(core, min=0.0) ** (1.0 / (m - 1))
+
+
+def bl_disc_fn(x, y, radius: float = 0.5):
+    return ((x * x + y * y) < radius * radius).to(torch.float64)
+
+
+def fourier8_fn(A, p, q, phi):
+    """clip(0.5 + sum_k A_k sin(2 pi (p_k x + q_k y) + phi_k), 0, 1)."""
+    def f(x, y):
+        s = torch.full(torch.broadcast_shapes(x.shape, y.shape), 0.5, dtype=torch.float64, device=x.device)
+        for k in range(len(A)):
+            s = s + A[k] * torch.sin(2 * math.pi * (p[k] * x + q[k] * y) + phi[k])
+        return torch.clamp(s, 0.0, 1.0)
+    return f
+
+
+# ----------------------------------------------------------------------------------
+# the five benchmark workloads
+
+def config1(n: int = 128) -> Spec:
+    """1D linear u_t + u_x = 0.01 u_xx on [0, 2 pi], SSP-RK3, limiter off, T = 1."""
+    return Spec(dim=1, nx=n, x0=0.0, x1=2 * math.pi, flux=("linear", (1.0, 0.0)), diff=("const", (0.01,)),
+                umin=-1.0, umax=1.0, limiter=False, rk=3, T=1.0, name="linear1d")
+
+
+def config1_dt(spec: Spec, frac: float = 0.9, cfl_limit: float = 0.5611) -> float:
+    """dt with dt*(c/dx + k0/dx^2) = frac * (SSP-RK3 von Neumann limit at this Peclet number)."""
+    c, k0 = spec.flux[1][0], spec.diff[1][0]
+    return frac * cfl_limit / (c / spec.dx + k0 / spec.dx ** 2)
+
+
+def config2(n: int = 1024) -> Spec:
+    """2D strongly degenerate Burgers: f = u^2/2, kappa = 0.1 [u > 0.5], discs +-1."""
+    return Spec(dim=2, nx=n, ny=n, x0=-1.5, x1=1.5, y0=-1.5, y1=1.5, flux=("burgers", (0.5,)),
+                diff=("pwl", (0.0, 0.0, 0.1, 0.5)), umin=-1.0, umax=1.0, limiter=True, rk=3, T=0.5,
+                name="degenerate_burgers2d")
+
+
+def config3(n: int = 4096) -> Spec:
+    """2D porous medium u_t = Lap(u^2) on [-10, 10]^2 from Barenblatt t=1 to t=2."""
+    return Spec(dim=2, nx=n, ny=n, x0=-10.0, x1=10.0, y0=-10.0, y1=10.0, flux=("zero", ()), diff=("pme", (2,)),
+                umin=0.0, umax=1.0, limiter=True, rk=3, T=1.0, name="pme2d")
+
+
+def config5(n: int = 4096) -> Spec:
+    """2D Buckley-Leverett with gravity, kappa = 0.04 u (1-u), u0 = 1 in r < 0.5."""
+    return Spec(dim=2, nx=n, ny=n, x0=-1.5, x1=1.5, y0=-1.5, y1=1.5, flux=("bl", (5.0,)),
+                diff=("cubic", (0.0, 0.02, -0.04 / 3.0)), umin=0.0, umax=1.0, limiter=True, blend="plain",
+                rk=3, T=0.5, name="buckley_leverett2d")
+
+
+def initial_state(spec: Spec, device="cpu", sub: int = 4, order: int = 5):
+    """Initial DoFs for the named workloads."""
+    if spec.name == "linear1d":
+        return sine_1d_state(spec, device=device)
+    if spec.name == "degenerate_burgers2d":
+        return state_2d(discs_fn, spec, device=device, sub=sub, order=order)
+    if spec.name == "pme2d":
+        return state_2d(lambda x, y: barenblatt(x, y, 1.0), spec, device=device, sub=sub, order=order)
+    if spec.name == "buckley_leverett2d":
+        return state_2d(bl_disc_fn, spec, device=device, sub=sub, order=order)
+    raise KeyError(spec.name)
+
+
+def batch_instances(count: int = 256, seed: int = 20251011, nmin: int = 64, nmax: int = 1024):
+    """Seeded batch of periodic 2D instances on [0,1]^2: Burgers f = u^2/2 and
+    kappa = eps * 1[|u - 0.5| > 0.25] with eps ~ U[0.005, 0.05]; u0 a clipped 8-mode
+    Fourier series. Returns a list of (Spec, (A, p, q, phi))."""
+    rng = np.random.default_rng(seed)
+    out = []
+    modes = [(a, b) for a in range(-4, 5) for b in range(-4, 5) if (a, b) != (0, 0)]
+    for k in range(count):
+        n = int(rng.integers(nmin, nmax + 1))
+        eps = float(rng.uniform(0.005, 0.05))
+        idx = rng.choice(len(modes), size=8, replace=False)
+        p = [modes[t][0] for t in idx]
+        q = [modes[t][1] for t in idx]
+        A = rng.uniform(0.0, 0.25, size=8).tolist()
+        phi = rng.uniform(0.0, 2 * math.pi, size=8).tolist()
+        spec = Spec(dim=2, nx=n, ny=n, flux=("burgers", (0.5,)), diff=("pwl", (eps, 0.25, eps, 0.75)),
+                    umin=0.0, umax=1.0, limiter=True, rk=3, name=f"batch{k}")
+        out.append((spec, (A, p, q, phi)))
+    return out
+
+
+def batch_state(spec: Spec, modes, device="cpu", sub: int = 2, order: int = 3):
+    A, p, q, phi = modes
+    return state_2d(fourier8_fn(A, p, q, phi), spec, device=device, sub=sub, order=order)
+
+
+def random_piecewise(spec: Spec, seed: int, nshapes: int = 6, device="cpu", sub: int = 2, order: int = 3):
+    """Random piecewise-constant field on the mesh: a seeded union of rectangles and discs
+    with values in [0, 1] painted over a random background (indicator-network data)."""
+    rng = np.random.default_rng(seed)
+    bg = float(rng.uniform(0, 1))
+    shapes = []
+    for _ in range(nshapes):
+        kind = int(rng.integers(0, 2))
+        cx = float(rng.uniform(spec.x0, spec.x1))
+        cy = float(rng.uniform(spec.y0, spec.y1))
+        sz = float(rng.uniform(0.05, 0.3)) * (spec.x1 - spec.x0)
+        sz2 = float(rng.uniform(0.05, 0.3)) * (spec.y1 - spec.y0)
+        val = float(rng.uniform(0, 1))
+        shapes.append((kind, cx, cy, sz, sz2, val))
+
+    def f(x, y):
+        out = torch.full(torch.broadcast_shapes(x.shape, y.shape), bg, dtype=torch.float64, device=x.device)
+        for kind, cx, cy, sz, sz2, val in shapes:
+            if kind == 0:
+                m = ((x - cx).abs() < sz / 2) & ((y - cy).abs() < sz2 / 2)
+            else:
+                m = ((x - cx) ** 2 + (y - cy) ** 2) < (sz / 2) ** 2
+            out = torch.where(m, torch.full_like(out, val), out)
+        return out
+
+    return state_2d(f, spec, device=device, sub=sub, order=order)
+
+
+def random_state_2d(spec: Spec, seed: int, lo: float | None = None, hi: float | None = None, device="cpu"):
+    """Uniform random DoFs in [lo, hi] (defaults to the spec's bounds): a rough state
+    that exercises every branch of the limiter."""
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    lo = spec.umin if lo is None else lo
+    hi = spec.umax if hi is None else hi
+    shape = (spec.ny, spec.nx)
+    return [(lo + (hi - lo) * torch.rand(shape, generator=g, dtype=torch.float64)).to(device) for _ in range(4)]
+
+
+def random_state_1d(spec: Spec, seed: int, lo: float | None = None, hi: float | None = None):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    lo = spec.umin if lo is None else lo
+    hi = spec.umax if hi is None else hi
+    return [lo + (hi - lo) * torch.rand((spec.nx,), generator=g, dtype=torch.float64) for _ in range(2)]

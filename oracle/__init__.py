@@ -1,0 +1,228 @@
+"""FP64 CPU oracle for the compact fourth-order doubly conservative active flux method
+with monolithic convex MPP limiting (arXiv 2510.11527).
+
+TEST INFRASTRUCTURE ONLY. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package. The CUDA
+library shares no code with it and never calls it.
+
+What lives here:
+  * ``af_oracle.cpp`` (loaded through ctypes): one forward-Euler evaluation of the
+    method (Sections 2, 4, 5), SSP-RK3 / SSP-RK(5,4) steps, the CFL time step, and a
+    flop-counting instantiation of the same source.
+  * ``fourier.py``: the semi-discrete Fourier matrix G and the von Neumann CFL search
+    (Section 3).
+  * ``mlp.py``: FP64 forward/backward of the small indicator network.
+
+Problem descriptions are any object with the attributes of ``af_inputs.Spec``.
+"""
+import ctypes
+import math
+
+import numpy as np
+
+from .build import build_oracle
+
+FLUX_KINDS = {"zero": 0, "linear": 1, "burgers": 2, "bl": 3}
+DIFF_KINDS = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4}
+BLEND_KINDS = {"off": 0, "plain": 1, "external": 2}
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("dx", ctypes.c_double), ("dy", ctypes.c_double),
+        ("flux_kind", ctypes.c_int), ("flux_p", ctypes.c_double * 4),
+        ("diff_kind", ctypes.c_int), ("diff_p", ctypes.c_double * 4),
+        ("umin", ctypes.c_double), ("umax", ctypes.c_double),
+        ("limiter", ctypes.c_int), ("blend", ctypes.c_int), ("gamma", ctypes.c_double),
+        ("clamp_tol", ctypes.c_double),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("clamps", ctypes.c_longlong), ("max_excess", ctypes.c_double),
+                ("error", ctypes.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build_oracle())
+        P = ctypes.POINTER(Problem)
+        dpp = ctypes.POINTER(ctypes.c_double)
+        arr = ctypes.POINTER(dpp)
+        _lib.ao_fe.argtypes = [P, arr, ctypes.c_double, dpp, arr]
+        _lib.ao_step.argtypes = [P, ctypes.c_int, arr, ctypes.c_double, dpp, ctypes.POINTER(Stats)]
+        _lib.ao_dt.argtypes = [P, dpp, ctypes.c_double, ctypes.c_double]
+        _lib.ao_dt.restype = ctypes.c_double
+        _lib.ao_kappa_max.argtypes = [P]
+        _lib.ao_kappa_max.restype = ctypes.c_double
+        _lib.ao_alpha_interval.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        _lib.ao_alpha_interval.restype = ctypes.c_double
+        _lib.ao_point_funcs.argtypes = [P, ctypes.c_int, ctypes.c_double, dpp, dpp, dpp]
+        _lib.ao_theta.argtypes = [P, ctypes.c_double, ctypes.c_double]
+        _lib.ao_theta.restype = ctypes.c_double
+        _lib.ao_rk54_coefs.argtypes = [dpp, dpp]
+        _lib.ao_flop_count.argtypes = [P, arr, ctypes.c_double, dpp, ctypes.POINTER(ctypes.c_longlong)]
+    return _lib
+
+
+def make_problem(spec) -> Problem:
+    """Translate a problem description (af_inputs.Spec-like) into the oracle's struct."""
+    p = Problem()
+    p.dim = spec.dim
+    p.nx = spec.nx
+    p.ny = spec.ny if spec.dim == 2 else 1
+    p.dx = (spec.x1 - spec.x0) / spec.nx
+    p.dy = (spec.y1 - spec.y0) / spec.ny if spec.dim == 2 else 1.0
+    p.flux_kind = FLUX_KINDS[spec.flux[0]]
+    for k, v in enumerate(spec.flux[1]):
+        p.flux_p[k] = float(v)
+    p.diff_kind = DIFF_KINDS[spec.diff[0]]
+    for k, v in enumerate(spec.diff[1]):
+        p.diff_p[k] = float(v)
+    p.umin, p.umax = float(spec.umin), float(spec.umax)
+    p.limiter = int(spec.limiter)
+    p.blend = BLEND_KINDS[spec.blend]
+    p.gamma = float(spec.gamma)
+    scale = max(abs(spec.umin), abs(spec.umax), 1e-300)
+    p.clamp_tol = 8.0 * np.finfo(np.float64).eps * scale
+    return p
+
+
+def _ptrs(arrays):
+    dpp = ctypes.POINTER(ctypes.c_double)
+    return (dpp * len(arrays))(*[a.ctypes.data_as(dpp) for a in arrays])
+
+
+def _prep(spec, state):
+    n = 2 if spec.dim == 1 else 4
+    assert len(state) == n
+    return [np.ascontiguousarray(np.asarray(a, dtype=np.float64)).copy() for a in state]
+
+
+def _sext(s_ext):
+    if s_ext is None:
+        return None, None
+    s = np.ascontiguousarray(np.asarray(s_ext, dtype=np.float64))
+    return s, s.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def fe(spec, state, tau, s_ext=None):
+    """One forward-Euler evaluation FE(state, tau) -> new state (list of arrays)."""
+    p = make_problem(spec)
+    a = _prep(spec, state)
+    out = [np.zeros_like(x) for x in a]
+    s, sp = _sext(s_ext)
+    lib().ao_fe(ctypes.byref(p), _ptrs(a), float(tau), sp, _ptrs(out))
+    return out
+
+
+def step(spec, rk, state, dt, s_ext=None):
+    """One SSP-RK time step (rk = 3 or 54). Returns (new_state, stats dict)."""
+    p = make_problem(spec)
+    a = _prep(spec, state)
+    st = Stats()
+    s, sp = _sext(s_ext)
+    rc = lib().ao_step(ctypes.byref(p), int(rk), _ptrs(a), float(dt), sp, ctypes.byref(st))
+    if rc == -1:
+        raise ValueError("unknown rk scheme")
+    return a, {"clamps": st.clamps, "max_excess": st.max_excess, "error": st.error}
+
+
+# 0.9 x the linear (von Neumann) stability limit of the unlimited scheme for pure
+# diffusion, kappa dt / h^2: 1D from Table 1 (0.157, 0.333), 2D from the 4x4 symbol
+# (spectral radius 40.78 kappa/h^2 -> 0.0616 for SSP-RK3, 0.1307 for SSP-RK(5,4)).
+DIFF_CAP = {(1, 3): 0.9 * 0.157, (1, 54): 0.9 * 0.333, (2, 3): 0.9 * 0.0616, (2, 54): 0.9 * 0.1307}
+
+
+def dt_cfl(spec, ub, cfl=None, cfl_diff=None):
+    """dt = min(C / max(alpha/h + kappa_max/h^2), Cd h^2 / kappa_max); C defaults to
+    0.33/d (the paper's experiments) and Cd to 0.9 x the diffusive linear limit."""
+    p = make_problem(spec)
+    u = np.ascontiguousarray(np.asarray(ub, dtype=np.float64))
+    if cfl is None:
+        cfl = spec.cfl if getattr(spec, "cfl", 0.0) else 0.33 / spec.dim
+    if cfl_diff is None:
+        cfl_diff = DIFF_CAP[(spec.dim, getattr(spec, "rk", 3))]
+    return lib().ao_dt(ctypes.byref(p), u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(cfl),
+                       float(cfl_diff))
+
+
+def kappa_max(spec):
+    p = make_problem(spec)
+    return lib().ao_kappa_max(ctypes.byref(p))
+
+
+def alpha_interval(spec, direction, a, b):
+    p = make_problem(spec)
+    return lib().ao_alpha_interval(ctypes.byref(p), int(direction), float(a), float(b))
+
+
+def point_funcs(spec, direction, u):
+    """(f_l(u), f_l'(u), a(u)) as the oracle evaluates them."""
+    p = make_problem(spec)
+    f, d, a = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    lib().ao_point_funcs(ctypes.byref(p), int(direction), float(u), ctypes.byref(f), ctypes.byref(d),
+                         ctypes.byref(a))
+    return f.value, d.value, a.value
+
+
+def theta(spec, zL, zH):
+    p = make_problem(spec)
+    return lib().ao_theta(ctypes.byref(p), float(zL), float(zH))
+
+
+def rk54_coefficients():
+    """Shu-Osher (alpha, beta) 5x5 tables of the oracle's SSP-RK(5,4)."""
+    a = np.zeros(25)
+    b = np.zeros(25)
+    dpp = ctypes.POINTER(ctypes.c_double)
+    lib().ao_rk54_coefs(a.ctypes.data_as(dpp), b.ctypes.data_as(dpp))
+    return a.reshape(5, 5), b.reshape(5, 5)
+
+
+def flop_count(spec, state, tau, s_ext=None):
+    """Flops of one FE evaluation: dict(add, mul, div, exp, cmp)."""
+    p = make_problem(spec)
+    a = _prep(spec, state)
+    s, sp = _sext(s_ext)
+    out = (ctypes.c_longlong * 5)()
+    lib().ao_flop_count(ctypes.byref(p), _ptrs(a), float(tau), sp, out)
+    return dict(zip(["add", "mul", "div", "exp", "cmp"], list(out)))
+
+
+def mass(spec, ub):
+    """Total mass sum(ub) * dx * dy (FP64, plain summation in index order)."""
+    p = make_problem(spec)
+    return float(math.fsum(np.asarray(ub, dtype=np.float64).ravel())) * p.dx * p.dy
+
+
+def bounds(state):
+    """Min and max over all DoFs."""
+    return (min(float(np.min(a)) for a in state), max(float(np.max(a)) for a in state))
+
+
+def run(spec, rk, state, T, cfl=None, dt_fixed=None, max_steps=10**7, cfl_diff=None):
+    """Integrate to time T (last step clipped). Returns (state, nsteps, stats)."""
+    t = 0.0
+    n = 0
+    tot = {"clamps": 0, "max_excess": 0.0, "error": 0}
+    state = _prep(spec, state)
+    while t < T * (1 - 1e-14) and n < max_steps:
+        if dt_fixed is not None:
+            dt = dt_fixed
+        else:
+            cd = cfl_diff if cfl_diff is not None else DIFF_CAP[(spec.dim, rk)]
+            dt = dt_cfl(spec, state[0], cfl, cd)
+        dt = min(dt, T - t)
+        state, st = step(spec, rk, state, dt)
+        tot["clamps"] += st["clamps"]
+        tot["max_excess"] = max(tot["max_excess"], st["max_excess"])
+        tot["error"] |= st["error"]
+        t += dt
+        n += 1
+    return state, n, tot

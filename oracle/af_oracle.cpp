@@ -1,0 +1,851 @@
+// Plain, slow FP64 CPU oracle for the compact fourth-order doubly conservative
+// active flux (AF) method with monolithic convex MPP limiting (arXiv 2510.11527).
+//
+// TEST INFRASTRUCTURE ONLY. Nothing on the product path may load, link or call this
+// code: only the test suite, the package smoke check and the benchmark's CPU-baseline
+// leg use it. It shares no code with the CUDA library.
+//
+// Everything is written in the paper's order and notation with plain loops over
+// periodic index maps; each quantity is evaluated once per location and kept in its own
+// array so that every step can be checked against the paper by eye. All functions are
+// templated on the scalar type R so that the same source can be instantiated with a
+// counting type (flop counts for the roofline); the exported entry points use double.
+//
+// Build: g++ -O2 -ffp-contract=off -std=c++17 -fPIC -shared (see oracle/build.py).
+//
+// DoF layout (2D, periodic, row-major [ny][nx], i fastest) -- Section 4, Fig. 2:
+//   ub[j][i] cell average of cell (i,j)
+//   V [j][i] point value at (x_{i+1/2}, y_{j+1/2})   (cell corner)
+//   X [j][i] point value at (x_{i+1/2}, y_j)         (midpoint of the vertical edge)
+//   Y [j][i] point value at (x_i, y_{j+1/2})         (midpoint of the horizontal edge)
+// 1D (Section 2): ub[i] and P[i] = u_{i+1/2}; periodic, so u_{1/2} = u_{N+1/2}.
+//
+// Readings where the paper is silent (also listed in the design notes):
+//   * 2D factors: directional split 1/(2d)=1/4, limiter factor 3*2d = 12, MPP CFL 1/4
+//     (derived from the 1D factors 2,6 and the 3D factors 6,18 of Section 5).
+//   * 2D cell potential A^H_l: tensor Simpson average of the 1D potential a-hat of
+//     Proposition 2.1 along the transverse direction (Section 4, face averages).
+//   * Low-order point residual used by the smoothness blend (Section 5.1.3 defers it):
+//     first-order LLF + central second difference on the +-h/2 neighbours of the
+//     5-point line, with a recovered centre replaced by that cell's average.
+//   * Point blend weight in 2D: min of theta^{c,s} over the l-faces the point lies on,
+//     else min of theta^{d,s}_l over the two cells sharing the point.
+//   * Theta(zL,zH) is clipped to [0,1]; a limiter parameter equal to 1 returns the
+//     (blended) high-order flux/potential itself (Remark after Proposition 5.2).
+//   * After every RK stage, values outside [umin,umax] by at most clamp_tol are clamped
+//     and counted; larger excesses are reported as an error.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// Counting scalar used only by ao_flop_count: every +,-,*,/ and exp is one flop.
+struct FlopCounter {
+  long long add = 0, mul = 0, div = 0, exp = 0, cmp = 0;
+};
+FlopCounter g_flops;
+
+struct Cnt {
+  double v;
+  Cnt() : v(0) {}
+  Cnt(double x) : v(x) {}
+};
+inline Cnt operator+(Cnt a, Cnt b) { g_flops.add++; return Cnt(a.v + b.v); }
+inline Cnt operator-(Cnt a, Cnt b) { g_flops.add++; return Cnt(a.v - b.v); }
+inline Cnt operator-(Cnt a) { return Cnt(-a.v); }
+inline Cnt operator*(Cnt a, Cnt b) { g_flops.mul++; return Cnt(a.v * b.v); }
+inline Cnt operator/(Cnt a, Cnt b) { g_flops.div++; return Cnt(a.v / b.v); }
+inline bool operator<(Cnt a, Cnt b) { g_flops.cmp++; return a.v < b.v; }
+inline bool operator>(Cnt a, Cnt b) { g_flops.cmp++; return a.v > b.v; }
+inline bool operator<=(Cnt a, Cnt b) { g_flops.cmp++; return a.v <= b.v; }
+inline bool operator>=(Cnt a, Cnt b) { g_flops.cmp++; return a.v >= b.v; }
+inline bool operator==(Cnt a, Cnt b) { g_flops.cmp++; return a.v == b.v; }
+inline bool operator!=(Cnt a, Cnt b) { g_flops.cmp++; return a.v != b.v; }
+inline Cnt fabs_(Cnt a) { return Cnt(std::fabs(a.v)); }
+inline Cnt exp_(Cnt a) { g_flops.exp++; return Cnt(std::exp(a.v)); }
+inline double val(Cnt a) { return a.v; }
+
+inline double fabs_(double a) { return std::fabs(a); }
+inline double exp_(double a) { return std::exp(a); }
+inline double val(double a) { return a; }
+
+template <class R> inline R maxr(R a, R b) { return (a < b) ? b : a; }
+template <class R> inline R minr(R a, R b) { return (b < a) ? b : a; }
+
+inline int wrap(int i, int n) { return ((i % n) + n) % n; }
+
+}  // namespace
+
+extern "C" {
+
+// Problem description shared with the Python side through ctypes.
+// flux_kind: 0 zero, 1 linear f1=p0*u f2=p1*u, 2 Burgers f1=f2=p0*u^2,
+//            3 Buckley-Leverett f1=u^2/(u^2+(1-u)^2), f2=f1*(1-p0*(1-u)^2).
+// diff_kind: 0 none, 1 constant a=p0*u, 2 piecewise linear
+//            a = p0*min(u-p1,0) + p2*max(u-p3,0), 3 porous medium a=u^p0 (integer p0>=1),
+//            4 cubic a = p0*u + p1*u^2 + p2*u^3.
+typedef struct {
+  int dim;
+  int nx, ny;
+  double dx, dy;
+  int flux_kind;
+  double flux_p[4];
+  int diff_kind;
+  double diff_p[4];
+  double umin, umax;
+  int limiter;          // 1: monolithic convex limiter for averages + point projection
+  int blend;            // 0 off, 1 smoothness indicator, 2 external per-cell indicator
+  double gamma;         // blend strength (gamma = 1 in the paper's examples)
+  double clamp_tol;     // absolute tolerance of the post-stage safeguard clamp
+} ao_problem;
+
+typedef struct {
+  long long clamps;     // values clamped by the post-stage safeguard
+  double max_excess;    // largest excess beyond [umin,umax] that was clamped
+  int error;            // 1 if an excess above clamp_tol was met
+} ao_stats;
+
+}  // extern "C"
+
+namespace {
+
+// ---------------------------------------------------------------------------------
+// Problem functions: f_l, f_l', a, and the interval maximum of |f_l'| (Section 1 and
+// eq. for the local wave speed in Section 5.1.1 / 5.2).
+
+struct Model {
+  ao_problem p;
+  // interior local extrema of f_l' (Buckley-Leverett only), found once at set-up
+  std::vector<double> crit[2];
+};
+
+template <class R> R flux(const Model& m, int dir, R u) {
+  const ao_problem& p = m.p;
+  switch (p.flux_kind) {
+    case 1: return R(dir == 0 ? p.flux_p[0] : p.flux_p[1]) * u;
+    case 2: return R(p.flux_p[0]) * u * u;
+    case 3: {
+      R v = R(1.0) - u;
+      R f1 = u * u / (u * u + v * v);
+      if (dir == 0) return f1;
+      return f1 * (R(1.0) - R(p.flux_p[0]) * v * v);
+    }
+    default: return R(0.0);
+  }
+}
+
+template <class R> R dflux(const Model& m, int dir, R u) {
+  const ao_problem& p = m.p;
+  switch (p.flux_kind) {
+    case 1: return R(dir == 0 ? p.flux_p[0] : p.flux_p[1]);
+    case 2: return R(2.0 * p.flux_p[0]) * u;
+    case 3: {
+      // f1 = u^2/D, D = u^2 + (1-u)^2, f1' = 2u(1-u)/D^2
+      R v = R(1.0) - u;
+      R D = u * u + v * v;
+      R f1 = u * u / D;
+      R d1 = R(2.0) * u * v / (D * D);
+      if (dir == 0) return d1;
+      R g = R(p.flux_p[0]);
+      // f2 = f1 (1 - g v^2), f2' = f1' (1 - g v^2) + f1 * 2 g v
+      return d1 * (R(1.0) - g * v * v) + f1 * R(2.0) * g * v;
+    }
+    default: return R(0.0);
+  }
+}
+
+template <class R> R apot(const Model& m, R u) {
+  const ao_problem& p = m.p;
+  switch (p.diff_kind) {
+    case 1: return R(p.diff_p[0]) * u;
+    case 2: return R(p.diff_p[0]) * minr(u - R(p.diff_p[1]), R(0.0)) +
+                   R(p.diff_p[2]) * maxr(u - R(p.diff_p[3]), R(0.0));
+    case 3: {
+      int e = (int)p.diff_p[0];
+      R r = u;
+      for (int k = 1; k < e; ++k) r = r * u;
+      return r;
+    }
+    case 4: return R(p.diff_p[0]) * u + R(p.diff_p[1]) * u * u + R(p.diff_p[2]) * u * u * u;
+    default: return R(0.0);
+  }
+}
+
+double kappa(const Model& m, double u) {
+  const ao_problem& p = m.p;
+  switch (p.diff_kind) {
+    case 1: return p.diff_p[0];
+    case 2: return (u < p.diff_p[1] ? p.diff_p[0] : 0.0) + (u > p.diff_p[3] ? p.diff_p[2] : 0.0);
+    case 3: {
+      int e = (int)p.diff_p[0];
+      return e * std::pow(u, e - 1);
+    }
+    case 4: return p.diff_p[0] + 2 * p.diff_p[1] * u + 3 * p.diff_p[2] * u * u;
+    default: return 0.0;
+  }
+}
+
+// kappa_max = max over [umin, umax] of kappa (Section 5.1.1). Plain dense sampling
+// plus the interval end points and the kinks of the piecewise form.
+double kappa_max(const Model& m) {
+  const ao_problem& p = m.p;
+  double lo = p.umin, hi = p.umax, best = 0.0;
+  const int n = 200000;
+  for (int k = 0; k <= n; ++k) best = std::max(best, kappa(m, lo + (hi - lo) * k / n));
+  best = std::max(best, kappa(m, lo));
+  best = std::max(best, kappa(m, hi));
+  if (p.diff_kind == 2) {
+    // one-sided limits at the kinks inside the interval
+    if (p.diff_p[1] > lo) best = std::max(best, p.diff_p[0]);
+    if (p.diff_p[3] < hi) best = std::max(best, p.diff_p[2]);
+  }
+  if (p.diff_kind == 4 && p.diff_p[2] != 0.0) {
+    double uv = -p.diff_p[1] / (3 * p.diff_p[2]);
+    if (uv > lo && uv < hi) best = std::max(best, kappa(m, uv));
+  }
+  return best;
+}
+
+// Interior local extrema of f_l' on [-1, 2] by sampling and golden-section refinement
+// (the value of f' at an extremum is insensitive to the location error).
+void find_crit(Model& m) {
+  for (int d = 0; d < 2; ++d) m.crit[d].clear();
+  if (m.p.flux_kind != 3) return;
+  for (int d = 0; d < 2; ++d) {
+    const double a = -1.0, b = 2.0;
+    const int n = 30000;
+    auto fp = [&](double u) { return dflux<double>(m, d, u); };
+    for (int k = 1; k < n; ++k) {
+      double u0 = a + (b - a) * (k - 1) / n, u1 = a + (b - a) * k / n, u2 = a + (b - a) * (k + 1) / n;
+      double g0 = fp(u0), g1 = fp(u1), g2 = fp(u2);
+      int sgn = 0;
+      if (g1 >= g0 && g1 > g2) sgn = 1;        // local max of f'
+      else if (g1 <= g0 && g1 < g2) sgn = -1;  // local min of f'
+      if (!sgn) continue;
+      double lo = u0, hi = u2;
+      const double gr = 0.5 * (std::sqrt(5.0) - 1.0);
+      for (int it = 0; it < 200; ++it) {
+        double c = hi - gr * (hi - lo), e = lo + gr * (hi - lo);
+        if (sgn * fp(c) > sgn * fp(e)) hi = e; else lo = c;
+      }
+      m.crit[d].push_back(0.5 * (lo + hi));
+    }
+  }
+}
+
+// alpha = max over u in [min(ua,ub), max(ua,ub)] of |f_l'(u)| (eq. of the local wave
+// speed, Section 5.1.1; multi-D form in Section 5.2).
+template <class R> R alpha_interval(const Model& m, int dir, R ua, R ub) {
+  R lo = minr(ua, ub), hi = maxr(ua, ub);
+  R best = maxr(fabs_(dflux<R>(m, dir, lo)), fabs_(dflux<R>(m, dir, hi)));
+  for (double c : m.crit[dir]) {
+    if (R(c) > lo && R(c) < hi) best = maxr(best, fabs_(dflux<R>(m, dir, R(c))));
+  }
+  return best;
+}
+
+// Theta(zL, zH): largest blend factor keeping (1-t) zL + t zH in [umin, umax]
+// (definition in Section 5.1.1), clipped to [0,1].
+template <class R> R Theta(const Model& m, R zL, R zH) {
+  R umin = R(m.p.umin), umax = R(m.p.umax);
+  R t;
+  if (zH < umin) {
+    if (zL == zH) return R(1.0);
+    t = (zL - umin) / (zL - zH);
+  } else if (zH > umax) {
+    if (zL == zH) return R(1.0);
+    t = (zL - umax) / (zL - zH);
+  } else {
+    return R(1.0);
+  }
+  if (t < R(0.0)) t = R(0.0);
+  if (t > R(1.0)) t = R(1.0);
+  return t;
+}
+
+// One 5-point line residual (spacing h/2, points z[0..4] at offsets -h..+h, the point
+// being updated is z[2]). Convection: FVS-LLF split with biased D+ / D- (eqs.
+// 1d_upwind_ops_4p / 4m) and alpha = max |f'| over the five points; diffusion: the
+// compact fourth-order second derivative of a (eq. 1d_diff_compact_a).
+template <class R>
+R line_residual(const R z[5], const R f[5], const R df[5], const R a[5], R h) {
+  R alpha = fabs_(df[0]);
+  for (int k = 1; k < 5; ++k) alpha = maxr(alpha, fabs_(df[k]));
+  R gp[5], gm[5];
+  for (int k = 0; k < 5; ++k) {
+    gp[k] = R(0.5) * (f[k] + alpha * z[k]);
+    gm[k] = R(0.5) * (f[k] - alpha * z[k]);
+  }
+  R Dp = (gp[0] - R(6.0) * gp[1] + R(3.0) * gp[2] + R(2.0) * gp[3]) / (R(3.0) * h);
+  R Dm = (R(-2.0) * gm[1] - R(3.0) * gm[2] + R(6.0) * gm[3] - gm[4]) / (R(3.0) * h);
+  R D2 = (R(-1.0 / 3.0) * a[0] + R(16.0 / 3.0) * a[1] - R(10.0) * a[2] + R(16.0 / 3.0) * a[3] -
+          R(1.0 / 3.0) * a[4]) / (h * h);
+  return -(Dp + Dm) + D2;
+}
+
+// First-order point residual on the +-h/2 neighbours (reading for the blend's
+// low-order point scheme): -(2/h)[F(z0,z+) - F(z-,z0)] + (4/h^2)(a+ - 2 a0 + a-).
+template <class R>
+R low_point_residual(const Model& m, int dir, R zm, R z0, R zp, R h) {
+  auto llf = [&](R ul, R ur) {
+    R al = alpha_interval<R>(m, dir, ul, ur);
+    return R(0.5) * (flux<R>(m, dir, ul) + flux<R>(m, dir, ur)) - R(0.5) * al * (ur - ul);
+  };
+  R conv = (llf(z0, zp) - llf(zm, z0)) * (R(2.0) / h);
+  R diff = (apot<R>(m, zp) - R(2.0) * apot<R>(m, z0) + apot<R>(m, zm)) * (R(4.0) / (h * h));
+  return -conv + diff;
+}
+
+// Smoothness indicator along one line of cell averages (Section 5.1.3):
+// s~_i = |u_{i-1} - 2u_i + u_{i+1}| / (|u_{i-1}| + 2|u_i| + |u_{i+1}| + 1e-13).
+template <class R> R s_tilde(R um, R u0, R up) {
+  return fabs_(um - R(2.0) * u0 + up) / (fabs_(um) + R(2.0) * fabs_(u0) + fabs_(up) + R(1e-13));
+}
+
+// ---------------------------------------------------------------------------------
+// 1D forward-Euler evaluation (Sections 2 and 5.1).
+template <class R>
+void fe1d(const Model& m, const R* ub, const R* P, R tau, const R* s_ext, R* ub_o, R* P_o) {
+  const ao_problem& p = m.p;
+  const int n = p.nx;
+  const R h = R(p.dx);
+  auto I = [&](int i) { return wrap(i, n); };
+  std::vector<R> c(n), fP(n), dP(n), aP(n), fC(n), dC(n), aC(n), fU(n), aU(n);
+  // centre value by Simpson's rule: z_i = (6 zbar_i - z_{i-1/2} - z_{i+1/2}) / 4
+  for (int i = 0; i < n; ++i) c[i] = (R(6.0) * ub[i] - P[I(i - 1)] - P[i]) / R(4.0);
+  for (int i = 0; i < n; ++i) {
+    fP[i] = flux<R>(m, 0, P[i]); dP[i] = dflux<R>(m, 0, P[i]); aP[i] = apot<R>(m, P[i]);
+    fC[i] = flux<R>(m, 0, c[i]); dC[i] = dflux<R>(m, 0, c[i]); aC[i] = apot<R>(m, c[i]);
+    fU[i] = flux<R>(m, 0, ub[i]); aU[i] = apot<R>(m, ub[i]);
+  }
+  // high-order flux f(u_{i+1/2}) and DC potential a^_i = (-a_{i-1/2} + 8 a_i - a_{i+1/2})/6
+  std::vector<R> FH(n), AH(n), RH(n);
+  for (int i = 0; i < n; ++i) {
+    FH[i] = fP[i];
+    AH[i] = (-aP[I(i - 1)] + R(8.0) * aC[i] - aP[i]) / R(6.0);
+  }
+  // point residual at x_{i+1/2}: line [u_{i-1/2}, u_i, u_{i+1/2}, u_{i+1}, u_{i+3/2}]
+  for (int i = 0; i < n; ++i) {
+    int ip = I(i + 1);
+    R z[5] = {P[I(i - 1)], c[i], P[i], c[ip], P[ip]};
+    R f[5] = {fP[I(i - 1)], fC[i], fP[i], fC[ip], fP[ip]};
+    R d[5] = {dP[I(i - 1)], dC[i], dP[i], dC[ip], dP[ip]};
+    R a[5] = {aP[I(i - 1)], aC[i], aP[i], aC[ip], aP[ip]};
+    RH[i] = line_residual<R>(z, f, d, a, h);
+  }
+  const R mu = tau / h, nu = tau / (h * h);
+  // low-order LLF scheme and its directional states u^{L,+-} (Lemma 5.1)
+  std::vector<R> FL(n), ULp(n), ULm(n);
+  for (int i = 0; i < n; ++i) {
+    int ip = I(i + 1);
+    R al = alpha_interval<R>(m, 0, ub[i], ub[ip]);
+    FL[i] = R(0.5) * (fU[i] + fU[ip]) - R(0.5) * al * (ub[ip] - ub[i]);
+  }
+  for (int i = 0; i < n; ++i) {
+    int ip = I(i + 1), im = I(i - 1);
+    ULp[i] = ub[i] - R(2.0) * mu * (FL[i] - fU[i]) + R(2.0) * nu * (aU[ip] - aU[i]);
+    ULm[i] = ub[i] - R(2.0) * mu * (fU[i] - FL[im]) - R(2.0) * nu * (aU[i] - aU[im]);
+  }
+  // optional smoothness blend (Section 5.1.3), applied before the limiter
+  std::vector<R> Fh(FH), Ah(AH), R_(RH), thcs(n, R(1.0));
+  if (p.blend) {
+    std::vector<R> st(n), s(n), thds(n);
+    if (p.blend == 1) {
+      for (int i = 0; i < n; ++i) st[i] = s_tilde<R>(ub[I(i - 1)], ub[i], ub[I(i + 1)]);
+      for (int i = 0; i < n; ++i) s[i] = (st[I(i - 1)] + R(4.0) * st[i] + st[I(i + 1)]) / R(6.0);
+    } else {
+      for (int i = 0; i < n; ++i) s[i] = s_ext[i];
+    }
+    for (int i = 0; i < n; ++i) {
+      thcs[i] = exp_(-R(p.gamma) * (R(0.5) * (s[i] + s[I(i + 1)])));
+      thds[i] = exp_(-R(p.gamma) * s[i]);
+    }
+    for (int i = 0; i < n; ++i) {
+      Fh[i] = thcs[i] * FH[i] + (R(1.0) - thcs[i]) * FL[i];
+      Ah[i] = thds[i] * AH[i] + (R(1.0) - thds[i]) * aU[i];
+      R RL = low_point_residual<R>(m, 0, ub[i], P[i], ub[I(i + 1)], h);
+      R_[i] = thcs[i] * RH[i] + (R(1.0) - thcs[i]) * RL;
+    }
+  }
+  // monolithic convex limiter (eqs. 1d_convection_limiting_parameter and
+  // 1d_diffusion_limiting_parameter), limited average (eq. 1d_limited_average)
+  std::vector<R> Flim(Fh), Alim(Ah);
+  if (p.limiter) {
+    for (int i = 0; i < n; ++i) {
+      int ip = I(i + 1);
+      R dF = Fh[i] - FL[i];
+      R t = minr(Theta<R>(m, ULp[i], ULp[i] - R(6.0) * mu * dF),
+                 Theta<R>(m, ULm[ip], ULm[ip] + R(6.0) * mu * dF));
+      Flim[i] = (t == R(1.0)) ? Fh[i] : FL[i] + t * dF;
+    }
+    for (int i = 0; i < n; ++i) {
+      int ip = I(i + 1), im = I(i - 1);
+      R dA = Ah[i] - aU[i];
+      R t = minr(minr(Theta<R>(m, ULp[im], ULp[im] + R(6.0) * nu * dA),
+                      Theta<R>(m, ULp[i], ULp[i] - R(6.0) * nu * dA)),
+                 minr(Theta<R>(m, ULm[i], ULm[i] - R(6.0) * nu * dA),
+                      Theta<R>(m, ULm[ip], ULm[ip] + R(6.0) * nu * dA)));
+      Alim[i] = (t == R(1.0)) ? Ah[i] : aU[i] + t * dA;
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    int ip = I(i + 1), im = I(i - 1);
+    ub_o[i] = ub[i] - mu * (Flim[i] - Flim[im]) + nu * (Alim[ip] - R(2.0) * Alim[i] + Alim[im]);
+  }
+  // point values: high-order update, then projection onto [umin, umax] (Section 5.1.2)
+  for (int i = 0; i < n; ++i) {
+    R v = P[i] + tau * R_[i];
+    if (p.limiter) v = minr(maxr(v, R(p.umin)), R(p.umax));
+    P_o[i] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// 2D forward-Euler evaluation (Sections 4 and 5.2 with d = 2).
+template <class R>
+void fe2d(const Model& m, const R* ub, const R* V, const R* X, const R* Y, R tau, const R* s_ext,
+          R* ub_o, R* V_o, R* X_o, R* Y_o) {
+  const ao_problem& p = m.p;
+  const int nx = p.nx, ny = p.ny;
+  const R h1 = R(p.dx), h2 = R(p.dy);
+  const size_t N = (size_t)nx * ny;
+  auto at = [&](int i, int j) { return (size_t)wrap(j, ny) * nx + wrap(i, nx); };
+
+  // (1) centre value z_{i,j} = [36 zbar - 4(X_{i-1,j}+X_{ij}+Y_{i,j-1}+Y_{ij})
+  //                              - (V_{i-1,j-1}+V_{i,j-1}+V_{i-1,j}+V_{ij})] / 16  (Section 4)
+  std::vector<R> C(N);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i)
+      C[at(i, j)] = (R(36.0) * ub[at(i, j)] -
+                     R(4.0) * (X[at(i - 1, j)] + X[at(i, j)] + Y[at(i, j - 1)] + Y[at(i, j)]) -
+                     (V[at(i - 1, j - 1)] + V[at(i, j - 1)] + V[at(i - 1, j)] + V[at(i, j)])) / R(16.0);
+
+  // (2) pointwise nonlinearities at every point type and at the cell averages
+  struct PF { std::vector<R> f1, f2, d1, d2, a; };
+  auto eval = [&](const R* z) {
+    PF q;
+    q.f1.resize(N); q.f2.resize(N); q.d1.resize(N); q.d2.resize(N); q.a.resize(N);
+    for (size_t k = 0; k < N; ++k) {
+      q.f1[k] = flux<R>(m, 0, z[k]); q.f2[k] = flux<R>(m, 1, z[k]);
+      q.d1[k] = dflux<R>(m, 0, z[k]); q.d2[k] = dflux<R>(m, 1, z[k]);
+      q.a[k] = apot<R>(m, z[k]);
+    }
+    return q;
+  };
+  PF pV = eval(V), pX = eval(X), pY = eval(Y), pC = eval(C.data());
+  std::vector<R> f1U(N), f2U(N), aU(N);
+  for (size_t k = 0; k < N; ++k) {
+    f1U[k] = flux<R>(m, 0, ub[k]); f2U[k] = flux<R>(m, 1, ub[k]); aU[k] = apot<R>(m, ub[k]);
+  }
+
+  // (3) high-order fluxes (Simpson face average of f_l at the face's three points) and
+  //     cell potentials A^H_l (transverse Simpson average of the 1D DC potential).
+  std::vector<R> FH1(N), FH2(N), AH1(N), AH2(N);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      // x-face (i+1/2, j): V_{i,j-1}, X_{ij}, V_{ij}
+      FH1[at(i, j)] = (pV.f1[at(i, j - 1)] + R(4.0) * pX.f1[at(i, j)] + pV.f1[at(i, j)]) / R(6.0);
+      // y-face (i, j+1/2): V_{i-1,j}, Y_{ij}, V_{ij}
+      FH2[at(i, j)] = (pV.f2[at(i - 1, j)] + R(4.0) * pY.f2[at(i, j)] + pV.f2[at(i, j)]) / R(6.0);
+      // a^ along x-lines at y_{j-1/2}, y_j, y_{j+1/2}, combined with Simpson weights 1,4,1
+      R lo = (-pV.a[at(i - 1, j - 1)] + R(8.0) * pY.a[at(i, j - 1)] - pV.a[at(i, j - 1)]) / R(6.0);
+      R mid = (-pX.a[at(i - 1, j)] + R(8.0) * pC.a[at(i, j)] - pX.a[at(i, j)]) / R(6.0);
+      R hi = (-pV.a[at(i - 1, j)] + R(8.0) * pY.a[at(i, j)] - pV.a[at(i, j)]) / R(6.0);
+      AH1[at(i, j)] = (lo + R(4.0) * mid + hi) / R(6.0);
+      // a^ along y-lines at x_{i-1/2}, x_i, x_{i+1/2}
+      R le = (-pV.a[at(i - 1, j - 1)] + R(8.0) * pX.a[at(i - 1, j)] - pV.a[at(i - 1, j)]) / R(6.0);
+      R ce = (-pY.a[at(i, j - 1)] + R(8.0) * pC.a[at(i, j)] - pY.a[at(i, j)]) / R(6.0);
+      R ri = (-pV.a[at(i, j - 1)] + R(8.0) * pX.a[at(i, j)] - pV.a[at(i, j)]) / R(6.0);
+      AH2[at(i, j)] = (le + R(4.0) * ce + ri) / R(6.0);
+    }
+
+  // (4) high-order point residuals per direction on the 5-point lines (eq. 2d_af_dc;
+  //     the operators are the 1D ones with half-index shifts)
+  auto line = [&](const PF& q0, size_t k0, const PF& q1, size_t k1, const PF& q2, size_t k2,
+                  const PF& q3, size_t k3, const PF& q4, size_t k4, const R* z0, const R* z1,
+                  const R* z2, const R* z3, const R* z4, int dir, R h) {
+    R z[5] = {z0[k0], z1[k1], z2[k2], z3[k3], z4[k4]};
+    const PF* q[5] = {&q0, &q1, &q2, &q3, &q4};
+    size_t kk[5] = {k0, k1, k2, k3, k4};
+    R f[5], d[5], a[5];
+    for (int t = 0; t < 5; ++t) {
+      f[t] = dir == 0 ? q[t]->f1[kk[t]] : q[t]->f2[kk[t]];
+      d[t] = dir == 0 ? q[t]->d1[kk[t]] : q[t]->d2[kk[t]];
+      a[t] = q[t]->a[kk[t]];
+    }
+    return line_residual<R>(z, f, d, a, h);
+  };
+  const R* Cp = C.data();
+  std::vector<R> RV1(N), RV2(N), RX1(N), RX2(N), RY1(N), RY2(N);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t k = at(i, j);
+      RV1[k] = line(pV, at(i - 1, j), pY, at(i, j), pV, k, pY, at(i + 1, j), pV, at(i + 1, j),
+                    V, Y, V, Y, V, 0, h1);
+      RV2[k] = line(pV, at(i, j - 1), pX, at(i, j), pV, k, pX, at(i, j + 1), pV, at(i, j + 1),
+                    V, X, V, X, V, 1, h2);
+      RX1[k] = line(pX, at(i - 1, j), pC, at(i, j), pX, k, pC, at(i + 1, j), pX, at(i + 1, j),
+                    X, Cp, X, Cp, X, 0, h1);
+      RX2[k] = line(pX, at(i, j - 1), pV, at(i, j - 1), pX, k, pV, at(i, j), pX, at(i, j + 1),
+                    X, V, X, V, X, 1, h2);
+      RY1[k] = line(pY, at(i - 1, j), pV, at(i - 1, j), pY, k, pV, at(i, j), pY, at(i + 1, j),
+                    Y, V, Y, V, Y, 0, h1);
+      RY2[k] = line(pY, at(i, j - 1), pC, at(i, j), pY, k, pC, at(i, j + 1), pY, at(i, j + 1),
+                    Y, Cp, Y, Cp, Y, 1, h2);
+    }
+
+  // (5) low-order LLF fluxes and the directional states u^{L,+-}_l with factor 2d = 4
+  const R mu1 = tau / h1, mu2 = tau / h2, nu1 = tau / (h1 * h1), nu2 = tau / (h2 * h2);
+  std::vector<R> FL1(N), FL2(N), ULp1(N), ULm1(N), ULp2(N), ULm2(N);
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t k = at(i, j), kx = at(i + 1, j), ky = at(i, j + 1);
+      R a1 = alpha_interval<R>(m, 0, ub[k], ub[kx]);
+      FL1[k] = R(0.5) * (f1U[k] + f1U[kx]) - R(0.5) * a1 * (ub[kx] - ub[k]);
+      R a2 = alpha_interval<R>(m, 1, ub[k], ub[ky]);
+      FL2[k] = R(0.5) * (f2U[k] + f2U[ky]) - R(0.5) * a2 * (ub[ky] - ub[k]);
+    }
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t k = at(i, j);
+      ULp1[k] = ub[k] - R(4.0) * mu1 * (FL1[k] - f1U[k]) + R(4.0) * nu1 * (aU[at(i + 1, j)] - aU[k]);
+      ULm1[k] = ub[k] - R(4.0) * mu1 * (f1U[k] - FL1[at(i - 1, j)]) - R(4.0) * nu1 * (aU[k] - aU[at(i - 1, j)]);
+      ULp2[k] = ub[k] - R(4.0) * mu2 * (FL2[k] - f2U[k]) + R(4.0) * nu2 * (aU[at(i, j + 1)] - aU[k]);
+      ULm2[k] = ub[k] - R(4.0) * mu2 * (f2U[k] - FL2[at(i, j - 1)]) - R(4.0) * nu2 * (aU[k] - aU[at(i, j - 1)]);
+    }
+
+  // (6) optional smoothness blend, direction by direction (Section 5.2.3 / 5.1.3)
+  std::vector<R> Fh1(FH1), Fh2(FH2), Ah1(AH1), Ah2(AH2);
+  std::vector<R> RV(N), RX(N), RY(N);
+  for (size_t k = 0; k < N; ++k) {
+    RV[k] = RV1[k] + RV2[k]; RX[k] = RX1[k] + RX2[k]; RY[k] = RY1[k] + RY2[k];
+  }
+  if (p.blend) {
+    std::vector<R> s1(N), s2(N);
+    if (p.blend == 1) {
+      std::vector<R> st1(N), st2(N);
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          st1[at(i, j)] = s_tilde<R>(ub[at(i - 1, j)], ub[at(i, j)], ub[at(i + 1, j)]);
+          st2[at(i, j)] = s_tilde<R>(ub[at(i, j - 1)], ub[at(i, j)], ub[at(i, j + 1)]);
+        }
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          s1[at(i, j)] = (st1[at(i - 1, j)] + R(4.0) * st1[at(i, j)] + st1[at(i + 1, j)]) / R(6.0);
+          s2[at(i, j)] = (st2[at(i, j - 1)] + R(4.0) * st2[at(i, j)] + st2[at(i, j + 1)]) / R(6.0);
+        }
+    } else {
+      for (size_t k = 0; k < N; ++k) { s1[k] = s_ext[k]; s2[k] = s_ext[k]; }
+    }
+    const R g = R(p.gamma);
+    std::vector<R> tc1(N), tc2(N), td1(N), td2(N);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t k = at(i, j);
+        tc1[k] = exp_(-g * (R(0.5) * (s1[k] + s1[at(i + 1, j)])));
+        tc2[k] = exp_(-g * (R(0.5) * (s2[k] + s2[at(i, j + 1)])));
+        td1[k] = exp_(-g * s1[k]);
+        td2[k] = exp_(-g * s2[k]);
+      }
+    for (size_t k = 0; k < N; ++k) {
+      Fh1[k] = tc1[k] * FH1[k] + (R(1.0) - tc1[k]) * FL1[k];
+      Fh2[k] = tc2[k] * FH2[k] + (R(1.0) - tc2[k]) * FL2[k];
+      Ah1[k] = td1[k] * AH1[k] + (R(1.0) - td1[k]) * aU[k];
+      Ah2[k] = td2[k] * AH2[k] + (R(1.0) - td2[k]) * aU[k];
+    }
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t k = at(i, j);
+        // low-order point residuals on the +-h/2 neighbours
+        R LV1 = low_point_residual<R>(m, 0, Y[k], V[k], Y[at(i + 1, j)], h1);
+        R LV2 = low_point_residual<R>(m, 1, X[k], V[k], X[at(i, j + 1)], h2);
+        R LX1 = low_point_residual<R>(m, 0, ub[k], X[k], ub[at(i + 1, j)], h1);
+        R LX2 = low_point_residual<R>(m, 1, V[at(i, j - 1)], X[k], V[k], h2);
+        R LY1 = low_point_residual<R>(m, 0, V[at(i - 1, j)], Y[k], V[k], h1);
+        R LY2 = low_point_residual<R>(m, 1, ub[k], Y[k], ub[at(i, j + 1)], h2);
+        // direction weights at each point type
+        R wV1 = minr(tc1[k], tc1[at(i, j + 1)]);
+        R wV2 = minr(tc2[k], tc2[at(i + 1, j)]);
+        R wX1 = tc1[k];
+        R wX2 = minr(td2[k], td2[at(i + 1, j)]);
+        R wY1 = minr(td1[k], td1[at(i, j + 1)]);
+        R wY2 = tc2[k];
+        RV[k] = (wV1 * RV1[k] + (R(1.0) - wV1) * LV1) + (wV2 * RV2[k] + (R(1.0) - wV2) * LV2);
+        RX[k] = (wX1 * RX1[k] + (R(1.0) - wX1) * LX1) + (wX2 * RX2[k] + (R(1.0) - wX2) * LX2);
+        RY[k] = (wY1 * RY1[k] + (R(1.0) - wY1) * LY1) + (wY2 * RY2[k] + (R(1.0) - wY2) * LY2);
+      }
+  }
+
+  // (7) monolithic convex limiter with factor 3*2d = 12 (eqs.
+  //     multid_convection_limiting_parameter, multid_diffusion_limiting_parameter)
+  std::vector<R> Fl1(Fh1), Fl2(Fh2), Al1(Ah1), Al2(Ah2);
+  if (p.limiter) {
+    const R k12 = R(12.0);
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t k = at(i, j), kx = at(i + 1, j), ky = at(i, j + 1);
+        R dF1 = Fh1[k] - FL1[k];
+        R t1 = minr(Theta<R>(m, ULp1[k], ULp1[k] - k12 * mu1 * dF1),
+                    Theta<R>(m, ULm1[kx], ULm1[kx] + k12 * mu1 * dF1));
+        Fl1[k] = (t1 == R(1.0)) ? Fh1[k] : FL1[k] + t1 * dF1;
+        R dF2 = Fh2[k] - FL2[k];
+        R t2 = minr(Theta<R>(m, ULp2[k], ULp2[k] - k12 * mu2 * dF2),
+                    Theta<R>(m, ULm2[ky], ULm2[ky] + k12 * mu2 * dF2));
+        Fl2[k] = (t2 == R(1.0)) ? Fh2[k] : FL2[k] + t2 * dF2;
+      }
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        size_t k = at(i, j);
+        size_t xm = at(i - 1, j), xp = at(i + 1, j), ym = at(i, j - 1), yp = at(i, j + 1);
+        R dA1 = Ah1[k] - aU[k];
+        R t1 = minr(minr(Theta<R>(m, ULp1[xm], ULp1[xm] + k12 * nu1 * dA1),
+                         Theta<R>(m, ULp1[k], ULp1[k] - k12 * nu1 * dA1)),
+                    minr(Theta<R>(m, ULm1[k], ULm1[k] - k12 * nu1 * dA1),
+                         Theta<R>(m, ULm1[xp], ULm1[xp] + k12 * nu1 * dA1)));
+        Al1[k] = (t1 == R(1.0)) ? Ah1[k] : aU[k] + t1 * dA1;
+        R dA2 = Ah2[k] - aU[k];
+        R t2 = minr(minr(Theta<R>(m, ULp2[ym], ULp2[ym] + k12 * nu2 * dA2),
+                         Theta<R>(m, ULp2[k], ULp2[k] - k12 * nu2 * dA2)),
+                    minr(Theta<R>(m, ULm2[k], ULm2[k] - k12 * nu2 * dA2),
+                         Theta<R>(m, ULm2[yp], ULm2[yp] + k12 * nu2 * dA2)));
+        Al2[k] = (t2 == R(1.0)) ? Ah2[k] : aU[k] + t2 * dA2;
+      }
+  }
+
+  // (8) limited cell-average update (eq. multid_limited_average)
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      size_t k = at(i, j);
+      ub_o[k] = ub[k] - mu1 * (Fl1[k] - Fl1[at(i - 1, j)]) - mu2 * (Fl2[k] - Fl2[at(i, j - 1)]) +
+                nu1 * (Al1[at(i + 1, j)] - R(2.0) * Al1[k] + Al1[at(i - 1, j)]) +
+                nu2 * (Al2[at(i, j + 1)] - R(2.0) * Al2[k] + Al2[at(i, j - 1)]);
+    }
+  // (9) point values: high-order update and projection (Section 5.2.2)
+  const R umin = R(p.umin), umax = R(p.umax);
+  for (size_t k = 0; k < N; ++k) {
+    R v = V[k] + tau * RV[k], x = X[k] + tau * RX[k], y = Y[k] + tau * RY[k];
+    if (p.limiter) {
+      v = minr(maxr(v, umin), umax); x = minr(maxr(x, umin), umax); y = minr(maxr(y, umin), umax);
+    }
+    V_o[k] = v; X_o[k] = x; Y_o[k] = y;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Time integration (Section 3.2; SSP-RK3 of Gottlieb-Shu-Tadmor and SSP-RK(5,4) of
+// Spiteri-Ruuth written as convex combinations of forward-Euler steps, Section 5).
+
+// SSP-RK(5,4) Shu-Osher coefficients alpha[k][l], beta[k][l] (row k = stage output k+1,
+// column l = input u^(l)); values from Spiteri & Ruuth (2002), pinned in the tests by
+// the order-4 conditions and by the z^5 coefficient eta = 0.004477718303076 (Section 3.2).
+const double RK54_A[5][5] = {
+    {1.0, 0, 0, 0, 0},
+    {0.444370493651235, 0.555629506348765, 0, 0, 0},
+    {0.620101851488403, 0, 0.379898148511597, 0, 0},
+    {0.178079954393132, 0, 0, 0.821920045606868, 0},
+    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269}};
+const double RK54_B[5][5] = {
+    {0.391752226571890, 0, 0, 0, 0},
+    {0, 0.368410593050371, 0, 0, 0},
+    {0, 0, 0.251891774271694, 0, 0},
+    {0, 0, 0, 0.544974750228521, 0},
+    {0, 0, 0, 0.063692468666290, 0.226007483236906}};
+
+struct State {
+  std::vector<double> a[4];
+};
+
+int ncomp(const ao_problem& p) { return p.dim == 1 ? 2 : 4; }
+size_t ncell(const ao_problem& p) { return (size_t)p.nx * (p.dim == 1 ? 1 : p.ny); }
+
+void fe(const Model& m, const State& in, double tau, const double* s_ext, State& out) {
+  const ao_problem& p = m.p;
+  size_t n = ncell(p);
+  for (int c = 0; c < ncomp(p); ++c) out.a[c].assign(n, 0.0);
+  if (p.dim == 1)
+    fe1d<double>(m, in.a[0].data(), in.a[1].data(), tau, s_ext, out.a[0].data(), out.a[1].data());
+  else
+    fe2d<double>(m, in.a[0].data(), in.a[1].data(), in.a[2].data(), in.a[3].data(), tau, s_ext,
+                 out.a[0].data(), out.a[1].data(), out.a[2].data(), out.a[3].data());
+}
+
+// Post-stage safeguard: exact comparisons against [umin, umax]; excesses up to clamp_tol
+// are clamped and counted, larger ones flag an error.
+void safeguard(const ao_problem& p, State& s, ao_stats* st) {
+  if (!p.limiter) return;
+  for (int c = 0; c < ncomp(p); ++c)
+    for (double& v : s.a[c]) {
+      double e = 0.0;
+      if (v < p.umin) e = p.umin - v;
+      else if (v > p.umax) e = v - p.umax;
+      if (e == 0.0) continue;
+      if (e > p.clamp_tol) { if (st) st->error = 1; continue; }
+      v = v < p.umin ? p.umin : p.umax;
+      if (st) { st->clamps++; st->max_excess = std::max(st->max_excess, e); }
+    }
+}
+
+State combine(const ao_problem& p, double a, const State& x, double b, const State& y) {
+  State r;
+  for (int c = 0; c < ncomp(p); ++c) {
+    r.a[c].resize(x.a[c].size());
+    for (size_t k = 0; k < x.a[c].size(); ++k) r.a[c][k] = a * x.a[c][k] + b * y.a[c][k];
+  }
+  return r;
+}
+
+Model make_model(const ao_problem* p) {
+  Model m;
+  m.p = *p;
+  find_crit(m);
+  return m;
+}
+
+State load(const ao_problem& p, double* const* arr) {
+  State s;
+  size_t n = ncell(p);
+  for (int c = 0; c < ncomp(p); ++c) s.a[c].assign(arr[c], arr[c] + n);
+  return s;
+}
+void store(const ao_problem& p, const State& s, double* const* arr) {
+  for (int c = 0; c < ncomp(p); ++c) std::memcpy(arr[c], s.a[c].data(), s.a[c].size() * sizeof(double));
+}
+
+}  // namespace
+
+extern "C" {
+
+// One forward-Euler evaluation out = FE(in, tau) with limiter/projection/blend as set
+// in *p. Arrays: dim 1 -> {ub, P}; dim 2 -> {ub, V, X, Y}. s_ext: per-cell indicator
+// (blend == 2) or NULL.
+int ao_fe(const ao_problem* p, double* const* in, double tau, const double* s_ext, double* const* out) {
+  Model m = make_model(p);
+  State a = load(*p, in), b;
+  fe(m, a, tau, s_ext, b);
+  store(*p, b, out);
+  return 0;
+}
+
+// One full time step with rk = 3 (SSP-RK3) or 54 (SSP-RK(5,4)); state updated in place.
+int ao_step(const ao_problem* p, int rk, double* const* state, double dt, const double* s_ext, ao_stats* st) {
+  Model m = make_model(p);
+  State u0 = load(*p, state), t;
+  if (rk == 3) {
+    fe(m, u0, dt, s_ext, t);
+    State u1 = t;
+    safeguard(*p, u1, st);
+    fe(m, u1, dt, s_ext, t);
+    State u2 = combine(*p, 0.75, u0, 0.25, t);
+    safeguard(*p, u2, st);
+    fe(m, u2, dt, s_ext, t);
+    State u3 = combine(*p, 1.0 / 3.0, u0, 2.0 / 3.0, t);
+    safeguard(*p, u3, st);
+    store(*p, u3, state);
+    return st && st->error ? -4 : 0;
+  }
+  if (rk == 54) {
+    const double(*A)[5] = RK54_A;
+    const double(*B)[5] = RK54_B;
+    State u[5];
+    u[0] = u0;
+    fe(m, u[0], B[0][0] / A[0][0] * dt, s_ext, t);
+    u[1] = combine(*p, 0.0, u0, A[0][0], t);
+    safeguard(*p, u[1], st);
+    fe(m, u[1], B[1][1] / A[1][1] * dt, s_ext, t);
+    u[2] = combine(*p, A[1][0], u[0], A[1][1], t);
+    safeguard(*p, u[2], st);
+    fe(m, u[2], B[2][2] / A[2][2] * dt, s_ext, t);
+    u[3] = combine(*p, A[2][0], u[0], A[2][2], t);
+    safeguard(*p, u[3], st);
+    fe(m, u[3], B[3][3] / A[3][3] * dt, s_ext, t);
+    u[4] = combine(*p, A[3][0], u[0], A[3][3], t);
+    safeguard(*p, u[4], st);
+    // last row: the same u^(3) enters with its own step ratio, so its limited FE step is
+    // evaluated again at that ratio (the limiter is nonlinear in tau).
+    fe(m, u[3], B[4][3] / A[4][3] * dt, s_ext, t);
+    State part = combine(*p, A[4][2], u[2], A[4][3], t);
+    fe(m, u[4], B[4][4] / A[4][4] * dt, s_ext, t);
+    State u5 = combine(*p, 1.0, part, A[4][4], t);
+    safeguard(*p, u5, st);
+    store(*p, u5, state);
+    return st && st->error ? -4 : 0;
+  }
+  return -1;
+}
+
+// CFL time step dt = C / max_{faces,l} (alpha_face / h_l + kappa_max / h_l^2)
+// (eq. multid_av_pp_dt; 1D eq. 1d_av_pp_dt), additionally capped by the linear
+// stability of the unlimited high-order scheme for diffusion, dt <= Cd h_l^2 / kappa_max
+// (cfl_diff <= 0 disables the cap).
+double ao_dt(const ao_problem* p, const double* ub, double cfl, double cfl_diff) {
+  Model m = make_model(p);
+  double km = kappa_max(m), worst = 0.0;
+  if (p->dim == 1) {
+    for (int i = 0; i < p->nx; ++i) {
+      double a = alpha_interval<double>(m, 0, ub[i], ub[wrap(i + 1, p->nx)]);
+      worst = std::max(worst, a / p->dx + km / (p->dx * p->dx));
+    }
+  } else {
+    for (int j = 0; j < p->ny; ++j)
+      for (int i = 0; i < p->nx; ++i) {
+        double u = ub[(size_t)j * p->nx + i];
+        double a1 = alpha_interval<double>(m, 0, u, ub[(size_t)j * p->nx + wrap(i + 1, p->nx)]);
+        double a2 = alpha_interval<double>(m, 1, u, ub[(size_t)wrap(j + 1, p->ny) * p->nx + i]);
+        worst = std::max(worst, a1 / p->dx + km / (p->dx * p->dx));
+        worst = std::max(worst, a2 / p->dy + km / (p->dy * p->dy));
+      }
+  }
+  double rate = worst / cfl;
+  if (cfl_diff > 0.0 && km > 0.0) {
+    double hmin = p->dim == 1 ? p->dx : std::min(p->dx, p->dy);
+    rate = std::max(rate, km / (hmin * hmin) / cfl_diff);
+  }
+  return rate > 0.0 ? 1.0 / rate : INFINITY;
+}
+
+double ao_kappa_max(const ao_problem* p) { return kappa_max(make_model(p)); }
+
+double ao_alpha_interval(const ao_problem* p, int dir, double a, double b) {
+  return alpha_interval<double>(make_model(p), dir, a, b);
+}
+
+void ao_point_funcs(const ao_problem* p, int dir, double u, double* f, double* df, double* a) {
+  Model m = make_model(p);
+  *f = flux<double>(m, dir, u);
+  *df = dflux<double>(m, dir, u);
+  *a = apot<double>(m, u);
+}
+
+double ao_theta(const ao_problem* p, double zL, double zH) { return Theta<double>(make_model(p), zL, zH); }
+
+void ao_rk54_coefs(double* alpha, double* beta) {
+  for (int k = 0; k < 5; ++k)
+    for (int l = 0; l < 5; ++l) { alpha[k * 5 + l] = RK54_A[k][l]; beta[k * 5 + l] = RK54_B[k][l]; }
+}
+
+// Flop count of one FE evaluation on the given state (counting scalar; every
+// +,-,*,/ and exp counts one). out[0..4] = add, mul, div, exp, cmp.
+void ao_flop_count(const ao_problem* p, double* const* in, double tau, const double* s_ext, long long* out) {
+  Model m = make_model(p);
+  g_flops = FlopCounter();
+  size_t n = ncell(*p);
+  std::vector<Cnt> a[4], b[4], se;
+  for (int c = 0; c < ncomp(*p); ++c) {
+    a[c].resize(n); b[c].resize(n);
+    for (size_t k = 0; k < n; ++k) a[c][k] = Cnt(in[c][k]);
+  }
+  if (s_ext) { se.resize(n); for (size_t k = 0; k < n; ++k) se[k] = Cnt(s_ext[k]); }
+  if (p->dim == 1)
+    fe1d<Cnt>(m, a[0].data(), a[1].data(), Cnt(tau), s_ext ? se.data() : nullptr, b[0].data(), b[1].data());
+  else
+    fe2d<Cnt>(m, a[0].data(), a[1].data(), a[2].data(), a[3].data(), Cnt(tau), s_ext ? se.data() : nullptr,
+              b[0].data(), b[1].data(), b[2].data(), b[3].data());
+  out[0] = g_flops.add; out[1] = g_flops.mul; out[2] = g_flops.div; out[3] = g_flops.exp; out[4] = g_flops.cmp;
+}
+
+}  // extern "C"
