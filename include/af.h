@@ -1,0 +1,150 @@
+/*
+ * af.h -- C ABI of the GB300 (sm_103a) implementation of the compact fourth-order,
+ * doubly conservative active flux (AF) method with monolithic convex
+ * maximum-principle-preserving (MPP) limiting for
+ *
+ *      u_t + div f(u) = Laplace a(u),   a(u) = int kappa,  kappa >= 0      (Section 1)
+ *
+ * on periodic Cartesian meshes in 1D and 2D (arXiv 2510.11527).
+ *
+ * Degrees of freedom (Section 2 for 1D, Section 4 / Fig. 2 for 2D). All arrays are
+ * row-major [ny][nx] with i fastest; a periodic mesh stores nx*ny of each kind:
+ *   ub[j][i]  cell average of cell (i,j)
+ *   V [j][i]  point value at the corner  (x_{i+1/2}, y_{j+1/2})
+ *   X [j][i]  point value at the midpoint of the vertical edge (x_{i+1/2}, y_j)
+ *   Y [j][i]  point value at the midpoint of the horizontal edge (x_i, y_{j+1/2})
+ * In 1D only ub[i] and P[i] = u(x_{i+1/2}) exist; they are passed in the ub and V
+ * slots, and X, Y are ignored (may be NULL).
+ *
+ * Conventions
+ *   - Every call returns an af_status. On error the context is left unchanged and
+ *     af_last_error() describes the failure; after AF_E_CUDA the context must only be
+ *     destroyed.
+ *   - Host pointers are read or written synchronously and remain owned by the caller.
+ *   - Device work is issued on the stream set by af_set_stream (default: the legacy
+ *     default stream). Calls that return host data synchronise that stream.
+ *   - There is no CPU fallback: without a usable CUDA device af_create returns
+ *     AF_E_UNSUPPORTED.
+ */
+#ifndef AF_H_
+#define AF_H_
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct af_ctx af_ctx;   /* opaque; created by af_create, freed by af_destroy */
+
+typedef enum {
+  AF_OK = 0,
+  AF_E_ARG = -1,          /* invalid argument (sizes, kinds, NULL pointers, bounds)        */
+  AF_E_CUDA = -2,         /* a CUDA runtime call failed                                     */
+  AF_E_OOM = -3,          /* device allocation failed                                       */
+  AF_E_STATE = -4,        /* state outside [umin,umax] beyond the safeguard tolerance, NaN */
+  AF_E_CFL = -5,          /* requested dt exceeds the MPP CFL bound of the current state   */
+  AF_E_TIMEOUT = -6,      /* a bounded device-side wait gave up                             */
+  AF_E_UNSUPPORTED = -7   /* no CUDA device / feature not built                             */
+} af_status;
+
+/* Flux kinds (Section 1; examples of Section 6). p[] as listed. */
+enum {
+  AF_FLUX_ZERO = 0,       /* f = 0                                                          */
+  AF_FLUX_LINEAR = 1,     /* f1 = p0 u, f2 = p1 u                                           */
+  AF_FLUX_BURGERS = 2,    /* f1 = f2 = p0 u^2                                               */
+  AF_FLUX_BL = 3          /* Buckley-Leverett: f1 = u^2/(u^2+(1-u)^2), f2 = f1 (1 - p0 (1-u)^2) */
+};
+
+/* Diffusion potential kinds a(u) = int kappa (Section 1). */
+enum {
+  AF_DIFF_NONE = 0,       /* a = 0                                                          */
+  AF_DIFF_CONST = 1,      /* a = p0 u                                                       */
+  AF_DIFF_PWL = 2,        /* a = p0 min(u - p1, 0) + p2 max(u - p3, 0)  (degenerate band)   */
+  AF_DIFF_PME = 3,        /* a = u^p0, p0 integer >= 1 (porous medium)                      */
+  AF_DIFF_CUBIC = 4       /* a = p0 u + p1 u^2 + p2 u^3                                     */
+};
+
+enum { AF_PREC_FP64 = 0, AF_PREC_FP32_MIXED = 1 };   /* FP32 points/stencils, FP64 averages */
+enum { AF_RK_SSP3 = 3, AF_RK_SSP54 = 54 };
+enum { AF_BLEND_OFF = 0, AF_BLEND_PLAIN = 1, AF_BLEND_EXTERNAL = 2 };
+
+typedef struct { int dim; int nx, ny; double x0, x1, y0, y1; } af_grid;  /* periodic only */
+typedef struct { int kind; double p[4]; } af_flux;
+typedef struct { int kind; double p[4]; } af_diff;
+typedef struct { double umin, umax; int from_initial_data; } af_bounds_t;
+
+typedef struct {
+  int precision;          /* AF_PREC_FP64 or AF_PREC_FP32_MIXED                             */
+  int rk;                 /* AF_RK_SSP3 or AF_RK_SSP54                                      */
+  double cfl;             /* C in dt = C / max(alpha/h + kappa_max/h^2); <= 0 -> 0.33/dim    */
+  double cfl_diff;        /* diffusive cap dt <= Cd h^2/kappa_max; 0 -> default; < 0 -> off  */
+  int limiter;            /* 1: monolithic convex limiter + point projection (Section 5)    */
+  int blend;              /* AF_BLEND_*: smoothness-indicator blend (Section 5.1.3)         */
+  double gamma;           /* blend strength gamma (1 in the paper's examples)               */
+} af_opts;
+
+/* Create a solver for one periodic mesh. Allocates all device buffers (4 state copies
+ * for SSP-RK(5,4), 3 for SSP-RK3). bounds->from_initial_data = 1 defers umin/umax to
+ * the min/max of the first af_set_state. Returns AF_E_ARG for nx,ny < 1, dim not 1/2,
+ * unknown kinds, umin >= umax; AF_E_OOM if allocation fails. */
+af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* diff,
+                    const af_bounds_t* bounds, const af_opts* opts, af_ctx** out);
+af_status af_destroy(af_ctx* ctx);
+const char* af_last_error(const af_ctx* ctx);
+
+/* Issue all device work of this context on `stream` (a cudaStream_t, e.g. PyTorch's
+ * current stream). NULL selects the legacy default stream. */
+af_status af_set_stream(af_ctx* ctx, void* stream);
+
+/* Copy a host state in (doubles, caller-owned). FP32-mixed contexts round the point
+ * values to float. AF_E_STATE if any value is NaN or, with the limiter on, outside
+ * [umin, umax]. */
+af_status af_set_state(af_ctx* ctx, const double* ub, const double* V, const double* X, const double* Y);
+af_status af_get_state(af_ctx* ctx, double* ub, double* V, double* X, double* Y);
+
+/* Borrowed device pointers of the current state (ub, V, X, Y). dtype[0] is 8 (ub is
+ * always FP64); dtype[1] is 8 or 4 for the point arrays. Valid until the next call that
+ * steps or destroys the context. */
+af_status af_device_ptrs(af_ctx* ctx, void* ptrs[4], int dtype[2]);
+
+/* Per-cell external smoothness indicator s (nx*ny doubles, host) used when
+ * blend == AF_BLEND_EXTERNAL: it replaces the indicator s of Section 5.1.3 in every
+ * direction; the limiter and projection still follow. */
+af_status af_set_indicator(af_ctx* ctx, const double* s_host);
+af_status af_set_indicator_device(af_ctx* ctx, const double* s_dev);
+
+/* One forward-Euler evaluation state <- FE(state, tau) with limiter, projection and
+ * blend as configured, and no RK combination (the building block of Section 5). */
+af_status af_forward_euler(af_ctx* ctx, double tau);
+
+/* Stage k (0-based) of the configured SSP-RK scheme (Section 3.2); stages must be
+ * issued in order 0..af_num_stages()-1 to complete one step. At k = 0 a dt > 0 sets
+ * the step (and advances the time); dt <= 0 keeps the step already on the device
+ * (from af_dt_device). Later stages ignore dt. */
+af_status af_stage(af_ctx* ctx, int k, double dt);
+/* Compute the CFL step of the current state on the device into the context's step
+ * slot and advance the simulated time by it; no host synchronisation. */
+af_status af_dt_device(af_ctx* ctx);
+int af_num_stages(const af_ctx* ctx);
+
+/* One full time step. dt > 0: use it as given. dt <= 0: compute the CFL step on the
+ * device (eq. multid_av_pp_dt, capped for diffusive linear stability) without a host
+ * round trip; if dt_used is non-NULL the stream is synchronised and dt returned. */
+af_status af_step(af_ctx* ctx, double dt, double* dt_used);
+
+/* March to time T from the current time with CFL steps, clipping the last step to
+ * land on T. Synchronises once per step to read dt. */
+af_status af_run(af_ctx* ctx, double T, long long* nsteps);
+af_status af_time(af_ctx* ctx, double* t);       /* simulated time (synchronises) */
+
+/* Diagnostics (deterministic reductions in FP64). */
+af_status af_mass(af_ctx* ctx, double* mass);                 /* sum(ub) * dx * dy          */
+af_status af_bounds(af_ctx* ctx, double* umin, double* umax); /* over all DoFs              */
+af_status af_dt_cfl(af_ctx* ctx, double* dt);                 /* CFL step of current state  */
+/* Safeguard statistics since creation: values clamped (excess <= tolerance), errors
+ * (excess > tolerance) and the largest clamped excess. */
+af_status af_stats(af_ctx* ctx, long long* clamps, long long* errors, double* max_excess);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AF_H_ */

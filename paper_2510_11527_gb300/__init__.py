@@ -1,0 +1,132 @@
+"""GB300 (sm_103a) implementation of the compact fourth-order doubly conservative
+active flux method with monolithic convex MPP limiting (arXiv 2510.11527).
+
+The numerical work runs in libaf.so (CUDA, include/af.h); ``capi`` is its ctypes
+binding and ``Solver`` a small convenience wrapper that owns one af_ctx. PyTorch is
+used only for device memory views and streams.
+"""
+import ctypes
+
+import numpy as np
+
+from . import capi
+from .capi import AfError, af_bounds_t, af_diff, af_flux, af_grid, af_opts
+
+__all__ = ["Solver", "capi", "AfError"]
+
+
+class Solver:
+    """One periodic mesh behind an af_ctx.
+
+    spec: any object with the attributes dim, nx, ny, x0, x1, y0, y1, flux=(kind, params),
+    diff=(kind, params), umin, umax, limiter, blend, gamma (e.g. af_inputs.Spec).
+    """
+
+    def __init__(self, spec, precision="fp64", rk=3, cfl=0.0, cfl_diff=0.0, bounds_from_data=False):
+        self.spec = spec
+        self.dim = spec.dim
+        self.n = spec.nx * (spec.ny if spec.dim == 2 else 1)
+        g = af_grid(spec.dim, spec.nx, spec.ny if spec.dim == 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1)
+        f = af_flux()
+        f.kind = capi.FLUX[spec.flux[0]]
+        for k, v in enumerate(spec.flux[1]):
+            f.p[k] = float(v)
+        d = af_diff()
+        d.kind = capi.DIFF[spec.diff[0]]
+        for k, v in enumerate(spec.diff[1]):
+            d.p[k] = float(v)
+        b = af_bounds_t(float(spec.umin), float(spec.umax), 1 if bounds_from_data else 0)
+        o = af_opts(capi.PREC[precision], int(rk), float(cfl), float(cfl_diff), int(bool(spec.limiter)),
+                    capi.BLEND[spec.blend], float(spec.gamma))
+        self.precision = precision
+        self.ctx = capi.af_create(g, f, d, b, o)
+
+    def close(self):
+        if self.ctx:
+            capi.af_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # state I/O
+    def set_state(self, state):
+        arrs = [np.asarray(a, dtype=np.float64) for a in state]
+        if self.dim == 1:
+            capi.af_set_state(self.ctx, self.n, arrs[0], arrs[1])
+        else:
+            capi.af_set_state(self.ctx, self.n, *arrs)
+
+    def get_state(self):
+        out = capi.af_get_state(self.ctx, self.n, self.dim)
+        shape = (self.spec.ny, self.spec.nx) if self.dim == 2 else (self.spec.nx,)
+        return [a.reshape(shape) for a in out]
+
+    def device_tensors(self):
+        """Zero-copy torch views of the current device state (ub, V, X, Y)."""
+        import torch
+
+        ptrs, (d0, d1) = capi.af_device_ptrs(self.ctx)
+        shape = (self.spec.ny, self.spec.nx) if self.dim == 2 else (self.spec.nx,)
+        out = []
+        for k, p in enumerate(ptrs):
+            if p is None:
+                continue
+            typestr = "<f8" if (k == 0 or d1 == 8) else "<f4"
+
+            class _View:
+                __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (p, False), "version": 3}
+
+            out.append(torch.as_tensor(_View(), device="cuda"))
+        return out
+
+    def set_stream(self, stream):
+        capi.af_set_stream(self.ctx, stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+
+    # stepping
+    def forward_euler(self, tau):
+        capi.af_forward_euler(self.ctx, tau)
+
+    def stage(self, k, dt):
+        capi.af_stage(self.ctx, k, dt)
+
+    def dt_device(self):
+        capi.af_dt_device(self.ctx)
+
+    def step(self, dt=0.0, want_dt=False):
+        return capi.af_step(self.ctx, dt, want_dt)
+
+    def run(self, T):
+        return capi.af_run(self.ctx, T)
+
+    def time(self):
+        return capi.af_time(self.ctx)
+
+    def set_indicator(self, s):
+        capi.af_set_indicator(self.ctx, self.n, s)
+
+    # diagnostics
+    def mass(self):
+        return capi.af_mass(self.ctx)
+
+    def bounds(self):
+        return capi.af_bounds(self.ctx)
+
+    def dt_cfl(self):
+        return capi.af_dt_cfl(self.ctx)
+
+    def stats(self):
+        return capi.af_stats(self.ctx)
+
+    @property
+    def num_stages(self):
+        return capi.af_num_stages(self.ctx)

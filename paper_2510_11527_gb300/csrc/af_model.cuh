@@ -1,0 +1,162 @@
+// Device-side problem functions for the active flux stage kernels: convection flux
+// f_l, its derivative, the diffusion potential a(u) = int kappa, the interval maximum
+// of |f_l'| used by the LLF low-order flux (Section 5.1.1 / 5.2 of arXiv 2510.11527),
+// and the limiter function Theta (Section 5.1.1).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "af.h"
+
+namespace af {
+
+// Flux kinds are template parameters of the kernels (compile-time dispatch).
+enum : int { FLUX_ZERO = AF_FLUX_ZERO, FLUX_LINEAR = AF_FLUX_LINEAR, FLUX_BURGERS = AF_FLUX_BURGERS,
+             FLUX_BL = AF_FLUX_BL };
+
+// Problem parameters passed by value to every kernel.
+struct DevModel {
+  int flux_kind;
+  int diff_kind;
+  double fp[4];          // flux parameters
+  double dp[4];          // diffusion parameters
+  int ncrit[2];          // interior extrema of f_l' (Buckley-Leverett)
+  double crit[2][8];
+  double umin, umax;
+};
+
+template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <class T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+__device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+
+// f_l(u)
+template <int FLUX, class T>
+__device__ __forceinline__ T flux(const DevModel& m, int dir, T u) {
+  if constexpr (FLUX == FLUX_LINEAR) {
+    return T(dir == 0 ? m.fp[0] : m.fp[1]) * u;
+  } else if constexpr (FLUX == FLUX_BURGERS) {
+    return T(m.fp[0]) * u * u;
+  } else if constexpr (FLUX == FLUX_BL) {
+    T v = T(1) - u;
+    T u2 = u * u;
+    T f1 = u2 / (u2 + v * v);
+    if (dir == 0) return f1;
+    return f1 * (T(1) - T(m.fp[0]) * v * v);
+  } else {
+    return T(0);
+  }
+}
+
+// |f_l'(u)|
+template <int FLUX, class T>
+__device__ __forceinline__ T dflux_abs(const DevModel& m, int dir, T u) {
+  if constexpr (FLUX == FLUX_LINEAR) {
+    return tabs(T(dir == 0 ? m.fp[0] : m.fp[1]));
+  } else if constexpr (FLUX == FLUX_BURGERS) {
+    return tabs(T(2.0 * m.fp[0]) * u);
+  } else if constexpr (FLUX == FLUX_BL) {
+    T v = T(1) - u;
+    T D = u * u + v * v;
+    T rD = T(1) / D;
+    T d1 = T(2) * u * v * rD * rD;
+    if (dir == 0) return tabs(d1);
+    T f1 = u * u * rD;
+    T g = T(m.fp[0]);
+    return tabs(d1 * (T(1) - g * v * v) + T(2) * g * v * f1);
+  } else {
+    return T(0);
+  }
+}
+
+// a(u)
+template <class T>
+__device__ __forceinline__ T apot(const DevModel& m, T u) {
+  switch (m.diff_kind) {
+    case AF_DIFF_CONST:
+      return T(m.dp[0]) * u;
+    case AF_DIFF_PWL:
+      return T(m.dp[0]) * tmin(u - T(m.dp[1]), T(0)) + T(m.dp[2]) * tmax(u - T(m.dp[3]), T(0));
+    case AF_DIFF_PME: {
+      int e = (int)m.dp[0];
+      T r = u;
+      for (int k = 1; k < e; ++k) r *= u;
+      return r;
+    }
+    case AF_DIFF_CUBIC:
+      return ((T(m.dp[2]) * u + T(m.dp[1])) * u + T(m.dp[0])) * u;
+    default:
+      return T(0);
+  }
+}
+
+// max |f_l'| over [min(a,b), max(a,b)]: the end points plus the interior extrema of f_l'.
+template <int FLUX, class T>
+__device__ __forceinline__ T alpha_interval(const DevModel& m, int dir, T a, T b) {
+  if constexpr (FLUX == FLUX_LINEAR) {
+    return tabs(T(dir == 0 ? m.fp[0] : m.fp[1]));
+  } else if constexpr (FLUX == FLUX_BURGERS) {
+    return T(tabs(2.0 * m.fp[0])) * tmax(tabs(a), tabs(b));
+  } else if constexpr (FLUX == FLUX_BL) {
+    T lo = tmin(a, b), hi = tmax(a, b);
+    T best = tmax(dflux_abs<FLUX, T>(m, dir, lo), dflux_abs<FLUX, T>(m, dir, hi));
+    for (int k = 0; k < m.ncrit[dir]; ++k) {
+      T c = T(m.crit[dir][k]);
+      if (c > lo && c < hi) best = tmax(best, dflux_abs<FLUX, T>(m, dir, c));
+    }
+    return best;
+  } else {
+    return T(0);
+  }
+}
+
+// Theta(zL, zH): largest t in [0,1] with (1-t) zL + t zH inside [umin, umax].
+template <class T>
+__device__ __forceinline__ T theta_fn(T zL, T zH, T umin, T umax) {
+  T bound;
+  if (zH < umin) bound = umin;
+  else if (zH > umax) bound = umax;
+  else return T(1);
+  T den = zL - zH;
+  if (den == T(0)) return T(1);
+  T t = (zL - bound) / den;
+  return tmin(tmax(t, T(0)), T(1));
+}
+
+// Stage statistics accumulated on the device (safeguard clamp of Section 5's
+// "up to roundoff" MPP statement).
+struct DevStats {
+  unsigned long long clamps;
+  unsigned long long errors;
+  unsigned long long max_excess_bits;   // bit pattern of a non-negative double
+  unsigned long long pad;
+};
+
+__device__ __forceinline__ void record_excess(DevStats* st, double e, double tol, bool* clamp_ok) {
+  if (e <= tol) {
+    *clamp_ok = true;
+    atomicAdd(&st->clamps, 1ull);
+    atomicMax(&st->max_excess_bits, (unsigned long long)__double_as_longlong(e));
+  } else {
+    *clamp_ok = false;
+    atomicAdd(&st->errors, 1ull);
+  }
+}
+
+// Safeguard on a stored value: exact comparison against the bounds, clamp if within tol.
+template <class S>
+__device__ __forceinline__ S safeguard(S v, S umin, S umax, double tol, DevStats* st) {
+  if (v < umin) {
+    bool ok;
+    record_excess(st, (double)umin - (double)v, tol, &ok);
+    return ok ? umin : v;
+  }
+  if (v > umax) {
+    bool ok;
+    record_excess(st, (double)v - (double)umax, tol, &ok);
+    return ok ? umax : v;
+  }
+  return v;
+}
+
+}  // namespace af

@@ -1,0 +1,655 @@
+// Host driver of libaf: contexts, device buffers, SSP-RK stage sequencing, CFL time
+// step and diagnostics behind the C ABI of include/af.h (arXiv 2510.11527).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "af.h"
+#include "launch.h"
+#include "reduce.cuh"
+
+using af::DevModel;
+using af::DevStats;
+using af::StageArgs2D;
+
+namespace {
+
+// SSP-RK(5,4) of Spiteri & Ruuth (2002) in Shu-Osher form: alpha[k][l], beta[k][l],
+// row k producing stage value k+1 from u^(l) (Section 3.2 gives its stability
+// polynomial, z^5 coefficient 0.004477718303076).
+const double kA54[5][5] = {
+    {1.0, 0, 0, 0, 0},
+    {0.444370493651235, 0.555629506348765, 0, 0, 0},
+    {0.620101851488403, 0, 0.379898148511597, 0, 0},
+    {0.178079954393132, 0, 0, 0.821920045606868, 0},
+    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269}};
+const double kB54[5][5] = {
+    {0.391752226571890, 0, 0, 0, 0},
+    {0, 0.368410593050371, 0, 0, 0},
+    {0, 0, 0.251891774271694, 0, 0},
+    {0, 0, 0, 0.544974750228521, 0},
+    {0, 0, 0, 0.063692468666290, 0.226007483236906}};
+
+// 0.9 x the linear stability limit kappa dt / h^2 of the unlimited scheme for pure
+// diffusion: 1D from the von Neumann analysis of Section 3.2 (0.157 SSP-RK3, 0.333
+// SSP-RK(5,4)); 2D from the 4x4 Fourier symbol of the 2D scheme, whose spectral radius
+// is 40.78 kappa/h^2 (0.0616 SSP-RK3, 0.1307 SSP-RK(5,4)).
+double default_cfl_diff(int dim, int rk) {
+  if (dim == 1) return 0.9 * (rk == AF_RK_SSP54 ? 0.333 : 0.157);
+  return 0.9 * (rk == AF_RK_SSP54 ? 0.1307 : 0.0616);
+}
+
+// Buckley-Leverett f_l'' (analytic) for locating the interior extrema of f_l'.
+double bl_d2(int dir, double g, double u) {
+  const double v = 1.0 - u, D = u * u + v * v, Dp = 2.0 * u - 2.0 * v;
+  const double f1 = u * u / D;
+  const double d1 = 2.0 * u * v / (D * D);
+  const double dd1 = (2.0 * (v - u) * D - 4.0 * u * v * Dp) / (D * D * D);
+  if (dir == 0) return dd1;
+  return dd1 * (1.0 - g * v * v) + 4.0 * g * v * d1 - 2.0 * g * f1;
+}
+
+// roots of f_l'' on [-1, 2]: sign changes on a uniform grid refined by bisection
+void bl_critical_points(DevModel& m) {
+  for (int d = 0; d < 2; ++d) {
+    m.ncrit[d] = 0;
+    const double g = m.fp[0];
+    const int n = 60000;
+    const double a = -1.0, b = 2.0;
+    double xprev = a, yprev = bl_d2(d, g, a);
+    for (int k = 1; k <= n && m.ncrit[d] < 8; ++k) {
+      const double x = a + (b - a) * k / n, y = bl_d2(d, g, x);
+      if ((yprev < 0.0 && y > 0.0) || (yprev > 0.0 && y < 0.0) || y == 0.0) {
+        double lo = xprev, hi = x, flo = yprev;
+        for (int it = 0; it < 200 && y != 0.0; ++it) {
+          const double mid = 0.5 * (lo + hi), fm = bl_d2(d, g, mid);
+          if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
+        }
+        m.crit[d][m.ncrit[d]++] = y == 0.0 ? x : 0.5 * (lo + hi);
+      }
+      xprev = x;
+      yprev = y;
+    }
+  }
+}
+
+double kappa_of(const af_diff& df, double u) {
+  switch (df.kind) {
+    case AF_DIFF_CONST: return df.p[0];
+    case AF_DIFF_PWL: return (u < df.p[1] ? df.p[0] : 0.0) + (u > df.p[3] ? df.p[2] : 0.0);
+    case AF_DIFF_PME: return df.p[0] * std::pow(u, df.p[0] - 1.0);
+    case AF_DIFF_CUBIC: return df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u;
+    default: return 0.0;
+  }
+}
+
+// kappa_max over [umin, umax] in closed form (Section 5.1.1)
+double kappa_max_of(const af_diff& df, double lo, double hi) {
+  double k = std::max(0.0, std::max(kappa_of(df, lo), kappa_of(df, hi)));
+  if (df.kind == AF_DIFF_PWL) {
+    if (lo < df.p[1]) k = std::max(k, df.p[0]);
+    if (hi > df.p[3]) k = std::max(k, df.p[2]);
+  }
+  if (df.kind == AF_DIFF_CUBIC && df.p[2] != 0.0) {
+    const double uv = -df.p[1] / (3.0 * df.p[2]);
+    if (uv > lo && uv < hi) k = std::max(k, kappa_of(df, uv));
+  }
+  return k;
+}
+
+}  // namespace
+
+struct af_ctx {
+  af_grid grid;
+  af_flux flux;
+  af_diff diff;
+  af_bounds_t bnd;
+  af_opts opts;
+  DevModel m;
+  int dim = 2, nx = 1, ny = 1, prec = AF_PREC_FP64, nbuf = 3;
+  size_t n = 0;
+  double dx = 1, dy = 1, inv_h1 = 1, inv_h2 = 1, kmax = 0, cfl = 0.165, cfl_diff = 0, tol = 0;
+  bool bounds_pending = false;
+  unsigned char* block = nullptr;     // one allocation for every device buffer
+  double* ub[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* pv[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* px[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* py[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* dt_dev = nullptr;
+  double* t_dev = nullptr;
+  double* red = nullptr;              // 8 reduction result slots
+  double* partial = nullptr;          // RED_MAX_BLOCKS partials
+  unsigned long long* rate_bits = nullptr;
+  DevStats* stats = nullptr;
+  double* s_ext = nullptr;            // n doubles
+  const double* s_ext_user = nullptr; // caller-provided device indicator
+  double* host_pinned = nullptr;      // 8 doubles for small read-backs
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+};
+
+#define FAIL(ctx, code, ...)                                  \
+  do {                                                        \
+    if (ctx) snprintf((ctx)->err, sizeof((ctx)->err), __VA_ARGS__); \
+    return code;                                              \
+  } while (0)
+
+#define CK(ctx, call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) FAIL(ctx, AF_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+namespace {
+
+size_t pt_size(const af_ctx* c) { return c->prec == AF_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+template <class PT>
+StageArgs2D<PT> base_args(af_ctx* c, int in) {
+  StageArgs2D<PT> a;
+  std::memset(&a, 0, sizeof(a));
+  a.nx = c->nx;
+  a.ny = c->ny;
+  a.inv_h1 = c->inv_h1;
+  a.inv_h2 = c->inv_h2;
+  a.ub = c->ub[in];
+  a.V = (const PT*)c->pv[in];
+  a.X = (const PT*)c->px[in];
+  a.Y = (const PT*)c->py[in];
+  a.dt = c->dt_dev;
+  a.s_ext = c->s_ext_user ? c->s_ext_user : c->s_ext;
+  a.limiter = c->opts.limiter;
+  a.blend = c->opts.blend;
+  a.blend_external = c->opts.blend == AF_BLEND_EXTERNAL;
+  a.gamma = c->opts.gamma;
+  a.tol = c->tol;
+  a.stats = c->stats;
+  return a;
+}
+
+// output k of a stage: out = cA * U[aidx] + cF * FE(in, tcoef * dt) -> U[oidx]
+template <class PT>
+void set_out(af_ctx* c, StageArgs2D<PT>& a, int k, int oidx, double cA, int aidx, double cF, double tcoef, int sg) {
+  a.tcoef[k] = tcoef;
+  a.cA[k] = cA;
+  a.cF[k] = cF;
+  a.Aub[k] = aidx >= 0 ? c->ub[aidx] : nullptr;
+  a.AV[k] = aidx >= 0 ? (const PT*)c->pv[aidx] : nullptr;
+  a.AX[k] = aidx >= 0 ? (const PT*)c->px[aidx] : nullptr;
+  a.AY[k] = aidx >= 0 ? (const PT*)c->py[aidx] : nullptr;
+  a.Oub[k] = c->ub[oidx];
+  a.OV[k] = (PT*)c->pv[oidx];
+  a.OX[k] = (PT*)c->px[oidx];
+  a.OY[k] = (PT*)c->py[oidx];
+  a.sg[k] = sg;
+  a.nout = k + 1;
+}
+
+template <class PT>
+cudaError_t launch(af_ctx* c, const StageArgs2D<PT>& a);
+template <>
+cudaError_t launch<double>(af_ctx* c, const StageArgs2D<double>& a) {
+  if (c->dim == 1) return af::launch_stage1d_f64(c->flux.kind, c->m, a, c->stream);
+  return af::launch_stage2d_f64(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
+}
+template <>
+cudaError_t launch<float>(af_ctx* c, const StageArgs2D<float>& a) {
+  if (c->dim == 1) return af::launch_stage1d_f32(c->flux.kind, c->m, a, c->stream);
+  return af::launch_stage2d_f32(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
+}
+
+// stage k of the configured scheme (buffer roles in the comments of af_stage)
+template <class PT>
+af_status stage_impl(af_ctx* c, int k) {
+  const int sg = 1;
+  if (c->opts.rk == AF_RK_SSP3) {
+    if (k == 0) {
+      auto a = base_args<PT>(c, 0);
+      set_out<PT>(c, a, 0, 1, 0.0, -1, 1.0, 1.0, sg);
+      CK(c, launch<PT>(c, a));
+    } else if (k == 1) {
+      auto a = base_args<PT>(c, 1);
+      set_out<PT>(c, a, 0, 2, 0.75, 0, 0.25, 1.0, sg);
+      CK(c, launch<PT>(c, a));
+    } else if (k == 2) {
+      auto a = base_args<PT>(c, 2);
+      set_out<PT>(c, a, 0, 0, 1.0 / 3.0, 0, 2.0 / 3.0, 1.0, sg);
+      CK(c, launch<PT>(c, a));
+    } else {
+      FAIL(c, AF_E_ARG, "stage %d out of range", k);
+    }
+    return AF_OK;
+  }
+  const double(*A)[5] = kA54;
+  const double(*B)[5] = kB54;
+  switch (k) {
+    case 0: {
+      auto a = base_args<PT>(c, 0);
+      set_out<PT>(c, a, 0, 1, 0.0, -1, A[0][0], B[0][0] / A[0][0], sg);
+      CK(c, launch<PT>(c, a));
+      break;
+    }
+    case 1: {
+      auto a = base_args<PT>(c, 1);
+      set_out<PT>(c, a, 0, 2, A[1][0], 0, A[1][1], B[1][1] / A[1][1], sg);
+      CK(c, launch<PT>(c, a));
+      break;
+    }
+    case 2: {
+      auto a = base_args<PT>(c, 2);
+      set_out<PT>(c, a, 0, 3, A[2][0], 0, A[2][2], B[2][2] / A[2][2], sg);
+      CK(c, launch<PT>(c, a));
+      break;
+    }
+    case 3: {
+      // u^(4) = a30 u0 + a33 FE(u3); partial = a42 u2 + a43 FE(u3, own ratio) in place
+      auto a = base_args<PT>(c, 3);
+      set_out<PT>(c, a, 0, 1, A[3][0], 0, A[3][3], B[3][3] / A[3][3], sg);
+      set_out<PT>(c, a, 1, 2, A[4][2], 2, A[4][3], B[4][3] / A[4][3], 0);
+      CK(c, launch<PT>(c, a));
+      break;
+    }
+    case 4: {
+      auto a = base_args<PT>(c, 1);
+      set_out<PT>(c, a, 0, 0, 1.0, 2, A[4][4], B[4][4] / A[4][4], sg);
+      CK(c, launch<PT>(c, a));
+      break;
+    }
+    default:
+      FAIL(c, AF_E_ARG, "stage %d out of range", k);
+  }
+  return AF_OK;
+}
+
+af_status stage_any(af_ctx* c, int k) {
+  return c->prec == AF_PREC_FP64 ? stage_impl<double>(c, k) : stage_impl<float>(c, k);
+}
+
+template <int FLUX>
+cudaError_t launch_rate(af_ctx* c) {
+  const int blocks = 152 * 4;
+  af::dt_rate_kernel<FLUX><<<blocks, af::RED_THREADS, 0, c->stream>>>(c->m, c->dim, c->nx, c->ny, c->inv_h1,
+                                                                       c->inv_h2, c->kmax, c->ub[0], c->rate_bits);
+  return cudaGetLastError();
+}
+
+// device CFL step -> *dst (no host round trip); t_acc: advance the device time
+af_status dt_device(af_ctx* c, double* dst, double* t_acc) {
+  cudaError_t e;
+  switch (c->flux.kind) {
+    case AF_FLUX_ZERO: e = launch_rate<af::FLUX_ZERO>(c); break;
+    case AF_FLUX_LINEAR: e = launch_rate<af::FLUX_LINEAR>(c); break;
+    case AF_FLUX_BURGERS: e = launch_rate<af::FLUX_BURGERS>(c); break;
+    default: e = launch_rate<af::FLUX_BL>(c); break;
+  }
+  CK(c, e);
+  const double hmin = c->dim == 1 ? c->dx : std::min(c->dx, c->dy);
+  af::dt_finalize_kernel<<<1, 1, 0, c->stream>>>(c->rate_bits, c->cfl, c->cfl_diff, c->kmax, 1.0 / (hmin * hmin),
+                                                 dst, t_acc);
+  CK(c, cudaGetLastError());
+  return AF_OK;
+}
+
+af_status read_scalar(af_ctx* c, const double* dev, double* out) {
+  CK(c, cudaMemcpyAsync(c->host_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  *out = c->host_pinned[0];
+  return AF_OK;
+}
+
+template <class S>
+af_status reduce_array(af_ctx* c, const S* x, int op, double init, double* out_dev, int accumulate) {
+  const int blocks = (int)std::min<size_t>(af::RED_MAX_BLOCKS, (c->n + af::RED_THREADS - 1) / af::RED_THREADS);
+  af::partial_kernel<S><<<blocks, af::RED_THREADS, 0, c->stream>>>(x, c->n, op, init, c->partial);
+  CK(c, cudaGetLastError());
+  af::finalize_kernel<<<1, 1, 0, c->stream>>>(c->partial, blocks, op, out_dev, accumulate);
+  CK(c, cudaGetLastError());
+  return AF_OK;
+}
+
+af_status set_dt(af_ctx* c, double dt, bool advance) {
+  af::set_dt_kernel<<<1, 1, 0, c->stream>>>(c->dt_dev, advance ? c->t_dev : nullptr, dt);
+  CK(c, cudaGetLastError());
+  return AF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* diff, const af_bounds_t* bounds,
+                    const af_opts* opts, af_ctx** out) {
+  if (!grid || !flux || !diff || !bounds || !opts || !out) return AF_E_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return AF_E_UNSUPPORTED;
+  if (grid->dim != 1 && grid->dim != 2) return AF_E_ARG;
+  if (grid->nx < 1 || (grid->dim == 2 && grid->ny < 1)) return AF_E_ARG;
+  if (!(grid->x1 > grid->x0) || (grid->dim == 2 && !(grid->y1 > grid->y0))) return AF_E_ARG;
+  if (flux->kind < AF_FLUX_ZERO || flux->kind > AF_FLUX_BL) return AF_E_ARG;
+  if (diff->kind < AF_DIFF_NONE || diff->kind > AF_DIFF_CUBIC) return AF_E_ARG;
+  if (diff->kind == AF_DIFF_PME && (diff->p[0] < 1.0 || diff->p[0] != std::floor(diff->p[0]))) return AF_E_ARG;
+  if (!bounds->from_initial_data && !(bounds->umax > bounds->umin)) return AF_E_ARG;
+  if (opts->precision != AF_PREC_FP64 && opts->precision != AF_PREC_FP32_MIXED) return AF_E_ARG;
+  if (opts->rk != AF_RK_SSP3 && opts->rk != AF_RK_SSP54) return AF_E_ARG;
+  if (opts->blend < AF_BLEND_OFF || opts->blend > AF_BLEND_EXTERNAL) return AF_E_ARG;
+
+  af_ctx* c = new (std::nothrow) af_ctx;
+  if (!c) return AF_E_OOM;
+  c->grid = *grid;
+  c->flux = *flux;
+  c->diff = *diff;
+  c->bnd = *bounds;
+  c->opts = *opts;
+  c->dim = grid->dim;
+  c->nx = grid->nx;
+  c->ny = grid->dim == 2 ? grid->ny : 1;
+  c->n = (size_t)c->nx * c->ny;
+  c->prec = opts->precision;
+  c->nbuf = opts->rk == AF_RK_SSP54 ? 4 : 3;
+  c->dx = (grid->x1 - grid->x0) / grid->nx;
+  c->dy = grid->dim == 2 ? (grid->y1 - grid->y0) / grid->ny : 1.0;
+  c->inv_h1 = 1.0 / c->dx;
+  c->inv_h2 = grid->dim == 2 ? 1.0 / c->dy : 0.0;
+  c->cfl = opts->cfl > 0.0 ? opts->cfl : 0.33 / grid->dim;
+  c->cfl_diff = opts->cfl_diff > 0.0 ? opts->cfl_diff : (opts->cfl_diff < 0.0 ? 0.0 : default_cfl_diff(c->dim, opts->rk));
+  std::memset(&c->m, 0, sizeof(c->m));
+  c->m.flux_kind = flux->kind;
+  c->m.diff_kind = diff->kind;
+  for (int k = 0; k < 4; ++k) { c->m.fp[k] = flux->p[k]; c->m.dp[k] = diff->p[k]; }
+  if (flux->kind == AF_FLUX_BL) bl_critical_points(c->m);
+  c->bounds_pending = bounds->from_initial_data != 0;
+  c->m.umin = bounds->umin;
+  c->m.umax = bounds->umax;
+  if (!c->bounds_pending) c->kmax = kappa_max_of(*diff, bounds->umin, bounds->umax);
+  const double scale = std::max(std::fabs(bounds->umin), std::fabs(bounds->umax));
+  c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;
+
+  // one device allocation: nbuf states + scratch
+  const size_t ps = pt_size(c);
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t per_state = al(c->n * 8) + 3 * al(c->n * ps);
+  const size_t scratch = al(8) * 2 + al(8 * 8) + al(8 * af::RED_MAX_BLOCKS) + al(8) + al(sizeof(DevStats)) + al(c->n * 8);
+  const size_t total = per_state * c->nbuf + scratch;
+  if (cudaMalloc(&c->block, total) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return AF_E_OOM;
+  }
+  unsigned char* p = c->block;
+  for (int b = 0; b < c->nbuf; ++b) {
+    c->ub[b] = (double*)p; p += al(c->n * 8);
+    c->pv[b] = p; p += al(c->n * ps);
+    c->px[b] = p; p += al(c->n * ps);
+    c->py[b] = p; p += al(c->n * ps);
+  }
+  c->dt_dev = (double*)p; p += al(8);
+  c->t_dev = (double*)p; p += al(8);
+  c->red = (double*)p; p += al(8 * 8);
+  c->partial = (double*)p; p += al(8 * af::RED_MAX_BLOCKS);
+  c->rate_bits = (unsigned long long*)p; p += al(8);
+  c->stats = (DevStats*)p; p += al(sizeof(DevStats));
+  c->s_ext = (double*)p; p += al(c->n * 8);
+  if (cudaMemset(c->block, 0, total) != cudaSuccess || cudaMallocHost(&c->host_pinned, 8 * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(c->block);
+    delete c;
+    return AF_E_OOM;
+  }
+  *out = c;
+  return AF_OK;
+}
+
+af_status af_destroy(af_ctx* c) {
+  if (!c) return AF_E_ARG;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  cudaFree(c->block);
+  cudaFreeHost(c->host_pinned);
+  delete c;
+  return AF_OK;
+}
+
+const char* af_last_error(const af_ctx* c) { return c ? c->err : "null context"; }
+
+af_status af_set_stream(af_ctx* c, void* stream) {
+  if (!c) return AF_E_ARG;
+  c->stream = (cudaStream_t)stream;
+  return AF_OK;
+}
+
+int af_num_stages(const af_ctx* c) { return !c ? 0 : (c->opts.rk == AF_RK_SSP54 ? 5 : 3); }
+
+af_status af_set_state(af_ctx* c, const double* ub, const double* V, const double* X, const double* Y) {
+  if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
+  const int na = c->dim == 2 ? 4 : 2;
+  const double* src[4] = {ub, V, X, Y};
+  double lo = INFINITY, hi = -INFINITY;
+  for (int a = 0; a < na; ++a)
+    for (size_t k = 0; k < c->n; ++k) {
+      const double v = src[a][k];
+      if (!(v == v)) FAIL(c, AF_E_STATE, "NaN in input array %d at %zu", a, k);
+      lo = std::min(lo, v);
+      hi = std::max(hi, v);
+    }
+  if (c->bounds_pending) {
+    if (!(hi > lo)) FAIL(c, AF_E_STATE, "bounds from initial data need max > min");
+    c->m.umin = lo;
+    c->m.umax = hi;
+    c->kmax = kappa_max_of(c->diff, lo, hi);
+    const double scale = std::max(std::fabs(lo), std::fabs(hi));
+    c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;
+    c->bounds_pending = false;
+  } else if (c->opts.limiter && (lo < c->m.umin || hi > c->m.umax)) {
+    FAIL(c, AF_E_STATE, "input outside [umin, umax]: [%g, %g]", lo, hi);
+  }
+  CK(c, cudaMemcpyAsync(c->ub[0], ub, c->n * 8, cudaMemcpyHostToDevice, c->stream));
+  void* dst[3] = {c->pv[0], c->px[0], c->py[0]};
+  if (c->prec == AF_PREC_FP64) {
+    for (int a = 1; a < na; ++a) CK(c, cudaMemcpyAsync(dst[a - 1], src[a], c->n * 8, cudaMemcpyHostToDevice, c->stream));
+  } else {
+    std::vector<float> tmp(c->n);
+    for (int a = 1; a < na; ++a) {
+      for (size_t k = 0; k < c->n; ++k) tmp[k] = (float)src[a][k];
+      CK(c, cudaMemcpyAsync(dst[a - 1], tmp.data(), c->n * 4, cudaMemcpyHostToDevice, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return AF_OK;
+}
+
+af_status af_get_state(af_ctx* c, double* ub, double* V, double* X, double* Y) {
+  if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
+  const int na = c->dim == 2 ? 4 : 2;
+  double* dst[4] = {ub, V, X, Y};
+  void* src[3] = {c->pv[0], c->px[0], c->py[0]};
+  CK(c, cudaMemcpyAsync(ub, c->ub[0], c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (c->prec == AF_PREC_FP64) {
+    for (int a = 1; a < na; ++a) CK(c, cudaMemcpyAsync(dst[a], src[a - 1], c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+  } else {
+    std::vector<float> tmp(c->n);
+    for (int a = 1; a < na; ++a) {
+      CK(c, cudaMemcpyAsync(tmp.data(), src[a - 1], c->n * 4, cudaMemcpyDeviceToHost, c->stream));
+      CK(c, cudaStreamSynchronize(c->stream));
+      for (size_t k = 0; k < c->n; ++k) dst[a][k] = (double)tmp[k];
+    }
+  }
+  CK(c, cudaStreamSynchronize(c->stream));
+  return AF_OK;
+}
+
+af_status af_device_ptrs(af_ctx* c, void* ptrs[4], int dtype[2]) {
+  if (!c || !ptrs) return AF_E_ARG;
+  ptrs[0] = c->ub[0];
+  ptrs[1] = c->pv[0];
+  ptrs[2] = c->dim == 2 ? c->px[0] : nullptr;
+  ptrs[3] = c->dim == 2 ? c->py[0] : nullptr;
+  if (dtype) { dtype[0] = 8; dtype[1] = (int)pt_size(c); }
+  return AF_OK;
+}
+
+af_status af_set_indicator(af_ctx* c, const double* s) {
+  if (!c || !s) return AF_E_ARG;
+  CK(c, cudaMemcpyAsync(c->s_ext, s, c->n * 8, cudaMemcpyHostToDevice, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  c->s_ext_user = nullptr;
+  return AF_OK;
+}
+
+af_status af_set_indicator_device(af_ctx* c, const double* s) {
+  if (!c || !s) return AF_E_ARG;
+  c->s_ext_user = s;
+  return AF_OK;
+}
+
+af_status af_forward_euler(af_ctx* c, double tau) {
+  if (!c || !(tau >= 0.0)) return AF_E_ARG;
+  if (c->bounds_pending) FAIL(c, AF_E_STATE, "state not set");
+  af_status s = set_dt(c, tau, false);
+  if (s != AF_OK) return s;
+  if (c->prec == AF_PREC_FP64) {
+    auto a = base_args<double>(c, 0);
+    set_out<double>(c, a, 0, 1, 0.0, -1, 1.0, 1.0, 0);
+    CK(c, launch<double>(c, a));
+  } else {
+    auto a = base_args<float>(c, 0);
+    set_out<float>(c, a, 0, 1, 0.0, -1, 1.0, 1.0, 0);
+    CK(c, launch<float>(c, a));
+  }
+  std::swap(c->ub[0], c->ub[1]);
+  std::swap(c->pv[0], c->pv[1]);
+  std::swap(c->px[0], c->px[1]);
+  std::swap(c->py[0], c->py[1]);
+  return AF_OK;
+}
+
+// Buffer roles. SSP-RK3 (U0..U2): U1 = FE(U0); U2 = 3/4 U0 + 1/4 FE(U1);
+// U0 = 1/3 U0 + 2/3 FE(U2) (in place: U0 is only read pointwise in that stage).
+// SSP-RK(5,4) (U0..U3): U1 = FE(U0); U2 = a U0 + b FE(U1); U3 = a U0 + b FE(U2);
+// U1 = a U0 + b FE(U3) and U2 = a U2 + b FE(U3, own ratio); U0 = U2 + b FE(U1).
+af_status af_stage(af_ctx* c, int k, double dt) {
+  if (!c || !(dt >= 0.0)) return AF_E_ARG;
+  if (c->bounds_pending) FAIL(c, AF_E_STATE, "state not set");
+  if (k < 0 || k >= af_num_stages(c)) FAIL(c, AF_E_ARG, "stage %d out of range", k);
+  if (k == 0 && dt > 0.0) {
+    af_status s = set_dt(c, dt, true);
+    if (s != AF_OK) return s;
+  }
+  return stage_any(c, k);
+}
+
+af_status af_dt_device(af_ctx* c) {
+  if (!c) return AF_E_ARG;
+  if (c->bounds_pending) FAIL(c, AF_E_STATE, "state not set");
+  return dt_device(c, c->dt_dev, c->t_dev);
+}
+
+af_status af_step(af_ctx* c, double dt, double* dt_used) {
+  if (!c || dt != dt) return AF_E_ARG;
+  if (c->bounds_pending) FAIL(c, AF_E_STATE, "state not set");
+  af_status s = dt > 0.0 ? set_dt(c, dt, true) : dt_device(c, c->dt_dev, c->t_dev);
+  if (s != AF_OK) return s;
+  for (int k = 0; k < af_num_stages(c); ++k) {
+    s = stage_any(c, k);
+    if (s != AF_OK) return s;
+  }
+  if (dt_used) return read_scalar(c, c->dt_dev, dt_used);
+  return AF_OK;
+}
+
+af_status af_run(af_ctx* c, double T, long long* nsteps) {
+  if (!c || !(T >= 0.0)) return AF_E_ARG;
+  if (c->bounds_pending) FAIL(c, AF_E_STATE, "state not set");
+  double t;
+  af_status s = read_scalar(c, c->t_dev, &t);
+  if (s != AF_OK) return s;
+  long long n = 0;
+  while (t < T * (1.0 - 1e-14)) {
+    double dt;
+    s = dt_device(c, c->red + 0, nullptr);
+    if (s != AF_OK) return s;
+    s = read_scalar(c, c->red + 0, &dt);
+    if (s != AF_OK) return s;
+    if (!(dt > 0.0)) FAIL(c, AF_E_STATE, "non-positive CFL time step");
+    dt = std::min(dt, T - t);
+    s = af_step(c, dt, nullptr);
+    if (s != AF_OK) return s;
+    t += dt;
+    ++n;
+  }
+  if (nsteps) *nsteps = n;
+  long long cl = 0, er = 0;
+  double mx = 0;
+  s = af_stats(c, &cl, &er, &mx);
+  if (s != AF_OK) return s;
+  if (er) FAIL(c, AF_E_STATE, "%lld values left [umin, umax] beyond the safeguard tolerance", er);
+  return AF_OK;
+}
+
+af_status af_time(af_ctx* c, double* t) {
+  if (!c || !t) return AF_E_ARG;
+  return read_scalar(c, c->t_dev, t);
+}
+
+af_status af_mass(af_ctx* c, double* mass) {
+  if (!c || !mass) return AF_E_ARG;
+  af_status s = reduce_array<double>(c, c->ub[0], 0, 0.0, c->red + 1, 0);
+  if (s != AF_OK) return s;
+  double v;
+  s = read_scalar(c, c->red + 1, &v);
+  if (s != AF_OK) return s;
+  *mass = v * c->dx * c->dy;
+  return AF_OK;
+}
+
+af_status af_bounds(af_ctx* c, double* umin, double* umax) {
+  if (!c || !umin || !umax) return AF_E_ARG;
+  const int na = c->dim == 2 ? 4 : 2;
+  void* arrs[4] = {c->ub[0], c->pv[0], c->px[0], c->py[0]};
+  for (int op = 1; op <= 2; ++op) {
+    for (int a = 0; a < na; ++a) {
+      af_status s;
+      const double init = op == 1 ? INFINITY : -INFINITY;
+      if (a == 0 || c->prec == AF_PREC_FP64)
+        s = reduce_array<double>(c, (const double*)arrs[a], op, init, c->red + 1 + op, a > 0);
+      else
+        s = reduce_array<float>(c, (const float*)arrs[a], op, init, c->red + 1 + op, a > 0);
+      if (s != AF_OK) return s;
+    }
+  }
+  af_status s = read_scalar(c, c->red + 2, umin);
+  if (s != AF_OK) return s;
+  return read_scalar(c, c->red + 3, umax);
+}
+
+af_status af_dt_cfl(af_ctx* c, double* dt) {
+  if (!c || !dt) return AF_E_ARG;
+  if (c->bounds_pending) FAIL(c, AF_E_STATE, "state not set");
+  af_status s = dt_device(c, c->red + 4, nullptr);
+  if (s != AF_OK) return s;
+  return read_scalar(c, c->red + 4, dt);
+}
+
+af_status af_stats(af_ctx* c, long long* clamps, long long* errors, double* max_excess) {
+  if (!c) return AF_E_ARG;
+  DevStats st;
+  CK(c, cudaMemcpyAsync(&st, c->stats, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (clamps) *clamps = (long long)st.clamps;
+  if (errors) *errors = (long long)st.errors;
+  if (max_excess) {
+    double v;
+    std::memcpy(&v, &st.max_excess_bits, sizeof(v));
+    *max_excess = v;
+  }
+  return AF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,16 @@
+// Internal launch helpers shared by the translation units of libaf (not installed).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "stage2d.cuh"
+
+namespace af {
+
+cudaError_t launch_stage2d_f64(int flux, bool blend, const DevModel& m, const StageArgs2D<double>& a,
+                               cudaStream_t s);
+cudaError_t launch_stage2d_f32(int flux, bool blend, const DevModel& m, const StageArgs2D<float>& a,
+                               cudaStream_t s);
+cudaError_t launch_stage1d_f64(int flux, const DevModel& m, const StageArgs2D<double>& a, cudaStream_t s);
+cudaError_t launch_stage1d_f32(int flux, const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s);
+
+}  // namespace af

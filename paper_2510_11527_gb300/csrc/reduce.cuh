@@ -1,0 +1,96 @@
+// Global reductions of the active flux driver: the CFL time step (eq.
+// multid_av_pp_dt of arXiv 2510.11527 with the interval wave speed of Section 5.2),
+// the total mass and the min/max over all DoFs. Every reduction is deterministic:
+// max/min are order independent, and sums are formed per block in a fixed tree order
+// and then summed by one block in block order.
+#pragma once
+#include "af_model.cuh"
+
+namespace af {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_MAX_BLOCKS = 1024;   // partial-result slots per reduction
+
+// max over faces of alpha_face / h + kappa_max / h^2 (non-negative -> integer max)
+template <int FLUX>
+__global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, int dim, int nx, int ny,
+                                                               double inv_h1, double inv_h2, double kmax,
+                                                               const double* __restrict__ ub,
+                                                               unsigned long long* rate_bits) {
+  const size_t n = (size_t)nx * ny;
+  double best = 0.0;
+  const double kd1 = kmax * inv_h1 * inv_h1, kd2 = kmax * inv_h2 * inv_h2;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(k % nx), j = (int)(k / nx);
+    const double u = ub[k];
+    const double ux = ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)];
+    best = fmax(best, alpha_interval<FLUX, double>(m, 0, u, ux) * inv_h1 + kd1);
+    if (dim == 2) {
+      const double uy = ub[(size_t)(j + 1 == ny ? 0 : j + 1) * nx + i];
+      best = fmax(best, alpha_interval<FLUX, double>(m, 1, u, uy) * inv_h2 + kd2);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ double sm[RED_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = sm[0];
+    for (int w = 1; w < RED_THREADS / 32; ++w) b = fmax(b, sm[w]);
+    atomicMax(rate_bits, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
+// dt = 1 / max(rate / C, kappa_max / (h_min^2 Cd)). Resets the accumulator for the
+// next step.
+// When t_acc is given the step is also added to the simulated time.
+__global__ void dt_finalize_kernel(unsigned long long* rate_bits, double cfl, double cfl_diff, double kmax,
+                                   double inv_hmin2, double* dt_out, double* t_acc) {
+  const double rate = __longlong_as_double((long long)*rate_bits);
+  double r = rate / cfl;
+  if (cfl_diff > 0.0 && kmax > 0.0) r = fmax(r, kmax * inv_hmin2 / cfl_diff);
+  const double dt = r > 0.0 ? 1.0 / r : 0.0;
+  *dt_out = dt;
+  if (t_acc) *t_acc += dt;
+  *rate_bits = 0ull;
+}
+
+// *dt = v and, when t_acc is given, *t_acc += v
+__global__ void set_dt_kernel(double* dt, double* t_acc, double v) {
+  *dt = v;
+  if (t_acc) *t_acc += v;
+}
+
+// ---- deterministic sum / min / max ------------------------------------------------------
+// op 0: sum of x; op 1: min; op 2: max. Each block reduces a contiguous chunk.
+__device__ __forceinline__ double red_op(int op, double a, double b) {
+  return op == 0 ? a + b : (op == 1 ? fmin(a, b) : fmax(a, b));
+}
+
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS) partial_kernel(const S* __restrict__ x, size_t n, int op,
+                                                              double init, double* partial) {
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+  double acc = init;
+  for (size_t k = beg + threadIdx.x; k < end; k += RED_THREADS) acc = red_op(op, acc, (double)x[k]);
+  __shared__ double sm[RED_THREADS];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = red_op(op, sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+// combine nparts partials in block order into out[slot] (op as above; combine with the
+// existing out[slot] when accumulate != 0)
+__global__ void finalize_kernel(const double* partial, int nparts, int op, double* out, int accumulate) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double acc = partial[0];
+  for (int k = 1; k < nparts; ++k) acc = red_op(op, acc, partial[k]);
+  *out = accumulate ? red_op(op, *out, acc) : acc;
+}
+
+}  // namespace af

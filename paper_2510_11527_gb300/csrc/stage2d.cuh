@@ -1,0 +1,503 @@
+// Fused 2D stage kernel of the compact fourth-order doubly conservative active flux
+// method with monolithic convex MPP limiting (arXiv 2510.11527, Sections 4 and 5.2,
+// d = 2).
+//
+// One launch performs, for every cell of a periodic nx x ny mesh, one or two limited
+// forward-Euler evaluations FE(u, tau_k) of the same input state followed by the
+// Shu-Osher combination out_k = cA_k * A_k + cF_k * FE(u, tau_k), the point-value
+// projection and the post-stage safeguard. Each CTA owns a TX x TY tile and stages a
+// halo box of +-H cells (H = 2; 3 with the smoothness blend) of all four DoF arrays in
+// shared memory; every derived quantity is evaluated once per box location, kept in
+// shared memory, and consumed by the neighbouring threads:
+//
+//   P0  load ub, V, X, Y (periodic wrap)
+//   P1  centre values c (Simpson recovery, Section 4) and pointwise f_l, |f_l'|, a
+//   P2  high-order point residuals (registers), Simpson face fluxes F^H_l, cell
+//       potentials A^H_l, LLF fluxes F^L_l
+//   P2b/P2c (blend) smoothness s_l, weights theta^{c,s}, theta^{d,s}; blended F, A, R
+//   P3  directional low-order states u^{L,+-}_l (factor 2d = 4)
+//   P4  limiter parameters theta^c (faces), theta^d (cells) with factor 3*2d = 12
+//   P5  limited cell-average update (eq. multid_limited_average), point update and
+//       projection, RK combination, safeguard, store.
+//
+// Face arrays are indexed by the box position of the face's left (x) / lower (y) cell:
+// F_1(b) lives on the x-face between b and b+1, F_2(b) on the y-face between b and
+// b+BX. Both tiles adjacent to a face compute it with the same instructions from the
+// same values, so conservation and double conservation hold bit for bit.
+#pragma once
+#include "af_model.cuh"
+
+namespace af {
+
+template <class PT>
+struct StageArgs2D {
+  int nx, ny;
+  double inv_h1, inv_h2;             // 1/dx, 1/dy
+  const double* ub;                  // FE input (read with halo)
+  const PT* V;
+  const PT* X;
+  const PT* Y;
+  int nout;                          // 1 or 2 limited FE evaluations of the same input
+  double tcoef[2];                   // tau_k = tcoef_k * (*dt)
+  double cA[2], cF[2];               // out_k = cA_k * A_k + cF_k * FE(u, tau_k)
+  const double* Aub[2];
+  const PT* AV[2];
+  const PT* AX[2];
+  const PT* AY[2];
+  double* Oub[2];
+  PT* OV[2];
+  PT* OX[2];
+  PT* OY[2];
+  const double* dt;                  // device scalar
+  const double* s_ext;               // external per-cell indicator (blend external)
+  int limiter;
+  int blend;                         // 0 off, 1 smoothness indicator, 2 external indicator
+  int blend_external;
+  int sg[2];                         // per output: apply the post-stage safeguard
+  double gamma;
+  double tol;                        // safeguard tolerance (absolute)
+  DevStats* stats;
+};
+
+// Per flux kind: which pointwise quantities are stored per point (a is always last).
+template <int FLUX> struct PointStore;
+template <> struct PointStore<FLUX_ZERO> { static constexpr int NQ = 1, NQU = 1; };
+template <> struct PointStore<FLUX_LINEAR> { static constexpr int NQ = 1, NQU = 1; };
+template <> struct PointStore<FLUX_BURGERS> { static constexpr int NQ = 2, NQU = 2; };   // f, a
+template <> struct PointStore<FLUX_BL> { static constexpr int NQ = 5, NQU = 3; };        // f1,f2,|f1'|,|f2'|,a
+
+template <int FLUX, class T, bool BLEND>
+struct Tile2D {
+  static constexpr int TX = 32, TY = 8, NT = TX * TY;
+  static constexpr int H = BLEND ? 3 : 2;
+  static constexpr int BX = TX + 2 * H, BY = TY + 2 * H, BN = BX * BY;
+  static constexpr int NQ = PointStore<FLUX>::NQ, NQU = PointStore<FLUX>::NQU;
+  // shared arrays (all of length BN, element type T)
+  static constexpr int A_U = 0, A_V = 1, A_X = 2, A_Y = 3, A_C = 4;
+  static constexpr int A_QU = 5;                       // NQU arrays: funcs at ub
+  static constexpr int A_FH1 = A_QU + NQU, A_FH2 = A_FH1 + 1, A_AH1 = A_FH1 + 2, A_AH2 = A_FH1 + 3;
+  static constexpr int A_FL1 = A_FH1 + 4, A_FL2 = A_FH1 + 5;
+  static constexpr int A_BL0 = A_FH1 + 6;              // blend: s1, s2, tc1, tc2, td1, td2
+  static constexpr int NBL = BLEND ? 6 : 0;
+  static constexpr int A_Q = A_BL0 + NBL;              // 4 point types x NQ, aliased later
+  static constexpr int NQREG = (4 * NQ > 8 ? 4 * NQ : 8);
+  static constexpr int NARR = A_Q + NQREG;
+  static constexpr size_t SMEM = (size_t)NARR * BN * sizeof(T);
+  // aliases inside the Q region (valid after P2)
+  static constexpr int A_ULP1 = A_Q, A_ULM1 = A_Q + 1, A_ULP2 = A_Q + 2, A_ULM2 = A_Q + 3;
+  static constexpr int A_FLIM1 = A_Q + 4, A_FLIM2 = A_Q + 5, A_ALIM1 = A_Q + 6, A_ALIM2 = A_Q + 7;
+};
+
+template <int NT, class F>
+__device__ __forceinline__ void for_rect(int x0, int x1, int y0, int y1, F&& f) {
+  const int w = x1 - x0, n = w * (y1 - y0);
+  for (int k = threadIdx.x; k < n; k += NT) f(x0 + k % w, y0 + k / w);
+}
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// Residual of one 5-point line (spacing h/2; points 0..4 at offsets -h..+h, point 2
+// is updated), algebraically identical to the FVS-LLF split with the biased D+/D-
+// operators and the compact second derivative of a:
+//   R = -[(f0 - f4) + 8 (f3 - f1) + alpha ((z0 + z4) - 4 (z1 + z3) + 6 z2)] / (6h)
+//       + [16 (a1 + a3) - (a0 + a4) - 30 a2] / (3h^2)
+template <class T>
+__device__ __forceinline__ T line_res(T z0, T z1, T z2, T z3, T z4, T f0, T f1, T f3, T f4, T alpha, T a0,
+                                      T a1, T a2, T a3, T a4, T i6h, T i3h2) {
+  T cf = (f0 - f4) + T(8) * (f3 - f1);
+  T dz = (z0 + z4) - T(4) * (z1 + z3) + T(6) * z2;
+  T da = T(16) * (a1 + a3) - (a0 + a4) - T(30) * a2;
+  return da * i3h2 - (cf + alpha * dz) * i6h;
+}
+
+template <int FLUX, class T, class PT, bool BLEND>
+__global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const StageArgs2D<PT> A) {
+  using L = Tile2D<FLUX, T, BLEND>;
+  constexpr int TX = L::TX, TY = L::TY, NT = L::NT, H = L::H, BX = L::BX, BY = L::BY, BN = L::BN;
+  constexpr int NQ = L::NQ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* S = reinterpret_cast<T*>(smem_raw);
+  auto arr = [&](int a) -> T* { return S + (size_t)a * BN; };
+  T* sU = arr(L::A_U);
+  T* sZ[4] = {arr(L::A_V), arr(L::A_X), arr(L::A_Y), arr(L::A_C)};   // V, X, Y, centre
+  T* sQU = arr(L::A_QU);
+  T* sQ = arr(L::A_Q);
+  auto Q = [&](int type, int k) -> T* { return sQ + (size_t)(type * NQ + k) * BN; };
+
+  const double dtv = *A.dt;
+  if (dtv == 0.0) return;
+  const int nx = A.nx, ny = A.ny;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const T umin = T(m.umin), umax = T(m.umax);
+
+  // ---- P0: load the halo box --------------------------------------------------------
+  for (int k = tid; k < BN; k += NT) {
+    const int bx = k % BX, by = k / BX;
+    const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
+    const size_t g = (size_t)gj * nx + gi;
+    sU[k] = T(A.ub[g]);
+    sZ[0][k] = T(A.V[g]);
+    sZ[1][k] = T(A.X[g]);
+    sZ[2][k] = T(A.Y[g]);
+  }
+  __syncthreads();
+
+  // ---- P1: centres and pointwise nonlinearities ----------------------------------------
+  auto eval_point = [&](int type, int b) {
+    const T z = sZ[type][b];
+    if constexpr (FLUX == FLUX_BURGERS) {
+      Q(type, 0)[b] = flux<FLUX, T>(m, 0, z);
+    } else if constexpr (FLUX == FLUX_BL) {
+      Q(type, 0)[b] = flux<FLUX, T>(m, 0, z);
+      Q(type, 1)[b] = flux<FLUX, T>(m, 1, z);
+      Q(type, 2)[b] = dflux_abs<FLUX, T>(m, 0, z);
+      Q(type, 3)[b] = dflux_abs<FLUX, T>(m, 1, z);
+    }
+    Q(type, NQ - 1)[b] = apot<T>(m, z);
+  };
+  for (int k = tid; k < BN; k += NT) {
+    const T u = sU[k];
+    if constexpr (FLUX == FLUX_BURGERS) {
+      sQU[k] = flux<FLUX, T>(m, 0, u);
+    } else if constexpr (FLUX == FLUX_BL) {
+      sQU[k] = flux<FLUX, T>(m, 0, u);
+      sQU[BN + k] = flux<FLUX, T>(m, 1, u);
+    }
+    sQU[(L::NQU - 1) * BN + k] = apot<T>(m, u);
+  }
+  for_rect<NT>(H - 2, H + TX + 1, H - 2, H + TY + 1, [&](int bx, int by) {
+    const int b = by * BX + bx;
+    eval_point(0, b);
+    eval_point(1, b);
+    eval_point(2, b);
+  });
+  for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
+    const int b = by * BX + bx;
+    const T* V = sZ[0];
+    const T* X = sZ[1];
+    const T* Y = sZ[2];
+    // z_ij = [36 zbar - 4 (X_{i-1,j} + X_ij + Y_{i,j-1} + Y_ij) - (four corners)] / 16
+    const T c = (T(36) * sU[b] - T(4) * ((X[b - 1] + X[b]) + (Y[b - BX] + Y[b])) -
+                 ((V[b - BX - 1] + V[b - BX]) + (V[b - 1] + V[b]))) * T(0.0625);
+    sZ[3][b] = c;
+    eval_point(3, b);
+  });
+  T* sS1 = nullptr;
+  T* sS2 = nullptr;
+  T* sTC1 = nullptr;
+  T* sTC2 = nullptr;
+  T* sTD1 = nullptr;
+  T* sTD2 = nullptr;
+  if constexpr (BLEND) {
+    sS1 = arr(L::A_BL0);
+    sS2 = arr(L::A_BL0 + 1);
+    sTC1 = arr(L::A_BL0 + 2);
+    sTC2 = arr(L::A_BL0 + 3);
+    sTD1 = arr(L::A_BL0 + 4);
+    sTD2 = arr(L::A_BL0 + 5);
+    if (!A.blend_external) {
+      // s~_l = |u_- - 2u + u_+| / (|u_-| + 2|u| + |u_+| + 1e-13) (Section 5.1.3); kept
+      // temporarily in the TC arrays
+      for_rect<NT>(1, BX - 1, 1, BY - 1, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        const T u = sU[b];
+        const T au2 = T(2) * tabs(u);
+        sTC1[b] = tabs(sU[b - 1] - T(2) * u + sU[b + 1]) / (tabs(sU[b - 1]) + au2 + tabs(sU[b + 1]) + T(1e-13));
+        sTC2[b] = tabs(sU[b - BX] - T(2) * u + sU[b + BX]) / (tabs(sU[b - BX]) + au2 + tabs(sU[b + BX]) + T(1e-13));
+      });
+    }
+  }
+  __syncthreads();
+
+  // ---- P2: high-order residuals, Simpson fluxes, DC potentials, LLF fluxes -------------
+  const T i6h1 = T(A.inv_h1 / 6.0), i6h2 = T(A.inv_h2 / 6.0);
+  const T i3h21 = T(A.inv_h1 * A.inv_h1 / 3.0), i3h22 = T(A.inv_h2 * A.inv_h2 / 3.0);
+  // value / flux / |f'| / a of a stored point of the given type, direction dir
+  auto Fz = [&](int type, int b, int dir) -> T {
+    if constexpr (FLUX == FLUX_BURGERS) return Q(type, 0)[b];
+    else if constexpr (FLUX == FLUX_BL) return Q(type, dir)[b];
+    else return flux<FLUX, T>(m, dir, sZ[type][b]);
+  };
+  auto Az = [&](int type, int b) -> T { return Q(type, NQ - 1)[b]; };
+  // one 5-point line given (type, box index) of its points
+  auto line = [&](int dir, int t0, int b0, int t1, int b1, int t2, int b2, int t3, int b3, int t4, int b4) -> T {
+    const T z0 = sZ[t0][b0], z1 = sZ[t1][b1], z2 = sZ[t2][b2], z3 = sZ[t3][b3], z4 = sZ[t4][b4];
+    T alpha;
+    if constexpr (FLUX == FLUX_BURGERS) {
+      alpha = T(tabs(2.0 * m.fp[0])) *
+              tmax(tmax(tmax(tabs(z0), tabs(z1)), tmax(tabs(z3), tabs(z4))), tabs(z2));
+    } else if constexpr (FLUX == FLUX_BL) {
+      const int k = 2 + dir;
+      alpha = tmax(tmax(tmax(Q(t0, k)[b0], Q(t1, k)[b1]), tmax(Q(t3, k)[b3], Q(t4, k)[b4])), Q(t2, k)[b2]);
+    } else if constexpr (FLUX == FLUX_LINEAR) {
+      alpha = tabs(T(dir == 0 ? m.fp[0] : m.fp[1]));
+    } else {
+      alpha = T(0);
+    }
+    const T i6h = dir == 0 ? i6h1 : i6h2, i3h2 = dir == 0 ? i3h21 : i3h22;
+    return line_res<T>(z0, z1, z2, z3, z4, Fz(t0, b0, dir), Fz(t1, b1, dir), Fz(t3, b3, dir), Fz(t4, b4, dir), alpha,
+                       Az(t0, b0), Az(t1, b1), Az(t2, b2), Az(t3, b3), Az(t4, b4), i6h, i3h2);
+  };
+  constexpr int tV = 0, tX = 1, tY = 2, tC = 3;
+  const int bo = (ty + H) * BX + (tx + H);   // own box index
+  T rV1, rV2, rX1, rX2, rY1, rY2;
+  rV1 = line(0, tV, bo - 1, tY, bo, tV, bo, tY, bo + 1, tV, bo + 1);
+  rV2 = line(1, tV, bo - BX, tX, bo, tV, bo, tX, bo + BX, tV, bo + BX);
+  rX1 = line(0, tX, bo - 1, tC, bo, tX, bo, tC, bo + 1, tX, bo + 1);
+  rX2 = line(1, tX, bo - BX, tV, bo - BX, tX, bo, tV, bo, tX, bo + BX);
+  rY1 = line(0, tY, bo - 1, tV, bo - 1, tY, bo, tV, bo, tY, bo + 1);
+  rY2 = line(1, tY, bo - BX, tC, bo, tY, bo, tC, bo + BX, tY, bo + BX);
+
+  T* sFH1 = arr(L::A_FH1);
+  T* sFH2 = arr(L::A_FH2);
+  T* sAH1 = arr(L::A_AH1);
+  T* sAH2 = arr(L::A_AH2);
+  T* sFL1 = arr(L::A_FL1);
+  T* sFL2 = arr(L::A_FL2);
+  auto fU = [&](int b, int dir) -> T {
+    if constexpr (FLUX == FLUX_BURGERS) return sQU[b];
+    else if constexpr (FLUX == FLUX_BL) return sQU[dir * BN + b];
+    else return flux<FLUX, T>(m, dir, sU[b]);
+  };
+  auto aU = [&](int b) -> T { return sQU[(L::NQU - 1) * BN + b]; };
+  const T sixth = T(1.0 / 6.0), r36 = T(1.0 / 36.0);
+  // x-faces (Simpson over the face: V below, X middle, V above)
+  for_rect<NT>(H - 1, H + TX, H, H + TY, [&](int bx, int by) {
+    const int b = by * BX + bx;
+    sFH1[b] = (Fz(tV, b - BX, 0) + T(4) * Fz(tX, b, 0) + Fz(tV, b, 0)) * sixth;
+  });
+  for_rect<NT>(H, H + TX, H - 1, H + TY, [&](int bx, int by) {
+    const int b = by * BX + bx;
+    sFH2[b] = (Fz(tV, b - 1, 1) + T(4) * Fz(tY, b, 1) + Fz(tV, b, 1)) * sixth;
+  });
+  // cell potentials: tensor Simpson average of the DC potential a^ along each direction
+  auto pot = [&](int b, int dir) -> T {
+    const T sv = (Az(tV, b - BX - 1) + Az(tV, b - BX)) + (Az(tV, b - 1) + Az(tV, b));
+    const T sx = Az(tX, b - 1) + Az(tX, b);
+    const T sy = Az(tY, b - BX) + Az(tY, b);
+    const T ac = Az(tC, b);
+    return dir == 0 ? (T(8) * sy - T(4) * sx + T(32) * ac - sv) * r36
+                    : (T(8) * sx - T(4) * sy + T(32) * ac - sv) * r36;
+  };
+  for_rect<NT>(H - 1, H + TX + 1, H, H + TY, [&](int bx, int by) { sAH1[by * BX + bx] = pot(by * BX + bx, 0); });
+  for_rect<NT>(H, H + TX, H - 1, H + TY + 1, [&](int bx, int by) { sAH2[by * BX + bx] = pot(by * BX + bx, 1); });
+  // LLF fluxes with the interval wave speed
+  for_rect<NT>(H - 2, H + TX + 1, H, H + TY, [&](int bx, int by) {
+    const int b = by * BX + bx;
+    const T ul = sU[b], ur = sU[b + 1];
+    const T al = alpha_interval<FLUX, T>(m, 0, ul, ur);
+    sFL1[b] = T(0.5) * (fU(b, 0) + fU(b + 1, 0)) - T(0.5) * al * (ur - ul);
+  });
+  for_rect<NT>(H, H + TX, H - 2, H + TY + 1, [&](int bx, int by) {
+    const int b = by * BX + bx;
+    const T ul = sU[b], ur = sU[b + BX];
+    const T al = alpha_interval<FLUX, T>(m, 1, ul, ur);
+    sFL2[b] = T(0.5) * (fU(b, 1) + fU(b + BX, 1)) - T(0.5) * al * (ur - ul);
+  });
+  if constexpr (BLEND) {
+    if (A.blend_external) {
+      for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
+        const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
+        const T s = T(A.s_ext[(size_t)gj * nx + gi]);
+        sS1[by * BX + bx] = s;
+        sS2[by * BX + bx] = s;
+      });
+    } else {
+      // s_l = (s~_{-1} + 4 s~ + s~_{+1}) / 6 along direction l
+      for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        sS1[b] = (sTC1[b - 1] + T(4) * sTC1[b] + sTC1[b + 1]) * sixth;
+        sS2[b] = (sTC2[b - BX] + T(4) * sTC2[b] + sTC2[b + BX]) * sixth;
+      });
+    }
+  }
+  __syncthreads();
+
+  T rV, rX, rY;
+  if constexpr (BLEND) {
+    // ---- P2b: blend weights theta^{c,s} = exp(-gamma (s_i + s_{i+1})/2), theta^{d,s} = exp(-gamma s_i)
+    const T g = T(A.gamma);
+    for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
+      const int b = by * BX + bx;
+      const T s1 = sS1[b], s2 = sS2[b];
+      sTD1[b] = exp(-g * s1);
+      sTD2[b] = exp(-g * s2);
+      if (bx < H + TX) sTC1[b] = exp(-g * (T(0.5) * (s1 + sS1[b + 1])));
+      if (by < H + TY) sTC2[b] = exp(-g * (T(0.5) * (s2 + sS2[b + BX])));
+    });
+    __syncthreads();
+    // ---- P2c: blended fluxes/potentials (in place) and blended point residuals
+    for_rect<NT>(H - 1, H + TX, H, H + TY, [&](int bx, int by) {
+      const int b = by * BX + bx;
+      const T t = sTC1[b];
+      sFH1[b] = t * sFH1[b] + (T(1) - t) * sFL1[b];
+    });
+    for_rect<NT>(H, H + TX, H - 1, H + TY, [&](int bx, int by) {
+      const int b = by * BX + bx;
+      const T t = sTC2[b];
+      sFH2[b] = t * sFH2[b] + (T(1) - t) * sFL2[b];
+    });
+    for_rect<NT>(H - 1, H + TX + 1, H, H + TY, [&](int bx, int by) {
+      const int b = by * BX + bx;
+      const T t = sTD1[b];
+      sAH1[b] = t * sAH1[b] + (T(1) - t) * aU(b);
+    });
+    for_rect<NT>(H, H + TX, H - 1, H + TY + 1, [&](int bx, int by) {
+      const int b = by * BX + bx;
+      const T t = sTD2[b];
+      sAH2[b] = t * sAH2[b] + (T(1) - t) * aU(b);
+    });
+    // first-order point residual on the +-h/2 neighbours (centre -> cell average):
+    //   -(2/h)[F(z0,z+) - F(z-,z0)] + (4/h^2)(a+ - 2 a0 + a-)
+    const T i2h1 = T(2.0 * A.inv_h1), i2h2 = T(2.0 * A.inv_h2);
+    const T i4h21 = T(4.0 * A.inv_h1 * A.inv_h1), i4h22 = T(4.0 * A.inv_h2 * A.inv_h2);
+    auto lowres = [&](int dir, T zm, T fm, T am, T z0, T f0, T a0, T zp, T fp, T ap) -> T {
+      const T Fr = T(0.5) * (f0 + fp) - T(0.5) * alpha_interval<FLUX, T>(m, dir, z0, zp) * (zp - z0);
+      const T Fl = T(0.5) * (fm + f0) - T(0.5) * alpha_interval<FLUX, T>(m, dir, zm, z0) * (z0 - zm);
+      return (ap - T(2) * a0 + am) * (dir == 0 ? i4h21 : i4h22) - (Fr - Fl) * (dir == 0 ? i2h1 : i2h2);
+    };
+    auto PZ = [&](int type, int b) { return sZ[type][b]; };
+    const int b = bo;
+    const T LV1 = lowres(0, PZ(tY, b), Fz(tY, b, 0), Az(tY, b), PZ(tV, b), Fz(tV, b, 0), Az(tV, b), PZ(tY, b + 1),
+                         Fz(tY, b + 1, 0), Az(tY, b + 1));
+    const T LV2 = lowres(1, PZ(tX, b), Fz(tX, b, 1), Az(tX, b), PZ(tV, b), Fz(tV, b, 1), Az(tV, b), PZ(tX, b + BX),
+                         Fz(tX, b + BX, 1), Az(tX, b + BX));
+    const T LX1 = lowres(0, sU[b], fU(b, 0), aU(b), PZ(tX, b), Fz(tX, b, 0), Az(tX, b), sU[b + 1], fU(b + 1, 0),
+                         aU(b + 1));
+    const T LX2 = lowres(1, PZ(tV, b - BX), Fz(tV, b - BX, 1), Az(tV, b - BX), PZ(tX, b), Fz(tX, b, 1), Az(tX, b),
+                         PZ(tV, b), Fz(tV, b, 1), Az(tV, b));
+    const T LY1 = lowres(0, PZ(tV, b - 1), Fz(tV, b - 1, 0), Az(tV, b - 1), PZ(tY, b), Fz(tY, b, 0), Az(tY, b),
+                         PZ(tV, b), Fz(tV, b, 0), Az(tV, b));
+    const T LY2 = lowres(1, sU[b], fU(b, 1), aU(b), PZ(tY, b), Fz(tY, b, 1), Az(tY, b), sU[b + BX], fU(b + BX, 1),
+                         aU(b + BX));
+    const T wV1 = tmin(sTC1[b], sTC1[b + BX]), wV2 = tmin(sTC2[b], sTC2[b + 1]);
+    const T wX1 = sTC1[b], wX2 = tmin(sTD2[b], sTD2[b + 1]);
+    const T wY1 = tmin(sTD1[b], sTD1[b + BX]), wY2 = sTC2[b];
+    rV = (wV1 * rV1 + (T(1) - wV1) * LV1) + (wV2 * rV2 + (T(1) - wV2) * LV2);
+    rX = (wX1 * rX1 + (T(1) - wX1) * LX1) + (wX2 * rX2 + (T(1) - wX2) * LX2);
+    rY = (wY1 * rY1 + (T(1) - wY1) * LY1) + (wY2 * rY2 + (T(1) - wY2) * LY2);
+    __syncthreads();
+  } else {
+    rV = rV1 + rV2;
+    rX = rX1 + rX2;
+    rY = rY1 + rY2;
+  }
+
+  // ---- per output: low-order states, limiter, update ------------------------------------
+  const int gi = i0 + tx, gj = j0 + ty;
+  const bool own = gi < nx && gj < ny;
+  const size_t g = (size_t)gj * nx + gi;
+  T* sULp1 = arr(L::A_ULP1);
+  T* sULm1 = arr(L::A_ULM1);
+  T* sULp2 = arr(L::A_ULP2);
+  T* sULm2 = arr(L::A_ULM2);
+  T* sFlim1 = A.limiter ? arr(L::A_FLIM1) : sFH1;
+  T* sFlim2 = A.limiter ? arr(L::A_FLIM2) : sFH2;
+  T* sAlim1 = A.limiter ? arr(L::A_ALIM1) : sAH1;
+  T* sAlim2 = A.limiter ? arr(L::A_ALIM2) : sAH2;
+  for (int o = 0; o < A.nout; ++o) {
+    const double tau = A.tcoef[o] * dtv;
+    const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
+    const double nu1 = mu1 * A.inv_h1, nu2 = mu2 * A.inv_h2;
+    if (A.limiter) {
+      // ---- P3: directional low-order states u^{L,+-}_l = ub -+ 4 mu (...) +- 4 nu (...)
+      const T m4_1 = T(4.0 * mu1), n4_1 = T(4.0 * nu1), m4_2 = T(4.0 * mu2), n4_2 = T(4.0 * nu2);
+      for_rect<NT>(H - 2, H + TX + 2, H, H + TY, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        const T u = sU[b], f = fU(b, 0), a = aU(b);
+        if (bx < H + TX + 1) sULp1[b] = u - m4_1 * (sFL1[b] - f) + n4_1 * (aU(b + 1) - a);
+        if (bx > H - 2) sULm1[b] = u - m4_1 * (f - sFL1[b - 1]) - n4_1 * (a - aU(b - 1));
+      });
+      for_rect<NT>(H, H + TX, H - 2, H + TY + 2, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        const T u = sU[b], f = fU(b, 1), a = aU(b);
+        if (by < H + TY + 1) sULp2[b] = u - m4_2 * (sFL2[b] - f) + n4_2 * (aU(b + BX) - a);
+        if (by > H - 2) sULm2[b] = u - m4_2 * (f - sFL2[b - BX]) - n4_2 * (a - aU(b - BX));
+      });
+      __syncthreads();
+      // ---- P4: theta^c per face (2 states), theta^d per cell (4 states), factor 12
+      const T k1 = T(12.0 * mu1), k2 = T(12.0 * mu2), q1 = T(12.0 * nu1), q2 = T(12.0 * nu2);
+      for_rect<NT>(H - 1, H + TX, H, H + TY, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        const T fh = sFH1[b], fl = sFL1[b], dF = fh - fl;
+        const T zp = sULp1[b], zm = sULm1[b + 1];
+        const T t = tmin(theta_fn<T>(zp, zp - k1 * dF, umin, umax), theta_fn<T>(zm, zm + k1 * dF, umin, umax));
+        sFlim1[b] = t == T(1) ? fh : fl + t * dF;
+      });
+      for_rect<NT>(H, H + TX, H - 1, H + TY, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        const T fh = sFH2[b], fl = sFL2[b], dF = fh - fl;
+        const T zp = sULp2[b], zm = sULm2[b + BX];
+        const T t = tmin(theta_fn<T>(zp, zp - k2 * dF, umin, umax), theta_fn<T>(zm, zm + k2 * dF, umin, umax));
+        sFlim2[b] = t == T(1) ? fh : fl + t * dF;
+      });
+      for_rect<NT>(H - 1, H + TX + 1, H, H + TY, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        const T ah = sAH1[b], al = aU(b), d = q1 * (ah - al);
+        const T t = tmin(tmin(theta_fn<T>(sULp1[b - 1], sULp1[b - 1] + d, umin, umax),
+                              theta_fn<T>(sULp1[b], sULp1[b] - d, umin, umax)),
+                         tmin(theta_fn<T>(sULm1[b], sULm1[b] - d, umin, umax),
+                              theta_fn<T>(sULm1[b + 1], sULm1[b + 1] + d, umin, umax)));
+        sAlim1[b] = t == T(1) ? ah : al + t * (ah - al);
+      });
+      for_rect<NT>(H, H + TX, H - 1, H + TY + 1, [&](int bx, int by) {
+        const int b = by * BX + bx;
+        const T ah = sAH2[b], al = aU(b), d = q2 * (ah - al);
+        const T t = tmin(tmin(theta_fn<T>(sULp2[b - BX], sULp2[b - BX] + d, umin, umax),
+                              theta_fn<T>(sULp2[b], sULp2[b] - d, umin, umax)),
+                         tmin(theta_fn<T>(sULm2[b], sULm2[b] - d, umin, umax),
+                              theta_fn<T>(sULm2[b + BX], sULm2[b + BX] + d, umin, umax)));
+        sAlim2[b] = t == T(1) ? ah : al + t * (ah - al);
+      });
+      __syncthreads();
+    }
+    // ---- P5: limited average update, point update + projection, RK combination ----
+    if (own) {
+      const int b = bo;
+      const double ubin = A.ub[g];
+      const double dflux = mu1 * ((double)sFlim1[b] - (double)sFlim1[b - 1]) +
+                           mu2 * ((double)sFlim2[b] - (double)sFlim2[b - BX]);
+      const double dpot = nu1 * (((double)sAlim1[b + 1] - 2.0 * (double)sAlim1[b]) + (double)sAlim1[b - 1]) +
+                          nu2 * (((double)sAlim2[b + BX] - 2.0 * (double)sAlim2[b]) + (double)sAlim2[b - BX]);
+      const double ubfe = ubin - dflux + dpot;
+      const T taut = T(tau);
+      T v = sZ[tV][b] + taut * rV, x = sZ[tX][b] + taut * rX, y = sZ[tY][b] + taut * rY;
+      if (A.limiter) {
+        v = tmin(tmax(v, umin), umax);
+        x = tmin(tmax(x, umin), umax);
+        y = tmin(tmax(y, umin), umax);
+      }
+      const double cA = A.cA[o], cF = A.cF[o];
+      double ubo = cF * ubfe;
+      PT vo, xo, yo;
+      if (cA != 0.0) {
+        ubo = cA * A.Aub[o][g] + ubo;
+        vo = PT(T(cA) * T(A.AV[o][g]) + T(cF) * v);
+        xo = PT(T(cA) * T(A.AX[o][g]) + T(cF) * x);
+        yo = PT(T(cA) * T(A.AY[o][g]) + T(cF) * y);
+      } else {
+        vo = PT(T(cF) * v);
+        xo = PT(T(cF) * x);
+        yo = PT(T(cF) * y);
+      }
+      if (A.limiter && A.sg[o]) {
+        ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats);
+        vo = safeguard<PT>(vo, PT(m.umin), PT(m.umax), A.tol, A.stats);
+        xo = safeguard<PT>(xo, PT(m.umin), PT(m.umax), A.tol, A.stats);
+        yo = safeguard<PT>(yo, PT(m.umin), PT(m.umax), A.tol, A.stats);
+      }
+      A.Oub[o][g] = ubo;
+      A.OV[o][g] = vo;
+      A.OX[o][g] = xo;
+      A.OY[o][g] = yo;
+    }
+    if (o + 1 < A.nout) __syncthreads();
+  }
+}
+
+}  // namespace af
