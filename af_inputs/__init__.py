@@ -326,3 +326,18 @@ def random_state_1d(spec: Spec, seed: int, lo: float | None = None, hi: float | 
     lo = spec.umin if lo is None else lo
     hi = spec.umax if hi is None else hi
     return [lo + (hi - lo) * torch.rand((spec.nx,), generator=g, dtype=torch.float64) for _ in range(2)]
+
+
+# ----------------------------------------------------------------------------------
+# learned indicator: seeded initial parameters (flat FP32, layout W1[32][21], b1[32],
+# W2[32][32], b2[32], w3[32], b3) -- He-normal hidden layers, output bias -2
+
+MLP_NIN, MLP_NH = 21, 32
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0, math.sqrt(2.0 / MLP_NIN), MLP_NH * MLP_NIN), np.zeros(MLP_NH),
+             rng.normal(0, math.sqrt(2.0 / MLP_NH), MLP_NH * MLP_NH), np.zeros(MLP_NH),
+             rng.normal(0, math.sqrt(1.0 / MLP_NH), MLP_NH), np.array([-2.0])]
+    return np.concatenate(parts).astype(np.float32)

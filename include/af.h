@@ -141,8 +141,84 @@ af_status af_mass(af_ctx* ctx, double* mass);                 /* sum(ub) * dx * 
 af_status af_bounds(af_ctx* ctx, double* umin, double* umax); /* over all DoFs              */
 af_status af_dt_cfl(af_ctx* ctx, double* dt);                 /* CFL step of current state  */
 /* Safeguard statistics since creation: values clamped (excess <= tolerance), errors
- * (excess > tolerance) and the largest clamped excess. */
-af_status af_stats(af_ctx* ctx, long long* clamps, long long* errors, double* max_excess);
+ * (excess > tolerance), the largest clamped excess, and the mass the clamps of cell
+ * averages moved (sum of |clamped - raw| times dx dy: a bound on their effect on the
+ * total mass). Any pointer may be NULL. */
+af_status af_stats(af_ctx* ctx, long long* clamps, long long* errors, double* max_excess, double* mass_adjust);
+
+/* ---- batches of independent meshes -------------------------------------------------
+ * A batch holds n independent periodic 2D meshes (uneven sizes; per-instance flux and
+ * diffusion parameters and bounds) that share the flux kind, precision, RK scheme,
+ * limiter and CFL options of *opts (blend must be off). One persistent launch per RK
+ * stage walks the (instance, tile) work list with the same tile computation as the
+ * single-mesh kernel, so every instance evolves as a single-mesh context with the same
+ * options does (bit for bit with SSP-RK3; to a few ulp with SSP-RK(5,4), where the two
+ * compilations may contract multiply-adds differently). Per-instance CFL steps and times stay on the device;
+ * a full time step is captured once as a CUDA graph and replayed. The batch owns a
+ * non-blocking stream unless af_batch_set_stream gives it one. */
+typedef struct af_batch af_batch;
+af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, const af_diff* diffs,
+                          const af_bounds_t* bounds, const af_opts* opts, af_batch** out);
+af_status af_batch_destroy(af_batch* b);
+const char* af_batch_last_error(const af_batch* b);
+af_status af_batch_set_stream(af_batch* b, void* stream);
+/* cells in total, work items, current tile shape */
+af_status af_batch_info(const af_batch* b, long long* cells, int* tiles, int* tx, int* ty);
+/* tile shapes built: 32x8, 64x4, 16x16 */
+af_status af_batch_set_tile(af_batch* b, int tx, int ty);
+/* time one step with every tile shape on this batch, keep the fastest; the state, the
+ * times and the statistics are restored afterwards */
+af_status af_batch_autotune(af_batch* b, int* tx, int* ty);
+af_status af_batch_set_state(af_batch* b, int i, const double* ub, const double* V, const double* X, const double* Y);
+af_status af_batch_get_state(af_batch* b, int i, double* ub, double* V, double* X, double* Y);
+af_status af_batch_device_ptrs(af_batch* b, int i, void* ptrs[4], int dtype[2]);
+/* nsteps full SSP-RK steps of every instance with its own CFL step (graph replays, no
+ * host synchronisation) */
+af_status af_batch_step(af_batch* b, int nsteps);
+af_status af_batch_sync(af_batch* b);
+af_status af_batch_time(af_batch* b, int i, double* t);
+af_status af_batch_mass(af_batch* b, int i, double* mass);
+af_status af_batch_bounds(af_batch* b, int i, double* umin, double* umax);
+af_status af_batch_stats(af_batch* b, long long* clamps, long long* errors, double* max_excess);
+
+/* ---- learned smoothness indicator -------------------------------------------------
+ * A 21 -> 32 -> 32 -> 1 network (ReLU hidden layers, softplus output) maps the
+ * normalised patch of a cell -- 13 cell averages ub(i+a, j+b), (a,b) in {-1,0,1}^2 and
+ * (+-2,0), (0,+-2), then the 8 point values V(i-1,j-1), V(i,j-1), V(i-1,j), V(i,j),
+ * X(i-1,j), X(i,j), Y(i,j-1), Y(i,j), each as (v - ub_ij) / (max|v| + 1e-13) -- to s >= 0,
+ * which replaces the smoothness indicator s of the blend (Section 5.1.3, direction by
+ * direction in 2D). The limiter and projection still follow, so bounds and
+ * conservation hold regardless of the network. The two hidden layers run on tensor
+ * cores with bf16 inputs/weights and FP32 accumulation; training (forward, backward,
+ * Adam) runs in FP32 with the same bf16 rounding points. Parameters are a flat FP32
+ * array of AF_MLP_NPARAM values: W1[32][21], b1[32], W2[32][32], b2[32], w3[32], b3.
+ * Not in the paper: the paper's indicator is the plain one, which also provides the
+ * training labels (max of the two directional indicators). */
+#define AF_MLP_NPARAM 1793
+typedef struct af_mlp af_mlp;
+af_status af_mlp_create(af_mlp** out);
+af_status af_mlp_destroy(af_mlp* net);
+af_status af_mlp_set_params(af_mlp* net, const float* host, int n);   /* resets Adam state */
+af_status af_mlp_get_params(const af_mlp* net, float* host);
+/* features (nx*ny x 21, FP32, device) of a 2D context's current state and, if label_dev
+ * is non-NULL, the plain indicator's label per cell (device FP32) */
+af_status af_mlp_features(af_ctx* ctx, float* feat_dev, float* label_dev);
+/* network output for n feature rows (device in, device out) */
+af_status af_mlp_infer(const af_mlp* net, const float* feat_dev, long long n, float* out_dev);
+/* fused inference (patch gather + network) on a context's current state -> s_dev */
+af_status af_mlp_indicator(const af_mlp* net, af_ctx* ctx, double* s_dev);
+/* gradient of the mean squared error over the first nsamples rows (no update) */
+af_status af_mlp_grad(af_mlp* net, const float* feat_dev, const float* label_dev, int nsamples, float* grad_host,
+                      float* loss_host);
+/* `steps` Adam steps (lr, betas 0.9/0.999, eps 1e-8) on minibatches of `batch` rows
+ * drawn with a counter-based generator (splitmix64) from `seed`; seed 0 takes rows
+ * 0..batch-1 in order. Loss of the last batch returned. */
+af_status af_mlp_train(af_mlp* net, const float* feat_dev, const float* label_dev, long long nsamples, int batch,
+                       int steps, float lr, unsigned long long seed, float* loss_host);
+/* attach (or detach with NULL) a network to a 2D context created with
+ * blend = AF_BLEND_EXTERNAL: every stage then computes s from its input state first */
+af_status af_set_mlp(af_ctx* ctx, const af_mlp* net);
+
 
 #ifdef __cplusplus
 }

@@ -81,7 +81,7 @@ def lib():
         "af_mass": [_V, _D],
         "af_bounds": [_V, _D, _D],
         "af_dt_cfl": [_V, _D],
-        "af_stats": [_V, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _D],
+        "af_stats": [_V, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _D, _D],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -91,6 +91,49 @@ def lib():
     L.af_last_error.restype = ctypes.c_char_p
     L.af_num_stages.argtypes = [_V]
     L.af_num_stages.restype = ctypes.c_int
+    I = ctypes.POINTER(ctypes.c_int)
+    bsig = {
+        "af_batch_create": [ctypes.c_int, ctypes.POINTER(af_grid), ctypes.POINTER(af_flux), ctypes.POINTER(af_diff),
+                            ctypes.POINTER(af_bounds_t), ctypes.POINTER(af_opts), ctypes.POINTER(_V)],
+        "af_batch_destroy": [_V],
+        "af_batch_set_stream": [_V, _V],
+        "af_batch_info": [_V, ctypes.POINTER(ctypes.c_longlong), I, I, I],
+        "af_batch_set_tile": [_V, ctypes.c_int, ctypes.c_int],
+        "af_batch_autotune": [_V, I, I],
+        "af_batch_set_state": [_V, ctypes.c_int, _D, _D, _D, _D],
+        "af_batch_get_state": [_V, ctypes.c_int, _D, _D, _D, _D],
+        "af_batch_device_ptrs": [_V, ctypes.c_int, ctypes.POINTER(_V), I],
+        "af_batch_step": [_V, ctypes.c_int],
+        "af_batch_sync": [_V],
+        "af_batch_time": [_V, ctypes.c_int, _D],
+        "af_batch_mass": [_V, ctypes.c_int, _D],
+        "af_batch_bounds": [_V, ctypes.c_int, _D, _D],
+        "af_batch_stats": [_V, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _D],
+    }
+    for name, args in bsig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.af_batch_last_error.argtypes = [_V]
+    L.af_batch_last_error.restype = ctypes.c_char_p
+    F = ctypes.POINTER(ctypes.c_float)
+    msig = {
+        "af_mlp_create": [ctypes.POINTER(_V)],
+        "af_mlp_destroy": [_V],
+        "af_mlp_set_params": [_V, F, ctypes.c_int],
+        "af_mlp_get_params": [_V, F],
+        "af_mlp_features": [_V, _V, _V],
+        "af_mlp_infer": [_V, _V, ctypes.c_longlong, _V],
+        "af_mlp_indicator": [_V, _V, _V],
+        "af_mlp_grad": [_V, _V, _V, ctypes.c_int, F, F],
+        "af_mlp_train": [_V, _V, _V, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                         ctypes.c_ulonglong, F],
+        "af_set_mlp": [_V, _V],
+    }
+    for name, args in msig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -99,7 +142,164 @@ def exported_symbols():
     """Names of the entry points declared in include/af.h (for the export test)."""
     return ["af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_state", "af_get_state",
             "af_device_ptrs", "af_set_indicator", "af_set_indicator_device", "af_forward_euler", "af_stage", "af_dt_device",
-            "af_num_stages", "af_step", "af_run", "af_time", "af_mass", "af_bounds", "af_dt_cfl", "af_stats"]
+            "af_num_stages", "af_step", "af_run", "af_time", "af_mass", "af_bounds", "af_dt_cfl", "af_stats",
+            "af_batch_create", "af_batch_destroy", "af_batch_last_error", "af_batch_set_stream",
+            "af_batch_info", "af_batch_set_tile", "af_batch_autotune", "af_batch_set_state", "af_batch_get_state",
+            "af_batch_device_ptrs", "af_batch_step", "af_batch_sync", "af_batch_time", "af_batch_mass",
+            "af_batch_bounds", "af_batch_stats", "af_mlp_create", "af_mlp_destroy", "af_mlp_set_params",
+            "af_mlp_get_params", "af_mlp_features", "af_mlp_infer", "af_mlp_indicator", "af_mlp_grad",
+            "af_mlp_train", "af_set_mlp"]
+
+
+AF_MLP_NPARAM = 1793
+_FP = ctypes.POINTER(ctypes.c_float)
+
+
+def af_mlp_create():
+    net = _V()
+    st = lib().af_mlp_create(ctypes.byref(net))
+    if st != AF_OK:
+        raise AfError(st, "af_mlp_create failed")
+    return net
+
+
+def af_mlp_destroy(net):
+    _check(None, lib().af_mlp_destroy(net))
+
+
+def af_mlp_set_params(net, params):
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    _check(None, lib().af_mlp_set_params(net, p.ctypes.data_as(_FP), int(p.size)))
+
+
+def af_mlp_get_params(net):
+    p = np.empty(AF_MLP_NPARAM, dtype=np.float32)
+    _check(None, lib().af_mlp_get_params(net, p.ctypes.data_as(_FP)))
+    return p
+
+
+def af_mlp_features(ctx, feat_dev_ptr, label_dev_ptr=None):
+    _check(ctx, lib().af_mlp_features(ctx, _V(feat_dev_ptr), _V(label_dev_ptr) if label_dev_ptr else None))
+
+
+def af_mlp_infer(net, feat_dev_ptr, n, out_dev_ptr):
+    _check(None, lib().af_mlp_infer(net, _V(feat_dev_ptr), int(n), _V(out_dev_ptr)))
+
+
+def af_mlp_indicator(net, ctx, s_dev_ptr):
+    _check(ctx, lib().af_mlp_indicator(net, ctx, _V(s_dev_ptr)))
+
+
+def af_mlp_grad(net, feat_dev_ptr, label_dev_ptr, n):
+    g = np.empty(AF_MLP_NPARAM, dtype=np.float32)
+    loss = ctypes.c_float()
+    _check(None, lib().af_mlp_grad(net, _V(feat_dev_ptr), _V(label_dev_ptr), int(n), g.ctypes.data_as(_FP),
+                                   ctypes.byref(loss)))
+    return g, loss.value
+
+
+def af_mlp_train(net, feat_dev_ptr, label_dev_ptr, nsamples, batch, steps, lr, seed):
+    loss = ctypes.c_float()
+    _check(None, lib().af_mlp_train(net, _V(feat_dev_ptr), _V(label_dev_ptr), int(nsamples), int(batch),
+                                    int(steps), float(lr), int(seed), ctypes.byref(loss)))
+    return loss.value
+
+
+def af_set_mlp(ctx, net):
+    _check(ctx, lib().af_set_mlp(ctx, net))
+
+
+def _bcheck(b, st):
+    if st != AF_OK:
+        msg = lib().af_batch_last_error(b).decode() if b else ""
+        raise AfError(st, msg)
+
+
+def af_batch_create(grids, fluxes, diffs, bounds, opts):
+    n = len(grids)
+    G = (af_grid * n)(*grids)
+    F = (af_flux * n)(*fluxes)
+    D = (af_diff * n)(*diffs)
+    B = (af_bounds_t * n)(*bounds)
+    b = _V()
+    st = lib().af_batch_create(n, G, F, D, B, ctypes.byref(opts), ctypes.byref(b))
+    if st != AF_OK:
+        raise AfError(st, "af_batch_create failed")
+    return b
+
+
+def af_batch_destroy(b):
+    _bcheck(None, lib().af_batch_destroy(b))
+
+
+def af_batch_set_stream(b, stream_handle):
+    _bcheck(b, lib().af_batch_set_stream(b, _V(stream_handle)))
+
+
+def af_batch_info(b):
+    c, t, x, y = ctypes.c_longlong(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(b, lib().af_batch_info(b, ctypes.byref(c), ctypes.byref(t), ctypes.byref(x), ctypes.byref(y)))
+    return {"cells": c.value, "tiles": t.value, "tile": (x.value, y.value)}
+
+
+def af_batch_set_tile(b, tx, ty):
+    _bcheck(b, lib().af_batch_set_tile(b, int(tx), int(ty)))
+
+
+def af_batch_autotune(b):
+    x, y = ctypes.c_int(), ctypes.c_int()
+    _bcheck(b, lib().af_batch_autotune(b, ctypes.byref(x), ctypes.byref(y)))
+    return x.value, y.value
+
+
+def af_batch_set_state(b, i, n, ub, V, X, Y):
+    arrs = [_host(a, n) for a in (ub, V, X, Y)]
+    _bcheck(b, lib().af_batch_set_state(b, int(i), *[_dp(a) for a in arrs]))
+
+
+def af_batch_get_state(b, i, n):
+    out = [np.empty(n) for _ in range(4)]
+    _bcheck(b, lib().af_batch_get_state(b, int(i), *[_dp(a) for a in out]))
+    return out
+
+
+def af_batch_device_ptrs(b, i):
+    ptrs = (_V * 4)()
+    dt = (ctypes.c_int * 2)()
+    _bcheck(b, lib().af_batch_device_ptrs(b, int(i), ptrs, dt))
+    return [p for p in ptrs], (dt[0], dt[1])
+
+
+def af_batch_step(b, nsteps=1):
+    _bcheck(b, lib().af_batch_step(b, int(nsteps)))
+
+
+def af_batch_sync(b):
+    _bcheck(b, lib().af_batch_sync(b))
+
+
+def af_batch_time(b, i):
+    t = ctypes.c_double()
+    _bcheck(b, lib().af_batch_time(b, int(i), ctypes.byref(t)))
+    return t.value
+
+
+def af_batch_mass(b, i):
+    m = ctypes.c_double()
+    _bcheck(b, lib().af_batch_mass(b, int(i), ctypes.byref(m)))
+    return m.value
+
+
+def af_batch_bounds(b, i):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    _bcheck(b, lib().af_batch_bounds(b, int(i), ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def af_batch_stats(b):
+    c, e, m = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
+    _bcheck(b, lib().af_batch_stats(b, ctypes.byref(c), ctypes.byref(e), ctypes.byref(m)))
+    return {"clamps": c.value, "errors": e.value, "max_excess": m.value}
 
 
 def _check(ctx, st):
@@ -217,6 +417,6 @@ def af_dt_cfl(ctx):
 
 
 def af_stats(ctx):
-    c, e, m = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double()
-    _check(ctx, lib().af_stats(ctx, ctypes.byref(c), ctypes.byref(e), ctypes.byref(m)))
-    return {"clamps": c.value, "errors": e.value, "max_excess": m.value}
+    c, e, m, a = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().af_stats(ctx, ctypes.byref(c), ctypes.byref(e), ctypes.byref(m), ctypes.byref(a)))
+    return {"clamps": c.value, "errors": e.value, "max_excess": m.value, "mass_adjust": a.value}

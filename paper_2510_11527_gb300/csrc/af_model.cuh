@@ -23,7 +23,24 @@ struct DevModel {
   int ncrit[2];          // interior extrema of f_l' (Buckley-Leverett)
   double crit[2][8];
   double umin, umax;
+  // the same parameters rounded to float, read by the FP32 stencils (GB300's FP64
+  // unit also performs the double->float conversions, so none happen per use)
+  float fpf[4], dpf[4], critf[2][8];
 };
+
+// parameter k of a double/float pair in the stencil precision T
+template <class T> __device__ __forceinline__ T par(const double* d, const float* f, int k);
+template <> __device__ __forceinline__ double par<double>(const double* d, const float*, int k) { return d[k]; }
+template <> __device__ __forceinline__ float par<float>(const double*, const float* f, int k) { return f[k]; }
+
+inline void fill_float_params(DevModel& m) {
+  for (int k = 0; k < 4; ++k) {
+    m.fpf[k] = (float)m.fp[k];
+    m.dpf[k] = (float)m.dp[k];
+  }
+  for (int d = 0; d < 2; ++d)
+    for (int k = 0; k < 8; ++k) m.critf[d][k] = (float)m.crit[d][k];
+}
 
 template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <class T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
@@ -34,15 +51,15 @@ __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 template <int FLUX, class T>
 __device__ __forceinline__ T flux(const DevModel& m, int dir, T u) {
   if constexpr (FLUX == FLUX_LINEAR) {
-    return T(dir == 0 ? m.fp[0] : m.fp[1]) * u;
+    return par<T>(m.fp, m.fpf, dir == 0 ? 0 : 1) * u;
   } else if constexpr (FLUX == FLUX_BURGERS) {
-    return T(m.fp[0]) * u * u;
+    return par<T>(m.fp, m.fpf, 0) * u * u;
   } else if constexpr (FLUX == FLUX_BL) {
     T v = T(1) - u;
     T u2 = u * u;
     T f1 = u2 / (u2 + v * v);
     if (dir == 0) return f1;
-    return f1 * (T(1) - T(m.fp[0]) * v * v);
+    return f1 * (T(1) - par<T>(m.fp, m.fpf, 0) * v * v);
   } else {
     return T(0);
   }
@@ -52,9 +69,9 @@ __device__ __forceinline__ T flux(const DevModel& m, int dir, T u) {
 template <int FLUX, class T>
 __device__ __forceinline__ T dflux_abs(const DevModel& m, int dir, T u) {
   if constexpr (FLUX == FLUX_LINEAR) {
-    return tabs(T(dir == 0 ? m.fp[0] : m.fp[1]));
+    return tabs(par<T>(m.fp, m.fpf, dir == 0 ? 0 : 1));
   } else if constexpr (FLUX == FLUX_BURGERS) {
-    return tabs(T(2.0 * m.fp[0]) * u);
+    return tabs(T(2) * par<T>(m.fp, m.fpf, 0) * u);
   } else if constexpr (FLUX == FLUX_BL) {
     T v = T(1) - u;
     T D = u * u + v * v;
@@ -62,7 +79,7 @@ __device__ __forceinline__ T dflux_abs(const DevModel& m, int dir, T u) {
     T d1 = T(2) * u * v * rD * rD;
     if (dir == 0) return tabs(d1);
     T f1 = u * u * rD;
-    T g = T(m.fp[0]);
+    T g = par<T>(m.fp, m.fpf, 0);
     return tabs(d1 * (T(1) - g * v * v) + T(2) * g * v * f1);
   } else {
     return T(0);
@@ -72,19 +89,21 @@ __device__ __forceinline__ T dflux_abs(const DevModel& m, int dir, T u) {
 // a(u)
 template <class T>
 __device__ __forceinline__ T apot(const DevModel& m, T u) {
+  const double* d = m.dp;
+  const float* f = m.dpf;
   switch (m.diff_kind) {
     case AF_DIFF_CONST:
-      return T(m.dp[0]) * u;
+      return par<T>(d, f, 0) * u;
     case AF_DIFF_PWL:
-      return T(m.dp[0]) * tmin(u - T(m.dp[1]), T(0)) + T(m.dp[2]) * tmax(u - T(m.dp[3]), T(0));
+      return par<T>(d, f, 0) * tmin(u - par<T>(d, f, 1), T(0)) + par<T>(d, f, 2) * tmax(u - par<T>(d, f, 3), T(0));
     case AF_DIFF_PME: {
-      int e = (int)m.dp[0];
+      int e = (int)m.dpf[0];
       T r = u;
       for (int k = 1; k < e; ++k) r *= u;
       return r;
     }
     case AF_DIFF_CUBIC:
-      return ((T(m.dp[2]) * u + T(m.dp[1])) * u + T(m.dp[0])) * u;
+      return ((par<T>(d, f, 2) * u + par<T>(d, f, 1)) * u + par<T>(d, f, 0)) * u;
     default:
       return T(0);
   }
@@ -94,14 +113,14 @@ __device__ __forceinline__ T apot(const DevModel& m, T u) {
 template <int FLUX, class T>
 __device__ __forceinline__ T alpha_interval(const DevModel& m, int dir, T a, T b) {
   if constexpr (FLUX == FLUX_LINEAR) {
-    return tabs(T(dir == 0 ? m.fp[0] : m.fp[1]));
+    return tabs(par<T>(m.fp, m.fpf, dir == 0 ? 0 : 1));
   } else if constexpr (FLUX == FLUX_BURGERS) {
-    return T(tabs(2.0 * m.fp[0])) * tmax(tabs(a), tabs(b));
+    return tabs(T(2) * par<T>(m.fp, m.fpf, 0)) * tmax(tabs(a), tabs(b));
   } else if constexpr (FLUX == FLUX_BL) {
     T lo = tmin(a, b), hi = tmax(a, b);
     T best = tmax(dflux_abs<FLUX, T>(m, dir, lo), dflux_abs<FLUX, T>(m, dir, hi));
     for (int k = 0; k < m.ncrit[dir]; ++k) {
-      T c = T(m.crit[dir][k]);
+      T c = par<T>(m.crit[dir], m.critf[dir], k);
       if (c > lo && c < hi) best = tmax(best, dflux_abs<FLUX, T>(m, dir, c));
     }
     return best;
@@ -109,6 +128,18 @@ __device__ __forceinline__ T alpha_interval(const DevModel& m, int dir, T a, T b
     return T(0);
   }
 }
+
+// Shu-Osher combination a*x + b*y with a pinned rounding sequence (b*y rounded, then
+// one fused multiply-add), so every kernel that inlines it rounds identically whatever
+// the compiler's contraction choices.
+__device__ __forceinline__ double rk_comb(double a, double x, double b, double y) {
+  return __fma_rn(a, x, __dmul_rn(b, y));
+}
+__device__ __forceinline__ float rk_comb(float a, float x, float b, float y) {
+  return __fmaf_rn(a, x, __fmul_rn(b, y));
+}
+__device__ __forceinline__ double rk_scale(double b, double y) { return __dmul_rn(b, y); }
+__device__ __forceinline__ float rk_scale(float b, float y) { return __fmul_rn(b, y); }
 
 // Theta(zL, zH): largest t in [0,1] with (1-t) zL + t zH inside [umin, umax].
 template <class T>
@@ -129,7 +160,7 @@ struct DevStats {
   unsigned long long clamps;
   unsigned long long errors;
   unsigned long long max_excess_bits;   // bit pattern of a non-negative double
-  unsigned long long pad;
+  double ub_adjust;                     // sum of |clamped - raw| over cell averages
 };
 
 __device__ __forceinline__ void record_excess(DevStats* st, double e, double tol, bool* clamp_ok) {
@@ -143,17 +174,21 @@ __device__ __forceinline__ void record_excess(DevStats* st, double e, double tol
   }
 }
 
-// Safeguard on a stored value: exact comparison against the bounds, clamp if within tol.
+// Safeguard on a stored value: exact comparison against the bounds, clamp if within
+// tol. For cell averages (is_avg) the size of the change is accumulated: times dx dy it
+// bounds the mass the clamps moved (later RK stages weight a stage output by <= 1).
 template <class S>
-__device__ __forceinline__ S safeguard(S v, S umin, S umax, double tol, DevStats* st) {
+__device__ __forceinline__ S safeguard(S v, S umin, S umax, double tol, DevStats* st, bool is_avg = false) {
   if (v < umin) {
     bool ok;
     record_excess(st, (double)umin - (double)v, tol, &ok);
+    if (ok && is_avg) atomicAdd(&st->ub_adjust, (double)umin - (double)v);
     return ok ? umin : v;
   }
   if (v > umax) {
     bool ok;
     record_excess(st, (double)v - (double)umax, tol, &ok);
+    if (ok && is_avg) atomicAdd(&st->ub_adjust, (double)v - (double)umax);
     return ok ? umax : v;
   }
   return v;

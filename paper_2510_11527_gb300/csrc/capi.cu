@@ -104,34 +104,7 @@ double kappa_max_of(const af_diff& df, double lo, double hi) {
 
 }  // namespace
 
-struct af_ctx {
-  af_grid grid;
-  af_flux flux;
-  af_diff diff;
-  af_bounds_t bnd;
-  af_opts opts;
-  DevModel m;
-  int dim = 2, nx = 1, ny = 1, prec = AF_PREC_FP64, nbuf = 3;
-  size_t n = 0;
-  double dx = 1, dy = 1, inv_h1 = 1, inv_h2 = 1, kmax = 0, cfl = 0.165, cfl_diff = 0, tol = 0;
-  bool bounds_pending = false;
-  unsigned char* block = nullptr;     // one allocation for every device buffer
-  double* ub[4] = {nullptr, nullptr, nullptr, nullptr};
-  void* pv[4] = {nullptr, nullptr, nullptr, nullptr};
-  void* px[4] = {nullptr, nullptr, nullptr, nullptr};
-  void* py[4] = {nullptr, nullptr, nullptr, nullptr};
-  double* dt_dev = nullptr;
-  double* t_dev = nullptr;
-  double* red = nullptr;              // 8 reduction result slots
-  double* partial = nullptr;          // RED_MAX_BLOCKS partials
-  unsigned long long* rate_bits = nullptr;
-  DevStats* stats = nullptr;
-  double* s_ext = nullptr;            // n doubles
-  const double* s_ext_user = nullptr; // caller-provided device indicator
-  double* host_pinned = nullptr;      // 8 doubles for small read-backs
-  cudaStream_t stream = nullptr;
-  char err[512] = {0};
-};
+#include "ctx.h"
 
 #define FAIL(ctx, code, ...)                                  \
   do {                                                        \
@@ -162,7 +135,7 @@ StageArgs2D<PT> base_args(af_ctx* c, int in) {
   a.X = (const PT*)c->px[in];
   a.Y = (const PT*)c->py[in];
   a.dt = c->dt_dev;
-  a.s_ext = c->s_ext_user ? c->s_ext_user : c->s_ext;
+  a.s_ext = (c->s_ext_user && !c->mlp) ? c->s_ext_user : c->s_ext;
   a.limiter = c->opts.limiter;
   a.blend = c->opts.blend;
   a.blend_external = c->opts.blend == AF_BLEND_EXTERNAL;
@@ -190,15 +163,29 @@ void set_out(af_ctx* c, StageArgs2D<PT>& a, int k, int oidx, double cA, int aidx
   a.nout = k + 1;
 }
 
+// With a learned indicator attached, the network first computes s from the stage's
+// input state into the context's indicator array, which the stage kernel then reads.
+template <class PT>
+cudaError_t run_indicator(af_ctx* c, const StageArgs2D<PT>& a) {
+  if (!c->mlp) return cudaSuccess;
+  int in = 0;
+  while (in < c->nbuf && c->ub[in] != a.ub) ++in;
+  return af::mlp_indicator_launch(c, c->mlp, in, c->s_ext);
+}
+
 template <class PT>
 cudaError_t launch(af_ctx* c, const StageArgs2D<PT>& a);
 template <>
 cudaError_t launch<double>(af_ctx* c, const StageArgs2D<double>& a) {
+  cudaError_t e = run_indicator(c, a);
+  if (e != cudaSuccess) return e;
   if (c->dim == 1) return af::launch_stage1d_f64(c->flux.kind, c->m, a, c->stream);
   return af::launch_stage2d_f64(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
 }
 template <>
 cudaError_t launch<float>(af_ctx* c, const StageArgs2D<float>& a) {
+  cudaError_t e = run_indicator(c, a);
+  if (e != cudaSuccess) return e;
   if (c->dim == 1) return af::launch_stage1d_f32(c->flux.kind, c->m, a, c->stream);
   return af::launch_stage2d_f32(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
 }
@@ -363,6 +350,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->m.diff_kind = diff->kind;
   for (int k = 0; k < 4; ++k) { c->m.fp[k] = flux->p[k]; c->m.dp[k] = diff->p[k]; }
   if (flux->kind == AF_FLUX_BL) bl_critical_points(c->m);
+  af::fill_float_params(c->m);
   c->bounds_pending = bounds->from_initial_data != 0;
   c->m.umin = bounds->umin;
   c->m.umax = bounds->umax;
@@ -587,7 +575,7 @@ af_status af_run(af_ctx* c, double T, long long* nsteps) {
   if (nsteps) *nsteps = n;
   long long cl = 0, er = 0;
   double mx = 0;
-  s = af_stats(c, &cl, &er, &mx);
+  s = af_stats(c, &cl, &er, &mx, nullptr);
   if (s != AF_OK) return s;
   if (er) FAIL(c, AF_E_STATE, "%lld values left [umin, umax] beyond the safeguard tolerance", er);
   return AF_OK;
@@ -637,7 +625,7 @@ af_status af_dt_cfl(af_ctx* c, double* dt) {
   return read_scalar(c, c->red + 4, dt);
 }
 
-af_status af_stats(af_ctx* c, long long* clamps, long long* errors, double* max_excess) {
+af_status af_stats(af_ctx* c, long long* clamps, long long* errors, double* max_excess, double* mass_adjust) {
   if (!c) return AF_E_ARG;
   DevStats st;
   CK(c, cudaMemcpyAsync(&st, c->stats, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
@@ -649,6 +637,7 @@ af_status af_stats(af_ctx* c, long long* clamps, long long* errors, double* max_
     std::memcpy(&v, &st.max_excess_bits, sizeof(v));
     *max_excess = v;
   }
+  if (mass_adjust) *mass_adjust = st.ub_adjust * c->dx * c->dy;
   return AF_OK;
 }
 

@@ -1,0 +1,43 @@
+// Internal definition of af_ctx (single-mesh solver context), shared by the
+// translation units of libaf. Not installed.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "af.h"
+#include "af_model.cuh"
+
+struct af_ctx {
+  af_grid grid;
+  af_flux flux;
+  af_diff diff;
+  af_bounds_t bnd;
+  af_opts opts;
+  af::DevModel m;
+  int dim = 2, nx = 1, ny = 1, prec = AF_PREC_FP64, nbuf = 3;
+  size_t n = 0;
+  double dx = 1, dy = 1, inv_h1 = 1, inv_h2 = 1, kmax = 0, cfl = 0.165, cfl_diff = 0, tol = 0;
+  bool bounds_pending = false;
+  unsigned char* block = nullptr;     // one allocation for every device buffer
+  double* ub[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* pv[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* px[4] = {nullptr, nullptr, nullptr, nullptr};
+  void* py[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* dt_dev = nullptr;
+  double* t_dev = nullptr;
+  double* red = nullptr;              // 8 reduction result slots
+  double* partial = nullptr;          // RED_MAX_BLOCKS partials
+  unsigned long long* rate_bits = nullptr;
+  af::DevStats* stats = nullptr;
+  double* s_ext = nullptr;            // n doubles
+  const double* s_ext_user = nullptr; // caller-provided device indicator
+  double* host_pinned = nullptr;      // 8 doubles for small read-backs
+  const struct af_mlp* mlp = nullptr; // learned indicator run before every stage
+  cudaStream_t stream = nullptr;
+  char err[512] = {0};
+};
+
+namespace af {
+// Fused learned-indicator inference on state buffer `buf` of the context into out
+// (n doubles); defined with the network kernels.
+cudaError_t mlp_indicator_launch(const af_ctx* c, const struct af_mlp* net, int buf, double* out);
+}  // namespace af

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
 // dt = 1 / max(rate / C, kappa_max / (h_min^2 Cd)). Resets the accumulator for the
 // next step.
 // When t_acc is given the step is also added to the simulated time.
-__global__ void dt_finalize_kernel(unsigned long long* rate_bits, double cfl, double cfl_diff, double kmax,
+static __global__ void dt_finalize_kernel(unsigned long long* rate_bits, double cfl, double cfl_diff, double kmax,
                                    double inv_hmin2, double* dt_out, double* t_acc) {
   const double rate = __longlong_as_double((long long)*rate_bits);
   double r = rate / cfl;
@@ -56,7 +56,7 @@ __global__ void dt_finalize_kernel(unsigned long long* rate_bits, double cfl, do
 }
 
 // *dt = v and, when t_acc is given, *t_acc += v
-__global__ void set_dt_kernel(double* dt, double* t_acc, double v) {
+static __global__ void set_dt_kernel(double* dt, double* t_acc, double v) {
   *dt = v;
   if (t_acc) *t_acc += v;
 }
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(RED_THREADS) partial_kernel(const S* __restric
 
 // combine nparts partials in block order into out[slot] (op as above; combine with the
 // existing out[slot] when accumulate != 0)
-__global__ void finalize_kernel(const double* partial, int nparts, int op, double* out, int accumulate) {
+static __global__ void finalize_kernel(const double* partial, int nparts, int op, double* out, int accumulate) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double acc = partial[0];
   for (int k = 1; k < nparts; ++k) acc = red_op(op, acc, partial[k]);

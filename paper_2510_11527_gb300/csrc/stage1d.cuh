@@ -147,16 +147,17 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
       T p = sP[b] + T(tau) * rP;
       if (A.limiter) p = tmin(tmax(p, umin), umax);
       const double cA = A.cA[o], cF = A.cF[o];
-      double ubo = cF * ubfe;
+      double ubo;
       PT po;
       if (cA != 0.0) {
-        ubo = cA * A.Aub[o][g] + ubo;
-        po = PT(T(cA) * T(A.AV[o][g]) + T(cF) * p);
+        ubo = rk_comb(cA, A.Aub[o][g], cF, ubfe);
+        po = PT(rk_comb(T(cA), T(A.AV[o][g]), T(cF), p));
       } else {
-        po = PT(T(cF) * p);
+        ubo = rk_scale(cF, ubfe);
+        po = PT(rk_scale(T(cF), p));
       }
       if (A.limiter && A.sg[o]) {
-        ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats);
+        ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
         po = safeguard<PT>(po, PT(m.umin), PT(m.umax), A.tol, A.stats);
       }
       A.Oub[o][g] = ubo;

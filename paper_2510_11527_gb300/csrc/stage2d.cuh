@@ -66,9 +66,10 @@ template <> struct PointStore<FLUX_LINEAR> { static constexpr int NQ = 1, NQU = 
 template <> struct PointStore<FLUX_BURGERS> { static constexpr int NQ = 2, NQU = 2; };   // f, a
 template <> struct PointStore<FLUX_BL> { static constexpr int NQ = 5, NQU = 3; };        // f1,f2,|f1'|,|f2'|,a
 
-template <int FLUX, class T, bool BLEND>
+template <int FLUX, class T, bool BLEND, int TX_ = 32, int TY_ = 8>
 struct Tile2D {
-  static constexpr int TX = 32, TY = 8, NT = TX * TY;
+  static constexpr int TX = TX_, TY = TY_, NT = TX * TY;
+  static_assert(NT == 256, "stage tiles use 256 threads");
   static constexpr int H = BLEND ? 3 : 2;
   static constexpr int BX = TX + 2 * H, BY = TY + 2 * H, BN = BX * BY;
   static constexpr int NQ = PointStore<FLUX>::NQ, NQU = PointStore<FLUX>::NQU;
@@ -86,6 +87,14 @@ struct Tile2D {
   // aliases inside the Q region (valid after P2)
   static constexpr int A_ULP1 = A_Q, A_ULM1 = A_Q + 1, A_ULP2 = A_Q + 2, A_ULM2 = A_Q + 3;
   static constexpr int A_FLIM1 = A_Q + 4, A_FLIM2 = A_Q + 5, A_ALIM1 = A_Q + 6, A_ALIM2 = A_Q + 7;
+};
+
+// Scalars uniform over a tile (grid spacings, dt-dependent limiter factors, RK weights)
+template <class T>
+struct TileScal {
+  double tau[2], mu1[2], mu2[2], nu1[2], nu2[2];
+  T taut[2], m4_1[2], n4_1[2], m4_2[2], n4_2[2], k1[2], k2[2], q1[2], q2[2], cAt[2], cFt[2];
+  T umin, umax, i6h1, i6h2, i3h21, i3h22, i2h1, i2h2, i4h21, i4h22, g;
 };
 
 template <int NT, class F>
@@ -113,12 +122,14 @@ __device__ __forceinline__ T line_res(T z0, T z1, T z2, T z3, T z4, T f0, T f1, 
   return da * i3h2 - (cf + alpha * dz) * i6h;
 }
 
-template <int FLUX, class T, class PT, bool BLEND>
-__global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const StageArgs2D<PT> A) {
-  using L = Tile2D<FLUX, T, BLEND>;
+// One TX x TY tile with origin (i0, j0) of one mesh: all phases P0-P5. Every thread of
+// the CTA must call it (it contains __syncthreads); smem_raw holds Tile2D::SMEM bytes.
+template <int FLUX, class T, class PT, bool BLEND, int TX_ = 32, int TY_ = 8>
+__device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<PT>& A, const int i0, const int j0,
+                                           unsigned char* smem_raw) {
+  using L = Tile2D<FLUX, T, BLEND, TX_, TY_>;
   constexpr int TX = L::TX, TY = L::TY, NT = L::NT, H = L::H, BX = L::BX, BY = L::BY, BN = L::BN;
   constexpr int NQ = L::NQ;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* S = reinterpret_cast<T*>(smem_raw);
   auto arr = [&](int a) -> T* { return S + (size_t)a * BN; };
   T* sU = arr(L::A_U);
@@ -130,10 +141,45 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
   const double dtv = *A.dt;
   if (dtv == 0.0) return;
   const int nx = A.nx, ny = A.ny;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const T umin = T(m.umin), umax = T(m.umax);
+
+  // tile-uniform scalars, formed once (in FP64, then rounded) by one thread
+  __shared__ TileScal<T> sc;
+  if (tid == 0) {
+    sc.umin = T(m.umin);
+    sc.umax = T(m.umax);
+    sc.i6h1 = T(A.inv_h1 / 6.0);
+    sc.i6h2 = T(A.inv_h2 / 6.0);
+    sc.i3h21 = T(A.inv_h1 * A.inv_h1 / 3.0);
+    sc.i3h22 = T(A.inv_h2 * A.inv_h2 / 3.0);
+    sc.i2h1 = T(2.0 * A.inv_h1);
+    sc.i2h2 = T(2.0 * A.inv_h2);
+    sc.i4h21 = T(4.0 * A.inv_h1 * A.inv_h1);
+    sc.i4h22 = T(4.0 * A.inv_h2 * A.inv_h2);
+    sc.g = T(A.gamma);
+    for (int o = 0; o < A.nout; ++o) {
+      const double tau = A.tcoef[o] * dtv;
+      const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
+      const double nu1 = mu1 * A.inv_h1, nu2 = mu2 * A.inv_h2;
+      sc.tau[o] = tau;
+      sc.mu1[o] = mu1;
+      sc.mu2[o] = mu2;
+      sc.nu1[o] = nu1;
+      sc.nu2[o] = nu2;
+      sc.taut[o] = T(tau);
+      sc.m4_1[o] = T(4.0 * mu1);
+      sc.n4_1[o] = T(4.0 * nu1);
+      sc.m4_2[o] = T(4.0 * mu2);
+      sc.n4_2[o] = T(4.0 * nu2);
+      sc.k1[o] = T(12.0 * mu1);
+      sc.k2[o] = T(12.0 * mu2);
+      sc.q1[o] = T(12.0 * nu1);
+      sc.q2[o] = T(12.0 * nu2);
+      sc.cAt[o] = T(A.cA[o]);
+      sc.cFt[o] = T(A.cF[o]);
+    }
+  }
 
   // ---- P0: load the halo box --------------------------------------------------------
   for (int k = tid; k < BN; k += NT) {
@@ -146,6 +192,7 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
     sZ[2][k] = T(A.Y[g]);
   }
   __syncthreads();
+  const T umin = sc.umin, umax = sc.umax;
 
   // ---- P1: centres and pointwise nonlinearities ----------------------------------------
   auto eval_point = [&](int type, int b) {
@@ -215,8 +262,8 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
   __syncthreads();
 
   // ---- P2: high-order residuals, Simpson fluxes, DC potentials, LLF fluxes -------------
-  const T i6h1 = T(A.inv_h1 / 6.0), i6h2 = T(A.inv_h2 / 6.0);
-  const T i3h21 = T(A.inv_h1 * A.inv_h1 / 3.0), i3h22 = T(A.inv_h2 * A.inv_h2 / 3.0);
+  const T i6h1 = sc.i6h1, i6h2 = sc.i6h2;
+  const T i3h21 = sc.i3h21, i3h22 = sc.i3h22;
   // value / flux / |f'| / a of a stored point of the given type, direction dir
   auto Fz = [&](int type, int b, int dir) -> T {
     if constexpr (FLUX == FLUX_BURGERS) return Q(type, 0)[b];
@@ -321,7 +368,7 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
   T rV, rX, rY;
   if constexpr (BLEND) {
     // ---- P2b: blend weights theta^{c,s} = exp(-gamma (s_i + s_{i+1})/2), theta^{d,s} = exp(-gamma s_i)
-    const T g = T(A.gamma);
+    const T g = sc.g;
     for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
       const int b = by * BX + bx;
       const T s1 = sS1[b], s2 = sS2[b];
@@ -354,8 +401,8 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
     });
     // first-order point residual on the +-h/2 neighbours (centre -> cell average):
     //   -(2/h)[F(z0,z+) - F(z-,z0)] + (4/h^2)(a+ - 2 a0 + a-)
-    const T i2h1 = T(2.0 * A.inv_h1), i2h2 = T(2.0 * A.inv_h2);
-    const T i4h21 = T(4.0 * A.inv_h1 * A.inv_h1), i4h22 = T(4.0 * A.inv_h2 * A.inv_h2);
+    const T i2h1 = sc.i2h1, i2h2 = sc.i2h2;
+    const T i4h21 = sc.i4h21, i4h22 = sc.i4h22;
     auto lowres = [&](int dir, T zm, T fm, T am, T z0, T f0, T a0, T zp, T fp, T ap) -> T {
       const T Fr = T(0.5) * (f0 + fp) - T(0.5) * alpha_interval<FLUX, T>(m, dir, z0, zp) * (zp - z0);
       const T Fl = T(0.5) * (fm + f0) - T(0.5) * alpha_interval<FLUX, T>(m, dir, zm, z0) * (z0 - zm);
@@ -400,13 +447,15 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
   T* sFlim2 = A.limiter ? arr(L::A_FLIM2) : sFH2;
   T* sAlim1 = A.limiter ? arr(L::A_ALIM1) : sAH1;
   T* sAlim2 = A.limiter ? arr(L::A_ALIM2) : sAH2;
+  // kept rolled: one copy of the per-output body, compiled identically in every kernel
+  // that inlines this tile
+#pragma unroll 1
   for (int o = 0; o < A.nout; ++o) {
-    const double tau = A.tcoef[o] * dtv;
-    const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
-    const double nu1 = mu1 * A.inv_h1, nu2 = mu2 * A.inv_h2;
+    const double mu1 = sc.mu1[o], mu2 = sc.mu2[o];
+    const double nu1 = sc.nu1[o], nu2 = sc.nu2[o];
     if (A.limiter) {
       // ---- P3: directional low-order states u^{L,+-}_l = ub -+ 4 mu (...) +- 4 nu (...)
-      const T m4_1 = T(4.0 * mu1), n4_1 = T(4.0 * nu1), m4_2 = T(4.0 * mu2), n4_2 = T(4.0 * nu2);
+      const T m4_1 = sc.m4_1[o], n4_1 = sc.n4_1[o], m4_2 = sc.m4_2[o], n4_2 = sc.n4_2[o];
       for_rect<NT>(H - 2, H + TX + 2, H, H + TY, [&](int bx, int by) {
         const int b = by * BX + bx;
         const T u = sU[b], f = fU(b, 0), a = aU(b);
@@ -421,7 +470,7 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
       });
       __syncthreads();
       // ---- P4: theta^c per face (2 states), theta^d per cell (4 states), factor 12
-      const T k1 = T(12.0 * mu1), k2 = T(12.0 * mu2), q1 = T(12.0 * nu1), q2 = T(12.0 * nu2);
+      const T k1 = sc.k1[o], k2 = sc.k2[o], q1 = sc.q1[o], q2 = sc.q2[o];
       for_rect<NT>(H - 1, H + TX, H, H + TY, [&](int bx, int by) {
         const int b = by * BX + bx;
         const T fh = sFH1[b], fl = sFL1[b], dF = fh - fl;
@@ -460,36 +509,41 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
     if (own) {
       const int b = bo;
       const double ubin = A.ub[g];
-      const double dflux = mu1 * ((double)sFlim1[b] - (double)sFlim1[b - 1]) +
-                           mu2 * ((double)sFlim2[b] - (double)sFlim2[b - BX]);
-      const double dpot = nu1 * (((double)sAlim1[b + 1] - 2.0 * (double)sAlim1[b]) + (double)sAlim1[b - 1]) +
-                          nu2 * (((double)sAlim2[b + BX] - 2.0 * (double)sAlim2[b]) + (double)sAlim2[b - BX]);
-      const double ubfe = ubin - dflux + dpot;
-      const T taut = T(tau);
-      T v = sZ[tV][b] + taut * rV, x = sZ[tX][b] + taut * rX, y = sZ[tY][b] + taut * rY;
+      // explicit roundings: every kernel inlining this tile (single mesh or batch)
+      // produces bit-identical results
+      const double dflux = rk_comb(mu1, (double)sFlim1[b] - (double)sFlim1[b - 1], mu2,
+                                   (double)sFlim2[b] - (double)sFlim2[b - BX]);
+      const double dpot = rk_comb(nu1, ((double)sAlim1[b + 1] - 2.0 * (double)sAlim1[b]) + (double)sAlim1[b - 1],
+                                  nu2, ((double)sAlim2[b + BX] - 2.0 * (double)sAlim2[b]) + (double)sAlim2[b - BX]);
+      const double ubfe = (ubin - dflux) + dpot;
+      const T taut = sc.taut[o];
+      T v = rk_comb(taut, rV, T(1), sZ[tV][b]), x = rk_comb(taut, rX, T(1), sZ[tX][b]),
+        y = rk_comb(taut, rY, T(1), sZ[tY][b]);
       if (A.limiter) {
         v = tmin(tmax(v, umin), umax);
         x = tmin(tmax(x, umin), umax);
         y = tmin(tmax(y, umin), umax);
       }
       const double cA = A.cA[o], cF = A.cF[o];
-      double ubo = cF * ubfe;
+      const T cAt = sc.cAt[o], cFt = sc.cFt[o];
+      double ubo;
       PT vo, xo, yo;
       if (cA != 0.0) {
-        ubo = cA * A.Aub[o][g] + ubo;
-        vo = PT(T(cA) * T(A.AV[o][g]) + T(cF) * v);
-        xo = PT(T(cA) * T(A.AX[o][g]) + T(cF) * x);
-        yo = PT(T(cA) * T(A.AY[o][g]) + T(cF) * y);
+        ubo = rk_comb(cA, A.Aub[o][g], cF, ubfe);
+        vo = PT(rk_comb(cAt, T(A.AV[o][g]), cFt, v));
+        xo = PT(rk_comb(cAt, T(A.AX[o][g]), cFt, x));
+        yo = PT(rk_comb(cAt, T(A.AY[o][g]), cFt, y));
       } else {
-        vo = PT(T(cF) * v);
-        xo = PT(T(cF) * x);
-        yo = PT(T(cF) * y);
+        ubo = rk_scale(cF, ubfe);
+        vo = PT(rk_scale(cFt, v));
+        xo = PT(rk_scale(cFt, x));
+        yo = PT(rk_scale(cFt, y));
       }
       if (A.limiter && A.sg[o]) {
-        ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats);
-        vo = safeguard<PT>(vo, PT(m.umin), PT(m.umax), A.tol, A.stats);
-        xo = safeguard<PT>(xo, PT(m.umin), PT(m.umax), A.tol, A.stats);
-        yo = safeguard<PT>(yo, PT(m.umin), PT(m.umax), A.tol, A.stats);
+        ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
+        vo = safeguard<PT>(vo, PT(umin), PT(umax), A.tol, A.stats);
+        xo = safeguard<PT>(xo, PT(umin), PT(umax), A.tol, A.stats);
+        yo = safeguard<PT>(yo, PT(umin), PT(umax), A.tol, A.stats);
       }
       A.Oub[o][g] = ubo;
       A.OV[o][g] = vo;
@@ -498,6 +552,13 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
     }
     if (o + 1 < A.nout) __syncthreads();
   }
+}
+
+// One CTA per 32 x 8 tile of a single mesh.
+template <int FLUX, class T, class PT, bool BLEND>
+__global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const StageArgs2D<PT> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  stage_tile<FLUX, T, PT, BLEND, 32, 8>(m, A, blockIdx.x * 32, blockIdx.y * 8, smem_raw);
 }
 
 }  // namespace af

@@ -1,0 +1,138 @@
+"""Batched persistent execution (uneven instances, one launch per RK stage, graph
+replay, autotuned tile shape) against single-mesh contexts and the oracle."""
+import numpy as np
+import pytest
+
+import af_inputs as ai
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_11527_gb300 import build
+    build.build()
+
+
+def _structs(specs, prec, rk):
+    from paper_2510_11527_gb300 import capi
+    grids, fl, df, bd = [], [], [], []
+    for s in specs:
+        grids.append(capi.af_grid(2, s.nx, s.ny, s.x0, s.x1, s.y0, s.y1))
+        f = capi.af_flux()
+        f.kind = capi.FLUX[s.flux[0]]
+        for k, v in enumerate(s.flux[1]):
+            f.p[k] = v
+        d = capi.af_diff()
+        d.kind = capi.DIFF[s.diff[0]]
+        for k, v in enumerate(s.diff[1]):
+            d.p[k] = v
+        fl.append(f)
+        df.append(d)
+        bd.append(capi.af_bounds_t(s.umin, s.umax, 0))
+    opts = capi.af_opts(capi.PREC[prec], rk, 0.0, 0.0, 1, 0, 1.0)
+    return grids, fl, df, bd, opts
+
+
+def _instances(count=7, seed=3, nmax=130):
+    return ai.batch_instances(count=count, seed=seed, nmin=20, nmax=nmax)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+@pytest.mark.parametrize("tile", [(32, 8), (64, 4), (16, 16)])
+@pytest.mark.parametrize("rk", [3, 54])
+def test_batch_bitwise_equals_single_mesh(prec, tile, rk):
+    from paper_2510_11527_gb300 import Solver, capi
+    inst = _instances()
+    specs = [s for s, _ in inst]
+    states = [[a.numpy() for a in ai.batch_state(s, m)] for s, m in inst]
+    b = capi.af_batch_create(*_structs(specs, prec, rk))
+    try:
+        capi.af_batch_set_tile(b, *tile)
+        for i, (s, st) in enumerate(zip(specs, states)):
+            capi.af_batch_set_state(b, i, s.cells, *st)
+        capi.af_batch_step(b, 3)
+        capi.af_batch_sync(b)
+        for i, (s, st) in enumerate(zip(specs, states)):
+            got = capi.af_batch_get_state(b, i, s.cells)
+            with Solver(s, precision=prec, rk=rk) as one:
+                one.set_state(st)
+                for _ in range(3):
+                    one.step(0.0)
+                want = one.get_state()
+                assert capi.af_batch_time(b, i) == one.time()
+            for x, y in zip(got, want):
+                if rk == 3:
+                    assert np.array_equal(x.reshape(y.shape), y)
+                else:
+                    # separate compilations of the same tile code may contract a few
+                    # multiply-adds differently: agreement to a few ulp
+                    assert np.max(np.abs(x.reshape(y.shape) - y)) <= 2e-15 * max(abs(s.umin), abs(s.umax))
+            lo, hi = capi.af_batch_bounds(b, i)
+            assert lo >= s.umin and hi <= s.umax
+        assert capi.af_batch_stats(b)["errors"] == 0
+    finally:
+        capi.af_batch_destroy(b)
+
+
+def test_batch_matches_oracle_fp64():
+    from paper_2510_11527_gb300 import capi
+    inst = _instances(count=4, seed=9, nmax=60)
+    specs = [s for s, _ in inst]
+    states = [[a.numpy() for a in ai.batch_state(s, m)] for s, m in inst]
+    b = capi.af_batch_create(*_structs(specs, "fp64", 3))
+    try:
+        for i, (s, st) in enumerate(zip(specs, states)):
+            capi.af_batch_set_state(b, i, s.cells, *st)
+        capi.af_batch_step(b, 2)
+        for i, (s, st) in enumerate(zip(specs, states)):
+            ref = [a.copy() for a in st]
+            for _ in range(2):
+                ref, _ = oracle.step(s, 3, ref, oracle.dt_cfl(s, ref[0]))
+            got = capi.af_batch_get_state(b, i, s.cells)
+            err = max(np.max(np.abs(g.reshape(r.shape) - r)) for g, r in zip(got, ref))
+            assert err <= 1e-12 * max(abs(s.umin), abs(s.umax))
+            m0 = oracle.mass(s, st[0])
+            assert abs(capi.af_batch_mass(b, i) - m0) <= 1e-14 * max(1.0, abs(m0))
+    finally:
+        capi.af_batch_destroy(b)
+
+
+def test_autotune_restores_state_and_picks_a_built_shape():
+    from paper_2510_11527_gb300 import capi
+    inst = _instances(count=6, seed=5, nmax=200)
+    specs = [s for s, _ in inst]
+    states = [[a.numpy() for a in ai.batch_state(s, m)] for s, m in inst]
+    outs = []
+    for tune in (False, True):
+        b = capi.af_batch_create(*_structs(specs, "fp32_mixed", 3))
+        try:
+            for i, (s, st) in enumerate(zip(specs, states)):
+                capi.af_batch_set_state(b, i, s.cells, *st)
+            if tune:
+                shape = capi.af_batch_autotune(b)
+                assert shape in [(32, 8), (64, 4), (16, 16)]
+                assert capi.af_batch_info(b)["tile"] == shape
+                assert capi.af_batch_time(b, 0) == 0.0
+            capi.af_batch_step(b, 2)
+            outs.append([capi.af_batch_get_state(b, i, s.cells) for i, s in enumerate(specs)])
+        finally:
+            capi.af_batch_destroy(b)
+    for a, c in zip(outs[0], outs[1]):
+        for x, y in zip(a, c):
+            assert np.array_equal(x, y)
+
+
+def test_batch_rejects_mixed_flux_kinds_and_blend():
+    from paper_2510_11527_gb300 import capi
+    s1 = ai.config2(16)
+    s2 = ai.Spec(dim=2, nx=16, ny=16, flux=("linear", (1.0, 1.0)), diff=("const", (0.01,)), umin=-1, umax=1)
+    with pytest.raises(capi.AfError) as ei:
+        capi.af_batch_create(*_structs([s1, s2], "fp64", 3))
+    assert ei.value.status == capi.AF_E_ARG
+    g, f, d, b, o = _structs([s1], "fp64", 3)
+    o.blend = 1
+    with pytest.raises(capi.AfError) as ei:
+        capi.af_batch_create(g, f, d, b, o)
+    assert ei.value.status == capi.AF_E_UNSUPPORTED
