@@ -219,6 +219,27 @@ af_status af_mlp_train(af_mlp* net, const float* feat_dev, const float* label_de
  * blend = AF_BLEND_EXTERNAL: every stage then computes s from its input state first */
 af_status af_set_mlp(af_ctx* ctx, const af_mlp* net);
 
+/* Allocation-free total mass: *mass = cell_area * sum(ub_dev[0..ncells-1]) for a
+ * caller-owned device array of cell averages, without any context and without
+ * allocating device memory. The paper has no counterpart: this entry point is for
+ * callers that cannot call cudaMalloc -- for example a host application whose memory
+ * pool has claimed (nearly) all device memory up front, a latency-critical loop that
+ * cannot afford the implicit device synchronisation of an allocation, or a plugin host
+ * that forbids a library from allocating on its own.
+ *   - Scratch: a file-scope device array of AF_MASS_NOALLOC_MAX_CELLS / 2048 partial
+ *     sums (512 KiB) plus one result slot, held by every GPU that loads the library until
+ *     the process exits. All slots a call uses are overwritten by that call.
+ *   - The first call on a device resolves the array's device address (with that device
+ *     current); calls that overlap on the GPU (e.g. on two streams) race on the shared
+ *     scratch and must be serialised by the caller.
+ *   - The summation order is fixed (2048-cell blocks, then a fixed tree), so repeated
+ *     calls on the same data return bit-identical results; the order differs from
+ *     af_mass, so the two agree to FP64 round-off.
+ *   - Returns AF_E_ARG for NULL pointers, ncells <= 0 or ncells >
+ *     AF_MASS_NOALLOC_MAX_CELLS, AF_E_CUDA if a launch or copy fails. Work is issued on
+ *     `stream` (NULL: legacy default stream), which is synchronised before returning. */
+#define AF_MASS_NOALLOC_MAX_CELLS 134217728LL
+af_status af_mass_noalloc(const double* ub_dev, long long ncells, double cell_area, double* mass, void* stream);
 
 #ifdef __cplusplus
 }

@@ -91,6 +91,8 @@ def lib():
     L.af_last_error.restype = ctypes.c_char_p
     L.af_num_stages.argtypes = [_V]
     L.af_num_stages.restype = ctypes.c_int
+    L.af_mass_noalloc.argtypes = [_V, ctypes.c_longlong, ctypes.c_double, _D, _V]
+    L.af_mass_noalloc.restype = ctypes.c_int
     I = ctypes.POINTER(ctypes.c_int)
     bsig = {
         "af_batch_create": [ctypes.c_int, ctypes.POINTER(af_grid), ctypes.POINTER(af_flux), ctypes.POINTER(af_diff),
@@ -143,7 +145,7 @@ def exported_symbols():
     return ["af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_state", "af_get_state",
             "af_device_ptrs", "af_set_indicator", "af_set_indicator_device", "af_forward_euler", "af_stage", "af_dt_device",
             "af_num_stages", "af_step", "af_run", "af_time", "af_mass", "af_bounds", "af_dt_cfl", "af_stats",
-            "af_batch_create", "af_batch_destroy", "af_batch_last_error", "af_batch_set_stream",
+            "af_mass_noalloc", "af_batch_create", "af_batch_destroy", "af_batch_last_error", "af_batch_set_stream",
             "af_batch_info", "af_batch_set_tile", "af_batch_autotune", "af_batch_set_state", "af_batch_get_state",
             "af_batch_device_ptrs", "af_batch_step", "af_batch_sync", "af_batch_time", "af_batch_mass",
             "af_batch_bounds", "af_batch_stats", "af_mlp_create", "af_mlp_destroy", "af_mlp_set_params",
@@ -414,6 +416,20 @@ def af_dt_cfl(ctx):
     d = ctypes.c_double()
     _check(ctx, lib().af_dt_cfl(ctx, ctypes.byref(d)))
     return d.value
+
+
+AF_MASS_NOALLOC_MAX_CELLS = 134217728
+
+
+def af_mass_noalloc(ub_dev_ptr, ncells, cell_area, stream_handle=None):
+    """Allocation-free total mass of a caller-owned device array of cell averages
+    (for callers that cannot allocate device memory; see include/af.h)."""
+    m = ctypes.c_double()
+    st = lib().af_mass_noalloc(_V(ub_dev_ptr), int(ncells), float(cell_area), ctypes.byref(m),
+                               _V(stream_handle) if stream_handle else None)
+    if st != AF_OK:
+        raise AfError(st, f"af_mass_noalloc(ncells={ncells}) failed (maximum {AF_MASS_NOALLOC_MAX_CELLS} cells)")
+    return m.value
 
 
 def af_stats(ctx):
