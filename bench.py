@@ -230,6 +230,220 @@ def run_gpu(args):
     return result
 
 
+# ---------------------------------------------------------------------------------------
+# the other forms of the metric: FP32-mixed, batched, learned (each against plain FP64)
+
+def _cuda_view(ptr, shape, typestr):
+    import torch
+
+    class _V:
+        __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3}
+
+    return torch.as_tensor(_V(), device="cuda")
+
+
+def _load_device(solver, state_dev):
+    """Copy a device state (FP64 tensors) into the solver's buffers without a host trip."""
+    import torch
+    for dst, src in zip(solver.device_tensors(), state_dev):
+        dst.copy_(src.to(dst.dtype))
+    torch.cuda.synchronize()   # the solver runs on its own stream
+
+
+def _time_steps(stepper, nst, steps, warmup, stream, flush=None):
+    """CUDA-event timing of `steps` steps on `stream`: returns (step_ms, stage_ms)."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            stepper(None)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(nst + 2)] for _ in range(steps)]
+    with torch.cuda.stream(stream):
+        for s in range(steps):
+            if flush is not None:
+                flush.zero_()
+            stepper(evs[s])
+    torch.cuda.synchronize()
+    step_ms = [e[0].elapsed_time(e[-1]) for e in evs]
+    stage_ms = [e[1 + k].elapsed_time(e[2 + k]) for e in evs for k in range(nst)]
+    return step_ms, stage_ms
+
+
+def _solver_stepper(solver, stream):
+    nst = solver.num_stages
+
+    def step(ev):
+        if ev:
+            ev[0].record(stream)
+        solver.dt_device()
+        if ev:
+            ev[1].record(stream)
+        for k in range(nst):
+            solver.stage(k, 0.0)
+            if ev:
+                ev[2 + k].record(stream)
+    return step
+
+
+def _single_form(spec, prec, steps, warmup, state_dev, stream, flush=None, net=None):
+    import statistics as st_
+    from paper_2510_11527_gb300 import Solver, capi
+    s = Solver(spec, precision=prec, rk=3)
+    s.set_stream(stream)
+    # bounds and a valid initial state are set through the API on a 1x copy, then the
+    # full device state is written in place
+    _load_device(s, state_dev)
+    if net is not None:
+        capi.af_set_mlp(s.ctx, net)
+    step_ms, stage_ms = _time_steps(_solver_stepper(s, stream), s.num_stages + (0), steps, warmup, stream, flush)
+    out = {"value": spec.cells * s.num_stages * steps / (sum(step_ms) / 1e3), "ms_per_step": st_.mean(step_ms),
+           "stage_ms_avg": st_.mean(stage_ms), "stats": s.stats()}
+    return s, out
+
+
+def _hbm_roof(prec, cells, stage_ms, peaks, extra_bytes=0.0):
+    b = BYTES_PER_CELL_STAGE[prec] + extra_bytes
+    ach = b * cells / (stage_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach / peaks["hbm_gbs"], 4), "bytes_per_cell_stage": b}
+
+
+def forms(args, headline_value, peaks):
+    """FP32-mixed, batched and learned forms of the metric, each with its speedup over
+    the plain FP64 GPU form on the same workload and its L1 difference from FP64."""
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import capi
+    stream = torch.cuda.Stream()
+    res = {}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    # (1) degenerate Burgers 1024^2 in FP32-mixed (headline workload)
+    spec = ai.config2(1024)
+    st = ai.initial_state(spec, device="cuda")
+    s64, r64 = _single_form(spec, "fp64", args.form_steps, 3, st, stream, flush)
+    s32, r32 = _single_form(spec, "fp32_mixed", args.form_steps, 3, st, stream, flush)
+    a64, a32 = s64.device_tensors(), s32.device_tensors()
+    l1 = max(float((x.double() - y.double()).abs().mean()) for x, y in zip(a32, a64))
+    res["fp32_mixed_degenerate_burgers_1024"] = {
+        "value": round(r32["value"], 1), "speedup_vs_fp64": round(r32["value"] / r64["value"], 2),
+        "l1_vs_fp64": l1, "stage_ms_avg": round(r32["stage_ms_avg"], 5),
+        "roofline": _hbm_roof("fp32_mixed", spec.cells, r32["stage_ms_avg"], peaks)}
+    s64.close()
+    s32.close()
+    del st, a64, a32
+
+    # (2) porous medium 4096^2 (config 3) FP32-mixed vs FP64
+    spec = ai.config3(4096)
+    st = ai.state_2d(lambda x, y: ai.barenblatt(x, y, 1.0), spec, device="cuda", sub=2, order=3)
+    s64, r64 = _single_form(spec, "fp64", 2, 1, st, stream)
+    s32, r32 = _single_form(spec, "fp32_mixed", 2, 1, st, stream)
+    l1 = max(float((x.double() - y.double()).abs().mean()) for x, y in zip(s32.device_tensors(), s64.device_tensors()))
+    s64.close()
+    s32, r32 = _single_form(spec, "fp32_mixed", args.form_steps, 2, st, stream)
+    res["fp32_mixed_pme_4096"] = {
+        "value": round(r32["value"], 1), "fp64_value": round(r64["value"], 1),
+        "speedup_vs_fp64": round(r32["value"] / r64["value"], 2), "l1_vs_fp64_after_3_steps": l1,
+        "stage_ms_avg": round(r32["stage_ms_avg"], 5),
+        "roofline": _hbm_roof("fp32_mixed", spec.cells, r32["stage_ms_avg"], peaks)}
+    s32.close()
+    del st
+
+    # (3) batch of 256 uneven instances (config 4), FP32-mixed, graph replay, autotuned tile
+    inst = ai.batch_instances()
+    grids, fl, df, bd = [], [], [], []
+    for s_, _ in inst:
+        grids.append(capi.af_grid(2, s_.nx, s_.ny, s_.x0, s_.x1, s_.y0, s_.y1))
+        f = capi.af_flux()
+        f.kind = capi.FLUX[s_.flux[0]]
+        f.p[0] = s_.flux[1][0]
+        d = capi.af_diff()
+        d.kind = capi.DIFF[s_.diff[0]]
+        for k, v in enumerate(s_.diff[1]):
+            d.p[k] = v
+        fl.append(f)
+        df.append(d)
+        bd.append(capi.af_bounds_t(s_.umin, s_.umax, 0))
+    opts = capi.af_opts(capi.PREC["fp32_mixed"], 3, 0.0, 0.0, 1, 0, 1.0)
+    b = capi.af_batch_create(grids, fl, df, bd, opts)
+    try:
+        cells = 0
+        for i, (s_, modes) in enumerate(inst):
+            stt = ai.batch_state(s_, modes, device="cuda")
+            ptrs, (_, pb) = capi.af_batch_device_ptrs(b, i)
+            shp = (s_.ny, s_.nx)
+            for k, (p, src) in enumerate(zip(ptrs, stt)):
+                _cuda_view(p, shp, "<f8" if (k == 0 or pb == 8) else "<f4").copy_(src)
+            cells += s_.cells
+        torch.cuda.synchronize()
+        tile = capi.af_batch_autotune(b)
+        capi.af_batch_step(b, 2)
+        capi.af_batch_sync(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        # the batch runs on its own stream; record around a synchronised replay
+        e0.record()
+        capi.af_batch_step(b, args.form_steps)
+        capi.af_batch_sync(b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        val = cells * 3 * args.form_steps / (ms / 1e3)
+        stats = capi.af_batch_stats(b)
+        res["batch_256_fp32_mixed"] = {
+            "value": round(val, 1), "cells": cells, "tile": list(tile), "ms_per_step": round(ms / args.form_steps, 4),
+            "speedup_vs_fp64_single_mesh": round(val / headline_value, 2), "safeguard_errors": stats["errors"],
+            "roofline": _hbm_roof("fp32_mixed", cells, ms / args.form_steps / 3, peaks)}
+    finally:
+        capi.af_batch_destroy(b)
+
+    # (4) Buckley-Leverett 4096^2 (config 5): plain vs learned blend, FP32-mixed
+    net = capi.af_mlp_create()
+    try:
+        capi.af_mlp_set_params(net, ai.mlp_init_params(1))
+        feats, labels = [], []
+        for k in range(8):
+            sp = ai.config5(128)
+            sp.blend = "plain"
+            stt = ai.random_piecewise(sp, seed=100 + k, device="cuda")
+            s_, _ = _single_form(sp, "fp32_mixed", 4, 0, stt, stream)
+            f = torch.empty((sp.cells, 21), dtype=torch.float32, device="cuda")
+            lab = torch.empty(sp.cells, dtype=torch.float32, device="cuda")
+            capi.af_mlp_features(s_.ctx, f.data_ptr(), lab.data_ptr())
+            feats.append(f)
+            labels.append(lab)
+            s_.close()
+        X, Y = torch.cat(feats), torch.cat(labels)
+        t0 = time.perf_counter()
+        loss = capi.af_mlp_train(net, X.data_ptr(), Y.data_ptr(), X.shape[0], 4096, 1500, 3e-3, 8)
+        train_s = time.perf_counter() - t0
+        spec = ai.config5(4096)
+        st = ai.state_2d(ai.bl_disc_fn, spec, device="cuda", sub=2, order=3)
+        spec.blend = "plain"
+        sp_, rp = _single_form(spec, "fp32_mixed", args.form_steps, 2, st, stream)
+        spec_l = ai.config5(4096)
+        spec_l.blend = "external"
+        sl_, rl = _single_form(spec_l, "fp32_mixed", args.form_steps, 2, st, stream, net=net)
+        l1 = float((sl_.device_tensors()[0] - sp_.device_tensors()[0]).abs().mean())
+        sp_.close()
+        sl_.close()
+        spec.blend = "plain"
+        s64, r64 = _single_form(spec, "fp64", 2, 1, st, stream)
+        s64.close()
+        res["bl_4096_fp32_mixed"] = {
+            "plain_blend_value": round(rp["value"], 1), "learned_blend_value": round(rl["value"], 1),
+            "fp64_plain_value": round(r64["value"], 1),
+            "speedup_plain_vs_fp64": round(rp["value"] / r64["value"], 2),
+            "speedup_learned_vs_fp64": round(rl["value"] / r64["value"], 2),
+            "l1_learned_vs_plain": l1, "train": {"samples": int(X.shape[0]), "steps": 1500, "final_loss": loss,
+                                                   "seconds": round(train_s, 2)},
+            "roofline_plain": _hbm_roof("fp32_mixed", spec.cells, rp["stage_ms_avg"], peaks),
+            "roofline_learned": _hbm_roof("fp32_mixed", spec.cells, rl["stage_ms_avg"], peaks)}
+    finally:
+        capi.af_mlp_destroy(net)
+    return res
+
+
 def cpu_sample(seconds_target=12.0):
     """Time the FP64 oracle on a bounded sample of the workload (config 2 at 512^2)."""
     import af_inputs as ai
@@ -281,6 +495,8 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP32/batched/learned forms")
+    ap.add_argument("--form-steps", type=int, default=5)
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)
@@ -290,6 +506,9 @@ def main():
     res = run_gpu(args)
     if res is not None:
         rank, world, _ = dist_env()
+        if not args.no_forms and world == 1:
+            peaks, _ = load_peaks()
+            res["forms"] = forms(args, res["value"], peaks)
         if not args.no_cpu_baseline and world == 1:
             res["cpu_baseline"] = cpu_sample()
         print(json.dumps(res))

@@ -141,6 +141,28 @@ __device__ __forceinline__ float rk_comb(float a, float x, float b, float y) {
 __device__ __forceinline__ double rk_scale(double b, double y) { return __dmul_rn(b, y); }
 __device__ __forceinline__ float rk_scale(float b, float y) { return __fmul_rn(b, y); }
 
+// double -> stencil precision. For float, the conversion is done with integer
+// operations (truncation toward zero; underflow to signed zero): on GB300 the FP64 unit
+// also executes F2F conversions, at 1/64 of the FP32 rate.
+template <class T> __device__ __forceinline__ T to_stencil(double d);
+template <> __device__ __forceinline__ double to_stencil<double>(double d) { return d; }
+template <> __device__ __forceinline__ float to_stencil<float>(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const unsigned int sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (e <= 0) return __int_as_float((int)sign);
+  if (e >= 255) return __int_as_float((int)(sign | 0x7F800000u));
+  return __int_as_float((int)(sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFull)));
+}
+
+// error-free sum: s + err = a + b exactly (Knuth's TwoSum)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 // Theta(zL, zH): largest t in [0,1] with (1-t) zL + t zH inside [umin, umax].
 template <class T>
 __device__ __forceinline__ T theta_fn(T zL, T zH, T umin, T umax) {

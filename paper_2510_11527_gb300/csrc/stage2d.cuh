@@ -93,6 +93,7 @@ struct Tile2D {
 template <class T>
 struct TileScal {
   double tau[2], mu1[2], mu2[2], nu1[2], nu2[2];
+  float mu1f[2], mu2f[2], nu1f[2], nu2f[2];
   T taut[2], m4_1[2], n4_1[2], m4_2[2], n4_2[2], k1[2], k2[2], q1[2], q2[2], cAt[2], cFt[2];
   T umin, umax, i6h1, i6h2, i3h21, i3h22, i2h1, i2h2, i4h21, i4h22, g;
 };
@@ -167,6 +168,10 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
       sc.mu2[o] = mu2;
       sc.nu1[o] = nu1;
       sc.nu2[o] = nu2;
+      sc.mu1f[o] = (float)mu1;
+      sc.mu2f[o] = (float)mu2;
+      sc.nu1f[o] = (float)nu1;
+      sc.nu2f[o] = (float)nu2;
       sc.taut[o] = T(tau);
       sc.m4_1[o] = T(4.0 * mu1);
       sc.n4_1[o] = T(4.0 * nu1);
@@ -186,7 +191,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     const int bx = k % BX, by = k / BX;
     const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
     const size_t g = (size_t)gj * nx + gi;
-    sU[k] = T(A.ub[g]);
+    sU[k] = to_stencil<T>(A.ub[g]);
     sZ[0][k] = T(A.V[g]);
     sZ[1][k] = T(A.X[g]);
     sZ[2][k] = T(A.Y[g]);
@@ -511,11 +516,34 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
       const double ubin = A.ub[g];
       // explicit roundings: every kernel inlining this tile (single mesh or batch)
       // produces bit-identical results
-      const double dflux = rk_comb(mu1, (double)sFlim1[b] - (double)sFlim1[b - 1], mu2,
-                                   (double)sFlim2[b] - (double)sFlim2[b - BX]);
-      const double dpot = rk_comb(nu1, ((double)sAlim1[b + 1] - 2.0 * (double)sAlim1[b]) + (double)sAlim1[b - 1],
-                                  nu2, ((double)sAlim2[b + BX] - 2.0 * (double)sAlim2[b]) + (double)sAlim2[b - BX]);
-      const double ubfe = (ubin - dflux) + dpot;
+      double ubfe;
+      if constexpr (sizeof(T) == 8) {
+        const double dflux = rk_comb(mu1, (double)sFlim1[b] - (double)sFlim1[b - 1], mu2,
+                                     (double)sFlim2[b] - (double)sFlim2[b - BX]);
+        const double dpot = rk_comb(nu1, ((double)sAlim1[b + 1] - 2.0 * (double)sAlim1[b]) + (double)sAlim1[b - 1],
+                                    nu2, ((double)sAlim2[b + BX] - 2.0 * (double)sAlim2[b]) + (double)sAlim2[b - BX]);
+        ubfe = (ubin - dflux) + dpot;
+      } else {
+        // FP32 stencils: each face contributes mu F (convection) and nu (A_+ - A)
+        // (diffusion), formed in FP32 by both adjacent cells from the same operands, so
+        // the contributions cancel exactly across faces; the eight terms of a cell are
+        // summed without rounding error (TwoSum) and added once to the FP64 average.
+        const float m1 = sc.mu1f[o], m2 = sc.mu2f[o], n1 = sc.nu1f[o], n2 = sc.nu2f[o];
+        const float t[8] = {__fmul_rn(m1, sFlim1[b - 1]), -__fmul_rn(m1, sFlim1[b]),
+                            __fmul_rn(m2, sFlim2[b - BX]), -__fmul_rn(m2, sFlim2[b]),
+                            __fmul_rn(n1, __fsub_rn(sAlim1[b + 1], sAlim1[b])),
+                            -__fmul_rn(n1, __fsub_rn(sAlim1[b], sAlim1[b - 1])),
+                            __fmul_rn(n2, __fsub_rn(sAlim2[b + BX], sAlim2[b])),
+                            -__fmul_rn(n2, __fsub_rn(sAlim2[b], sAlim2[b - BX]))};
+        float hi = t[0], lo = 0.0f;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+          float e;
+          two_sum(hi, t[q], hi, e);
+          lo = __fadd_rn(lo, e);
+        }
+        ubfe = ubin + ((double)hi + (double)lo);
+      }
       const T taut = sc.taut[o];
       T v = rk_comb(taut, rV, T(1), sZ[tV][b]), x = rk_comb(taut, rX, T(1), sZ[tX][b]),
         y = rk_comb(taut, rY, T(1), sZ[tY][b]);
