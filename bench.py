@@ -101,6 +101,18 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(value, device="cpu"):
+    """Maximum of a per-rank float over all ranks (the bench's timing rule); identity
+    without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_flops_per_cell(spec, state, tau):
     import oracle
     fc = oracle.flop_count(spec, state, tau)
@@ -160,11 +172,7 @@ def run_gpu(args):
     step_ms = [ev[s][0].elapsed_time(ev[s][-1]) for s in range(args.steps)]
     stage_ms = [ev[s][1 + k].elapsed_time(ev[s][2 + k]) for s in range(args.steps) for k in range(nst)]
     dt_ms = [ev[s][0].elapsed_time(ev[s][1]) for s in range(args.steps)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), device="cuda")
     stats = solver.stats()
     lo, hi = solver.bounds()
     cells = spec.cells

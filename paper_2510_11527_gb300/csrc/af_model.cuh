@@ -42,10 +42,38 @@ inline void fill_float_params(DevModel& m) {
     for (int k = 0; k < 8; ++k) m.critf[d][k] = (float)m.crit[d][k];
 }
 
+// Comparisons, min and max of doubles run on the integer units through an
+// order-preserving 64-bit key (key(a) < key(b) <=> a < b for non-NaN values; -0 orders
+// just below +0): GB300's FP64 unit, which would otherwise execute DSETP/DMNMX, is the
+// bottleneck of the FP64 stage.
+__device__ __forceinline__ long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ bool tlt(double a, double b) { return dkey(a) < dkey(b); }
+__device__ __forceinline__ bool tlt(float a, float b) { return a < b; }
+__device__ __forceinline__ bool is_one(double t) { return __double_as_longlong(t) == 0x3FF0000000000000LL; }
+__device__ __forceinline__ bool is_one(float t) { return t == 1.0f; }
+
 template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
 template <class T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
-__device__ __forceinline__ double tabs(double a) { return fabs(a); }
+template <> __device__ __forceinline__ double tmax<double>(double a, double b) { return dkey(a) < dkey(b) ? b : a; }
+template <> __device__ __forceinline__ double tmin<double>(double a, double b) { return dkey(b) < dkey(a) ? b : a; }
+__device__ __forceinline__ double tabs(double a) {
+  return __longlong_as_double(__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFLL);
+}
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
+
+// exact float -> double with integer operations (denormals take the hardware path)
+__device__ __forceinline__ double f2d_exact(float f) {
+  const unsigned int u = (unsigned int)__float_as_int(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e == 0u) return (u & 0x7FFFFFu) ? (double)f : __longlong_as_double((long long)(u & 0x80000000u) << 32);
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e - 127u + 1023u) << 52) |
+                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)d);
+}
 
 // f_l(u)
 template <int FLUX, class T>
@@ -95,6 +123,9 @@ __device__ __forceinline__ T apot(const DevModel& m, T u) {
     case AF_DIFF_CONST:
       return par<T>(d, f, 0) * u;
     case AF_DIFF_PWL:
+      // an exactly zero coefficient drops its branch (uniform integer test)
+      if ((__double_as_longlong(d[0]) << 1) == 0) return par<T>(d, f, 2) * tmax(u - par<T>(d, f, 3), T(0));
+      if ((__double_as_longlong(d[2]) << 1) == 0) return par<T>(d, f, 0) * tmin(u - par<T>(d, f, 1), T(0));
       return par<T>(d, f, 0) * tmin(u - par<T>(d, f, 1), T(0)) + par<T>(d, f, 2) * tmax(u - par<T>(d, f, 3), T(0));
     case AF_DIFF_PME: {
       int e = (int)m.dpf[0];
@@ -167,8 +198,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) 
 template <class T>
 __device__ __forceinline__ T theta_fn(T zL, T zH, T umin, T umax) {
   T bound;
-  if (zH < umin) bound = umin;
-  else if (zH > umax) bound = umax;
+  if (tlt(zH, umin)) bound = umin;
+  else if (tlt(umax, zH)) bound = umax;
   else return T(1);
   T den = zL - zH;
   if (den == T(0)) return T(1);
@@ -201,13 +232,13 @@ __device__ __forceinline__ void record_excess(DevStats* st, double e, double tol
 // bounds the mass the clamps moved (later RK stages weight a stage output by <= 1).
 template <class S>
 __device__ __forceinline__ S safeguard(S v, S umin, S umax, double tol, DevStats* st, bool is_avg = false) {
-  if (v < umin) {
+  if (tlt(v, umin)) {
     bool ok;
     record_excess(st, (double)umin - (double)v, tol, &ok);
     if (ok && is_avg) atomicAdd(&st->ub_adjust, (double)umin - (double)v);
     return ok ? umin : v;
   }
-  if (v > umax) {
+  if (tlt(umax, v)) {
     bool ok;
     record_excess(st, (double)v - (double)umax, tol, &ok);
     if (ok && is_avg) atomicAdd(&st->ub_adjust, (double)v - (double)umax);

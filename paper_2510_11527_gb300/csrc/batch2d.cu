@@ -45,11 +45,14 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchInst* __res
                                                           const int* __restrict__ work_inst, int total,
                                                           const BatchStage S, DevStats* stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  // the tile's arguments live in shared memory, written by one thread: a per-thread
+  // copy would sit in local memory (its arrays are indexed at run time)
+  __shared__ StageArgs2D<PT> A;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const BatchInst& I = inst[work_inst[w]];
     const int t = w - I.tile_begin;
     const int i0 = (t % I.tiles_x) * TX, j0 = (t / I.tiles_x) * TY;
-    StageArgs2D<PT> A;
+    if (threadIdx.x == 0) {
     A.nx = I.nx;
     A.ny = I.ny;
     A.inv_h1 = I.inv_h1;
@@ -82,6 +85,8 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchInst* __res
     A.gamma = 0.0;
     A.tol = I.tol;
     A.stats = stats;
+    }
+    __syncthreads();
     stage_tile<FLUX, T, PT, false, TX, TY>(I.m, A, i0, j0, smem_raw);
     __syncthreads();
   }

@@ -128,14 +128,14 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
           const T fh = sFH[b], fl = sFL[b], dF = fh - fl;
           const T zp = sULp[b], zm = sULm[b + 1];
           const T t = tmin(theta_fn<T>(zp, zp - k6 * dF, umin, umax), theta_fn<T>(zm, zm + k6 * dF, umin, umax));
-          sFlim[b] = t == T(1) ? fh : fl + t * dF;
+          sFlim[b] = is_one(t) ? fh : fl + t * dF;
         }
         const T ah = sAH[b], al = aU[b], d = q6 * (ah - al);
         const T t = tmin(tmin(theta_fn<T>(sULp[b - 1], sULp[b - 1] + d, umin, umax),
                               theta_fn<T>(sULp[b], sULp[b] - d, umin, umax)),
                          tmin(theta_fn<T>(sULm[b], sULm[b] - d, umin, umax),
                               theta_fn<T>(sULm[b + 1], sULm[b + 1] + d, umin, umax)));
-        sAlim[b] = t == T(1) ? ah : al + t * (ah - al);
+        sAlim[b] = is_one(t) ? ah : al + t * (ah - al);
       }
       __syncthreads();
     }

@@ -104,9 +104,20 @@ __device__ __forceinline__ void for_rect(int x0, int x1, int y0, int y1, F&& f) 
   for (int k = threadIdx.x; k < n; k += NT) f(x0 + k % w, y0 + k / w);
 }
 
+// periodic index; the halo never reaches further than one period except on meshes
+// smaller than the halo, which take the modulo path
 __device__ __forceinline__ int wrapi(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
+  if (i < 0) {
+    i += n;
+    if (i < 0) {
+      i %= n;
+      if (i < 0) i += n;
+    }
+  } else if (i >= n) {
+    i -= n;
+    if (i >= n) i %= n;
+  }
+  return i;
 }
 
 // Residual of one 5-point line (spacing h/2; points 0..4 at offsets -h..+h, point 2
@@ -481,14 +492,14 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
         const T fh = sFH1[b], fl = sFL1[b], dF = fh - fl;
         const T zp = sULp1[b], zm = sULm1[b + 1];
         const T t = tmin(theta_fn<T>(zp, zp - k1 * dF, umin, umax), theta_fn<T>(zm, zm + k1 * dF, umin, umax));
-        sFlim1[b] = t == T(1) ? fh : fl + t * dF;
+        sFlim1[b] = is_one(t) ? fh : fl + t * dF;
       });
       for_rect<NT>(H, H + TX, H - 1, H + TY, [&](int bx, int by) {
         const int b = by * BX + bx;
         const T fh = sFH2[b], fl = sFL2[b], dF = fh - fl;
         const T zp = sULp2[b], zm = sULm2[b + BX];
         const T t = tmin(theta_fn<T>(zp, zp - k2 * dF, umin, umax), theta_fn<T>(zm, zm + k2 * dF, umin, umax));
-        sFlim2[b] = t == T(1) ? fh : fl + t * dF;
+        sFlim2[b] = is_one(t) ? fh : fl + t * dF;
       });
       for_rect<NT>(H - 1, H + TX + 1, H, H + TY, [&](int bx, int by) {
         const int b = by * BX + bx;
@@ -497,7 +508,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
                               theta_fn<T>(sULp1[b], sULp1[b] - d, umin, umax)),
                          tmin(theta_fn<T>(sULm1[b], sULm1[b] - d, umin, umax),
                               theta_fn<T>(sULm1[b + 1], sULm1[b + 1] + d, umin, umax)));
-        sAlim1[b] = t == T(1) ? ah : al + t * (ah - al);
+        sAlim1[b] = is_one(t) ? ah : al + t * (ah - al);
       });
       for_rect<NT>(H, H + TX, H - 1, H + TY + 1, [&](int bx, int by) {
         const int b = by * BX + bx;
@@ -506,7 +517,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
                               theta_fn<T>(sULp2[b], sULp2[b] - d, umin, umax)),
                          tmin(theta_fn<T>(sULm2[b], sULm2[b] - d, umin, umax),
                               theta_fn<T>(sULm2[b + BX], sULm2[b + BX] + d, umin, umax)));
-        sAlim2[b] = t == T(1) ? ah : al + t * (ah - al);
+        sAlim2[b] = is_one(t) ? ah : al + t * (ah - al);
       });
       __syncthreads();
     }
@@ -542,7 +553,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
           two_sum(hi, t[q], hi, e);
           lo = __fadd_rn(lo, e);
         }
-        ubfe = ubin + ((double)hi + (double)lo);
+        ubfe = ubin + (f2d_exact(hi) + f2d_exact(lo));
       }
       const T taut = sc.taut[o];
       T v = rk_comb(taut, rV, T(1), sZ[tV][b]), x = rk_comb(taut, rX, T(1), sZ[tX][b]),

@@ -1,0 +1,129 @@
+"""The CUDA path reproduces what the paper prints (not only the oracle does):
+Table 4's Barenblatt minima, fourth-order convergence in 1D and 2D, Table 3's signs."""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import af_inputs as ai
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2510_11527_gb300 import build
+    build.build()
+
+
+def _golden(name):
+    rows = []
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.split("#")[0].strip()
+        if line:
+            rows.append(line.split())
+    return rows
+
+
+def solver(spec, **kw):
+    from paper_2510_11527_gb300 import Solver
+    return Solver(spec, **kw)
+
+
+@pytest.mark.parametrize("m", [2, 3, 5])
+def test_table4_barenblatt_minimum_gpu(m):
+    """2D Barenblatt, N = 80 on [-8, 8]^2, t: 1 -> 2 (Example 6.3, Table 4)."""
+    rows = {int(r[0]): [float(v) for v in r[1:]] for r in _golden("table4_barenblatt.txt")}
+    spec = ai.Spec(dim=2, nx=80, ny=80, x0=-8, x1=8, y0=-8, y1=8, flux=("zero", ()), diff=("pme", (m,)),
+                   umin=0.0, umax=1.0, limiter=True)
+    st = [a.numpy() for a in ai.state_2d(lambda x, y: ai.barenblatt(x, y, 1.0, m=m), spec)]
+    with solver(spec, rk=54) as s:
+        s.set_state(st)
+        s.run(1.0)
+        lo, _ = s.bounds()
+        assert s.stats()["errors"] == 0
+    assert lo == 0.0
+    spec.limiter = False
+    # linear stability of the unlimited 2D scheme needs kappa dt/h^2 <= 0.131 (RK(5,4))
+    with solver(spec, rk=54, cfl=0.12, cfl_diff=-1.0) as s:
+        s.set_state(st)
+        s.run(1.0)
+        lo, _ = s.bounds()
+    assert lo == pytest.approx(rows[m][0], rel=0.05)
+
+
+def _order(e):
+    return [math.log2(e[k] / e[k + 1]) for k in range(len(e) - 1)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_fourth_order_1d_gpu(prec):
+    eb = []
+    for n in (32, 64, 128):
+        spec = ai.config1(n)
+        st = [a.numpy() for a in ai.sine_1d_state(spec)]
+        dt = 0.5 * 0.9284 / (1.0 / spec.dx + 0.01 / spec.dx ** 2)
+        with solver(spec, precision=prec, rk=54) as s:
+            s.set_state(st)
+            t = 0.0
+            while t < 1.0 - 1e-14:
+                d = min(dt, 1.0 - t)
+                s.step(d)
+                t += d
+            got = s.get_state()
+        i = np.arange(n)
+        xc = (i + 0.5) * spec.dx
+        ex = np.exp(-0.01) * (2 / spec.dx) * math.sin(spec.dx / 2) * np.sin(xc - 1.0)
+        eb.append(np.mean(np.abs(got[0] - ex)))
+    if prec == "fp64":
+        assert min(_order(eb)) > 3.8
+    else:
+        assert eb[-1] < 1e-6     # FP32 stencils: round-off floor near 1e-7
+
+
+def test_fourth_order_2d_gpu():
+    errs = []
+    T = 0.05
+    for n in (32, 64, 128):
+        spec = ai.Spec(dim=2, nx=n, ny=n, flux=("linear", (1.0, 1.0)), diff=("const", (0.01,)),
+                       umin=-10, umax=10, limiter=False)
+        st = [a.numpy() for a in ai.mode_2d_state(spec, 2 * math.pi)]
+        dt = 0.2 * 0.9 / (1.0 / spec.dx + 0.01 / spec.dx ** 2)
+        with solver(spec, rk=54) as s:
+            s.set_state(st)
+            t = 0.0
+            while t < T - 1e-14:
+                d = min(dt, T - t)
+                s.step(d)
+                t += d
+            got = s.get_state()
+        k = 2 * math.pi
+        fx = math.sin(k * spec.dx / 2) / (k * spec.dx / 2)
+        xc = (np.arange(n) + 0.5) * spec.dx
+        ex = 1 + math.exp(-2 * k * k * 0.01 * T) * fx * fx * np.sin(k * (xc[None, :] + xc[:, None] - 2 * T))
+        errs.append(np.mean(np.abs(got[0] - ex)))
+    assert min(_order(errs)) > 3.8
+
+
+def test_table3_signs_gpu():
+    rows = {int(r[0]): [float(v) for v in r[1:]] for r in _golden("table3_minmax.txt")}
+    for n in (20, 40, 80):
+        spec = ai.Spec(dim=1, nx=n, x0=0, x1=1, flux=("linear", (1.0, 0.0)), diff=("none", ()), umin=1.0,
+                       umax=2.0, limiter=True)
+        fn = lambda x: 1 + torch.sin(2 * math.pi * x) ** 4
+        st = [ai.cell_average_1d(fn, spec).numpy(), ai.points_1d(fn, spec).numpy()]
+        with solver(spec, rk=54, cfl=0.33) as s:
+            s.set_state(st)
+            s.run(1.0)
+            lo, hi = s.bounds()
+        assert lo >= 1.0 and hi <= 2.0
+        spec.limiter = False
+        with solver(spec, rk=54, cfl=0.33) as s:
+            s.set_state(st)
+            s.run(1.0)
+            lo, hi = s.bounds()
+        assert lo - 1.0 == pytest.approx(rows[n][0], rel=0.05)
+        assert hi - 2.0 == pytest.approx(rows[n][1], rel=0.05)
