@@ -16,6 +16,7 @@ import json
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -27,13 +28,19 @@ sys.path.insert(0, ROOT)
 METRIC = "cell-stage updates/s + HBM roofline fraction, FP32/batched/learned vs plain FP64"
 UNIT = "cell-stage updates/s"
 FP64_PEAK_TFLOPS = 1.25     # GB300 non-tensor FP64 peak (nominal; a DFMA loop measured 1.19)
+# Algorithmic FP64 flops of one limited forward-Euler evaluation per cell on the
+# degenerate Burgers workload (adds, multiplies, divisions and exponentials counted by
+# the oracle's counting scalar on the 256^2 case; tests/test_bench_constants.py
+# recomputes it).
+FLOPS_PER_CELL_STAGE = 571.03
 # Algorithmic HBM bytes per cell-stage of SSP-RK3 (read the stage input and the RK
 # combination input once, write the output once; 10.67 value slots per 4 DoFs).
 BYTES_PER_CELL_STAGE = {"fp64": 85.33, "fp32_mixed": 53.33}
-# dram__bytes_read.sum + dram__bytes_write.sum per stage launch from the ncu capture
-# summarised in profiles/stage2d_fp64_burgers_1024.md (None until captured for this
-# kernel version).
-NCU_TRAFFIC_PER_LAUNCH = {"fp64": None, "fp32_mixed": None}
+# dram__bytes_read.sum + dram__bytes_write.sum of one stage launch (SSP-RK3 stage 2) from
+# the ncu captures summarised in profiles/stage2d_fp64_degenerate_burgers_1024.md and
+# profiles/stage2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
+# for any other size.
+NCU_TRAFFIC_PER_LAUNCH = {("fp64", 1024): 75.98e6, ("fp32_mixed", 2048): 226.72e6}
 
 
 def load_peaks():
@@ -50,17 +57,17 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="af_clocks_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -111,12 +118,6 @@ def max_over_ranks(value, device="cpu"):
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
-
-
-def oracle_flops_per_cell(spec, state, tau):
-    import oracle
-    fc = oracle.flop_count(spec, state, tau)
-    return (fc["add"] + fc["mul"] + fc["div"] + fc["exp"]) / spec.cells
 
 
 def run_gpu(args):
@@ -198,12 +199,11 @@ def run_gpu(args):
     avg_stage_s = statistics.mean(stage_ms) / 1e3
     result = None
     if rank == 0:
-        tau = 1e-4
-        fpc = oracle_flops_per_cell(ai.config2(256), [a.numpy() for a in ai.initial_state(ai.config2(256))], tau)
+        fpc = FLOPS_PER_CELL_STAGE
         if prec == "fp64":
             ach = fpc * cells / avg_stage_s / 1e12
             roof = {"bound": "alu", "achieved": round(ach, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC_PER_LAUNCH[prec],
+                    "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get((prec, args.n)),
                     "peak_source": "derived (GB300 FP64 non-tensor nominal)",
                     "flops_per_cell_stage": round(fpc, 1),
                     "hbm_view": {"achieved_gbs": round(BYTES_PER_CELL_STAGE[prec] * cells / avg_stage_s / 1e9, 1),
@@ -212,7 +212,7 @@ def run_gpu(args):
         else:
             ach = BYTES_PER_CELL_STAGE[prec] * cells / avg_stage_s / 1e9
             roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": NCU_TRAFFIC_PER_LAUNCH[prec],
+                    "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get((prec, args.n)),
                     "peak_source": peak_src}
         result = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -320,13 +320,25 @@ def forms(args, headline_value, peaks):
     """FP32-mixed, batched and learned forms of the metric, each with its speedup over
     the plain FP64 GPU form on the same workload and its L1 difference from FP64."""
     import torch
-    import af_inputs as ai
-    from paper_2510_11527_gb300 import capi
     stream = torch.cuda.Stream()
     res = {}
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sel = set(args.forms.split(","))
+    if "fp32" in sel:
+        res.update(_form_fp32(args, stream, flush, peaks))
+    if "pme" in sel:
+        res.update(_form_pme(args, stream, peaks))
+    if "batch" in sel:
+        res.update(_form_batch(args, stream, headline_value, peaks))
+    if "bl" in sel:
+        res.update(_form_bl(args, stream, peaks))
+    return res
 
-    # (1) degenerate Burgers 1024^2 in FP32-mixed (headline workload)
+
+def _form_fp32(args, stream, flush, peaks):
+    """Degenerate Burgers 1024^2 (the headline workload) in FP32-mixed."""
+    import af_inputs as ai
+    res = {}
     spec = ai.config2(1024)
     st = ai.initial_state(spec, device="cuda")
     s64, r64 = _single_form(spec, "fp64", args.form_steps, 3, st, stream, flush)
@@ -340,8 +352,13 @@ def forms(args, headline_value, peaks):
     s64.close()
     s32.close()
     del st, a64, a32
+    return res
 
-    # (2) porous medium 4096^2 (config 3) FP32-mixed vs FP64
+
+def _form_pme(args, stream, peaks):
+    """Porous medium 4096^2 from the Barenblatt profile, FP32-mixed vs FP64."""
+    import af_inputs as ai
+    res = {}
     spec = ai.config3(4096)
     st = ai.state_2d(lambda x, y: ai.barenblatt(x, y, 1.0), spec, device="cuda", sub=2, order=3)
     s64, r64 = _single_form(spec, "fp64", 2, 1, st, stream)
@@ -356,8 +373,15 @@ def forms(args, headline_value, peaks):
         "roofline": _hbm_roof("fp32_mixed", spec.cells, r32["stage_ms_avg"], peaks)}
     s32.close()
     del st
+    return res
 
-    # (3) batch of 256 uneven instances (config 4), FP32-mixed, graph replay, autotuned tile
+
+def _form_batch(args, stream, headline_value, peaks):
+    """256 uneven instances, FP32-mixed, graph replay, autotuned tile."""
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import capi
+    res = {}
     inst = ai.batch_instances()
     grids, fl, df, bd = [], [], [], []
     for s_, _ in inst:
@@ -404,8 +428,15 @@ def forms(args, headline_value, peaks):
             "roofline": _hbm_roof("fp32_mixed", cells, ms / args.form_steps / 3, peaks)}
     finally:
         capi.af_batch_destroy(b)
+    return res
 
-    # (4) Buckley-Leverett 4096^2 (config 5): plain vs learned blend, FP32-mixed
+
+def _form_bl(args, stream, peaks):
+    """Buckley-Leverett 4096^2: plain vs learned blend (trained here), FP32-mixed."""
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import capi
+    res = {}
     net = capi.af_mlp_create()
     try:
         capi.af_mlp_set_params(net, ai.mlp_init_params(1))
@@ -497,7 +528,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
@@ -505,6 +536,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/batched/learned forms")
     ap.add_argument("--form-steps", type=int, default=5)
+    ap.add_argument("--forms", default="fp32,pme,batch,bl",
+                    help="comma list of forms to run: fp32 (Burgers 1024^2), pme (4096^2), batch (256), bl (4096^2)")
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)

@@ -22,10 +22,11 @@ struct DevModel {
   double dp[4];          // diffusion parameters
   int ncrit[2];          // interior extrema of f_l' (Buckley-Leverett)
   double crit[2][8];
+  double critv[2][8];    // |f_l'| at those extrema
   double umin, umax;
   // the same parameters rounded to float, read by the FP32 stencils (GB300's FP64
   // unit also performs the double->float conversions, so none happen per use)
-  float fpf[4], dpf[4], critf[2][8];
+  float fpf[4], dpf[4], critf[2][8], critvf[2][8];
 };
 
 // parameter k of a double/float pair in the stencil precision T
@@ -39,7 +40,10 @@ inline void fill_float_params(DevModel& m) {
     m.dpf[k] = (float)m.dp[k];
   }
   for (int d = 0; d < 2; ++d)
-    for (int k = 0; k < 8; ++k) m.critf[d][k] = (float)m.crit[d][k];
+    for (int k = 0; k < 8; ++k) {
+      m.critf[d][k] = (float)m.crit[d][k];
+      m.critvf[d][k] = (float)m.critv[d][k];
+    }
 }
 
 // Comparisons, min and max of doubles run on the integer units through an
@@ -64,15 +68,47 @@ __device__ __forceinline__ double tabs(double a) {
 }
 __device__ __forceinline__ float tabs(float a) { return fabsf(a); }
 
-// exact float -> double with integer operations (denormals take the hardware path)
+// exact float -> double with integer operations only (finite inputs). A subnormal
+// float m * 2^-149 with leading bit p of m becomes the normal double
+// 1.f * 2^(p - 149); the FP64 unit is never used.
 __device__ __forceinline__ double f2d_exact(float f) {
   const unsigned int u = (unsigned int)__float_as_int(f);
   const unsigned int e = (u >> 23) & 0xFFu;
-  if (e == 0u) return (u & 0x7FFFFFu) ? (double)f : __longlong_as_double((long long)(u & 0x80000000u) << 32);
-  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
-                               ((unsigned long long)(e - 127u + 1023u) << 52) |
-                               ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  const unsigned int mant = u & 0x7FFFFFu;
+  const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+  if (e == 0u) {
+    if (mant == 0u) return __longlong_as_double((long long)s);
+    const int p = 31 - __clz((int)mant);
+    const unsigned long long fr = ((unsigned long long)mant << (52 - p)) & 0xFFFFFFFFFFFFFull;
+    return __longlong_as_double((long long)(s | ((unsigned long long)(p + 874) << 52) | fr));
+  }
+  const unsigned long long d = s | ((unsigned long long)(e - 127u + 1023u) << 52) | ((unsigned long long)mant << 29);
   return __longlong_as_double((long long)d);
+}
+
+// x == 0.0 (either sign) tested on the integer units
+__device__ __forceinline__ bool is_zero_bits(double x) { return (__double_as_longlong(x) << 1) == 0; }
+
+// Buckley-Leverett with gravity: f_1 = u^2 / (u^2 + (1-u)^2), f_2 = f_1 (1 - g (1-u)^2)
+// and |f_1'|, |f_2'|, from one reciprocal of the denominator.
+template <class T>
+struct BLVals {
+  T f[2], d[2];
+};
+template <class T>
+__device__ __forceinline__ BLVals<T> bl_eval(const DevModel& m, T u) {
+  const T v = T(1) - u, u2 = u * u;
+  const T rD = T(1) / (u2 + v * v);
+  const T g = par<T>(m.fp, m.fpf, 0);
+  const T w = T(1) - g * v * v;
+  const T f1 = u2 * rD;
+  const T d1 = T(2) * u * v * rD * rD;   // f_1'
+  BLVals<T> r;
+  r.f[0] = f1;
+  r.f[1] = f1 * w;
+  r.d[0] = tabs(d1);
+  r.d[1] = tabs(d1 * w + T(2) * g * v * f1);
+  return r;
 }
 
 // f_l(u)
@@ -83,11 +119,7 @@ __device__ __forceinline__ T flux(const DevModel& m, int dir, T u) {
   } else if constexpr (FLUX == FLUX_BURGERS) {
     return par<T>(m.fp, m.fpf, 0) * u * u;
   } else if constexpr (FLUX == FLUX_BL) {
-    T v = T(1) - u;
-    T u2 = u * u;
-    T f1 = u2 / (u2 + v * v);
-    if (dir == 0) return f1;
-    return f1 * (T(1) - par<T>(m.fp, m.fpf, 0) * v * v);
+    return bl_eval<T>(m, u).f[dir];
   } else {
     return T(0);
   }
@@ -101,14 +133,7 @@ __device__ __forceinline__ T dflux_abs(const DevModel& m, int dir, T u) {
   } else if constexpr (FLUX == FLUX_BURGERS) {
     return tabs(T(2) * par<T>(m.fp, m.fpf, 0) * u);
   } else if constexpr (FLUX == FLUX_BL) {
-    T v = T(1) - u;
-    T D = u * u + v * v;
-    T rD = T(1) / D;
-    T d1 = T(2) * u * v * rD * rD;
-    if (dir == 0) return tabs(d1);
-    T f1 = u * u * rD;
-    T g = par<T>(m.fp, m.fpf, 0);
-    return tabs(d1 * (T(1) - g * v * v) + T(2) * g * v * f1);
+    return bl_eval<T>(m, u).d[dir];
   } else {
     return T(0);
   }
@@ -140,23 +165,35 @@ __device__ __forceinline__ T apot(const DevModel& m, T u) {
   }
 }
 
-// max |f_l'| over [min(a,b), max(a,b)]: the end points plus the interior extrema of f_l'.
+// max |f_l'| over [min(a,b), max(a,b)] given the end-point values da = |f_l'(a)| and
+// db = |f_l'(b)|: the end points plus the interior extrema of f_l' that lie strictly
+// inside (their |f_l'| is tabulated in the model).
 template <int FLUX, class T>
-__device__ __forceinline__ T alpha_interval(const DevModel& m, int dir, T a, T b) {
+__device__ __forceinline__ T alpha_interval_pre(const DevModel& m, int dir, T a, T b, T da, T db) {
   if constexpr (FLUX == FLUX_LINEAR) {
     return tabs(par<T>(m.fp, m.fpf, dir == 0 ? 0 : 1));
   } else if constexpr (FLUX == FLUX_BURGERS) {
     return tabs(T(2) * par<T>(m.fp, m.fpf, 0)) * tmax(tabs(a), tabs(b));
   } else if constexpr (FLUX == FLUX_BL) {
-    T lo = tmin(a, b), hi = tmax(a, b);
-    T best = tmax(dflux_abs<FLUX, T>(m, dir, lo), dflux_abs<FLUX, T>(m, dir, hi));
+    const T lo = tmin(a, b), hi = tmax(a, b);
+    T best = tmax(da, db);
     for (int k = 0; k < m.ncrit[dir]; ++k) {
-      T c = par<T>(m.crit[dir], m.critf[dir], k);
-      if (c > lo && c < hi) best = tmax(best, dflux_abs<FLUX, T>(m, dir, c));
+      const T c = par<T>(m.crit[dir], m.critf[dir], k);
+      if (tlt(lo, c) && tlt(c, hi)) best = tmax(best, par<T>(m.critv[dir], m.critvf[dir], k));
     }
     return best;
   } else {
     return T(0);
+  }
+}
+
+// max |f_l'| over [min(a,b), max(a,b)]
+template <int FLUX, class T>
+__device__ __forceinline__ T alpha_interval(const DevModel& m, int dir, T a, T b) {
+  if constexpr (FLUX == FLUX_BL) {
+    return alpha_interval_pre<FLUX, T>(m, dir, a, b, dflux_abs<FLUX, T>(m, dir, a), dflux_abs<FLUX, T>(m, dir, b));
+  } else {
+    return alpha_interval_pre<FLUX, T>(m, dir, a, b, T(0), T(0));
   }
 }
 
@@ -169,6 +206,9 @@ __device__ __forceinline__ double rk_comb(double a, double x, double b, double y
 __device__ __forceinline__ float rk_comb(float a, float x, float b, float y) {
   return __fmaf_rn(a, x, __fmul_rn(b, y));
 }
+// a*x + y with one rounding (the point update z + tau R)
+__device__ __forceinline__ double rk_fma(double a, double x, double y) { return __fma_rn(a, x, y); }
+__device__ __forceinline__ float rk_fma(float a, float x, float y) { return __fmaf_rn(a, x, y); }
 __device__ __forceinline__ double rk_scale(double b, double y) { return __dmul_rn(b, y); }
 __device__ __forceinline__ float rk_scale(float b, float y) { return __fmul_rn(b, y); }
 
@@ -205,6 +245,27 @@ __device__ __forceinline__ T theta_fn(T zL, T zH, T umin, T umax) {
   if (den == T(0)) return T(1);
   T t = (zL - bound) / den;
   return tmin(tmax(t, T(0)), T(1));
+}
+
+template <class T>
+__device__ __forceinline__ bool inb(T z, T umin, T umax) {
+  return !tlt(z, umin) & !tlt(umax, z);
+}
+// min of Theta over two / four (zL, zH) pairs. In FP64 the common case (every zH inside
+// the bounds, so the minimum is 1) is tested first with integer compares; in FP32 the
+// plain evaluation measured as fast.
+template <class T>
+__device__ __forceinline__ T theta_pair(T a0, T a1, T b0, T b1, T umin, T umax) {
+  if constexpr (sizeof(T) == 8)
+    if (inb(a1, umin, umax) & inb(b1, umin, umax)) return T(1);
+  return tmin(theta_fn<T>(a0, a1, umin, umax), theta_fn<T>(b0, b1, umin, umax));
+}
+template <class T>
+__device__ __forceinline__ T theta_quad(T a0, T a1, T b0, T b1, T c0, T c1, T d0, T d1, T umin, T umax) {
+  if constexpr (sizeof(T) == 8)
+    if (inb(a1, umin, umax) & inb(b1, umin, umax) & inb(c1, umin, umax) & inb(d1, umin, umax)) return T(1);
+  return tmin(tmin(theta_fn<T>(a0, a1, umin, umax), theta_fn<T>(b0, b1, umin, umax)),
+              tmin(theta_fn<T>(c0, c1, umin, umax), theta_fn<T>(d0, d1, umin, umax)));
 }
 
 // Stage statistics accumulated on the device (safeguard clamp of Section 5's

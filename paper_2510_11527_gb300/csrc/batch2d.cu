@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "af.h"
+#include "model_host.h"
 #include "reduce.cuh"
 #include "stage2d.cuh"
 
@@ -92,34 +93,54 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchInst* __res
   }
 }
 
-// per-tile maximum of alpha_face / h + kappa_max / h^2 into rate_bits[instance]
+// per-tile part of the CFL rate (see dt_rate_kernel) into rate_bits[2 instance] and the
+// interior-extremum flags into rate_bits[2 instance + 1]
 template <int FLUX, int TX, int TY>
 __global__ void __launch_bounds__(256) batch_rate_kernel(const BatchInst* __restrict__ inst,
                                                          const int* __restrict__ work_inst, int total, int in,
                                                          unsigned long long* rate_bits) {
   __shared__ double sm[8];
+  __shared__ unsigned sf[8];
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const int k = work_inst[w];
     const BatchInst& I = inst[k];
     const int t = w - I.tile_begin;
     const int i = (t % I.tiles_x) * TX + (int)threadIdx.x % TX, j = (t / I.tiles_x) * TY + (int)threadIdx.x / TX;
     double best = 0.0;
+    unsigned flags = 0u;
     if (i < I.nx && j < I.ny) {
       const double* ub = I.ub[in];
       const double u = ub[(size_t)j * I.nx + i];
-      const double ux = ub[(size_t)j * I.nx + (i + 1 == I.nx ? 0 : i + 1)];
-      const double uy = ub[(size_t)(j + 1 == I.ny ? 0 : j + 1) * I.nx + i];
       const double kd1 = I.kmax * I.inv_h1 * I.inv_h1, kd2 = I.kmax * I.inv_h2 * I.inv_h2;
-      best = fmax(alpha_interval<FLUX, double>(I.m, 0, u, ux) * I.inv_h1 + kd1,
-                  alpha_interval<FLUX, double>(I.m, 1, u, uy) * I.inv_h2 + kd2);
+      double a1, a2;
+      if constexpr (FLUX == FLUX_BL) {
+        const BLVals<double> r = bl_eval<double>(I.m, u);
+        a1 = r.d[0];
+        a2 = r.d[1];
+        flags = crit_flags<FLUX>(I.m, 0, u, ub[(size_t)j * I.nx + (i + 1 == I.nx ? 0 : i + 1)]) |
+                (crit_flags<FLUX>(I.m, 1, u, ub[(size_t)(j + 1 == I.ny ? 0 : j + 1) * I.nx + i]) << 8);
+      } else {
+        a1 = alpha_interval<FLUX, double>(I.m, 0, u, u);
+        a2 = alpha_interval<FLUX, double>(I.m, 1, u, u);
+      }
+      best = tmax(a1 * I.inv_h1 + kd1, a2 * I.inv_h2 + kd2);
     }
-    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
-    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+    for (int o = 16; o > 0; o >>= 1) best = tmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    flags = __reduce_or_sync(0xffffffffu, flags);
+    if ((threadIdx.x & 31) == 0) {
+      sm[threadIdx.x >> 5] = best;
+      sf[threadIdx.x >> 5] = flags;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       double b = sm[0];
-      for (int q = 1; q < 8; ++q) b = fmax(b, sm[q]);
-      atomicMax(rate_bits + k, (unsigned long long)__double_as_longlong(b));
+      unsigned f = sf[0];
+      for (int q = 1; q < 8; ++q) {
+        b = tmax(b, sm[q]);
+        f |= sf[q];
+      }
+      atomicMax(rate_bits + 2 * k, (unsigned long long)__double_as_longlong(b));
+      if (f) atomicOr(rate_bits + 2 * k + 1, (unsigned long long)f);
     }
     __syncthreads();
   }
@@ -130,13 +151,15 @@ __global__ void batch_dt_kernel(const BatchInst* __restrict__ inst, int n, doubl
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const BatchInst& I = inst[k];
-  const double rate = __longlong_as_double((long long)rate_bits[k]);
+  const double rate = crit_rate(I.m, 2, I.inv_h1, I.inv_h2, I.kmax, rate_bits[2 * k + 1],
+                                __longlong_as_double((long long)rate_bits[2 * k]));
   double r = rate / cfl;
   if (cfl_diff > 0.0 && I.kmax > 0.0) r = fmax(r, I.kmax * I.inv_hmin2 / cfl_diff);
   const double dt = r > 0.0 ? 1.0 / r : 0.0;
   *I.dt = dt;
   *I.t += dt;
-  rate_bits[k] = 0ull;
+  rate_bits[2 * k] = 0ull;
+  rate_bits[2 * k + 1] = 0ull;
 }
 
 }  // namespace af
@@ -165,58 +188,6 @@ struct Shape {
   int tx, ty;
 };
 const Shape kShapes[] = {{32, 8}, {64, 4}, {16, 16}};
-
-double bl_d2(int dir, double g, double u) {
-  const double v = 1.0 - u, D = u * u + v * v, Dp = 2.0 * u - 2.0 * v;
-  const double f1 = u * u / D, d1 = 2.0 * u * v / (D * D);
-  const double dd1 = (2.0 * (v - u) * D - 4.0 * u * v * Dp) / (D * D * D);
-  if (dir == 0) return dd1;
-  return dd1 * (1.0 - g * v * v) + 4.0 * g * v * d1 - 2.0 * g * f1;
-}
-
-void bl_crit(DevModel& m) {
-  for (int d = 0; d < 2; ++d) {
-    m.ncrit[d] = 0;
-    const int n = 60000;
-    double xp = -1.0, yp = bl_d2(d, m.fp[0], xp);
-    for (int k = 1; k <= n && m.ncrit[d] < 8; ++k) {
-      const double x = -1.0 + 3.0 * k / n, y = bl_d2(d, m.fp[0], x);
-      if ((yp < 0.0 && y > 0.0) || (yp > 0.0 && y < 0.0)) {
-        double lo = xp, hi = x, flo = yp;
-        for (int it = 0; it < 200; ++it) {
-          const double mid = 0.5 * (lo + hi), fm = bl_d2(d, m.fp[0], mid);
-          if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
-        }
-        m.crit[d][m.ncrit[d]++] = 0.5 * (lo + hi);
-      }
-      xp = x;
-      yp = y;
-    }
-  }
-}
-
-double kappa_of(const af_diff& df, double u) {
-  switch (df.kind) {
-    case AF_DIFF_CONST: return df.p[0];
-    case AF_DIFF_PWL: return (u < df.p[1] ? df.p[0] : 0.0) + (u > df.p[3] ? df.p[2] : 0.0);
-    case AF_DIFF_PME: return df.p[0] * std::pow(u, df.p[0] - 1.0);
-    case AF_DIFF_CUBIC: return df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u;
-    default: return 0.0;
-  }
-}
-
-double kappa_max_of(const af_diff& df, double lo, double hi) {
-  double k = std::max(0.0, std::max(kappa_of(df, lo), kappa_of(df, hi)));
-  if (df.kind == AF_DIFF_PWL) {
-    if (lo < df.p[1]) k = std::max(k, df.p[0]);
-    if (hi > df.p[3]) k = std::max(k, df.p[2]);
-  }
-  if (df.kind == AF_DIFF_CUBIC && df.p[2] != 0.0) {
-    const double uv = -df.p[1] / (3.0 * df.p[2]);
-    if (uv > lo && uv < hi) k = std::max(k, kappa_of(df, uv));
-  }
-  return k;
-}
 
 }  // namespace
 
@@ -476,11 +447,10 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     I.m.flux_kind = fluxes[k].kind;
     I.m.diff_kind = diffs[k].kind;
     for (int q = 0; q < 4; ++q) { I.m.fp[q] = fluxes[k].p[q]; I.m.dp[q] = diffs[k].p[q]; }
-    if (fluxes[k].kind == AF_FLUX_BL) bl_crit(I.m);
-    af::fill_float_params(I.m);
     I.m.umin = bounds[k].umin;
     I.m.umax = bounds[k].umax;
-    I.kmax = kappa_max_of(diffs[k], bounds[k].umin, bounds[k].umax);
+    af::finish_model(I.m, fluxes[k].kind);
+    I.kmax = af::kappa_max_of(diffs[k], bounds[k].umin, bounds[k].umax);
     const double scale = std::max(std::fabs(bounds[k].umin), std::fabs(bounds[k].umax));
     I.tol = (b->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;
     for (int s = 0; s < b->nbuf; ++s) {
@@ -491,7 +461,7 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     }
   }
   bool ok = cudaMalloc(&b->d_inst, n * sizeof(BatchInst)) == cudaSuccess &&
-            cudaMalloc(&b->d_rate, n * sizeof(unsigned long long)) == cudaSuccess &&
+            cudaMalloc(&b->d_rate, 2 * n * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&b->d_dt, n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&b->d_t, n * sizeof(double)) == cudaSuccess &&
             cudaMalloc(&b->d_stats, sizeof(DevStats)) == cudaSuccess &&
@@ -503,7 +473,7 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     af_batch_destroy(b);
     return AF_E_OOM;
   }
-  cudaMemset(b->d_rate, 0, n * sizeof(unsigned long long));
+  cudaMemset(b->d_rate, 0, 2 * n * sizeof(unsigned long long));
   cudaMemset(b->d_dt, 0, n * sizeof(double));
   cudaMemset(b->d_t, 0, n * sizeof(double));
   cudaMemset(b->d_stats, 0, sizeof(DevStats));

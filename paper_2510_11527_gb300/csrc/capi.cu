@@ -11,6 +11,7 @@
 
 #include "af.h"
 #include "launch.h"
+#include "model_host.h"
 #include "reduce.cuh"
 
 using af::DevModel;
@@ -42,64 +43,6 @@ const double kB54[5][5] = {
 double default_cfl_diff(int dim, int rk) {
   if (dim == 1) return 0.9 * (rk == AF_RK_SSP54 ? 0.333 : 0.157);
   return 0.9 * (rk == AF_RK_SSP54 ? 0.1307 : 0.0616);
-}
-
-// Buckley-Leverett f_l'' (analytic) for locating the interior extrema of f_l'.
-double bl_d2(int dir, double g, double u) {
-  const double v = 1.0 - u, D = u * u + v * v, Dp = 2.0 * u - 2.0 * v;
-  const double f1 = u * u / D;
-  const double d1 = 2.0 * u * v / (D * D);
-  const double dd1 = (2.0 * (v - u) * D - 4.0 * u * v * Dp) / (D * D * D);
-  if (dir == 0) return dd1;
-  return dd1 * (1.0 - g * v * v) + 4.0 * g * v * d1 - 2.0 * g * f1;
-}
-
-// roots of f_l'' on [-1, 2]: sign changes on a uniform grid refined by bisection
-void bl_critical_points(DevModel& m) {
-  for (int d = 0; d < 2; ++d) {
-    m.ncrit[d] = 0;
-    const double g = m.fp[0];
-    const int n = 60000;
-    const double a = -1.0, b = 2.0;
-    double xprev = a, yprev = bl_d2(d, g, a);
-    for (int k = 1; k <= n && m.ncrit[d] < 8; ++k) {
-      const double x = a + (b - a) * k / n, y = bl_d2(d, g, x);
-      if ((yprev < 0.0 && y > 0.0) || (yprev > 0.0 && y < 0.0) || y == 0.0) {
-        double lo = xprev, hi = x, flo = yprev;
-        for (int it = 0; it < 200 && y != 0.0; ++it) {
-          const double mid = 0.5 * (lo + hi), fm = bl_d2(d, g, mid);
-          if ((fm < 0.0) == (flo < 0.0)) { lo = mid; flo = fm; } else { hi = mid; }
-        }
-        m.crit[d][m.ncrit[d]++] = y == 0.0 ? x : 0.5 * (lo + hi);
-      }
-      xprev = x;
-      yprev = y;
-    }
-  }
-}
-
-double kappa_of(const af_diff& df, double u) {
-  switch (df.kind) {
-    case AF_DIFF_CONST: return df.p[0];
-    case AF_DIFF_PWL: return (u < df.p[1] ? df.p[0] : 0.0) + (u > df.p[3] ? df.p[2] : 0.0);
-    case AF_DIFF_PME: return df.p[0] * std::pow(u, df.p[0] - 1.0);
-    case AF_DIFF_CUBIC: return df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u;
-    default: return 0.0;
-  }
-}
-
-// kappa_max over [umin, umax] in closed form (Section 5.1.1)
-double kappa_max_of(const af_diff& df, double lo, double hi) {
-  double k = std::max(0.0, std::max(kappa_of(df, lo), kappa_of(df, hi)));
-  if (df.kind == AF_DIFF_PWL) {
-    if (lo < df.p[1]) k = std::max(k, df.p[0]);
-    if (hi > df.p[3]) k = std::max(k, df.p[2]);
-  }
-  if (df.kind == AF_DIFF_CUBIC && df.p[2] != 0.0) {
-    const double uv = -df.p[1] / (3.0 * df.p[2]);
-    if (uv > lo && uv < hi) k = std::max(k, kappa_of(df, uv));
-  }
-  return k;
 }
 
 }  // namespace
@@ -276,8 +219,8 @@ af_status dt_device(af_ctx* c, double* dst, double* t_acc) {
   }
   CK(c, e);
   const double hmin = c->dim == 1 ? c->dx : std::min(c->dx, c->dy);
-  af::dt_finalize_kernel<<<1, 1, 0, c->stream>>>(c->rate_bits, c->cfl, c->cfl_diff, c->kmax, 1.0 / (hmin * hmin),
-                                                 dst, t_acc);
+  af::dt_finalize_kernel<<<1, 1, 0, c->stream>>>(c->rate_bits, c->m, c->dim, c->inv_h1, c->inv_h2, c->cfl,
+                                                 c->cfl_diff, c->kmax, 1.0 / (hmin * hmin), dst, t_acc);
   CK(c, cudaGetLastError());
   return AF_OK;
 }
@@ -349,12 +292,11 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->m.flux_kind = flux->kind;
   c->m.diff_kind = diff->kind;
   for (int k = 0; k < 4; ++k) { c->m.fp[k] = flux->p[k]; c->m.dp[k] = diff->p[k]; }
-  if (flux->kind == AF_FLUX_BL) bl_critical_points(c->m);
-  af::fill_float_params(c->m);
   c->bounds_pending = bounds->from_initial_data != 0;
   c->m.umin = bounds->umin;
   c->m.umax = bounds->umax;
-  if (!c->bounds_pending) c->kmax = kappa_max_of(*diff, bounds->umin, bounds->umax);
+  af::finish_model(c->m, flux->kind);
+  if (!c->bounds_pending) c->kmax = af::kappa_max_of(*diff, bounds->umin, bounds->umax);
   const double scale = std::max(std::fabs(bounds->umin), std::fabs(bounds->umax));
   c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;
 
@@ -380,7 +322,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->t_dev = (double*)p; p += al(8);
   c->red = (double*)p; p += al(8 * 8);
   c->partial = (double*)p; p += al(8 * af::RED_MAX_BLOCKS);
-  c->rate_bits = (unsigned long long*)p; p += al(8);
+  c->rate_bits = (unsigned long long*)p; p += al(16);
   c->stats = (DevStats*)p; p += al(sizeof(DevStats));
   c->s_ext = (double*)p; p += al(c->n * 8);
   if (cudaMemset(c->block, 0, total) != cudaSuccess || cudaMallocHost(&c->host_pinned, 8 * sizeof(double)) != cudaSuccess) {
@@ -429,7 +371,7 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
     if (!(hi > lo)) FAIL(c, AF_E_STATE, "bounds from initial data need max > min");
     c->m.umin = lo;
     c->m.umax = hi;
-    c->kmax = kappa_max_of(c->diff, lo, hi);
+    c->kmax = af::kappa_max_of(c->diff, lo, hi);
     const double scale = std::max(std::fabs(lo), std::fabs(hi));
     c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;
     c->bounds_pending = false;

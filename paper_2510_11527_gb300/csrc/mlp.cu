@@ -40,6 +40,10 @@ __device__ __forceinline__ int wrapm(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// FP32 copies of state values without the FP64 unit (truncating, as the stage kernels)
+__device__ __forceinline__ float to_f32(float x) { return x; }
+__device__ __forceinline__ float to_f32(double x) { return af::to_stencil<float>(x); }
+
 // normalised patch of cell (i, j) in FP32: (v_k - ub_ij) / (max_k |v_k| + 1e-13)
 template <class PT>
 __device__ __forceinline__ void gather(const double* __restrict__ ub, const PT* __restrict__ V,
@@ -48,17 +52,17 @@ __device__ __forceinline__ void gather(const double* __restrict__ ub, const PT* 
   float v[NIN];
 #pragma unroll
   for (int k = 0; k < 13; ++k)
-    v[k] = (float)ub[(size_t)wrapm(j + kPatchB[k], ny) * nx + wrapm(i + kPatchA[k], nx)];
+    v[k] = af::to_stencil<float>(ub[(size_t)wrapm(j + kPatchB[k], ny) * nx + wrapm(i + kPatchA[k], nx)]);
   const int im = wrapm(i - 1, nx), jm = wrapm(j - 1, ny);
   const size_t c = (size_t)j * nx + i;
-  v[13] = (float)V[(size_t)jm * nx + im];
-  v[14] = (float)V[(size_t)jm * nx + i];
-  v[15] = (float)V[(size_t)j * nx + im];
-  v[16] = (float)V[c];
-  v[17] = (float)X[(size_t)j * nx + im];
-  v[18] = (float)X[c];
-  v[19] = (float)Y[(size_t)jm * nx + i];
-  v[20] = (float)Y[c];
+  v[13] = to_f32(V[(size_t)jm * nx + im]);
+  v[14] = to_f32(V[(size_t)jm * nx + i]);
+  v[15] = to_f32(V[(size_t)j * nx + im]);
+  v[16] = to_f32(V[c]);
+  v[17] = to_f32(X[(size_t)j * nx + im]);
+  v[18] = to_f32(X[c]);
+  v[19] = to_f32(Y[(size_t)jm * nx + i]);
+  v[20] = to_f32(Y[c]);
   float sc = 0.0f;
 #pragma unroll
   for (int k = 0; k < NIN; ++k) sc = fmaxf(sc, fabsf(v[k]));
@@ -172,13 +176,15 @@ __global__ void __launch_bounds__(256) indicator_kernel(const double* __restrict
                                                         int ny, const __nv_bfloat16* __restrict__ w1q,
                                                         const __nv_bfloat16* __restrict__ w2q,
                                                         const float* __restrict__ params, double* __restrict__ out) {
-  __shared__ __align__(16) __nv_bfloat16 sx[8][16][40];
+  // each warp takes 32 cells per pass: every lane gathers one patch, then the network
+  // runs on the two 16-row blocks
+  __shared__ __align__(16) __nv_bfloat16 sx[8][32][40];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   NetFrags F;
   load_frags(F, w1q, w2q, params, lane);
   const long long n = (long long)nx * ny;
-  for (long long base = ((long long)blockIdx.x * 8 + warp) * 16; base < n; base += (long long)gridDim.x * 128) {
-    if (lane < 16) {
+  for (long long base = ((long long)blockIdx.x * 8 + warp) * 32; base < n; base += (long long)gridDim.x * 256) {
+    {
       const long long cell = base + lane;
       float f[NIN];
       if (cell < n) {
@@ -193,12 +199,15 @@ __global__ void __launch_bounds__(256) indicator_kernel(const double* __restrict
             pack_bf16(k < NIN ? f[k] : 0.f, k + 1 < NIN ? f[k + 1] : 0.f);
     }
     __syncwarp();
-    float s0, s8;
-    net_rows(F, sx[warp], lane, &s0, &s8);
-    if ((lane & 3) == 0) {
-      const long long r0 = base + (lane >> 2), r8 = r0 + 8;
-      if (r0 < n) out[r0] = (double)s0;
-      if (r8 < n) out[r8] = (double)s8;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float s0, s8;
+      net_rows(F, sx[warp] + 16 * h, lane, &s0, &s8);
+      if ((lane & 3) == 0) {
+        const long long r0 = base + 16 * h + (lane >> 2), r8 = r0 + 8;
+        if (r0 < n) out[r0] = af::f2d_exact(s0);
+        if (r8 < n) out[r8] = af::f2d_exact(s8);
+      }
     }
     __syncwarp();
   }
@@ -389,7 +398,7 @@ namespace af {
 cudaError_t mlp_indicator_launch(const af_ctx* c, const af_mlp* net, int buf, double* out) {
   if (c->dim != 2) return cudaErrorInvalidValue;
   const long long n = (long long)c->n;
-  const int grid = (int)std::min<long long>((n + 127) / 128, 152 * 16);
+  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
   if (c->prec == AF_PREC_FP64)
     indicator_kernel<double><<<grid, 256, 0, c->stream>>>(c->ub[buf], (const double*)c->pv[buf],
                                                           (const double*)c->px[buf], (const double*)c->py[buf],

@@ -1,0 +1,95 @@
+// Host-side completion of a DevModel: the interior extrema of f_l' for the
+// Buckley-Leverett flux (needed by the interval wave speed of the LLF flux, Section
+// 5.2 of arXiv 2510.11527), |f_l'| there, and the float copies of all parameters.
+#pragma once
+#include <algorithm>
+#include <cmath>
+
+#include "af_model.cuh"
+
+namespace af {
+
+// Buckley-Leverett f_l'' (analytic) for locating the interior extrema of f_l'.
+inline double bl_d2(int dir, double g, double u) {
+  const double v = 1.0 - u, D = u * u + v * v, Dp = 2.0 * u - 2.0 * v;
+  const double f1 = u * u / D;
+  const double d1 = 2.0 * u * v / (D * D);
+  const double dd1 = (2.0 * (v - u) * D - 4.0 * u * v * Dp) / (D * D * D);
+  if (dir == 0) return dd1;
+  return dd1 * (1.0 - g * v * v) + 4.0 * g * v * d1 - 2.0 * g * f1;
+}
+
+// |f_l'(u)| of the Buckley-Leverett flux
+inline double bl_dabs(int dir, double g, double u) {
+  const double v = 1.0 - u, D = u * u + v * v;
+  const double f1 = u * u / D, d1 = 2.0 * u * v / (D * D);
+  return std::fabs(dir == 0 ? d1 : d1 * (1.0 - g * v * v) + 2.0 * g * v * f1);
+}
+
+// roots of f_l'' on [-1, 2]: sign changes on a uniform grid refined by bisection
+inline void bl_critical_points(DevModel& m) {
+  for (int d = 0; d < 2; ++d) {
+    m.ncrit[d] = 0;
+    const double g = m.fp[0];
+    const int n = 60000;
+    const double a = -1.0, b = 2.0;
+    double xprev = a, yprev = bl_d2(d, g, a);
+    for (int k = 1; k <= n && m.ncrit[d] < 8; ++k) {
+      const double x = a + (b - a) * k / n, y = bl_d2(d, g, x);
+      if ((yprev < 0.0 && y > 0.0) || (yprev > 0.0 && y < 0.0) || y == 0.0) {
+        double lo = xprev, hi = x, flo = yprev;
+        for (int it = 0; it < 200 && y != 0.0; ++it) {
+          const double mid = 0.5 * (lo + hi), fm = bl_d2(d, g, mid);
+          if ((fm < 0.0) == (flo < 0.0)) {
+            lo = mid;
+            flo = fm;
+          } else {
+            hi = mid;
+          }
+        }
+        const double c = y == 0.0 ? x : 0.5 * (lo + hi);
+        m.critv[d][m.ncrit[d]] = bl_dabs(d, g, c);
+        m.crit[d][m.ncrit[d]++] = c;
+      }
+      xprev = x;
+      yprev = y;
+    }
+  }
+}
+
+// after fp/dp/umin/umax are set: flux-specific tables and float copies
+inline void finish_model(DevModel& m, int flux_kind) {
+  for (int d = 0; d < 2; ++d) {
+    m.ncrit[d] = 0;
+    for (int k = 0; k < 8; ++k) m.crit[d][k] = m.critv[d][k] = 0.0;
+  }
+  if (flux_kind == AF_FLUX_BL) bl_critical_points(m);
+  fill_float_params(m);
+}
+
+// kappa(u) = a'(u) of the diffusion kinds
+inline double kappa_of(const af_diff& df, double u) {
+  switch (df.kind) {
+    case AF_DIFF_CONST: return df.p[0];
+    case AF_DIFF_PWL: return (u < df.p[1] ? df.p[0] : 0.0) + (u > df.p[3] ? df.p[2] : 0.0);
+    case AF_DIFF_PME: return df.p[0] * std::pow(u, df.p[0] - 1.0);
+    case AF_DIFF_CUBIC: return df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u;
+    default: return 0.0;
+  }
+}
+
+// kappa_max over [umin, umax] in closed form (Section 5.1.1)
+inline double kappa_max_of(const af_diff& df, double lo, double hi) {
+  double k = std::max(0.0, std::max(kappa_of(df, lo), kappa_of(df, hi)));
+  if (df.kind == AF_DIFF_PWL) {
+    if (lo < df.p[1]) k = std::max(k, df.p[0]);
+    if (hi > df.p[3]) k = std::max(k, df.p[2]);
+  }
+  if (df.kind == AF_DIFF_CUBIC && df.p[2] != 0.0) {
+    const double uv = -df.p[1] / (3.0 * df.p[2]);
+    if (uv > lo && uv < hi) k = std::max(k, kappa_of(df, uv));
+  }
+  return k;
+}
+
+}  // namespace af

@@ -11,7 +11,25 @@ namespace af {
 constexpr int RED_THREADS = 256;
 constexpr int RED_MAX_BLOCKS = 1024;   // partial-result slots per reduction
 
-// max over faces of alpha_face / h + kappa_max / h^2 (non-negative -> integer max)
+// The CFL rate max over faces of alpha_face / h + kappa_max / h^2, with alpha_face =
+// max |f_l'| over the interval spanned by the two cell averages. Its maximum over all
+// faces equals the maximum over cells of |f_l'(u)| / h + kappa_max / h^2 (every cell
+// average is an end point of faces in both directions, and rounding is monotone),
+// together with |f_l'(c)| / h + kappa_max / h^2 for each interior extremum c of f_l'
+// that lies strictly inside some face interval. The kernel reduces the first term into
+// rate_bits[0] (non-negative doubles order like their bit patterns) and flags the
+// extrema met (bit 8 l + k) in rate_bits[1]; dt_finalize_kernel adds their terms.
+template <int FLUX>
+__device__ __forceinline__ unsigned crit_flags(const DevModel& m, int dir, double a, double b) {
+  unsigned f = 0u;
+  if constexpr (FLUX == FLUX_BL) {
+    const double lo = tmin(a, b), hi = tmax(a, b);
+    for (int k = 0; k < m.ncrit[dir]; ++k)
+      if (tlt(lo, m.crit[dir][k]) && tlt(m.crit[dir][k], hi)) f |= 1u << k;
+  }
+  return f;
+}
+
 template <int FLUX>
 __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, int dim, int nx, int ny,
                                                                double inv_h1, double inv_h2, double kmax,
@@ -19,40 +37,71 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
                                                                unsigned long long* rate_bits) {
   const size_t n = (size_t)nx * ny;
   double best = 0.0;
+  unsigned flags = 0u;
   const double kd1 = kmax * inv_h1 * inv_h1, kd2 = kmax * inv_h2 * inv_h2;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    const int i = (int)(k % nx), j = (int)(k / nx);
     const double u = ub[k];
-    const double ux = ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)];
-    best = fmax(best, alpha_interval<FLUX, double>(m, 0, u, ux) * inv_h1 + kd1);
-    if (dim == 2) {
-      const double uy = ub[(size_t)(j + 1 == ny ? 0 : j + 1) * nx + i];
-      best = fmax(best, alpha_interval<FLUX, double>(m, 1, u, uy) * inv_h2 + kd2);
+    double a1, a2;
+    if constexpr (FLUX == FLUX_BL) {
+      const BLVals<double> r = bl_eval<double>(m, u);
+      a1 = r.d[0];
+      a2 = r.d[1];
+      const int i = (int)(k % nx), j = (int)(k / nx);
+      flags |= crit_flags<FLUX>(m, 0, u, ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)]);
+      if (dim == 2) flags |= crit_flags<FLUX>(m, 1, u, ub[(size_t)(j + 1 == ny ? 0 : j + 1) * nx + i]) << 8;
+    } else {
+      a1 = alpha_interval<FLUX, double>(m, 0, u, u);
+      a2 = alpha_interval<FLUX, double>(m, 1, u, u);
     }
+    best = tmax(best, a1 * inv_h1 + kd1);
+    if (dim == 2) best = tmax(best, a2 * inv_h2 + kd2);
   }
-  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  for (int o = 16; o > 0; o >>= 1) best = tmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  flags = __reduce_or_sync(0xffffffffu, flags);
   __shared__ double sm[RED_THREADS / 32];
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = best;
+  __shared__ unsigned sf[RED_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) {
+    sm[threadIdx.x >> 5] = best;
+    sf[threadIdx.x >> 5] = flags;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double b = sm[0];
-    for (int w = 1; w < RED_THREADS / 32; ++w) b = fmax(b, sm[w]);
+    unsigned f = sf[0];
+    for (int w = 1; w < RED_THREADS / 32; ++w) {
+      b = tmax(b, sm[w]);
+      f |= sf[w];
+    }
     atomicMax(rate_bits, (unsigned long long)__double_as_longlong(b));
+    if (f) atomicOr(rate_bits + 1, (unsigned long long)f);
   }
 }
 
-// dt = 1 / max(rate / C, kappa_max / (h_min^2 Cd)). Resets the accumulator for the
-// next step.
-// When t_acc is given the step is also added to the simulated time.
-static __global__ void dt_finalize_kernel(unsigned long long* rate_bits, double cfl, double cfl_diff, double kmax,
-                                   double inv_hmin2, double* dt_out, double* t_acc) {
-  const double rate = __longlong_as_double((long long)*rate_bits);
+// rate over the flagged extrema (see dt_rate_kernel)
+__device__ __forceinline__ double crit_rate(const DevModel& m, int dim, double inv_h1, double inv_h2, double kmax,
+                                            unsigned long long flags, double rate) {
+  const double kd1 = kmax * inv_h1 * inv_h1, kd2 = kmax * inv_h2 * inv_h2;
+  for (int d = 0; d < dim; ++d)
+    for (int k = 0; k < m.ncrit[d]; ++k)
+      if ((flags >> (8 * d + k)) & 1ull)
+        rate = tmax(rate, d == 0 ? m.critv[0][k] * inv_h1 + kd1 : m.critv[1][k] * inv_h2 + kd2);
+  return rate;
+}
+
+// dt = 1 / max(rate / C, kappa_max / (h_min^2 Cd)). Resets the accumulators for the
+// next step. When t_acc is given the step is also added to the simulated time.
+static __global__ void dt_finalize_kernel(unsigned long long* rate_bits, const DevModel m, int dim, double inv_h1,
+                                          double inv_h2, double cfl, double cfl_diff, double kmax, double inv_hmin2,
+                                          double* dt_out, double* t_acc) {
+  const double rate =
+      crit_rate(m, dim, inv_h1, inv_h2, kmax, rate_bits[1], __longlong_as_double((long long)rate_bits[0]));
   double r = rate / cfl;
   if (cfl_diff > 0.0 && kmax > 0.0) r = fmax(r, kmax * inv_hmin2 / cfl_diff);
   const double dt = r > 0.0 ? 1.0 / r : 0.0;
   *dt_out = dt;
   if (t_acc) *t_acc += dt;
-  *rate_bits = 0ull;
+  rate_bits[0] = 0ull;
+  rate_bits[1] = 0ull;
 }
 
 // *dt = v and, when t_acc is given, *t_acc += v

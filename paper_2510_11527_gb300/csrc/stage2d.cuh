@@ -64,7 +64,7 @@ template <int FLUX> struct PointStore;
 template <> struct PointStore<FLUX_ZERO> { static constexpr int NQ = 1, NQU = 1; };
 template <> struct PointStore<FLUX_LINEAR> { static constexpr int NQ = 1, NQU = 1; };
 template <> struct PointStore<FLUX_BURGERS> { static constexpr int NQ = 2, NQU = 2; };   // f, a
-template <> struct PointStore<FLUX_BL> { static constexpr int NQ = 5, NQU = 3; };        // f1,f2,|f1'|,|f2'|,a
+template <> struct PointStore<FLUX_BL> { static constexpr int NQ = 5, NQU = 5; };        // f1,f2,|f1'|,|f2'|,a
 
 template <int FLUX, class T, bool BLEND, int TX_ = 32, int TY_ = 8>
 struct Tile2D {
@@ -102,6 +102,28 @@ template <int NT, class F>
 __device__ __forceinline__ void for_rect(int x0, int x1, int y0, int y1, F&& f) {
   const int w = x1 - x0, n = w * (y1 - y0);
   for (int k = threadIdx.x; k < n; k += NT) f(x0 + k % w, y0 + k / w);
+}
+
+// A rectangle [X0, X1) x [Y0, Y1) of box positions with the body applied to each.
+template <int X0_, int X1_, int Y0_, int Y1_, class F>
+struct Seg {
+  static constexpr int X0 = X0_, Y0 = Y0_, W = X1_ - X0_, N = (X1_ - X0_) * (Y1_ - Y0_);
+  F f;
+};
+template <int X0, int X1, int Y0, int Y1, class F>
+__device__ __forceinline__ Seg<X0, X1, Y0, Y1, F> seg(F f) {
+  return Seg<X0, X1, Y0, Y1, F>{f};
+}
+template <int NT, class S>
+__device__ __forceinline__ void for_seg(const S& s) {
+  for (int k = threadIdx.x; k < S::N; k += NT) s.f(S::X0 + k % S::W, S::Y0 + k / S::W);
+}
+// The independent loops of one phase, one after the other. (Merging them into one
+// balanced iteration space was measured slower on GB300: the per-item dispatch costs
+// more branches than the shorter barrier waits save.)
+template <int NT, class... Ss>
+__device__ __forceinline__ void for_segs(const Ss&... ss) {
+  (for_seg<NT>(ss), ...);
 }
 
 // periodic index; the halo never reaches further than one period except on meshes
@@ -151,7 +173,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   auto Q = [&](int type, int k) -> T* { return sQ + (size_t)(type * NQ + k) * BN; };
 
   const double dtv = *A.dt;
-  if (dtv == 0.0) return;
+  if (is_zero_bits(dtv)) return;
   const int nx = A.nx, ny = A.ny;
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
@@ -198,14 +220,32 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   }
 
   // ---- P0: load the halo box --------------------------------------------------------
-  for (int k = tid; k < BN; k += NT) {
-    const int bx = k % BX, by = k / BX;
-    const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
-    const size_t g = (size_t)gj * nx + gi;
-    sU[k] = to_stencil<T>(A.ub[g]);
-    sZ[0][k] = T(A.V[g]);
-    sZ[1][k] = T(A.X[g]);
-    sZ[2][k] = T(A.Y[g]);
+  // all loads of a thread are issued before the first store, so their latencies overlap
+  constexpr int NP0 = (BN + NT - 1) / NT;
+  double ldU[NP0];
+  PT ldV[NP0], ldX[NP0], ldY[NP0];
+#pragma unroll
+  for (int it = 0; it < NP0; ++it) {
+    const int k = tid + it * NT;
+    if (k < BN) {
+      const int bx = k % BX, by = k / BX;
+      const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
+      const size_t g = (size_t)gj * nx + gi;
+      ldU[it] = A.ub[g];
+      ldV[it] = A.V[g];
+      ldX[it] = A.X[g];
+      ldY[it] = A.Y[g];
+    }
+  }
+#pragma unroll
+  for (int it = 0; it < NP0; ++it) {
+    const int k = tid + it * NT;
+    if (k < BN) {
+      sU[k] = to_stencil<T>(ldU[it]);
+      sZ[0][k] = T(ldV[it]);
+      sZ[1][k] = T(ldX[it]);
+      sZ[2][k] = T(ldY[it]);
+    }
   }
   __syncthreads();
   const T umin = sc.umin, umax = sc.umax;
@@ -216,40 +256,14 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     if constexpr (FLUX == FLUX_BURGERS) {
       Q(type, 0)[b] = flux<FLUX, T>(m, 0, z);
     } else if constexpr (FLUX == FLUX_BL) {
-      Q(type, 0)[b] = flux<FLUX, T>(m, 0, z);
-      Q(type, 1)[b] = flux<FLUX, T>(m, 1, z);
-      Q(type, 2)[b] = dflux_abs<FLUX, T>(m, 0, z);
-      Q(type, 3)[b] = dflux_abs<FLUX, T>(m, 1, z);
+      const BLVals<T> r = bl_eval<T>(m, z);
+      Q(type, 0)[b] = r.f[0];
+      Q(type, 1)[b] = r.f[1];
+      Q(type, 2)[b] = r.d[0];
+      Q(type, 3)[b] = r.d[1];
     }
     Q(type, NQ - 1)[b] = apot<T>(m, z);
   };
-  for (int k = tid; k < BN; k += NT) {
-    const T u = sU[k];
-    if constexpr (FLUX == FLUX_BURGERS) {
-      sQU[k] = flux<FLUX, T>(m, 0, u);
-    } else if constexpr (FLUX == FLUX_BL) {
-      sQU[k] = flux<FLUX, T>(m, 0, u);
-      sQU[BN + k] = flux<FLUX, T>(m, 1, u);
-    }
-    sQU[(L::NQU - 1) * BN + k] = apot<T>(m, u);
-  }
-  for_rect<NT>(H - 2, H + TX + 1, H - 2, H + TY + 1, [&](int bx, int by) {
-    const int b = by * BX + bx;
-    eval_point(0, b);
-    eval_point(1, b);
-    eval_point(2, b);
-  });
-  for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
-    const int b = by * BX + bx;
-    const T* V = sZ[0];
-    const T* X = sZ[1];
-    const T* Y = sZ[2];
-    // z_ij = [36 zbar - 4 (X_{i-1,j} + X_ij + Y_{i,j-1} + Y_ij) - (four corners)] / 16
-    const T c = (T(36) * sU[b] - T(4) * ((X[b - 1] + X[b]) + (Y[b - BX] + Y[b])) -
-                 ((V[b - BX - 1] + V[b - BX]) + (V[b - 1] + V[b]))) * T(0.0625);
-    sZ[3][b] = c;
-    eval_point(3, b);
-  });
   T* sS1 = nullptr;
   T* sS2 = nullptr;
   T* sTC1 = nullptr;
@@ -263,17 +277,56 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     sTC2 = arr(L::A_BL0 + 3);
     sTD1 = arr(L::A_BL0 + 4);
     sTD2 = arr(L::A_BL0 + 5);
+  }
+  const auto p1_qu = seg<0, BX, 0, BY>([&](int bx, int by) {
+    const int k = by * BX + bx;
+    const T u = sU[k];
+    if constexpr (FLUX == FLUX_BURGERS) {
+      sQU[k] = flux<FLUX, T>(m, 0, u);
+    } else if constexpr (FLUX == FLUX_BL) {
+      const BLVals<T> r = bl_eval<T>(m, u);
+      sQU[k] = r.f[0];
+      sQU[BN + k] = r.f[1];
+      sQU[2 * BN + k] = r.d[0];
+      sQU[3 * BN + k] = r.d[1];
+    }
+    sQU[(L::NQU - 1) * BN + k] = apot<T>(m, u);
+  });
+  const auto p1_pts = seg<H - 2, H + TX + 1, H - 2, H + TY + 1>([&](int bx, int by) {
+    const int b = by * BX + bx;
+    eval_point(0, b);
+    eval_point(1, b);
+    eval_point(2, b);
+  });
+  const auto p1_ctr = seg<H - 1, H + TX + 1, H - 1, H + TY + 1>([&](int bx, int by) {
+    const int b = by * BX + bx;
+    const T* V = sZ[0];
+    const T* X = sZ[1];
+    const T* Y = sZ[2];
+    // z_ij = [36 zbar - 4 (X_{i-1,j} + X_ij + Y_{i,j-1} + Y_ij) - (four corners)] / 16
+    const T c = (T(36) * sU[b] - T(4) * ((X[b - 1] + X[b]) + (Y[b - BX] + Y[b])) -
+                 ((V[b - BX - 1] + V[b - BX]) + (V[b - 1] + V[b]))) * T(0.0625);
+    sZ[3][b] = c;
+    eval_point(3, b);
+  });
+  if constexpr (BLEND) {
     if (!A.blend_external) {
       // s~_l = |u_- - 2u + u_+| / (|u_-| + 2|u| + |u_+| + 1e-13) (Section 5.1.3); kept
       // temporarily in the TC arrays
-      for_rect<NT>(1, BX - 1, 1, BY - 1, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        const T u = sU[b];
-        const T au2 = T(2) * tabs(u);
-        sTC1[b] = tabs(sU[b - 1] - T(2) * u + sU[b + 1]) / (tabs(sU[b - 1]) + au2 + tabs(sU[b + 1]) + T(1e-13));
-        sTC2[b] = tabs(sU[b - BX] - T(2) * u + sU[b + BX]) / (tabs(sU[b - BX]) + au2 + tabs(sU[b + BX]) + T(1e-13));
-      });
+      for_segs<NT>(p1_qu, p1_pts, p1_ctr, seg<1, BX - 1, 1, BY - 1>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     const T u = sU[b];
+                     const T au2 = T(2) * tabs(u);
+                     sTC1[b] = tabs(sU[b - 1] - T(2) * u + sU[b + 1]) /
+                               (tabs(sU[b - 1]) + au2 + tabs(sU[b + 1]) + T(1e-13));
+                     sTC2[b] = tabs(sU[b - BX] - T(2) * u + sU[b + BX]) /
+                               (tabs(sU[b - BX]) + au2 + tabs(sU[b + BX]) + T(1e-13));
+                   }));
+    } else {
+      for_segs<NT>(p1_qu, p1_pts, p1_ctr);
     }
+  } else {
+    for_segs<NT>(p1_qu, p1_pts, p1_ctr);
   }
   __syncthreads();
 
@@ -292,7 +345,8 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     const T z0 = sZ[t0][b0], z1 = sZ[t1][b1], z2 = sZ[t2][b2], z3 = sZ[t3][b3], z4 = sZ[t4][b4];
     T alpha;
     if constexpr (FLUX == FLUX_BURGERS) {
-      alpha = T(tabs(2.0 * m.fp[0])) *
+      // |2 p0| rounded to T equals |2 T(p0)| (scaling by 2 is exact)
+      alpha = tabs(T(2) * par<T>(m.fp, m.fpf, 0)) *
               tmax(tmax(tmax(tabs(z0), tabs(z1)), tmax(tabs(z3), tabs(z4))), tabs(z2));
     } else if constexpr (FLUX == FLUX_BL) {
       const int k = 2 + dir;
@@ -328,13 +382,23 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     else return flux<FLUX, T>(m, dir, sU[b]);
   };
   auto aU = [&](int b) -> T { return sQU[(L::NQU - 1) * BN + b]; };
+  // |f_dir'| at a cell average (stored for the Buckley-Leverett flux only)
+  auto dU = [&](int b, int dir) -> T {
+    if constexpr (FLUX == FLUX_BL) return sQU[(2 + dir) * BN + b];
+    else return T(0);
+  };
+  // |f_dir'| at a stored point
+  auto Dz = [&](int type, int b, int dir) -> T {
+    if constexpr (FLUX == FLUX_BL) return Q(type, 2 + dir)[b];
+    else return T(0);
+  };
   const T sixth = T(1.0 / 6.0), r36 = T(1.0 / 36.0);
   // x-faces (Simpson over the face: V below, X middle, V above)
-  for_rect<NT>(H - 1, H + TX, H, H + TY, [&](int bx, int by) {
+  const auto p2_fh1 = seg<H - 1, H + TX, H, H + TY>([&](int bx, int by) {
     const int b = by * BX + bx;
     sFH1[b] = (Fz(tV, b - BX, 0) + T(4) * Fz(tX, b, 0) + Fz(tV, b, 0)) * sixth;
   });
-  for_rect<NT>(H, H + TX, H - 1, H + TY, [&](int bx, int by) {
+  const auto p2_fh2 = seg<H, H + TX, H - 1, H + TY>([&](int bx, int by) {
     const int b = by * BX + bx;
     sFH2[b] = (Fz(tV, b - 1, 1) + T(4) * Fz(tY, b, 1) + Fz(tV, b, 1)) * sixth;
   });
@@ -347,37 +411,41 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     return dir == 0 ? (T(8) * sy - T(4) * sx + T(32) * ac - sv) * r36
                     : (T(8) * sx - T(4) * sy + T(32) * ac - sv) * r36;
   };
-  for_rect<NT>(H - 1, H + TX + 1, H, H + TY, [&](int bx, int by) { sAH1[by * BX + bx] = pot(by * BX + bx, 0); });
-  for_rect<NT>(H, H + TX, H - 1, H + TY + 1, [&](int bx, int by) { sAH2[by * BX + bx] = pot(by * BX + bx, 1); });
+  const auto p2_ah1 = seg<H - 1, H + TX + 1, H, H + TY>([&](int bx, int by) { sAH1[by * BX + bx] = pot(by * BX + bx, 0); });
+  const auto p2_ah2 = seg<H, H + TX, H - 1, H + TY + 1>([&](int bx, int by) { sAH2[by * BX + bx] = pot(by * BX + bx, 1); });
   // LLF fluxes with the interval wave speed
-  for_rect<NT>(H - 2, H + TX + 1, H, H + TY, [&](int bx, int by) {
+  const auto p2_fl1 = seg<H - 2, H + TX + 1, H, H + TY>([&](int bx, int by) {
     const int b = by * BX + bx;
     const T ul = sU[b], ur = sU[b + 1];
-    const T al = alpha_interval<FLUX, T>(m, 0, ul, ur);
+    const T al = alpha_interval_pre<FLUX, T>(m, 0, ul, ur, dU(b, 0), dU(b + 1, 0));
     sFL1[b] = T(0.5) * (fU(b, 0) + fU(b + 1, 0)) - T(0.5) * al * (ur - ul);
   });
-  for_rect<NT>(H, H + TX, H - 2, H + TY + 1, [&](int bx, int by) {
+  const auto p2_fl2 = seg<H, H + TX, H - 2, H + TY + 1>([&](int bx, int by) {
     const int b = by * BX + bx;
     const T ul = sU[b], ur = sU[b + BX];
-    const T al = alpha_interval<FLUX, T>(m, 1, ul, ur);
+    const T al = alpha_interval_pre<FLUX, T>(m, 1, ul, ur, dU(b, 1), dU(b + BX, 1));
     sFL2[b] = T(0.5) * (fU(b, 1) + fU(b + BX, 1)) - T(0.5) * al * (ur - ul);
   });
   if constexpr (BLEND) {
     if (A.blend_external) {
-      for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
-        const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
-        const T s = T(A.s_ext[(size_t)gj * nx + gi]);
-        sS1[by * BX + bx] = s;
-        sS2[by * BX + bx] = s;
-      });
+      for_segs<NT>(p2_fh1, p2_fh2, p2_ah1, p2_ah2, p2_fl1, p2_fl2,
+                   seg<H - 1, H + TX + 1, H - 1, H + TY + 1>([&](int bx, int by) {
+                     const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
+                     const T s = T(A.s_ext[(size_t)gj * nx + gi]);
+                     sS1[by * BX + bx] = s;
+                     sS2[by * BX + bx] = s;
+                   }));
     } else {
       // s_l = (s~_{-1} + 4 s~ + s~_{+1}) / 6 along direction l
-      for_rect<NT>(H - 1, H + TX + 1, H - 1, H + TY + 1, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        sS1[b] = (sTC1[b - 1] + T(4) * sTC1[b] + sTC1[b + 1]) * sixth;
-        sS2[b] = (sTC2[b - BX] + T(4) * sTC2[b] + sTC2[b + BX]) * sixth;
-      });
+      for_segs<NT>(p2_fh1, p2_fh2, p2_ah1, p2_ah2, p2_fl1, p2_fl2,
+                   seg<H - 1, H + TX + 1, H - 1, H + TY + 1>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     sS1[b] = (sTC1[b - 1] + T(4) * sTC1[b] + sTC1[b + 1]) * sixth;
+                     sS2[b] = (sTC2[b - BX] + T(4) * sTC2[b] + sTC2[b + BX]) * sixth;
+                   }));
     }
+  } else {
+    for_segs<NT>(p2_fh1, p2_fh2, p2_ah1, p2_ah2, p2_fl1, p2_fl2);
   }
   __syncthreads();
 
@@ -395,49 +463,52 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     });
     __syncthreads();
     // ---- P2c: blended fluxes/potentials (in place) and blended point residuals
-    for_rect<NT>(H - 1, H + TX, H, H + TY, [&](int bx, int by) {
-      const int b = by * BX + bx;
-      const T t = sTC1[b];
-      sFH1[b] = t * sFH1[b] + (T(1) - t) * sFL1[b];
-    });
-    for_rect<NT>(H, H + TX, H - 1, H + TY, [&](int bx, int by) {
-      const int b = by * BX + bx;
-      const T t = sTC2[b];
-      sFH2[b] = t * sFH2[b] + (T(1) - t) * sFL2[b];
-    });
-    for_rect<NT>(H - 1, H + TX + 1, H, H + TY, [&](int bx, int by) {
-      const int b = by * BX + bx;
-      const T t = sTD1[b];
-      sAH1[b] = t * sAH1[b] + (T(1) - t) * aU(b);
-    });
-    for_rect<NT>(H, H + TX, H - 1, H + TY + 1, [&](int bx, int by) {
-      const int b = by * BX + bx;
-      const T t = sTD2[b];
-      sAH2[b] = t * sAH2[b] + (T(1) - t) * aU(b);
-    });
+    for_segs<NT>(seg<H - 1, H + TX, H, H + TY>([&](int bx, int by) {
+                   const int b = by * BX + bx;
+                   const T t = sTC1[b];
+                   sFH1[b] = t * sFH1[b] + (T(1) - t) * sFL1[b];
+                 }),
+                 seg<H, H + TX, H - 1, H + TY>([&](int bx, int by) {
+                   const int b = by * BX + bx;
+                   const T t = sTC2[b];
+                   sFH2[b] = t * sFH2[b] + (T(1) - t) * sFL2[b];
+                 }),
+                 seg<H - 1, H + TX + 1, H, H + TY>([&](int bx, int by) {
+                   const int b = by * BX + bx;
+                   const T t = sTD1[b];
+                   sAH1[b] = t * sAH1[b] + (T(1) - t) * aU(b);
+                 }),
+                 seg<H, H + TX, H - 1, H + TY + 1>([&](int bx, int by) {
+                   const int b = by * BX + bx;
+                   const T t = sTD2[b];
+                   sAH2[b] = t * sAH2[b] + (T(1) - t) * aU(b);
+                 }));
     // first-order point residual on the +-h/2 neighbours (centre -> cell average):
     //   -(2/h)[F(z0,z+) - F(z-,z0)] + (4/h^2)(a+ - 2 a0 + a-)
     const T i2h1 = sc.i2h1, i2h2 = sc.i2h2;
     const T i4h21 = sc.i4h21, i4h22 = sc.i4h22;
-    auto lowres = [&](int dir, T zm, T fm, T am, T z0, T f0, T a0, T zp, T fp, T ap) -> T {
-      const T Fr = T(0.5) * (f0 + fp) - T(0.5) * alpha_interval<FLUX, T>(m, dir, z0, zp) * (zp - z0);
-      const T Fl = T(0.5) * (fm + f0) - T(0.5) * alpha_interval<FLUX, T>(m, dir, zm, z0) * (z0 - zm);
-      return (ap - T(2) * a0 + am) * (dir == 0 ? i4h21 : i4h22) - (Fr - Fl) * (dir == 0 ? i2h1 : i2h2);
+    // value, flux, potential and |f'| (direction dir) at a stored point / a cell average
+    struct PV {
+      T z, f, a, d;
     };
-    auto PZ = [&](int type, int b) { return sZ[type][b]; };
+    auto pt = [&](int type, int bb, int dir) -> PV {
+      return PV{sZ[type][bb], Fz(type, bb, dir), Az(type, bb), Dz(type, bb, dir)};
+    };
+    auto cu = [&](int bb, int dir) -> PV { return PV{sU[bb], fU(bb, dir), aU(bb), dU(bb, dir)}; };
+    auto lowres = [&](int dir, const PV& pm, const PV& p0, const PV& pp) -> T {
+      const T Fr = T(0.5) * (p0.f + pp.f) -
+                   T(0.5) * alpha_interval_pre<FLUX, T>(m, dir, p0.z, pp.z, p0.d, pp.d) * (pp.z - p0.z);
+      const T Fl = T(0.5) * (pm.f + p0.f) -
+                   T(0.5) * alpha_interval_pre<FLUX, T>(m, dir, pm.z, p0.z, pm.d, p0.d) * (p0.z - pm.z);
+      return (pp.a - T(2) * p0.a + pm.a) * (dir == 0 ? i4h21 : i4h22) - (Fr - Fl) * (dir == 0 ? i2h1 : i2h2);
+    };
     const int b = bo;
-    const T LV1 = lowres(0, PZ(tY, b), Fz(tY, b, 0), Az(tY, b), PZ(tV, b), Fz(tV, b, 0), Az(tV, b), PZ(tY, b + 1),
-                         Fz(tY, b + 1, 0), Az(tY, b + 1));
-    const T LV2 = lowres(1, PZ(tX, b), Fz(tX, b, 1), Az(tX, b), PZ(tV, b), Fz(tV, b, 1), Az(tV, b), PZ(tX, b + BX),
-                         Fz(tX, b + BX, 1), Az(tX, b + BX));
-    const T LX1 = lowres(0, sU[b], fU(b, 0), aU(b), PZ(tX, b), Fz(tX, b, 0), Az(tX, b), sU[b + 1], fU(b + 1, 0),
-                         aU(b + 1));
-    const T LX2 = lowres(1, PZ(tV, b - BX), Fz(tV, b - BX, 1), Az(tV, b - BX), PZ(tX, b), Fz(tX, b, 1), Az(tX, b),
-                         PZ(tV, b), Fz(tV, b, 1), Az(tV, b));
-    const T LY1 = lowres(0, PZ(tV, b - 1), Fz(tV, b - 1, 0), Az(tV, b - 1), PZ(tY, b), Fz(tY, b, 0), Az(tY, b),
-                         PZ(tV, b), Fz(tV, b, 0), Az(tV, b));
-    const T LY2 = lowres(1, sU[b], fU(b, 1), aU(b), PZ(tY, b), Fz(tY, b, 1), Az(tY, b), sU[b + BX], fU(b + BX, 1),
-                         aU(b + BX));
+    const T LV1 = lowres(0, pt(tY, b, 0), pt(tV, b, 0), pt(tY, b + 1, 0));
+    const T LV2 = lowres(1, pt(tX, b, 1), pt(tV, b, 1), pt(tX, b + BX, 1));
+    const T LX1 = lowres(0, cu(b, 0), pt(tX, b, 0), cu(b + 1, 0));
+    const T LX2 = lowres(1, pt(tV, b - BX, 1), pt(tX, b, 1), pt(tV, b, 1));
+    const T LY1 = lowres(0, pt(tV, b - 1, 0), pt(tY, b, 0), pt(tV, b, 0));
+    const T LY2 = lowres(1, cu(b, 1), pt(tY, b, 1), cu(b + BX, 1));
     const T wV1 = tmin(sTC1[b], sTC1[b + BX]), wV2 = tmin(sTC2[b], sTC2[b + 1]);
     const T wX1 = sTC1[b], wX2 = tmin(sTD2[b], sTD2[b + 1]);
     const T wY1 = tmin(sTD1[b], sTD1[b + BX]), wY2 = sTC2[b];
@@ -472,53 +543,49 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     if (A.limiter) {
       // ---- P3: directional low-order states u^{L,+-}_l = ub -+ 4 mu (...) +- 4 nu (...)
       const T m4_1 = sc.m4_1[o], n4_1 = sc.n4_1[o], m4_2 = sc.m4_2[o], n4_2 = sc.n4_2[o];
-      for_rect<NT>(H - 2, H + TX + 2, H, H + TY, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        const T u = sU[b], f = fU(b, 0), a = aU(b);
-        if (bx < H + TX + 1) sULp1[b] = u - m4_1 * (sFL1[b] - f) + n4_1 * (aU(b + 1) - a);
-        if (bx > H - 2) sULm1[b] = u - m4_1 * (f - sFL1[b - 1]) - n4_1 * (a - aU(b - 1));
-      });
-      for_rect<NT>(H, H + TX, H - 2, H + TY + 2, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        const T u = sU[b], f = fU(b, 1), a = aU(b);
-        if (by < H + TY + 1) sULp2[b] = u - m4_2 * (sFL2[b] - f) + n4_2 * (aU(b + BX) - a);
-        if (by > H - 2) sULm2[b] = u - m4_2 * (f - sFL2[b - BX]) - n4_2 * (a - aU(b - BX));
-      });
+      for_segs<NT>(seg<H - 2, H + TX + 2, H, H + TY>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     const T u = sU[b], f = fU(b, 0), a = aU(b);
+                     if (bx < H + TX + 1) sULp1[b] = u - m4_1 * (sFL1[b] - f) + n4_1 * (aU(b + 1) - a);
+                     if (bx > H - 2) sULm1[b] = u - m4_1 * (f - sFL1[b - 1]) - n4_1 * (a - aU(b - 1));
+                   }),
+                   seg<H, H + TX, H - 2, H + TY + 2>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     const T u = sU[b], f = fU(b, 1), a = aU(b);
+                     if (by < H + TY + 1) sULp2[b] = u - m4_2 * (sFL2[b] - f) + n4_2 * (aU(b + BX) - a);
+                     if (by > H - 2) sULm2[b] = u - m4_2 * (f - sFL2[b - BX]) - n4_2 * (a - aU(b - BX));
+                   }));
       __syncthreads();
       // ---- P4: theta^c per face (2 states), theta^d per cell (4 states), factor 12
       const T k1 = sc.k1[o], k2 = sc.k2[o], q1 = sc.q1[o], q2 = sc.q2[o];
-      for_rect<NT>(H - 1, H + TX, H, H + TY, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        const T fh = sFH1[b], fl = sFL1[b], dF = fh - fl;
-        const T zp = sULp1[b], zm = sULm1[b + 1];
-        const T t = tmin(theta_fn<T>(zp, zp - k1 * dF, umin, umax), theta_fn<T>(zm, zm + k1 * dF, umin, umax));
-        sFlim1[b] = is_one(t) ? fh : fl + t * dF;
-      });
-      for_rect<NT>(H, H + TX, H - 1, H + TY, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        const T fh = sFH2[b], fl = sFL2[b], dF = fh - fl;
-        const T zp = sULp2[b], zm = sULm2[b + BX];
-        const T t = tmin(theta_fn<T>(zp, zp - k2 * dF, umin, umax), theta_fn<T>(zm, zm + k2 * dF, umin, umax));
-        sFlim2[b] = is_one(t) ? fh : fl + t * dF;
-      });
-      for_rect<NT>(H - 1, H + TX + 1, H, H + TY, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        const T ah = sAH1[b], al = aU(b), d = q1 * (ah - al);
-        const T t = tmin(tmin(theta_fn<T>(sULp1[b - 1], sULp1[b - 1] + d, umin, umax),
-                              theta_fn<T>(sULp1[b], sULp1[b] - d, umin, umax)),
-                         tmin(theta_fn<T>(sULm1[b], sULm1[b] - d, umin, umax),
-                              theta_fn<T>(sULm1[b + 1], sULm1[b + 1] + d, umin, umax)));
-        sAlim1[b] = is_one(t) ? ah : al + t * (ah - al);
-      });
-      for_rect<NT>(H, H + TX, H - 1, H + TY + 1, [&](int bx, int by) {
-        const int b = by * BX + bx;
-        const T ah = sAH2[b], al = aU(b), d = q2 * (ah - al);
-        const T t = tmin(tmin(theta_fn<T>(sULp2[b - BX], sULp2[b - BX] + d, umin, umax),
-                              theta_fn<T>(sULp2[b], sULp2[b] - d, umin, umax)),
-                         tmin(theta_fn<T>(sULm2[b], sULm2[b] - d, umin, umax),
-                              theta_fn<T>(sULm2[b + BX], sULm2[b + BX] + d, umin, umax)));
-        sAlim2[b] = is_one(t) ? ah : al + t * (ah - al);
-      });
+      for_segs<NT>(seg<H - 1, H + TX, H, H + TY>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     const T fh = sFH1[b], fl = sFL1[b], dF = fh - fl;
+                     const T zp = sULp1[b], zm = sULm1[b + 1];
+                     const T t = theta_pair<T>(zp, zp - k1 * dF, zm, zm + k1 * dF, umin, umax);
+                     sFlim1[b] = is_one(t) ? fh : fl + t * dF;
+                   }),
+                   seg<H, H + TX, H - 1, H + TY>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     const T fh = sFH2[b], fl = sFL2[b], dF = fh - fl;
+                     const T zp = sULp2[b], zm = sULm2[b + BX];
+                     const T t = theta_pair<T>(zp, zp - k2 * dF, zm, zm + k2 * dF, umin, umax);
+                     sFlim2[b] = is_one(t) ? fh : fl + t * dF;
+                   }),
+                   seg<H - 1, H + TX + 1, H, H + TY>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     const T ah = sAH1[b], al = aU(b), d = q1 * (ah - al);
+                     const T p0 = sULp1[b - 1], p1 = sULp1[b], q0 = sULm1[b], q1 = sULm1[b + 1];
+                     const T t = theta_quad<T>(p0, p0 + d, p1, p1 - d, q0, q0 - d, q1, q1 + d, umin, umax);
+                     sAlim1[b] = is_one(t) ? ah : al + t * (ah - al);
+                   }),
+                   seg<H, H + TX, H - 1, H + TY + 1>([&](int bx, int by) {
+                     const int b = by * BX + bx;
+                     const T ah = sAH2[b], al = aU(b), d = q2 * (ah - al);
+                     const T p0 = sULp2[b - BX], p1 = sULp2[b], q0 = sULm2[b], q1 = sULm2[b + BX];
+                     const T t = theta_quad<T>(p0, p0 + d, p1, p1 - d, q0, q0 - d, q1, q1 + d, umin, umax);
+                     sAlim2[b] = is_one(t) ? ah : al + t * (ah - al);
+                   }));
       __syncthreads();
     }
     // ---- P5: limited average update, point update + projection, RK combination ----
@@ -556,8 +623,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
         ubfe = ubin + (f2d_exact(hi) + f2d_exact(lo));
       }
       const T taut = sc.taut[o];
-      T v = rk_comb(taut, rV, T(1), sZ[tV][b]), x = rk_comb(taut, rX, T(1), sZ[tX][b]),
-        y = rk_comb(taut, rY, T(1), sZ[tY][b]);
+      T v = rk_fma(taut, rV, sZ[tV][b]), x = rk_fma(taut, rX, sZ[tX][b]), y = rk_fma(taut, rY, sZ[tY][b]);
       if (A.limiter) {
         v = tmin(tmax(v, umin), umax);
         x = tmin(tmax(x, umin), umax);
@@ -567,7 +633,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
       const T cAt = sc.cAt[o], cFt = sc.cFt[o];
       double ubo;
       PT vo, xo, yo;
-      if (cA != 0.0) {
+      if (!is_zero_bits(cA)) {
         ubo = rk_comb(cA, A.Aub[o][g], cF, ubfe);
         vo = PT(rk_comb(cAt, T(A.AV[o][g]), cFt, v));
         xo = PT(rk_comb(cAt, T(A.AX[o][g]), cFt, x));

@@ -141,3 +141,28 @@ def test_batch_rejects_mixed_flux_kinds_and_blend():
     with pytest.raises(capi.AfError) as ei:
         capi.af_batch_create(g, f, d, b, o)
     assert ei.value.status == capi.AF_E_UNSUPPORTED
+
+
+def test_batch_cfl_interior_extrema_bl():
+    """Per-instance device dt of Buckley-Leverett instances on 0/1 patterns, where the
+    wave speed of every face comes from an interior extremum of f_l', equals the
+    oracle's CFL step."""
+    from paper_2510_11527_gb300 import capi
+    specs, states = [], []
+    for k, (nx, ny) in enumerate([(40, 24), (33, 17)]):
+        s = ai.Spec(dim=2, nx=nx, ny=ny, x0=0.0, x1=1.3, y0=0.0, y1=0.9, flux=("bl", (5.0,)),
+                    diff=("cubic", (0.0, 0.02, -0.04 / 3)), umin=0.0, umax=1.0)
+        j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+        ub = ((i + j) % 2 if k == 0 else i % 2).astype(np.float64)
+        specs.append(s)
+        states.append([ub, np.zeros_like(ub), np.zeros_like(ub), np.zeros_like(ub)])
+    b = capi.af_batch_create(*_structs(specs, "fp64", 3))
+    try:
+        for i, (s, st) in enumerate(zip(specs, states)):
+            capi.af_batch_set_state(b, i, s.cells, *st)
+        capi.af_batch_step(b, 1)
+        capi.af_batch_sync(b)
+        for i, (s, st) in enumerate(zip(specs, states)):
+            assert capi.af_batch_time(b, i) == pytest.approx(oracle.dt_cfl(s, st[0]), rel=1e-14)
+    finally:
+        capi.af_batch_destroy(b)

@@ -169,7 +169,7 @@ def _tv(a):
 
 def test_learned_blend_gain_over_no_blend(trained):
     """Buckley-Leverett disc (the paper's Example 6.7 setting, periodic), 128^2, FP32-mixed.
-    The plain smoothness indicator is the judge: the learned blend must move the
+    The plain smoothness indicator is the reference: the learned blend must move the
     solution toward the plain-blend solution and reduce the oscillation (total variation
     growth) of the method without a blend; bounds and conservation hold in every case."""
     from paper_2510_11527_gb300 import Solver, capi

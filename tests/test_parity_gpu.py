@@ -315,3 +315,17 @@ def test_config2_full_size_sampled(prec):
     rng = np.random.default_rng(0)
     # half the samples on the disc edges, where the limiter acts
     _sampled_step_check(spec, st, dt, got, 3, 60, rng, r=10)
+
+
+@pytest.mark.parametrize("pattern", ["checker", "stripes_x", "stripes_y"])
+def test_device_cfl_step_interior_extrema(pattern):
+    """Buckley-Leverett: |f_l'| vanishes at u = 0 and u = 1, so on a 0/1 pattern every
+    face's interval wave speed comes from the interior extrema of f_l' (the flagged
+    path of the reduction); stripes exercise one direction at a time."""
+    spec = spec2d("bl_cubic", 40, 24)
+    j, i = np.meshgrid(np.arange(spec.ny), np.arange(spec.nx), indexing="ij")
+    ub = {"checker": (i + j) % 2, "stripes_x": i % 2, "stripes_y": j % 2}[pattern].astype(np.float64)
+    st = [ub, np.zeros_like(ub), np.zeros_like(ub), np.zeros_like(ub)]
+    with solver(spec) as s:
+        s.set_state(st)
+        assert s.dt_cfl() == pytest.approx(oracle.dt_cfl(spec, ub), rel=1e-14)
