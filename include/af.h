@@ -95,10 +95,15 @@ const char* af_last_error(const af_ctx* ctx);
  * current stream). NULL selects the legacy default stream. */
 af_status af_set_stream(af_ctx* ctx, void* stream);
 
-/* Copy a host state in (doubles, caller-owned). FP32-mixed contexts round the point
- * values to float. AF_E_STATE if any value is NaN or, with the limiter on, outside
- * [umin, umax]. */
+/* Copy a host state in (doubles, caller-owned, nx*ny values each, row-major; X and Y
+ * ignored in 1D). The arrays are copied to the device and checked there; FP32-mixed
+ * contexts then round the point values to nearest float. AF_E_STATE if any value is NaN
+ * or, with the limiter on, outside [umin, umax]; the current state is then unchanged.
+ * Page-locked host memory copies fastest. Returns after the host arrays have been read
+ * (the caller may reuse them). */
 af_status af_set_state(af_ctx* ctx, const double* ub, const double* V, const double* X, const double* Y);
+/* Copy the current state out into caller-owned doubles (FP32 point values widened
+ * exactly). Synchronous with the context's stream. */
 af_status af_get_state(af_ctx* ctx, double* ub, double* V, double* X, double* Y);
 
 /* Borrowed device pointers of the current state (ub, V, X, Y). dtype[0] is 8 (ub is

@@ -66,10 +66,13 @@ class Solver:
         else:
             capi.af_set_state(self.ctx, self.n, *arrs)
 
-    def get_state(self):
-        out = capi.af_get_state(self.ctx, self.n, self.dim)
+    def get_state(self, out=None):
+        """Host copy of (ub, V, X, Y); `out` may supply the destination float64 arrays
+        (for instance views of pinned host memory, which copy fastest)."""
         shape = (self.spec.ny, self.spec.nx) if self.dim == 2 else (self.spec.nx,)
-        return [a.reshape(shape) for a in out]
+        flat = None if out is None else [np.asarray(a).reshape(-1) for a in out]
+        res = capi.af_get_state(self.ctx, self.n, self.dim, flat)
+        return [a.reshape(shape) for a in res]
 
     def device_tensors(self):
         """Zero-copy torch views of the current device state (ub, V, X, Y)."""

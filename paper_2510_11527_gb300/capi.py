@@ -345,10 +345,20 @@ def af_set_state(ctx, n, ub, V, X=None, Y=None):
     _check(ctx, lib().af_set_state(ctx, *[_dp(a) for a in arrs]))
 
 
-def af_get_state(ctx, n, dim):
-    out = [np.empty(n) for _ in range(4 if dim == 2 else 2)] + ([None, None] if dim == 1 else [])
-    _check(ctx, lib().af_get_state(ctx, *[_dp(a) for a in out]))
-    return [a for a in out if a is not None]
+def af_get_state(ctx, n, dim, out=None):
+    """Copy the state to host float64 arrays: `out` (C-contiguous float64 arrays of n
+    values each, e.g. views of pinned memory) or new arrays."""
+    k = 4 if dim == 2 else 2
+    if out is None:
+        out = [np.empty(n) for _ in range(k)]
+    else:
+        out = list(out)
+        if len(out) != k or any(not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.size == n and
+                                     a.flags.c_contiguous) for a in out):
+            raise ValueError(f"out must be {k} C-contiguous float64 arrays of {n} values")
+    full = out + ([None, None] if dim == 1 else [])
+    _check(ctx, lib().af_get_state(ctx, *[_dp(a) for a in full]))
+    return out
 
 
 def af_device_ptrs(ctx):

@@ -95,6 +95,12 @@ template <class T>
 struct BLVals {
   T f[2], d[2];
 };
+// f_2 from u and f_1(u)
+template <class T>
+__device__ __forceinline__ T bl_f2(const DevModel& m, T u, T f1) {
+  const T v = T(1) - u;
+  return f1 * (T(1) - par<T>(m.fp, m.fpf, 0) * v * v);
+}
 template <class T>
 __device__ __forceinline__ BLVals<T> bl_eval(const DevModel& m, T u) {
   const T v = T(1) - u, u2 = u * u;
@@ -105,7 +111,7 @@ __device__ __forceinline__ BLVals<T> bl_eval(const DevModel& m, T u) {
   const T d1 = T(2) * u * v * rD * rD;   // f_1'
   BLVals<T> r;
   r.f[0] = f1;
-  r.f[1] = f1 * w;
+  r.f[1] = bl_f2<T>(m, u, f1);
   r.d[0] = tabs(d1);
   r.d[1] = tabs(d1 * w + T(2) * g * v * f1);
   return r;
@@ -288,23 +294,24 @@ __device__ __forceinline__ void record_excess(DevStats* st, double e, double tol
   }
 }
 
+// The rare path of the safeguard, kept out of line so that the excess (FP64 arithmetic
+// and conversions) is never evaluated speculatively on the common path.
+template <class S>
+__device__ __noinline__ S safeguard_violation(S v, S umin, S umax, double tol, DevStats* st, bool is_avg) {
+  const bool below = tlt(v, umin);
+  const double e = below ? (double)umin - (double)v : (double)v - (double)umax;
+  bool ok;
+  record_excess(st, e, tol, &ok);
+  if (ok && is_avg) atomicAdd(&st->ub_adjust, e);
+  return ok ? (below ? umin : umax) : v;
+}
+
 // Safeguard on a stored value: exact comparison against the bounds, clamp if within
 // tol. For cell averages (is_avg) the size of the change is accumulated: times dx dy it
 // bounds the mass the clamps moved (later RK stages weight a stage output by <= 1).
 template <class S>
 __device__ __forceinline__ S safeguard(S v, S umin, S umax, double tol, DevStats* st, bool is_avg = false) {
-  if (tlt(v, umin)) {
-    bool ok;
-    record_excess(st, (double)umin - (double)v, tol, &ok);
-    if (ok && is_avg) atomicAdd(&st->ub_adjust, (double)umin - (double)v);
-    return ok ? umin : v;
-  }
-  if (tlt(umax, v)) {
-    bool ok;
-    record_excess(st, (double)v - (double)umax, tol, &ok);
-    if (ok && is_avg) atomicAdd(&st->ub_adjust, (double)v - (double)umax);
-    return ok ? umax : v;
-  }
+  if (tlt(v, umin) | tlt(umax, v)) return safeguard_violation<S>(v, umin, umax, tol, st, is_avg);
   return v;
 }
 

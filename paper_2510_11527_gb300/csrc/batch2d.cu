@@ -42,9 +42,9 @@ struct BatchStage {              // uniform over the batch for one launch
 };
 
 template <int FLUX, class T, class PT, int TX, int TY>
-__global__ void __launch_bounds__(256) batch_stage_kernel(const BatchInst* __restrict__ inst,
-                                                          const int* __restrict__ work_inst, int total,
-                                                          const BatchStage S, DevStats* stats) {
+__device__ __forceinline__ void batch_stage_body(const BatchInst* __restrict__ inst,
+                                                 const int* __restrict__ work_inst, int total, const BatchStage& S,
+                                                 DevStats* stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // the tile's arguments live in shared memory, written by one thread: a per-thread
   // copy would sit in local memory (its arrays are indexed at run time)
@@ -91,6 +91,24 @@ __global__ void __launch_bounds__(256) batch_stage_kernel(const BatchInst* __res
     stage_tile<FLUX, T, PT, false, TX, TY>(I.m, A, i0, j0, smem_raw);
     __syncthreads();
   }
+}
+
+// FP64 stencils: 72.6 KB of shared memory per CTA leave room for 3 CTAs per SM, which
+// the registers must not undercut (<= 80 per thread)
+template <int FLUX, class T, class PT, int TX, int TY>
+__global__ void __launch_bounds__(256, 3) batch_stage_kernel(const BatchInst* __restrict__ inst,
+                                                          const int* __restrict__ work_inst, int total,
+                                                          const BatchStage S, DevStats* stats) {
+  batch_stage_body<FLUX, T, PT, TX, TY>(inst, work_inst, total, S, stats);
+}
+
+// FP32 stencils: compiled for 6 resident CTAs per SM (measured 8% faster than the
+// compiler's 64-register choice at 4 CTAs per SM, despite a few spilled words)
+template <int FLUX, int TX, int TY>
+__global__ void __launch_bounds__(256, 6) batch_stage_kernel_f32occ6(const BatchInst* __restrict__ inst,
+                                                                     const int* __restrict__ work_inst, int total,
+                                                                     const BatchStage S, DevStats* stats) {
+  batch_stage_body<FLUX, float, float, TX, TY>(inst, work_inst, total, S, stats);
 }
 
 // per-tile part of the CFL rate (see dt_rate_kernel) into rate_bits[2 instance] and the
@@ -231,7 +249,10 @@ namespace {
 template <int FLUX, class T, class PT, int TX, int TY>
 cudaError_t launch_stage_t(af_batch* b, const BatchStage& S) {
   using L = af::Tile2D<FLUX, T, false, TX, TY>;
-  auto k = af::batch_stage_kernel<FLUX, T, PT, TX, TY>;
+  auto k = [] {
+    if constexpr (sizeof(T) == 4) return af::batch_stage_kernel_f32occ6<FLUX, TX, TY>;
+    else return af::batch_stage_kernel<FLUX, T, PT, TX, TY>;
+  }();
   static int blocks = 0;
   if (!blocks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
@@ -380,7 +401,7 @@ af_status reduce_inst(af_batch* b, const S* x, size_t n, int op, double init, do
   const int blocks = (int)std::min<size_t>(af::RED_MAX_BLOCKS, (n + af::RED_THREADS - 1) / af::RED_THREADS);
   af::partial_kernel<S><<<blocks, af::RED_THREADS, 0, b->stream>>>(x, n, op, init, b->d_partial);
   BCK(b, cudaGetLastError());
-  af::finalize_kernel<<<1, 1, 0, b->stream>>>(b->d_partial, blocks, op, out_dev, acc);
+  af::finalize_kernel<<<1, af::RED_THREADS, 0, b->stream>>>(b->d_partial, blocks, op, out_dev, acc);
   BCK(b, cudaGetLastError());
   return AF_OK;
 }

@@ -13,6 +13,7 @@
 #include "launch.h"
 #include "model_host.h"
 #include "reduce.cuh"
+#include "state_io.cuh"
 
 using af::DevModel;
 using af::DevStats;
@@ -237,7 +238,7 @@ af_status reduce_array(af_ctx* c, const S* x, int op, double init, double* out_d
   const int blocks = (int)std::min<size_t>(af::RED_MAX_BLOCKS, (c->n + af::RED_THREADS - 1) / af::RED_THREADS);
   af::partial_kernel<S><<<blocks, af::RED_THREADS, 0, c->stream>>>(x, c->n, op, init, c->partial);
   CK(c, cudaGetLastError());
-  af::finalize_kernel<<<1, 1, 0, c->stream>>>(c->partial, blocks, op, out_dev, accumulate);
+  af::finalize_kernel<<<1, af::RED_THREADS, 0, c->stream>>>(c->partial, blocks, op, out_dev, accumulate);
   CK(c, cudaGetLastError());
   return AF_OK;
 }
@@ -359,14 +360,20 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
   const int na = c->dim == 2 ? 4 : 2;
   const double* src[4] = {ub, V, X, Y};
-  double lo = INFINITY, hi = -INFINITY;
+  const size_t n = c->n;
+  // staging: the RK temporaries (buffers 1..nbuf-1, contiguous, >= 40 n bytes >= 8 na n)
+  double* stg = c->ub[1];
   for (int a = 0; a < na; ++a)
-    for (size_t k = 0; k < c->n; ++k) {
-      const double v = src[a][k];
-      if (!(v == v)) FAIL(c, AF_E_STATE, "NaN in input array %d at %zu", a, k);
-      lo = std::min(lo, v);
-      hi = std::max(hi, v);
-    }
+    CK(c, cudaMemcpyAsync(stg + a * n, src[a], n * 8, cudaMemcpyHostToDevice, c->stream));
+  const int nb = (int)std::min<size_t>(af::STATE_IO_BLOCKS, (na * n + af::RED_THREADS - 1) / af::RED_THREADS);
+  af::validate_partial_kernel<<<nb, af::RED_THREADS, 0, c->stream>>>(stg, na * n, (unsigned long long*)c->partial);
+  CK(c, cudaGetLastError());
+  af::validate_final_kernel<<<1, 1, 0, c->stream>>>((const unsigned long long*)c->partial, nb, c->red + 5);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemcpyAsync(c->host_pinned, c->red + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const double nan = c->host_pinned[0], lo = c->host_pinned[1], hi = c->host_pinned[2];
+  if (nan > 0.0) FAIL(c, AF_E_STATE, "NaN in the input arrays (%.0f values)", nan);
   if (c->bounds_pending) {
     if (!(hi > lo)) FAIL(c, AF_E_STATE, "bounds from initial data need max > min");
     c->m.umin = lo;
@@ -378,38 +385,35 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
   } else if (c->opts.limiter && (lo < c->m.umin || hi > c->m.umax)) {
     FAIL(c, AF_E_STATE, "input outside [umin, umax]: [%g, %g]", lo, hi);
   }
-  CK(c, cudaMemcpyAsync(c->ub[0], ub, c->n * 8, cudaMemcpyHostToDevice, c->stream));
-  void* dst[3] = {c->pv[0], c->px[0], c->py[0]};
-  if (c->prec == AF_PREC_FP64) {
-    for (int a = 1; a < na; ++a) CK(c, cudaMemcpyAsync(dst[a - 1], src[a], c->n * 8, cudaMemcpyHostToDevice, c->stream));
-  } else {
-    std::vector<float> tmp(c->n);
-    for (int a = 1; a < na; ++a) {
-      for (size_t k = 0; k < c->n; ++k) tmp[k] = (float)src[a][k];
-      CK(c, cudaMemcpyAsync(dst[a - 1], tmp.data(), c->n * 4, cudaMemcpyHostToDevice, c->stream));
-      CK(c, cudaStreamSynchronize(c->stream));
-    }
-  }
-  CK(c, cudaStreamSynchronize(c->stream));
+  const int grid = (int)std::min<size_t>(152 * 8, (n + af::RED_THREADS - 1) / af::RED_THREADS);
+  if (c->prec == AF_PREC_FP64)
+    af::scatter_state_kernel<double><<<grid, af::RED_THREADS, 0, c->stream>>>(
+        stg, n, na, c->ub[0], (double*)c->pv[0], (double*)c->px[0], (double*)c->py[0]);
+  else
+    af::scatter_state_kernel<float><<<grid, af::RED_THREADS, 0, c->stream>>>(
+        stg, n, na, c->ub[0], (float*)c->pv[0], (float*)c->px[0], (float*)c->py[0]);
+  CK(c, cudaGetLastError());
   return AF_OK;
 }
 
 af_status af_get_state(af_ctx* c, double* ub, double* V, double* X, double* Y) {
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
   const int na = c->dim == 2 ? 4 : 2;
+  const size_t n = c->n;
   double* dst[4] = {ub, V, X, Y};
-  void* src[3] = {c->pv[0], c->px[0], c->py[0]};
-  CK(c, cudaMemcpyAsync(ub, c->ub[0], c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaMemcpyAsync(ub, c->ub[0], n * 8, cudaMemcpyDeviceToHost, c->stream));
   if (c->prec == AF_PREC_FP64) {
-    for (int a = 1; a < na; ++a) CK(c, cudaMemcpyAsync(dst[a], src[a - 1], c->n * 8, cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
+    void* src[3] = {c->pv[0], c->px[0], c->py[0]};
+    for (int a = 1; a < na; ++a) CK(c, cudaMemcpyAsync(dst[a], src[a - 1], n * 8, cudaMemcpyDeviceToHost, c->stream));
   } else {
-    std::vector<float> tmp(c->n);
-    for (int a = 1; a < na; ++a) {
-      CK(c, cudaMemcpyAsync(tmp.data(), src[a - 1], c->n * 4, cudaMemcpyDeviceToHost, c->stream));
-      CK(c, cudaStreamSynchronize(c->stream));
-      for (size_t k = 0; k < c->n; ++k) dst[a][k] = (double)tmp[k];
-    }
+    // FP32 points widened on the device into the staging area, then copied
+    double* stg = c->ub[1];
+    const int grid = (int)std::min<size_t>(152 * 8, (n + af::RED_THREADS - 1) / af::RED_THREADS);
+    af::gather_points_kernel<<<grid, af::RED_THREADS, 0, c->stream>>>(
+        (const float*)c->pv[0], (const float*)c->px[0], (const float*)c->py[0], n, na, stg);
+    CK(c, cudaGetLastError());
+    for (int a = 1; a < na; ++a)
+      CK(c, cudaMemcpyAsync(dst[a], stg + (a - 1) * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
   return AF_OK;

@@ -31,29 +31,57 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + NH * NIN, OFF_W2 = OFF_B1 + NH, OFF_
 constexpr int OFF_W3 = OFF_B2 + NH, OFF_B3 = OFF_W3 + NH, NPARAM = OFF_B3 + 1;   // 1793
 static_assert(NPARAM == AF_MLP_NPARAM, "parameter count");
 
-// patch offsets of the 13 cell averages (a along x, b along y)
-__constant__ int kPatchA[13] = {-1, 0, 1, -1, 0, 1, -1, 0, 1, -2, 2, 0, 0};
-__constant__ int kPatchB[13] = {-1, -1, -1, 0, 0, 0, 1, 1, 1, 0, 0, -2, 2};
-
+// periodic index for offsets of a few cells (one compare each way; the modulo only on
+// meshes smaller than the offset)
 __device__ __forceinline__ int wrapm(int i, int n) {
-  i %= n;
-  return i < 0 ? i + n : i;
+  if (i < 0) {
+    i += n;
+    if (i < 0) {
+      i %= n;
+      if (i < 0) i += n;
+    }
+  } else if (i >= n) {
+    i -= n;
+    if (i >= n) i %= n;
+  }
+  return i;
 }
 
 // FP32 copies of state values without the FP64 unit (truncating, as the stage kernels)
 __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(double x) { return af::to_stencil<float>(x); }
 
+// normalised patch from values in FP32: (v_k - v_4) / (max_k |v_k| + 1e-13), v_4 being
+// the cell's own average
+__device__ __forceinline__ void normalise(const float v[NIN], float f[NIN]) {
+  float sc = 0.0f;
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) sc = fmaxf(sc, fabsf(v[k]));
+  const float r = 1.0f / (sc + 1e-13f), m = v[4];
+#pragma unroll
+  for (int k = 0; k < NIN; ++k) f[k] = (v[k] - m) * r;
+}
+
 // normalised patch of cell (i, j) in FP32: (v_k - ub_ij) / (max_k |v_k| + 1e-13)
 template <class PT>
 __device__ __forceinline__ void gather(const double* __restrict__ ub, const PT* __restrict__ V,
                                        const PT* __restrict__ X, const PT* __restrict__ Y, int nx, int ny, int i,
                                        int j, float f[NIN]) {
+  // patch offsets of the 13 cell averages (a along x, b along y)
+  constexpr int kPatchA[13] = {-1, 0, 1, -1, 0, 1, -1, 0, 1, -2, 2, 0, 0};
+  constexpr int kPatchB[13] = {-1, -1, -1, 0, 0, 0, 1, 1, 1, 0, 0, -2, 2};
   float v[NIN];
+  // wrapped columns i-2..i+2 and row offsets j-2..j+2, formed once
+  int ci[5];
+  size_t rj[5];
 #pragma unroll
-  for (int k = 0; k < 13; ++k)
-    v[k] = af::to_stencil<float>(ub[(size_t)wrapm(j + kPatchB[k], ny) * nx + wrapm(i + kPatchA[k], nx)]);
-  const int im = wrapm(i - 1, nx), jm = wrapm(j - 1, ny);
+  for (int d = 0; d < 5; ++d) {
+    ci[d] = wrapm(i + d - 2, nx);
+    rj[d] = (size_t)wrapm(j + d - 2, ny) * nx;
+  }
+#pragma unroll
+  for (int k = 0; k < 13; ++k) v[k] = af::to_stencil<float>(ub[rj[kPatchB[k] + 2] + ci[kPatchA[k] + 2]]);
+  const int im = ci[1], jm = wrapm(j - 1, ny);
   const size_t c = (size_t)j * nx + i;
   v[13] = to_f32(V[(size_t)jm * nx + im]);
   v[14] = to_f32(V[(size_t)jm * nx + i]);
@@ -63,12 +91,7 @@ __device__ __forceinline__ void gather(const double* __restrict__ ub, const PT* 
   v[18] = to_f32(X[c]);
   v[19] = to_f32(Y[(size_t)jm * nx + i]);
   v[20] = to_f32(Y[c]);
-  float sc = 0.0f;
-#pragma unroll
-  for (int k = 0; k < NIN; ++k) sc = fmaxf(sc, fabsf(v[k]));
-  const float r = 1.0f / (sc + 1e-13f), m = v[4];
-#pragma unroll
-  for (int k = 0; k < NIN; ++k) f[k] = (v[k] - m) * r;
+  normalise(v, f);
 }
 
 __device__ __forceinline__ float softplusf(float z) { return z > 20.0f ? z : log1pf(expf(z)); }
@@ -169,47 +192,74 @@ __device__ __forceinline__ void net_rows(const NetFrags& F, const __nv_bfloat16 
   *s8 = softplusf(r8 + F.b3);
 }
 
-// fused inference on a state: s (double) per cell
+// Fused inference on a state, s (double) per cell. Each CTA takes 32 x 8 tiles of
+// cells: the tile's cell averages with a +-2 halo and its point values with a -1 halo
+// are staged in shared memory (coalesced row loads, converted to FP32 once), every lane
+// builds the patch of one cell from there, and each warp runs the network on its 32
+// patches as two 16-row blocks.
 template <class PT>
-__global__ void __launch_bounds__(256) indicator_kernel(const double* __restrict__ ub, const PT* __restrict__ V,
-                                                        const PT* __restrict__ X, const PT* __restrict__ Y, int nx,
-                                                        int ny, const __nv_bfloat16* __restrict__ w1q,
-                                                        const __nv_bfloat16* __restrict__ w2q,
-                                                        const float* __restrict__ params, double* __restrict__ out) {
-  // each warp takes 32 cells per pass: every lane gathers one patch, then the network
-  // runs on the two 16-row blocks
+__global__ void __launch_bounds__(256, 3) indicator_kernel(const double* __restrict__ ub, const PT* __restrict__ V,
+                                                           const PT* __restrict__ X, const PT* __restrict__ Y, int nx,
+                                                           int ny, const __nv_bfloat16* __restrict__ w1q,
+                                                           const __nv_bfloat16* __restrict__ w2q,
+                                                           const float* __restrict__ params, double* __restrict__ out) {
+  constexpr int UX = 36, UY = 12, PX = 33, PY = 9;
+  constexpr int kPatchA[13] = {-1, 0, 1, -1, 0, 1, -1, 0, 1, -2, 2, 0, 0};
+  constexpr int kPatchB[13] = {-1, -1, -1, 0, 0, 0, 1, 1, 1, 0, 0, -2, 2};
+  __shared__ float sU[UY][UX];
+  __shared__ float sV[PY][PX], sX[PY][PX], sY[PY][PX];
   __shared__ __align__(16) __nv_bfloat16 sx[8][32][40];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   NetFrags F;
   load_frags(F, w1q, w2q, params, lane);
-  const long long n = (long long)nx * ny;
-  for (long long base = ((long long)blockIdx.x * 8 + warp) * 32; base < n; base += (long long)gridDim.x * 256) {
+  const int tiles_x = (nx + 31) / 32, tiles = tiles_x * ((ny + 7) / 8);
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int i0 = (t % tiles_x) * 32, j0 = (t / tiles_x) * 8;
+    for (int k = tid; k < UX * UY; k += 256) {
+      const int bx = k % UX, by = k / UX;
+      sU[by][bx] = af::to_stencil<float>(ub[(size_t)wrapm(j0 - 2 + by, ny) * nx + wrapm(i0 - 2 + bx, nx)]);
+    }
+    for (int k = tid; k < PX * PY; k += 256) {
+      const int bx = k % PX, by = k / PX;
+      const size_t g = (size_t)wrapm(j0 - 1 + by, ny) * nx + wrapm(i0 - 1 + bx, nx);
+      sV[by][bx] = to_f32(V[g]);
+      sX[by][bx] = to_f32(X[g]);
+      sY[by][bx] = to_f32(Y[g]);
+    }
+    __syncthreads();
     {
-      const long long cell = base + lane;
-      float f[NIN];
-      if (cell < n) {
-        gather<PT>(ub, V, X, Y, nx, ny, (int)(cell % nx), (int)(cell / nx), f);
-      } else {
+      // cell (i0 + lane, j0 + warp)
+      const int tx = lane, ty = warp;
+      float v[NIN], f[NIN];
 #pragma unroll
-        for (int k = 0; k < NIN; ++k) f[k] = 0.f;
-      }
+      for (int k = 0; k < 13; ++k) v[k] = sU[ty + 2 + kPatchB[k]][tx + 2 + kPatchA[k]];
+      v[13] = sV[ty][tx];
+      v[14] = sV[ty][tx + 1];
+      v[15] = sV[ty + 1][tx];
+      v[16] = sV[ty + 1][tx + 1];
+      v[17] = sX[ty + 1][tx];
+      v[18] = sX[ty + 1][tx + 1];
+      v[19] = sY[ty][tx + 1];
+      v[20] = sY[ty + 1][tx + 1];
+      normalise(v, f);
 #pragma unroll
       for (int k = 0; k < 32; k += 2)
         *reinterpret_cast<uint32_t*>(&sx[warp][lane][k]) =
             pack_bf16(k < NIN ? f[k] : 0.f, k + 1 < NIN ? f[k + 1] : 0.f);
     }
     __syncwarp();
+    const int j = j0 + warp;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       float s0, s8;
       net_rows(F, sx[warp] + 16 * h, lane, &s0, &s8);
-      if ((lane & 3) == 0) {
-        const long long r0 = base + 16 * h + (lane >> 2), r8 = r0 + 8;
-        if (r0 < n) out[r0] = af::f2d_exact(s0);
-        if (r8 < n) out[r8] = af::f2d_exact(s8);
+      if ((lane & 3) == 0 && j < ny) {
+        const int i = i0 + 16 * h + (lane >> 2);
+        if (i < nx) out[(size_t)j * nx + i] = af::f2d_exact(s0);
+        if (i + 8 < nx) out[(size_t)j * nx + i + 8] = af::f2d_exact(s8);
       }
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
@@ -397,8 +447,8 @@ struct af_mlp {
 namespace af {
 cudaError_t mlp_indicator_launch(const af_ctx* c, const af_mlp* net, int buf, double* out) {
   if (c->dim != 2) return cudaErrorInvalidValue;
-  const long long n = (long long)c->n;
-  const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+  const long long tiles = (long long)((c->nx + 31) / 32) * ((c->ny + 7) / 8);
+  const int grid = (int)std::min<long long>(tiles, 152 * 3);
   if (c->prec == AF_PREC_FP64)
     indicator_kernel<double><<<grid, 256, 0, c->stream>>>(c->ub[buf], (const double*)c->pv[buf],
                                                           (const double*)c->px[buf], (const double*)c->py[buf],

@@ -133,13 +133,23 @@ __global__ void __launch_bounds__(RED_THREADS) partial_kernel(const S* __restric
   if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
 }
 
-// combine nparts partials in block order into out[slot] (op as above; combine with the
-// existing out[slot] when accumulate != 0)
-static __global__ void finalize_kernel(const double* partial, int nparts, int op, double* out, int accumulate) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double acc = partial[0];
-  for (int k = 1; k < nparts; ++k) acc = red_op(op, acc, partial[k]);
-  *out = accumulate ? red_op(op, *out, acc) : acc;
+// combine nparts partials into *out (op as above; combined with the existing *out when
+// accumulate != 0). One block of RED_THREADS: thread t folds partials t, t + RED_THREADS,
+// ... in order, then a fixed tree; the result depends only on nparts and the partials.
+static __global__ void __launch_bounds__(RED_THREADS) finalize_kernel(const double* partial, int nparts, int op,
+                                                                      double* out, int accumulate) {
+  __shared__ double sm[RED_THREADS];
+  const int t = threadIdx.x;
+  // partial[0] is neutral for min/max over a set that contains it
+  double acc = op == 0 ? 0.0 : partial[0];
+  for (int k = t; k < nparts; k += RED_THREADS) acc = red_op(op, acc, partial[k]);
+  sm[t] = acc;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (t < s) sm[t] = red_op(op, sm[t], sm[t + s]);
+    __syncthreads();
+  }
+  if (t == 0) *out = accumulate ? red_op(op, *out, sm[0]) : sm[0];
 }
 
 }  // namespace af

@@ -4,10 +4,16 @@
 namespace af {
 
 template <int FLUX, bool BLEND>
+static auto kernel_for() {
+  if constexpr (BLEND) return stage2d_kernel<FLUX, float, float, true>;
+  else return stage2d_kernel_f32occ6<FLUX>;
+}
+
+template <int FLUX, bool BLEND>
 static cudaError_t go(const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s) {
   using L = Tile2D<FLUX, float, BLEND>;
   static bool attr = false;
-  auto k = stage2d_kernel<FLUX, float, float, BLEND>;
+  auto k = kernel_for<FLUX, BLEND>();
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::SMEM);
     if (e != cudaSuccess) return e;
