@@ -189,18 +189,6 @@ using af::DevStats;
 
 namespace {
 
-const double kA54[5][5] = {
-    {1.0, 0, 0, 0, 0},
-    {0.444370493651235, 0.555629506348765, 0, 0, 0},
-    {0.620101851488403, 0, 0.379898148511597, 0, 0},
-    {0.178079954393132, 0, 0, 0.821920045606868, 0},
-    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269}};
-const double kB54[5][5] = {
-    {0.391752226571890, 0, 0, 0, 0},
-    {0, 0.368410593050371, 0, 0, 0},
-    {0, 0, 0.251891774271694, 0, 0},
-    {0, 0, 0, 0.544974750228521, 0},
-    {0, 0, 0, 0.063692468666290, 0.226007483236906}};
 
 struct Shape {
   int tx, ty;
@@ -345,8 +333,8 @@ std::vector<BatchStage> stages_of(const af_batch* b) {
     BatchStage s1 = make_stage(1, 1); set_o(s1, 0, 2, 0.75, 0, 0.25, 1.0, 1); v.push_back(s1);
     BatchStage s2 = make_stage(2, 1); set_o(s2, 0, 0, 1.0 / 3.0, 0, 2.0 / 3.0, 1.0, 1); v.push_back(s2);
   } else {
-    const double(*A)[5] = kA54;
-    const double(*B)[5] = kB54;
+    const double(*A)[5] = af::kA54;
+    const double(*B)[5] = af::kB54;
     BatchStage s0 = make_stage(0, 1); set_o(s0, 0, 1, 0.0, -1, A[0][0], B[0][0] / A[0][0], 1); v.push_back(s0);
     BatchStage s1 = make_stage(1, 1); set_o(s1, 0, 2, A[1][0], 0, A[1][1], B[1][1] / A[1][1], 1); v.push_back(s1);
     BatchStage s2 = make_stage(2, 1); set_o(s2, 0, 3, A[2][0], 0, A[2][2], B[2][2] / A[2][2], 1); v.push_back(s2);

@@ -21,21 +21,6 @@ using af::StageArgs2D;
 
 namespace {
 
-// SSP-RK(5,4) of Spiteri & Ruuth (2002) in Shu-Osher form: alpha[k][l], beta[k][l],
-// row k producing stage value k+1 from u^(l) (Section 3.2 gives its stability
-// polynomial, z^5 coefficient 0.004477718303076).
-const double kA54[5][5] = {
-    {1.0, 0, 0, 0, 0},
-    {0.444370493651235, 0.555629506348765, 0, 0, 0},
-    {0.620101851488403, 0, 0.379898148511597, 0, 0},
-    {0.178079954393132, 0, 0, 0.821920045606868, 0},
-    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269}};
-const double kB54[5][5] = {
-    {0.391752226571890, 0, 0, 0, 0},
-    {0, 0.368410593050371, 0, 0, 0},
-    {0, 0, 0.251891774271694, 0, 0},
-    {0, 0, 0, 0.544974750228521, 0},
-    {0, 0, 0, 0.063692468666290, 0.226007483236906}};
 
 // 0.9 x the linear stability limit kappa dt / h^2 of the unlimited scheme for pure
 // diffusion: 1D from the von Neumann analysis of Section 3.2 (0.157 SSP-RK3, 0.333
@@ -156,8 +141,8 @@ af_status stage_impl(af_ctx* c, int k) {
     }
     return AF_OK;
   }
-  const double(*A)[5] = kA54;
-  const double(*B)[5] = kB54;
+  const double(*A)[5] = af::kA54;
+  const double(*B)[5] = af::kB54;
   switch (k) {
     case 0: {
       auto a = base_args<PT>(c, 0);

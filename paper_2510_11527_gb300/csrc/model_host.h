@@ -9,6 +9,22 @@
 
 namespace af {
 
+// SSP-RK(5,4) of Spiteri & Ruuth (2002) in Shu-Osher form: alpha[k][l], beta[k][l],
+// row k producing stage value k+1 from u^(l) (Section 3.2 gives its stability
+// polynomial, z^5 coefficient 0.004477718303076).
+inline const double kA54[5][5] = {
+    {1.0, 0, 0, 0, 0},
+    {0.444370493651235, 0.555629506348765, 0, 0, 0},
+    {0.620101851488403, 0, 0.379898148511597, 0, 0},
+    {0.178079954393132, 0, 0, 0.821920045606868, 0},
+    {0, 0, 0.517231671970585, 0.096059710526147, 0.386708617503269}};
+inline const double kB54[5][5] = {
+    {0.391752226571890, 0, 0, 0, 0},
+    {0, 0.368410593050371, 0, 0, 0},
+    {0, 0, 0.251891774271694, 0, 0},
+    {0, 0, 0, 0.544974750228521, 0},
+    {0, 0, 0, 0.063692468666290, 0.226007483236906}};
+
 // Buckley-Leverett f_l'' (analytic) for locating the interior extrema of f_l'.
 inline double bl_d2(int dir, double g, double u) {
   const double v = 1.0 - u, D = u * u + v * v, Dp = 2.0 * u - 2.0 * v;
