@@ -25,6 +25,8 @@
 // b+BX. Both tiles adjacent to a face compute it with the same instructions from the
 // same values, so conservation and double conservation hold bit for bit.
 #pragma once
+#include <type_traits>
+
 #include "af_model.cuh"
 
 namespace af {
@@ -228,31 +230,71 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   }
 
   // ---- P0: load the halo box --------------------------------------------------------
-  // all loads of a thread are issued before the first store, so their latencies overlap
-  constexpr int NP0 = (BN + NT - 1) / NT;
-  double ldU[NP0];
-  PT ldV[NP0], ldX[NP0], ldY[NP0];
-#pragma unroll
-  for (int it = 0; it < NP0; ++it) {
-    const int k = tid + it * NT;
-    if (k < BN) {
-      const int bx = k % BX, by = k / BX;
-      const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
-      const size_t g = (size_t)gj * nx + gi;
-      ldU[it] = A.ub[g];
-      ldV[it] = A.V[g];
-      ldX[it] = A.X[g];
-      ldY[it] = A.Y[g];
-    }
+  // Tiles whose halo box lies inside an even-width mesh load the box as aligned pairs
+  // (8- or 16-byte vector loads; rows start at the even column i0 - 2); other tiles
+  // (periodic wrap, odd widths, the +-3 blend halo) load element by element. In both,
+  // all loads of a thread are issued before its first store, so their latencies overlap.
+  bool paired = false;
+  if constexpr (H == 2) {
+    paired = (nx % 2 == 0) && i0 - H >= 0 && i0 + TX + H <= nx && j0 - H >= 0 && j0 + TY + H <= ny;
   }
+  if (paired) {
+    using P2 = std::conditional_t<sizeof(PT) == 4, float2, double2>;
+    constexpr int PW = BX / 2, NV = PW * BY, NPV = (NV + NT - 1) / NT;
+    double2 ldU[NPV];
+    P2 ldV[NPV], ldX[NPV], ldY[NPV];
 #pragma unroll
-  for (int it = 0; it < NP0; ++it) {
-    const int k = tid + it * NT;
-    if (k < BN) {
-      sU[k] = to_stencil<T>(ldU[it]);
-      sZ[0][k] = T(ldV[it]);
-      sZ[1][k] = T(ldX[it]);
-      sZ[2][k] = T(ldY[it]);
+    for (int it = 0; it < NPV; ++it) {
+      const int k = tid + it * NT;
+      if (k < NV) {
+        const size_t g = (size_t)(j0 - H + k / PW) * nx + (i0 - H + 2 * (k % PW));
+        ldU[it] = *reinterpret_cast<const double2*>(A.ub + g);
+        ldV[it] = *reinterpret_cast<const P2*>(A.V + g);
+        ldX[it] = *reinterpret_cast<const P2*>(A.X + g);
+        ldY[it] = *reinterpret_cast<const P2*>(A.Y + g);
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NPV; ++it) {
+      const int k = tid + it * NT;
+      if (k < NV) {
+        const int b = (k / PW) * BX + 2 * (k % PW);
+        sU[b] = to_stencil<T>(ldU[it].x);
+        sU[b + 1] = to_stencil<T>(ldU[it].y);
+        sZ[0][b] = T(ldV[it].x);
+        sZ[0][b + 1] = T(ldV[it].y);
+        sZ[1][b] = T(ldX[it].x);
+        sZ[1][b + 1] = T(ldX[it].y);
+        sZ[2][b] = T(ldY[it].x);
+        sZ[2][b + 1] = T(ldY[it].y);
+      }
+    }
+  } else {
+    constexpr int NP0 = (BN + NT - 1) / NT;
+    double ldU[NP0];
+    PT ldV[NP0], ldX[NP0], ldY[NP0];
+#pragma unroll
+    for (int it = 0; it < NP0; ++it) {
+      const int k = tid + it * NT;
+      if (k < BN) {
+        const int bx = k % BX, by = k / BX;
+        const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
+        const size_t g = (size_t)gj * nx + gi;
+        ldU[it] = A.ub[g];
+        ldV[it] = A.V[g];
+        ldX[it] = A.X[g];
+        ldY[it] = A.Y[g];
+      }
+    }
+#pragma unroll
+    for (int it = 0; it < NP0; ++it) {
+      const int k = tid + it * NT;
+      if (k < BN) {
+        sU[k] = to_stencil<T>(ldU[it]);
+        sZ[0][k] = T(ldV[it]);
+        sZ[1][k] = T(ldX[it]);
+        sZ[2][k] = T(ldY[it]);
+      }
     }
   }
   __syncthreads();
