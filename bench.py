@@ -40,7 +40,7 @@ BYTES_PER_CELL_STAGE = {"fp64": 85.33, "fp32_mixed": 53.33}
 # the ncu captures summarised in profiles/stage2d_fp64_degenerate_burgers_1024.md and
 # profiles/stage2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
 # for any other size.
-NCU_TRAFFIC_PER_LAUNCH = {("fp64", 1024): 75.98e6, ("fp32_mixed", 2048): 226.59e6}
+NCU_TRAFFIC_PER_LAUNCH = {("fp64", 1024): 75.74e6, ("fp32_mixed", 2048): 226.64e6}
 
 
 def load_peaks():

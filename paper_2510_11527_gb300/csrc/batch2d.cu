@@ -88,7 +88,8 @@ __device__ __forceinline__ void batch_stage_body(const BatchInst* __restrict__ i
     A.stats = stats;
     }
     __syncthreads();
-    stage_tile<FLUX, T, PT, false, TX, TY>(I.m, A, i0, j0, smem_raw);
+    // element-wise halo loads: the paired path's extra registers spill in this kernel
+    stage_tile<FLUX, T, PT, false, TX, TY, false>(I.m, A, i0, j0, smem_raw);
     __syncthreads();
   }
 }

@@ -353,7 +353,7 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
   const int nb = (int)std::min<size_t>(af::STATE_IO_BLOCKS, (na * n + af::RED_THREADS - 1) / af::RED_THREADS);
   af::validate_partial_kernel<<<nb, af::RED_THREADS, 0, c->stream>>>(stg, na * n, (unsigned long long*)c->partial);
   CK(c, cudaGetLastError());
-  af::validate_final_kernel<<<1, 1, 0, c->stream>>>((const unsigned long long*)c->partial, nb, c->red + 5);
+  af::validate_final_kernel<<<1, af::RED_THREADS, 0, c->stream>>>((const unsigned long long*)c->partial, nb, c->red + 5);
   CK(c, cudaGetLastError());
   CK(c, cudaMemcpyAsync(c->host_pinned, c->red + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(c, cudaStreamSynchronize(c->stream));

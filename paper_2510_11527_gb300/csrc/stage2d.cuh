@@ -167,7 +167,8 @@ __device__ __forceinline__ T line_res(T z0, T z1, T z2, T z3, T z4, T f0, T f1, 
 
 // One TX x TY tile with origin (i0, j0) of one mesh: all phases P0-P5. Every thread of
 // the CTA must call it (it contains __syncthreads); smem_raw holds Tile2D::SMEM bytes.
-template <int FLUX, class T, class PT, bool BLEND, int TX_ = 32, int TY_ = 8>
+// PAIRED enables the paired vector loads of interior halo boxes (P0).
+template <int FLUX, class T, class PT, bool BLEND, int TX_ = 32, int TY_ = 8, bool PAIRED = true>
 __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<PT>& A, const int i0, const int j0,
                                            unsigned char* smem_raw) {
   using L = Tile2D<FLUX, T, BLEND, TX_, TY_>;
@@ -235,7 +236,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   // (periodic wrap, odd widths, the +-3 blend halo) load element by element. In both,
   // all loads of a thread are issued before its first store, so their latencies overlap.
   bool paired = false;
-  if constexpr (H == 2) {
+  if constexpr (H == 2 && PAIRED) {
     paired = (nx % 2 == 0) && i0 - H >= 0 && i0 + TX + H <= nx && j0 - H >= 0 && j0 + TY + H <= ny;
   }
   if (paired) {

@@ -15,21 +15,8 @@ __device__ __forceinline__ double undkey(long long k) {
   return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
 }
 
-// per block: number of NaNs, min and max (as order-preserving keys) of x[0, n)
-__global__ void __launch_bounds__(RED_THREADS) validate_partial_kernel(const double* __restrict__ x, size_t n,
-                                                                       unsigned long long* partial) {
-  unsigned long long nan = 0;
-  long long lo = LLONG_MAX, hi = LLONG_MIN;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    const long long b = __double_as_longlong(x[k]);
-    if ((b & 0x7FFFFFFFFFFFFFFFLL) > 0x7FF0000000000000LL) {
-      ++nan;
-    } else {
-      const long long key = b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
-      lo = key < lo ? key : lo;
-      hi = key > hi ? key : hi;
-    }
-  }
+// (NaN count, min key, max key) over the block; the result is valid in thread 0
+__device__ __forceinline__ void block_nan_min_max(unsigned long long& nan, long long& lo, long long& hi) {
   for (int o = 16; o > 0; o >>= 1) {
     nan += __shfl_xor_sync(0xffffffffu, nan, o);
     const long long l2 = __shfl_xor_sync(0xffffffffu, lo, o), h2 = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -50,26 +37,50 @@ __global__ void __launch_bounds__(RED_THREADS) validate_partial_kernel(const dou
       lo = sl[w] < lo ? sl[w] : lo;
       hi = sh[w] > hi ? sh[w] : hi;
     }
+  }
+}
+
+// per block: number of NaNs, min and max (as order-preserving keys) of x[0, n)
+__global__ void __launch_bounds__(RED_THREADS) validate_partial_kernel(const double* __restrict__ x, size_t n,
+                                                                       unsigned long long* partial) {
+  unsigned long long nan = 0;
+  long long lo = LLONG_MAX, hi = LLONG_MIN;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const long long b = __double_as_longlong(x[k]);
+    if ((b & 0x7FFFFFFFFFFFFFFFLL) > 0x7FF0000000000000LL) {
+      ++nan;
+    } else {
+      const long long key = b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+      lo = key < lo ? key : lo;
+      hi = key > hi ? key : hi;
+    }
+  }
+  block_nan_min_max(nan, lo, hi);
+  if (threadIdx.x == 0) {
     partial[blockIdx.x] = nan;
     partial[gridDim.x + blockIdx.x] = (unsigned long long)lo;
     partial[2 * gridDim.x + blockIdx.x] = (unsigned long long)hi;
   }
 }
 
-// out[0] = NaN count, out[1] = min, out[2] = max over the nb block partials
-static __global__ void validate_final_kernel(const unsigned long long* partial, int nb, double* out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// out[0] = NaN count, out[1] = min, out[2] = max over the nb block partials (one block
+// of RED_THREADS)
+static __global__ void __launch_bounds__(RED_THREADS) validate_final_kernel(const unsigned long long* partial,
+                                                                            int nb, double* out) {
   unsigned long long nan = 0;
   long long lo = LLONG_MAX, hi = LLONG_MIN;
-  for (int b = 0; b < nb; ++b) {
+  for (int b = threadIdx.x; b < nb; b += RED_THREADS) {
     nan += partial[b];
     const long long l = (long long)partial[nb + b], h = (long long)partial[2 * nb + b];
     lo = l < lo ? l : lo;
     hi = h > hi ? h : hi;
   }
-  out[0] = (double)nan;
-  out[1] = undkey(lo);
-  out[2] = undkey(hi);
+  block_nan_min_max(nan, lo, hi);
+  if (threadIdx.x == 0) {
+    out[0] = (double)nan;
+    out[1] = undkey(lo);
+    out[2] = undkey(hi);
+  }
 }
 
 // staged doubles (na arrays of n, back to back) -> state buffers (points rounded to
