@@ -36,6 +36,9 @@ FLOPS_PER_CELL_STAGE = 571.03
 # Algorithmic HBM bytes per cell-stage of SSP-RK3 (read the stage input and the RK
 # combination input once, write the output once; 10.67 value slots per 4 DoFs).
 BYTES_PER_CELL_STAGE = {"fp64": 85.33, "fp32_mixed": 53.33}
+# SSP-RK(5,4) in the stage layout of the library: 2 + 3 + 3 + 5 + 3 = 16 state passes
+# over 5 stages (the fourth stage reads U3, U0, U2 and writes U1, U2), 3.2 per stage.
+BYTES_PER_CELL_STAGE_RK54 = {"fp64": 102.4, "fp32_mixed": 64.0}
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch (SSP-RK3 stage 2) from
 # the ncu captures summarised in profiles/stage2d_fp64_degenerate_burgers_1024.md and
 # profiles/stage2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
@@ -297,10 +300,10 @@ def _solver_stepper(solver, stream):
     return step
 
 
-def _single_form(spec, prec, steps, warmup, state_dev, stream, flush=None, net=None):
+def _single_form(spec, prec, steps, warmup, state_dev, stream, flush=None, net=None, rk=3):
     import statistics as st_
     from paper_2510_11527_gb300 import Solver, capi
-    s = Solver(spec, precision=prec, rk=3)
+    s = Solver(spec, precision=prec, rk=rk)
     s.set_stream(stream)
     # bounds and a valid initial state are set through the API on a 1x copy, then the
     # full device state is written in place
@@ -313,8 +316,8 @@ def _single_form(spec, prec, steps, warmup, state_dev, stream, flush=None, net=N
     return s, out
 
 
-def _hbm_roof(prec, cells, stage_ms, peaks, extra_bytes=0.0):
-    b = BYTES_PER_CELL_STAGE[prec] + extra_bytes
+def _hbm_roof(prec, cells, stage_ms, peaks, extra_bytes=0.0, rk=3):
+    b = (BYTES_PER_CELL_STAGE if rk == 3 else BYTES_PER_CELL_STAGE_RK54)[prec] + extra_bytes
     ach = b * cells / (stage_ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": round(ach / peaks["hbm_gbs"], 4), "bytes_per_cell_stage": b}
@@ -330,6 +333,8 @@ def forms(args, headline_value, peaks):
     sel = set(args.forms.split(","))
     if "fp32" in sel:
         res.update(_form_fp32(args, stream, flush, peaks))
+    if "rk54" in sel:
+        res.update(_form_rk54(args, stream, flush, peaks))
     if "pme" in sel:
         res.update(_form_pme(args, stream, peaks))
     if "batch" in sel:
@@ -359,6 +364,26 @@ def _form_fp32(args, stream, flush, peaks):
     return res
 
 
+def _form_rk54(args, stream, flush, peaks):
+    """Degenerate Burgers 1024^2 with SSP-RK(5,4), FP64 and FP32-mixed."""
+    import af_inputs as ai
+    spec = ai.config2(1024)
+    st = ai.initial_state(spec, device="cuda")
+    s64, r64 = _single_form(spec, "fp64", args.form_steps, 3, st, stream, flush, rk=54)
+    s32, r32 = _single_form(spec, "fp32_mixed", args.form_steps, 3, st, stream, flush, rk=54)
+    l1 = max(float((x.double() - y.double()).abs().mean()) for x, y in zip(s32.device_tensors(), s64.device_tensors()))
+    res = {"rk54_degenerate_burgers_1024": {
+        "fp64_value": round(r64["value"], 1), "fp32_mixed_value": round(r32["value"], 1),
+        "speedup_fp32_vs_fp64": round(r32["value"] / r64["value"], 2), "l1_fp32_vs_fp64": l1,
+        "roofline_fp32": _hbm_roof("fp32_mixed", spec.cells, r32["stage_ms_avg"], peaks, rk=54),
+        # one limited forward-Euler evaluation's flops per stage (conservative: the fourth
+        # stage's second evaluation, which shares the tau-independent work, is not counted)
+        "fp64_tflops": round(FLOPS_PER_CELL_STAGE * spec.cells / (r64["stage_ms_avg"] / 1e3) / 1e12, 4)}}
+    s64.close()
+    s32.close()
+    return res
+
+
 def _form_pme(args, stream, peaks):
     """Porous medium 4096^2 from the Barenblatt profile, FP32-mixed vs FP64."""
     import af_inputs as ai
@@ -380,13 +405,12 @@ def _form_pme(args, stream, peaks):
     return res
 
 
-def _form_batch(args, stream, headline_value, peaks):
-    """256 uneven instances, FP32-mixed, graph replay, autotuned tile."""
+def _batch_run(inst, prec, steps):
+    """Build the batch in precision `prec`, autotune its tile, time `steps` graph-replayed
+    steps; returns (cell-stage/s, cells, tile, ms per step, safeguard errors)."""
     import torch
     import af_inputs as ai
     from paper_2510_11527_gb300 import capi
-    res = {}
-    inst = ai.batch_instances()
     grids, fl, df, bd = [], [], [], []
     for s_, _ in inst:
         grids.append(capi.af_grid(2, s_.nx, s_.ny, s_.x0, s_.x1, s_.y0, s_.y1))
@@ -400,7 +424,7 @@ def _form_batch(args, stream, headline_value, peaks):
         fl.append(f)
         df.append(d)
         bd.append(capi.af_bounds_t(s_.umin, s_.umax, 0))
-    opts = capi.af_opts(capi.PREC["fp32_mixed"], 3, 0.0, 0.0, 1, 0, 1.0)
+    opts = capi.af_opts(capi.PREC[prec], 3, 0.0, 0.0, 1, 0, 1.0)
     b = capi.af_batch_create(grids, fl, df, bd, opts)
     try:
         cells = 0
@@ -419,20 +443,27 @@ def _form_batch(args, stream, headline_value, peaks):
         torch.cuda.synchronize()
         # the batch runs on its own stream; record around a synchronised replay
         e0.record()
-        capi.af_batch_step(b, args.form_steps)
+        capi.af_batch_step(b, steps)
         capi.af_batch_sync(b)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
-        val = cells * 3 * args.form_steps / (ms / 1e3)
-        stats = capi.af_batch_stats(b)
-        res["batch_256_fp32_mixed"] = {
-            "value": round(val, 1), "cells": cells, "tile": list(tile), "ms_per_step": round(ms / args.form_steps, 4),
-            "speedup_vs_fp64_single_mesh": round(val / headline_value, 2), "safeguard_errors": stats["errors"],
-            "roofline": _hbm_roof("fp32_mixed", cells, ms / args.form_steps / 3, peaks)}
+        return cells * 3 * steps / (ms / 1e3), cells, tile, ms / steps, capi.af_batch_stats(b)["errors"]
     finally:
         capi.af_batch_destroy(b)
-    return res
+
+
+def _form_batch(args, stream, headline_value, peaks):
+    """256 uneven instances (FP32-mixed and FP64), graph replay, autotuned tile."""
+    import af_inputs as ai
+    inst = ai.batch_instances()
+    val, cells, tile, ms_step, errors = _batch_run(inst, "fp32_mixed", args.form_steps)
+    v64, _, tile64, _, err64 = _batch_run(inst, "fp64", max(1, args.form_steps // 2))
+    return {"batch_256_fp32_mixed": {
+        "value": round(val, 1), "cells": cells, "tile": list(tile), "ms_per_step": round(ms_step, 4),
+        "fp64_value": round(v64, 1), "fp64_tile": list(tile64), "speedup_vs_fp64": round(val / v64, 2),
+        "speedup_vs_fp64_single_mesh": round(val / headline_value, 2), "safeguard_errors": errors + err64,
+        "roofline": _hbm_roof("fp32_mixed", cells, ms_step / 3, peaks)}}
 
 
 def _form_bl(args, stream, peaks):
@@ -565,8 +596,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/batched/learned forms")
     ap.add_argument("--form-steps", type=int, default=5)
-    ap.add_argument("--forms", default="fp32,pme,batch,bl",
-                    help="comma list of forms to run: fp32 (Burgers 1024^2), pme (4096^2), batch (256), bl (4096^2)")
+    ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl",
+                    help="comma list of forms to run: fp32 (Burgers 1024^2), rk54 (Burgers 1024^2 with "
+                         "SSP-RK(5,4)), pme (4096^2), batch (256), bl (4096^2)")
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)

@@ -28,3 +28,7 @@ def test_bytes_per_cell_stage():
     arrays = (2 + 3 + 3) / 3
     assert np.isclose(bench.BYTES_PER_CELL_STAGE["fp64"], round(arrays * 4 * 8, 2), atol=0.01)
     assert np.isclose(bench.BYTES_PER_CELL_STAGE["fp32_mixed"], round(arrays * (8 + 3 * 4), 2), atol=0.01)
+    # SSP-RK(5,4): stage passes 2, 3, 3, 5 (reads U3, U0, U2, writes U1, U2), 3 over 5 stages
+    arrays54 = (2 + 3 + 3 + 5 + 3) / 5
+    assert np.isclose(bench.BYTES_PER_CELL_STAGE_RK54["fp64"], arrays54 * 4 * 8)
+    assert np.isclose(bench.BYTES_PER_CELL_STAGE_RK54["fp32_mixed"], arrays54 * (8 + 3 * 4))
