@@ -43,7 +43,10 @@ BYTES_PER_CELL_STAGE_RK54 = {"fp64": 102.4, "fp32_mixed": 64.0}
 # the ncu captures summarised in profiles/stage2d_fp64_degenerate_burgers_1024.md and
 # profiles/stage2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
 # for any other size.
-NCU_TRAFFIC_PER_LAUNCH = {("fp64", 1024): 75.74e6, ("fp32_mixed", 2048): 226.64e6}
+NCU_TRAFFIC_PER_LAUNCH = {("fp64", 1024): 75.29e6, ("fp32_mixed", 2048): 227.18e6}
+# thread instructions per cell-stage of the FP32-mixed stage from the same capture
+# (smsp__inst_executed.sum x 32 / cells)
+NCU_INSTR_PER_CELL_STAGE = {("fp32_mixed", 2048): 1664.0}
 
 
 def load_peaks():
@@ -221,6 +224,17 @@ def run_gpu(args):
             roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                     "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get((prec, args.n)),
                     "peak_source": peak_src}
+            ipc = NCU_INSTR_PER_CELL_STAGE.get((prec, args.n))
+            if ipc:
+                # what actually bounds this form: instruction issue (one warp instruction
+                # per clock per SM sub-partition at the sampled maximum SM clock)
+                props = torch.cuda.get_device_properties(local)
+                mhz = clk.summary().get("sm_max_mhz") or 2070.0
+                peak_issue = props.multi_processor_count * 4 * mhz * 1e6
+                got = ipc / 32 * cells / avg_stage_s
+                roof["issue_view"] = {"warp_instr_per_cell_stage": round(ipc / 32, 2), "achieved": round(got, 1),
+                                      "peak": round(peak_issue, 1), "unit": "warp instructions/s",
+                                      "frac": round(got / peak_issue, 4)}
         result = {
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,

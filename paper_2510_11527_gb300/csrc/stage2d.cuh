@@ -720,11 +720,12 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   }
 }
 
-// One CTA per 32 x 8 tile of a single mesh.
+// One CTA per 32 x 8 tile of a single mesh (row-major tile index in blockIdx.x).
 template <int FLUX, class T, class PT, bool BLEND>
 __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const StageArgs2D<PT> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_tile<FLUX, T, PT, BLEND, 32, 8>(m, A, blockIdx.x * 32, blockIdx.y * 8, smem_raw);
+  const int tiles_x = (A.nx + 31) / 32, t = blockIdx.x;   // 1D grid: no 65535 limit on rows
+  stage_tile<FLUX, T, PT, BLEND, 32, 8>(m, A, (t % tiles_x) * 32, (t / tiles_x) * 8, smem_raw);
 }
 
 // The same for the FP32 stencils without the blend, compiled for 6 resident CTAs per SM
@@ -733,7 +734,8 @@ __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const St
 template <int FLUX>
 __global__ void __launch_bounds__(256, 6) stage2d_kernel_f32occ6(const DevModel m, const StageArgs2D<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  stage_tile<FLUX, float, float, false, 32, 8>(m, A, blockIdx.x * 32, blockIdx.y * 8, smem_raw);
+  const int tiles_x = (A.nx + 31) / 32, t = blockIdx.x;
+  stage_tile<FLUX, float, float, false, 32, 8>(m, A, (t % tiles_x) * 32, (t / tiles_x) * 8, smem_raw);
 }
 
 }  // namespace af

@@ -19,7 +19,9 @@ static cudaError_t go(const DevModel& m, const StageArgs2D<float>& a, cudaStream
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  dim3 grid((a.nx + L::TX - 1) / L::TX, (a.ny + L::TY - 1) / L::TY);
+  const long long tiles = (long long)((a.nx + L::TX - 1) / L::TX) * ((a.ny + L::TY - 1) / L::TY);
+  if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)tiles);
   k<<<grid, L::NT, L::SMEM, s>>>(m, a);
   return cudaGetLastError();
 }

@@ -100,3 +100,20 @@ def test_checkpoint_resume_is_bitwise(prec):
         resumed = c.get_state()
     for x, y in zip(full, resumed):
         assert np.array_equal(x, y)
+
+
+def test_oversize_mesh_reports_oom_and_device_stays_usable():
+    """A mesh far larger than device memory (1e6 x 1e6 cells, ~1e14 bytes) fails with
+    AF_E_OOM at creation, without a fault; a normal context works afterwards."""
+    from paper_2510_11527_gb300 import Solver, capi
+    g = capi.af_grid(2, 1000000, 1000000, 0.0, 1.0, 0.0, 1.0)
+    f, d = capi.af_flux(), capi.af_diff()
+    with pytest.raises(capi.AfError) as ei:
+        capi.af_create(g, f, d, capi.af_bounds_t(0.0, 1.0, 0), capi.af_opts(0, 3, 0.0, 0.0, 1, 0, 1.0))
+    assert ei.value.status == capi.AF_E_OOM
+    spec = ai.config2(16)
+    st = [a.numpy() for a in ai.random_state_2d(spec, seed=2, lo=-1, hi=1)]
+    with Solver(spec) as s:
+        s.set_state(st)
+        s.step(0.0)
+        assert s.stats()["errors"] == 0

@@ -329,3 +329,17 @@ def test_device_cfl_step_interior_extrema(pattern):
     with solver(spec) as s:
         s.set_state(st)
         assert s.dt_cfl() == pytest.approx(oracle.dt_cfl(spec, ub), rel=1e-14)
+
+
+def test_forward_euler_tall_mesh():
+    """A mesh with more than 65535 tile rows (8 x 600000 cells): the stage grid is linear
+    in the tile index, so any aspect ratio launches."""
+    spec = spec2d("burgers_pwl", 8, 600000, x1=0.05, y1=600.0)
+    st = np_state(ai.random_state_2d(spec, seed=11))
+    tau = oracle.dt_cfl(spec, st[0])
+    want = oracle.fe(spec, st, tau)
+    with solver(spec) as s:
+        s.set_state(st)
+        s.forward_euler(tau)
+        got = s.get_state()
+    assert relerr(got, want) <= TOL64
