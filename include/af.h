@@ -137,7 +137,11 @@ int af_num_stages(const af_ctx* ctx);
 af_status af_step(af_ctx* ctx, double dt, double* dt_used);
 
 /* March to time T from the current time with CFL steps, clipping the last step to
- * land on T. Synchronises once per step to read dt. */
+ * land on T; *nsteps (if non-NULL) receives the number of steps taken (0 if the time
+ * is already T). The device clips each step and counts them; the host issues steps in
+ * chunks of 16 and synchronises once per chunk to read the time (steps issued past T
+ * have dt = 0 and change nothing). AF_E_STATE if the CFL step is not positive or a
+ * value left [umin, umax] beyond the safeguard tolerance. */
 af_status af_run(af_ctx* ctx, double T, long long* nsteps);
 af_status af_time(af_ctx* ctx, double* t);       /* simulated time (synchronises) */
 

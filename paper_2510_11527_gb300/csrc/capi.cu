@@ -195,7 +195,7 @@ cudaError_t launch_rate(af_ctx* c) {
 }
 
 // device CFL step -> *dst (no host round trip); t_acc: advance the device time
-af_status dt_device(af_ctx* c, double* dst, double* t_acc) {
+af_status dt_device(af_ctx* c, double* dst, double* t_acc, double t_end = -1.0, double* count = nullptr) {
   cudaError_t e;
   switch (c->flux.kind) {
     case AF_FLUX_ZERO: e = launch_rate<af::FLUX_ZERO>(c); break;
@@ -206,7 +206,7 @@ af_status dt_device(af_ctx* c, double* dst, double* t_acc) {
   CK(c, e);
   const double hmin = c->dim == 1 ? c->dx : std::min(c->dx, c->dy);
   af::dt_finalize_kernel<<<1, 1, 0, c->stream>>>(c->rate_bits, c->m, c->dim, c->inv_h1, c->inv_h2, c->cfl,
-                                                 c->cfl_diff, c->kmax, 1.0 / (hmin * hmin), dst, t_acc);
+                                                 c->cfl_diff, c->kmax, 1.0 / (hmin * hmin), dst, t_acc, t_end, count);
   CK(c, cudaGetLastError());
   return AF_OK;
 }
@@ -489,21 +489,30 @@ af_status af_run(af_ctx* c, double T, long long* nsteps) {
   double t;
   af_status s = read_scalar(c, c->t_dev, &t);
   if (s != AF_OK) return s;
-  long long n = 0;
+  // Steps are issued in chunks without a host round trip: the device clips each CFL
+  // step to the time left before T and counts the positive ones; the steps of a chunk
+  // after T is reached have dt = 0, and a stage with dt = 0 writes nothing.
+  double* count = c->red + 0;   // slot 0: step count of af_run
+  CK(c, cudaMemsetAsync(count, 0, sizeof(double), c->stream));
+  const int chunk = 16;
   while (t < T * (1.0 - 1e-14)) {
-    double dt;
-    s = dt_device(c, c->red + 0, nullptr);
+    for (int q = 0; q < chunk; ++q) {
+      s = dt_device(c, c->dt_dev, c->t_dev, T, count);
+      if (s != AF_OK) return s;
+      for (int k = 0; k < af_num_stages(c); ++k) {
+        s = stage_any(c, k);
+        if (s != AF_OK) return s;
+      }
+    }
+    const double t_prev = t;
+    s = read_scalar(c, c->t_dev, &t);
     if (s != AF_OK) return s;
-    s = read_scalar(c, c->red + 0, &dt);
-    if (s != AF_OK) return s;
-    if (!(dt > 0.0)) FAIL(c, AF_E_STATE, "non-positive CFL time step");
-    dt = std::min(dt, T - t);
-    s = af_step(c, dt, nullptr);
-    if (s != AF_OK) return s;
-    t += dt;
-    ++n;
+    if (!(t > t_prev)) FAIL(c, AF_E_STATE, "non-positive CFL time step");
   }
-  if (nsteps) *nsteps = n;
+  double n = 0.0;
+  s = read_scalar(c, count, &n);
+  if (s != AF_OK) return s;
+  if (nsteps) *nsteps = (long long)n;
   long long cl = 0, er = 0;
   double mx = 0;
   s = af_stats(c, &cl, &er, &mx, nullptr);

@@ -89,15 +89,22 @@ __device__ __forceinline__ double crit_rate(const DevModel& m, int dim, double i
 }
 
 // dt = 1 / max(rate / C, kappa_max / (h_min^2 Cd)). Resets the accumulators for the
-// next step. When t_acc is given the step is also added to the simulated time.
+// next step. When t_acc is given the step is also added to the simulated time; with
+// t_end > 0 the step is first clipped to the time left before t_end (0 once less than
+// t_end * 1e-14 is left) and each positive step is counted in *count.
 static __global__ void dt_finalize_kernel(unsigned long long* rate_bits, const DevModel m, int dim, double inv_h1,
                                           double inv_h2, double cfl, double cfl_diff, double kmax, double inv_hmin2,
-                                          double* dt_out, double* t_acc) {
+                                          double* dt_out, double* t_acc, double t_end, double* count) {
   const double rate =
       crit_rate(m, dim, inv_h1, inv_h2, kmax, rate_bits[1], __longlong_as_double((long long)rate_bits[0]));
   double r = rate / cfl;
   if (cfl_diff > 0.0 && kmax > 0.0) r = fmax(r, kmax * inv_hmin2 / cfl_diff);
-  const double dt = r > 0.0 ? 1.0 / r : 0.0;
+  double dt = r > 0.0 ? 1.0 / r : 0.0;
+  if (t_acc && t_end > 0.0) {
+    const double left = t_end - *t_acc;
+    dt = left > t_end * 1e-14 ? fmin(dt, left) : 0.0;
+    if (dt > 0.0) *count += 1.0;
+  }
   *dt_out = dt;
   if (t_acc) *t_acc += dt;
   rate_bits[0] = 0ull;

@@ -343,3 +343,20 @@ def test_forward_euler_tall_mesh():
         s.forward_euler(tau)
         got = s.get_state()
     assert relerr(got, want) <= TOL64
+
+
+def test_run_is_idempotent_at_its_end_time():
+    """af_run issues steps in chunks and clips on the device: a second run to the same
+    time takes no step and leaves the state unchanged; a later end time continues."""
+    spec = ai.config2(40)
+    st = np_state(ai.initial_state(spec))
+    with solver(spec) as s:
+        s.set_state(st)
+        n1 = s.run(0.02)
+        a = s.get_state()
+        assert s.run(0.02) == 0
+        b = s.get_state()
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+        n2 = s.run(0.03)
+        assert n1 > 0 and n2 > 0 and s.time() == pytest.approx(0.03, rel=1e-14)
+        assert s.stats()["errors"] == 0
