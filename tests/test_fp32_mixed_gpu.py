@@ -90,3 +90,25 @@ def test_fp32_1d_config1_accuracy():
     i = np.arange(128)
     ex = np.exp(-0.01) * np.sin((i + 1.0) * spec.dx - 1.0)
     assert np.max(np.abs(got[1] - ex)) < 1e-4
+
+
+@pytest.mark.parametrize("rk", [3, 54])
+def test_fp32_rk_steps_vs_oracle(rk):
+    """Three limited SSP-RK3 / SSP-RK(5,4) steps of the FP32-mixed form on a rough
+    Burgers state against the FP64 oracle: within the FP32 tolerance, bounds exact."""
+    spec = ai.Spec(dim=2, nx=48, ny=40, x0=0, x1=1.2, y0=0, y1=1.0, flux=("burgers", (0.5,)),
+                   diff=("pwl", (0.0, 0.0, 0.1, 0.5)), umin=-1.0, umax=1.0, limiter=True)
+    st = [a.numpy() for a in ai.random_state_2d(spec, seed=21)]
+    ref = [np.array(a) for a in st]
+    with solver(spec, "fp32_mixed", rk=rk) as s:
+        s.set_state(st)
+        for _ in range(3):
+            dt = oracle.dt_cfl(spec, ref[0])
+            ref, _ = oracle.step(spec, rk, ref, dt)
+            s.step(dt)
+        got = s.get_state()
+        lo, hi = s.bounds()
+        assert s.stats()["errors"] == 0
+    assert lo >= -1.0 and hi <= 1.0
+    assert linf(got, ref) <= 1e-5
+    assert l1(got, ref) <= 1e-6
