@@ -109,8 +109,9 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&p);
 }
 
-// Tensor-core network on 16 rows held (bf16, [16][40]) in shared memory; returns s for
-// rows g and g + 8 in lanes with t == 0.
+// Tensor-core network on 16 rows held (bf16, [16][40]) in shared memory; returns the
+// output pre-activation z (s = softplus(z)) of rows g and g + 8 in all four lanes of
+// quad g.
 struct NetFrags {
   uint32_t b1[2][4][2], b2[2][4][2];
   float bias1[4][2], bias2[4][2], w3[4][2], b3;
@@ -188,8 +189,8 @@ __device__ __forceinline__ void net_rows(const NetFrags& F, const __nv_bfloat16 
   r8 += __shfl_xor_sync(0xffffffffu, r8, 1);
   r8 += __shfl_xor_sync(0xffffffffu, r8, 2);
   (void)t;
-  *s0 = softplusf(r0 + F.b3);
-  *s8 = softplusf(r8 + F.b3);
+  *s0 = r0 + F.b3;
+  *s8 = r8 + F.b3;
 }
 
 // Fused inference on a state, s (double) per cell. Each CTA takes 32 x 8 tiles of
@@ -249,15 +250,16 @@ __global__ void __launch_bounds__(256, 3) indicator_kernel(const double* __restr
     }
     __syncwarp();
     const int j = j0 + warp;
+    float z[2][2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      float s0, s8;
-      net_rows(F, sx[warp] + 16 * h, lane, &s0, &s8);
-      if ((lane & 3) == 0 && j < ny) {
-        const int i = i0 + 16 * h + (lane >> 2);
-        if (i < nx) out[(size_t)j * nx + i] = af::f2d_exact(s0);
-        if (i + 8 < nx) out[(size_t)j * nx + i + 8] = af::f2d_exact(s8);
-      }
+    for (int h = 0; h < 2; ++h) net_rows(F, sx[warp] + 16 * h, lane, &z[h][0], &z[h][1]);
+    {
+      // the four lanes of a quad share the four pre-activations (rows g, g + 8 of both
+      // 16-row blocks): each applies the output activation to one of them
+      const int t = lane & 3, h = t >> 1, w = t & 1;
+      const float s = softplusf(z[h][w]);
+      const int i = i0 + 16 * h + (lane >> 2) + 8 * w;
+      if (j < ny && i < nx) out[(size_t)j * nx + i] = af::f2d_exact(s);
     }
     __syncthreads();
   }
@@ -283,12 +285,14 @@ __global__ void __launch_bounds__(256) infer_rows_kernel(const float* __restrict
       }
     }
     __syncwarp();
-    float s0, s8;
-    net_rows(F, sx[warp], lane, &s0, &s8);
-    if ((lane & 3) == 0) {
-      const long long r0 = base + (lane >> 2), r8 = r0 + 8;
-      if (r0 < n) out[r0] = s0;
-      if (r8 < n) out[r8] = s8;
+    float z0, z8;
+    net_rows(F, sx[warp], lane, &z0, &z8);
+    // lanes t = 0, 1 of each quad apply the output activation to rows g, g + 8
+    const int t = lane & 3;
+    if (t < 2) {
+      const long long row = base + (lane >> 2) + 8 * t;
+      const float s = softplusf(t ? z8 : z0);
+      if (row < n) out[row] = s;
     }
     __syncwarp();
   }
