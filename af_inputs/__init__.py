@@ -7,7 +7,8 @@ it produces, so the two sides always start from identical inputs.
 
 Layout of a 2D state (periodic, row-major [ny][nx], i fastest):
   ub[j,i] cell average, V[j,i] at (x_{i+1/2}, y_{j+1/2}), X[j,i] at (x_{i+1/2}, y_j),
-  Y[j,i] at (x_i, y_{j+1/2}).  A 1D state is (ub[i], P[i] = u(x_{i+1/2})).
+  Y[j,i] at (x_i, y_{j+1/2}).  A 1D state is (ub[i], P[i] = u(x_{i+1/2})); on a 1D
+  interval with Dirichlet or outflow ends P has nx+1 entries, P[k] = u(x0 + k dx).
 
 Cell averages use a tensor Gauss-Legendre rule on sub-cells (exact closed forms for
 single Fourier modes); point values are exact evaluations. Disc indicators use the
@@ -25,14 +26,19 @@ import torch
 
 @dataclasses.dataclass
 class Spec:
-    """Problem description: periodic mesh, flux, diffusion potential, bounds, options.
+    """Problem description: mesh, flux, diffusion potential, bounds, options.
 
     flux: ("zero", ()), ("linear", (cx, cy)), ("burgers", (coef,)) for f = coef*u^2 in
           every direction, ("bl", (g,)) for f1 = u^2/(u^2+(1-u)^2), f2 = f1*(1-g(1-u)^2).
     diff: ("none", ()), ("const", (k0,)) for a = k0*u,
           ("pwl", (klo, lo, khi, hi)) for a = klo*min(u-lo,0) + khi*max(u-hi,0),
-          ("pme", (m,)) for a = u^m, ("cubic", (c1, c2, c3)) for a = c1 u + c2 u^2 + c3 u^3.
+          ("pme", (m,)) for a = u^m, ("cubic", (c1, c2, c3)) for a = c1 u + c2 u^2 + c3 u^3,
+          ("ramp", (k, lo, w)) for a = 0 (u <= lo), k (u-lo)^2/(2w) (lo < u < lo+w),
+          k (u - lo - w/2) (u >= lo+w).
     blend: "off", "plain" (smoothness indicator) or "external" (per-cell indicator input).
+    bc: "periodic", or in 1D "dirichlet" (end values bc_values) or "outflow".
+    diffusion_form: "dc" (doubly conservative) or, in 1D, "nodc" (the diffusion
+          discretization without double conservation of Appendix A).
     """
     dim: int
     nx: int
@@ -52,6 +58,9 @@ class Spec:
     cfl: float = 0.0          # 0 -> 0.33/d (the paper's experiments)
     T: float = 0.0
     name: str = ""
+    bc: str = "periodic"
+    bc_values: Tuple[float, float] = (0.0, 0.0)
+    diffusion_form: str = "dc"
 
     @property
     def dx(self) -> float:
@@ -134,8 +143,18 @@ def points_2d(func: Callable, spec: Spec, device="cpu"):
 
 
 def points_1d(func: Callable, spec: Spec, device="cpu"):
+    """Point values u(x_{i+1/2}), i = 0..nx-1 (periodic), or u(x0 + k dx), k = 0..nx
+    (an interval with boundary conditions)."""
+    if spec.bc != "periodic":
+        k = torch.arange(spec.nx + 1, dtype=torch.float64, device=device)
+        return func(spec.x0 + k * spec.dx)
     i = torch.arange(spec.nx, dtype=torch.float64, device=device)
     return func(spec.x0 + (i + 1.0) * spec.dx)
+
+
+def state_1d(func: Callable, spec: Spec, device="cpu", sub: int = 4, order: int = 5) -> List[torch.Tensor]:
+    return [cell_average_1d(func, spec, sub=sub, order=order, device=device).contiguous(),
+            points_1d(func, spec, device=device).contiguous()]
 
 
 def state_2d(func: Callable, spec: Spec, device="cpu", sub: int = 4, order: int = 5) -> List[torch.Tensor]:
@@ -224,6 +243,36 @@ def config1_dt(spec: Spec, frac: float = 0.9, cfl_limit: float = 0.5611) -> floa
     return frac * cfl_limit / (c / spec.dx + k0 / spec.dx ** 2)
 
 
+def evje_karlsen(n: int = 200, diffusion_form: str = "dc") -> Spec:
+    """Example 6.5 (Evje and Karlsen): f = u^2/4, a = 0 (u <= 0.5), 5(2u-1)^2/4
+    (0.5 < u < 0.6), u - 11/20 (u >= 0.6) on [-1, 1], Dirichlet u(-1) = 1, u(1) = 0,
+    MPP limiting, T = 1."""
+    return Spec(dim=1, nx=n, x0=-1.0, x1=1.0, flux=("burgers", (0.25,)), diff=("ramp", (1.0, 0.5, 0.1)),
+                umin=0.0, umax=1.0, limiter=True, rk=3, T=1.0, name="evje_karlsen", bc="dirichlet",
+                bc_values=(1.0, 0.0), diffusion_form=diffusion_form)
+
+
+def evje_karlsen_fn(x):
+    """1 on [-1, -0.4), -2.5 x on [-0.4, 0), 0 otherwise."""
+    return torch.where(x < -0.4, torch.ones_like(x), torch.where(x < 0.0, -2.5 * x, torch.zeros_like(x)))
+
+
+def strongly_degenerate_1d(n: int = 100, blend: str = "plain", limiter: bool = True,
+                           diffusion_form: str = "dc") -> Spec:
+    """Example 6.8: f = u^2, a = 0.1 (u + 0.25) (u <= -0.25), 0.1 (u - 0.25) (u >= 0.25),
+    0 otherwise, on [-2, 2] with outflow ends, T = 0.7, bounds [-1, 1]."""
+    return Spec(dim=1, nx=n, x0=-2.0, x1=2.0, flux=("burgers", (1.0,)), diff=("pwl", (0.1, -0.25, 0.1, 0.25)),
+                umin=-1.0, umax=1.0, limiter=limiter, blend=blend, gamma=1.0, rk=3, T=0.7,
+                name="strongly_degenerate1d", bc="outflow", diffusion_form=diffusion_form)
+
+
+def strongly_degenerate_fn(x):
+    """1 where |x + 1/sqrt(2)| < 0.4, -1 where |x - 1/sqrt(2)| < 0.4, 0 otherwise."""
+    r = 1.0 / math.sqrt(2.0)
+    one = torch.ones_like(x)
+    return torch.where((x + r).abs() < 0.4, one, torch.where((x - r).abs() < 0.4, -one, torch.zeros_like(x)))
+
+
 def config2(n: int = 1024) -> Spec:
     """2D strongly degenerate Burgers: f = u^2/2, kappa = 0.1 [u > 0.5], discs +-1."""
     return Spec(dim=2, nx=n, ny=n, x0=-1.5, x1=1.5, y0=-1.5, y1=1.5, flux=("burgers", (0.5,)),
@@ -248,6 +297,10 @@ def initial_state(spec: Spec, device="cpu", sub: int = 4, order: int = 5):
     """Initial DoFs for the named workloads."""
     if spec.name == "linear1d":
         return sine_1d_state(spec, device=device)
+    if spec.name == "evje_karlsen":
+        return state_1d(evje_karlsen_fn, spec, device=device, sub=sub, order=order)
+    if spec.name == "strongly_degenerate1d":
+        return state_1d(strongly_degenerate_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "degenerate_burgers2d":
         return state_2d(discs_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "pme2d":
@@ -325,7 +378,11 @@ def random_state_1d(spec: Spec, seed: int, lo: float | None = None, hi: float | 
     g = torch.Generator(device="cpu").manual_seed(seed)
     lo = spec.umin if lo is None else lo
     hi = spec.umax if hi is None else hi
-    return [lo + (hi - lo) * torch.rand((spec.nx,), generator=g, dtype=torch.float64) for _ in range(2)]
+    npts = spec.nx + (1 if spec.bc != "periodic" else 0)
+    out = [lo + (hi - lo) * torch.rand((n,), generator=g, dtype=torch.float64) for n in (spec.nx, npts)]
+    if spec.bc == "dirichlet":
+        out[1][0], out[1][-1] = spec.bc_values
+    return out
 
 
 # ----------------------------------------------------------------------------------

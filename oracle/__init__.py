@@ -23,7 +23,8 @@ import numpy as np
 from .build import build_oracle
 
 FLUX_KINDS = {"zero": 0, "linear": 1, "burgers": 2, "bl": 3}
-DIFF_KINDS = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4}
+DIFF_KINDS = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4, "ramp": 5}
+BC_KINDS = {"periodic": 0, "dirichlet": 1, "outflow": 2}
 BLEND_KINDS = {"off": 0, "plain": 1, "external": 2}
 
 
@@ -36,6 +37,8 @@ class Problem(ctypes.Structure):
         ("umin", ctypes.c_double), ("umax", ctypes.c_double),
         ("limiter", ctypes.c_int), ("blend", ctypes.c_int), ("gamma", ctypes.c_double),
         ("clamp_tol", ctypes.c_double),
+        ("bc", ctypes.c_int), ("bc_left", ctypes.c_double), ("bc_right", ctypes.c_double),
+        ("nodc", ctypes.c_int),
     ]
 
 
@@ -67,6 +70,10 @@ def lib():
         _lib.ao_theta.restype = ctypes.c_double
         _lib.ao_rk54_coefs.argtypes = [dpp, dpp]
         _lib.ao_flop_count.argtypes = [P, arr, ctypes.c_double, dpp, ctypes.POINTER(ctypes.c_longlong)]
+        _lib.ao_run.argtypes = [P, ctypes.c_int, arr, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(Stats)]
+        _lib.ao_first_order_run.argtypes = [P, dpp, ctypes.c_double, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_longlong)]
     return _lib
 
 
@@ -90,6 +97,9 @@ def make_problem(spec) -> Problem:
     p.gamma = float(spec.gamma)
     scale = max(abs(spec.umin), abs(spec.umax), 1e-300)
     p.clamp_tol = 8.0 * np.finfo(np.float64).eps * scale
+    p.bc = BC_KINDS[getattr(spec, "bc", "periodic")]
+    p.bc_left, p.bc_right = (float(v) for v in getattr(spec, "bc_values", (0.0, 0.0)))
+    p.nodc = int(getattr(spec, "diffusion_form", "dc") == "nodc")
     return p
 
 
@@ -101,7 +111,11 @@ def _ptrs(arrays):
 def _prep(spec, state):
     n = 2 if spec.dim == 1 else 4
     assert len(state) == n
-    return [np.ascontiguousarray(np.asarray(a, dtype=np.float64)).copy() for a in state]
+    out = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)).copy() for a in state]
+    npts = spec.nx + 1 if spec.dim == 1 and getattr(spec, "bc", "periodic") != "periodic" else None
+    if npts is not None:
+        assert out[0].size == spec.nx and out[1].size == npts, "bounded 1D state: nx averages, nx+1 points"
+    return out
 
 
 def _sext(s_ext):
@@ -117,7 +131,8 @@ def fe(spec, state, tau, s_ext=None):
     a = _prep(spec, state)
     out = [np.zeros_like(x) for x in a]
     s, sp = _sext(s_ext)
-    lib().ao_fe(ctypes.byref(p), _ptrs(a), float(tau), sp, _ptrs(out))
+    if lib().ao_fe(ctypes.byref(p), _ptrs(a), float(tau), sp, _ptrs(out)) == -2:
+        raise ValueError("combination not supported by the oracle")
     return out
 
 
@@ -130,6 +145,8 @@ def step(spec, rk, state, dt, s_ext=None):
     rc = lib().ao_step(ctypes.byref(p), int(rk), _ptrs(a), float(dt), sp, ctypes.byref(st))
     if rc == -1:
         raise ValueError("unknown rk scheme")
+    if rc == -2:
+        raise ValueError("combination not supported by the oracle")
     return a, {"clamps": st.clamps, "max_excess": st.max_excess, "error": st.error}
 
 
@@ -226,3 +243,37 @@ def run(spec, rk, state, T, cfl=None, dt_fixed=None, max_steps=10**7, cfl_diff=N
         t += dt
         n += 1
     return state, n, tot
+
+
+def run_native(spec, rk, state, T, cfl=None, cfl_diff=None):
+    """Integrate to time T with the CFL step inside the oracle library (same clipping
+    rule as ``run``). Returns (state, nsteps, stats)."""
+    p = make_problem(spec)
+    a = _prep(spec, state)
+    if cfl is None:
+        cfl = spec.cfl if getattr(spec, "cfl", 0.0) else 0.33 / spec.dim
+    if cfl_diff is None:
+        cfl_diff = DIFF_CAP[(spec.dim, rk)]
+    st = Stats()
+    n = ctypes.c_longlong(0)
+    rc = lib().ao_run(ctypes.byref(p), int(rk), _ptrs(a), float(T), float(cfl), float(cfl_diff),
+                      ctypes.byref(n), ctypes.byref(st))
+    if rc == -2:
+        raise ValueError("combination not supported by the oracle")
+    if rc not in (0, -4):
+        raise ValueError(f"oracle run failed ({rc})")
+    return a, n.value, {"clamps": st.clamps, "max_excess": st.max_excess, "error": st.error}
+
+
+def first_order_run(spec, ub, T, cfl=0.9):
+    """First-order LLF + central-difference reference scheme for the cell averages of a
+    1D problem (forward Euler, dt = cfl / max(alpha/h + 2 kappa_max/h^2)) to time T.
+    Returns (ub, nsteps)."""
+    p = make_problem(spec)
+    u = np.ascontiguousarray(np.asarray(ub, dtype=np.float64)).copy()
+    n = ctypes.c_longlong(0)
+    rc = lib().ao_first_order_run(ctypes.byref(p), u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                  float(T), float(cfl), ctypes.byref(n))
+    if rc:
+        raise ValueError("combination not supported by the oracle")
+    return u, n.value

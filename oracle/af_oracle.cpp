@@ -19,6 +19,8 @@
 //   X [j][i] point value at (x_{i+1/2}, y_j)         (midpoint of the vertical edge)
 //   Y [j][i] point value at (x_i, y_{j+1/2})         (midpoint of the horizontal edge)
 // 1D (Section 2): ub[i] and P[i] = u_{i+1/2}; periodic, so u_{1/2} = u_{N+1/2}.
+// 1D with a Dirichlet or outflow boundary: P[j+1] = u_{j+1/2}, j = -1..N-1 (N+1 values
+// from the left to the right end of the interval).
 //
 // Readings where the paper is silent (also listed in the design notes):
 //   * 2D factors: directional split 1/(2d)=1/4, limiter factor 3*2d = 12, MPP CFL 1/4
@@ -34,6 +36,18 @@
 //     (blended) high-order flux/potential itself (Remark after Proposition 5.2).
 //   * After every RK stage, values outside [umin,umax] by at most clamp_tol are clamped
 //     and counted; larger excesses are reported as an error.
+//   * Boundaries of a 1D interval (Section 6 names Dirichlet and outflow conditions but
+//     not their discrete form): ghost cells and ghost points beyond each end. Dirichlet:
+//     every ghost DoF holds the boundary value and the boundary point value is held
+//     at it. Outflow: even reflection of the DoFs about the boundary point (a
+//     zero-gradient extension); the boundary point values evolve like interior ones.
+//     The CFL maximum also runs over the two boundary faces.
+//   * AF method without double conservation (Appendix A, 1D): the cell average
+//     receives the face flux f(u_{i+1/2}) - kappa(u_{i+1/2}) D_c(u)_{i+1/2}; the point
+//     value the compact operator 4/h^2 sum b_mn kappa(z_m) z_n on its 5-point line.
+//     Its limiter blends the total face flux with the low-order total face flux
+//     F^L - (a(ub_{i+1}) - a(ub_i))/h, with Theta on u^{L,+-} and factor 2 (the
+//     update is a mean of two states, each receiving one face correction).
 
 #include <algorithm>
 #include <cmath>
@@ -88,7 +102,12 @@ extern "C" {
 //            3 Buckley-Leverett f1=u^2/(u^2+(1-u)^2), f2=f1*(1-p0*(1-u)^2).
 // diff_kind: 0 none, 1 constant a=p0*u, 2 piecewise linear
 //            a = p0*min(u-p1,0) + p2*max(u-p3,0), 3 porous medium a=u^p0 (integer p0>=1),
-//            4 cubic a = p0*u + p1*u^2 + p2*u^3.
+//            4 cubic a = p0*u + p1*u^2 + p2*u^3,
+//            5 ramp a = 0 (u <= p1), p0 (u-p1)^2 / (2 p2) (p1 < u < p1+p2),
+//              p0 (u - p1 - p2/2) (u >= p1+p2)  (kappa rises linearly from 0 to p0).
+// bc: 0 periodic, 1 Dirichlet (bc_left, bc_right), 2 outflow -- 1D only.
+// nodc: 1 selects the AF method without double conservation of Appendix A (1D only,
+//       blend off).
 typedef struct {
   int dim;
   int nx, ny;
@@ -102,6 +121,9 @@ typedef struct {
   int blend;            // 0 off, 1 smoothness indicator, 2 external per-cell indicator
   double gamma;         // blend strength (gamma = 1 in the paper's examples)
   double clamp_tol;     // absolute tolerance of the post-stage safeguard clamp
+  int bc;               // 0 periodic, 1 Dirichlet, 2 outflow (1D)
+  double bc_left, bc_right;
+  int nodc;             // 1: Appendix A discretization of the diffusion term
 } ao_problem;
 
 typedef struct {
@@ -172,21 +194,37 @@ template <class R> R apot(const Model& m, R u) {
       return r;
     }
     case 4: return R(p.diff_p[0]) * u + R(p.diff_p[1]) * u * u + R(p.diff_p[2]) * u * u * u;
+    case 5: {
+      R lo = R(p.diff_p[1]), w = R(p.diff_p[2]);
+      if (u <= lo) return R(0.0);
+      if (u < lo + w) return R(p.diff_p[0]) * (u - lo) * (u - lo) / (R(2.0) * w);
+      return R(p.diff_p[0]) * (u - lo - R(0.5) * w);
+    }
     default: return R(0.0);
   }
 }
 
-double kappa(const Model& m, double u) {
+// kappa(u) = a'(u); at a kink of the piecewise forms the one-sided value nearer the
+// degenerate side is taken (kappa is 0 exactly at u = p1 and u = p3 of kind 2).
+template <class R> R kappa(const Model& m, R u) {
   const ao_problem& p = m.p;
   switch (p.diff_kind) {
-    case 1: return p.diff_p[0];
-    case 2: return (u < p.diff_p[1] ? p.diff_p[0] : 0.0) + (u > p.diff_p[3] ? p.diff_p[2] : 0.0);
+    case 1: return R(p.diff_p[0]);
+    case 2: return (u < R(p.diff_p[1]) ? R(p.diff_p[0]) : R(0.0)) + (u > R(p.diff_p[3]) ? R(p.diff_p[2]) : R(0.0));
     case 3: {
       int e = (int)p.diff_p[0];
-      return e * std::pow(u, e - 1);
+      R r = R(double(e));
+      for (int k = 1; k < e; ++k) r = r * u;
+      return r;
     }
-    case 4: return p.diff_p[0] + 2 * p.diff_p[1] * u + 3 * p.diff_p[2] * u * u;
-    default: return 0.0;
+    case 4: return R(p.diff_p[0]) + R(2.0 * p.diff_p[1]) * u + R(3.0 * p.diff_p[2]) * u * u;
+    case 5: {
+      R lo = R(p.diff_p[1]), w = R(p.diff_p[2]);
+      if (u <= lo) return R(0.0);
+      if (u < lo + w) return R(p.diff_p[0]) * (u - lo) / w;
+      return R(p.diff_p[0]);
+    }
+    default: return R(0.0);
   }
 }
 
@@ -196,9 +234,9 @@ double kappa_max(const Model& m) {
   const ao_problem& p = m.p;
   double lo = p.umin, hi = p.umax, best = 0.0;
   const int n = 200000;
-  for (int k = 0; k <= n; ++k) best = std::max(best, kappa(m, lo + (hi - lo) * k / n));
-  best = std::max(best, kappa(m, lo));
-  best = std::max(best, kappa(m, hi));
+  for (int k = 0; k <= n; ++k) best = std::max(best, kappa<double>(m, lo + (hi - lo) * k / n));
+  best = std::max(best, kappa<double>(m, lo));
+  best = std::max(best, kappa<double>(m, hi));
   if (p.diff_kind == 2) {
     // one-sided limits at the kinks inside the interval
     if (p.diff_p[1] > lo) best = std::max(best, p.diff_p[0]);
@@ -206,7 +244,7 @@ double kappa_max(const Model& m) {
   }
   if (p.diff_kind == 4 && p.diff_p[2] != 0.0) {
     double uv = -p.diff_p[1] / (3 * p.diff_p[2]);
-    if (uv > lo && uv < hi) best = std::max(best, kappa(m, uv));
+    if (uv > lo && uv < hi) best = std::max(best, kappa<double>(m, uv));
   }
   return best;
 }
@@ -307,101 +345,182 @@ template <class R> R s_tilde(R um, R u0, R up) {
   return fabs_(um - R(2.0) * u0 + up) / (fabs_(um) + R(2.0) * fabs_(u0) + fabs_(up) + R(1e-13));
 }
 
+// Values on the index range [lo, hi), addressed by the mesh index itself: indices below
+// 0 or at/above n are ghost entries beyond the two ends (or periodic images).
+template <class R> struct Span {
+  int lo;
+  std::vector<R> v;
+  Span(int lo_, int hi_) : lo(lo_), v((size_t)(hi_ - lo_), R(0.0)) {}
+  R& operator[](int i) { return v.at((size_t)(i - lo)); }
+  const R& operator[](int i) const { return v.at((size_t)(i - lo)); }
+};
+
+// Cell average ub_i and point value u_{j+1/2} at any index of a 1D mesh: stored values
+// inside, the boundary rule outside (periodic image, Dirichlet value, or even
+// reflection about the boundary point for outflow).
+template <class R> R cell_at(const ao_problem& p, const R* ub, int i) {
+  const int n = p.nx;
+  if (p.bc == 0) return ub[wrap(i, n)];
+  if (i >= 0 && i < n) return ub[i];
+  if (p.bc == 1) return R(i < 0 ? p.bc_left : p.bc_right);
+  return ub[i < 0 ? -1 - i : 2 * n - 1 - i];
+}
+template <class R> R point_at(const ao_problem& p, const R* P, int j) {
+  const int n = p.nx;
+  if (p.bc == 0) return P[wrap(j, n)];
+  if (j >= -1 && j <= n - 1) return P[j + 1];
+  if (p.bc == 1) return R(j < -1 ? p.bc_left : p.bc_right);
+  return P[(j < -1 ? -2 - j : 2 * (n - 1) - j) + 1];
+}
+
+// Appendix A: B = [0 0; 0 M] - [M 0; 0 0] (5x5), b_mn for m, n = -2..2 at B[m+2][n+2].
+inline double nodc_b(int r, int s) {
+  static const double M[4][4] = {{1.0 / 8, -1.0 / 6, 1.0 / 24, 0.0},
+                                 {-1.0 / 6, -3.0 / 8, 2.0 / 3, -1.0 / 8},
+                                 {1.0 / 8, -2.0 / 3, 3.0 / 8, 1.0 / 6},
+                                 {0.0, -1.0 / 24, 1.0 / 6, -1.0 / 8}};
+  double v = 0.0;
+  if (r >= 1 && s >= 1) v += M[r - 1][s - 1];
+  if (r <= 3 && s <= 3) v -= M[r][s];
+  return v;
+}
+
 // ---------------------------------------------------------------------------------
-// 1D forward-Euler evaluation (Sections 2 and 5.1).
+// 1D forward-Euler evaluation (Sections 2 and 5.1; Appendix A when p.nodc).
+// Cells i = 0..n-1; point j is u_{j+1/2}, the right end of cell i = j. Updated points:
+// j = 0..n-1 (periodic) or j = -1..n-1 (bounded). Everything is first gathered on the
+// index range it is needed on, ghost entries included, then computed with plain loops.
 template <class R>
 void fe1d(const Model& m, const R* ub, const R* P, R tau, const R* s_ext, R* ub_o, R* P_o) {
   const ao_problem& p = m.p;
-  const int n = p.nx;
+  const int n = p.nx, G = 3;
+  const bool bounded = p.bc != 0;
+  const int jlo = bounded ? -1 : 0;
   const R h = R(p.dx);
-  auto I = [&](int i) { return wrap(i, n); };
-  std::vector<R> c(n), fP(n), dP(n), aP(n), fC(n), dC(n), aC(n), fU(n), aU(n);
-  // centre value by Simpson's rule: z_i = (6 zbar_i - z_{i-1/2} - z_{i+1/2}) / 4
-  for (int i = 0; i < n; ++i) c[i] = (R(6.0) * ub[i] - P[I(i - 1)] - P[i]) / R(4.0);
-  for (int i = 0; i < n; ++i) {
-    fP[i] = flux<R>(m, 0, P[i]); dP[i] = dflux<R>(m, 0, P[i]); aP[i] = apot<R>(m, P[i]);
+  Span<R> U(-G, n + G), Pt(-G - 1, n + G), c(-G, n + G);
+  for (int i = -G; i < n + G; ++i) U[i] = cell_at<R>(p, ub, i);
+  for (int j = -G - 1; j < n + G; ++j) Pt[j] = point_at<R>(p, P, j);
+  // centre value by Simpson's rule: u_i = (6 ub_i - u_{i-1/2} - u_{i+1/2}) / 4
+  for (int i = -G; i < n + G; ++i) c[i] = (R(6.0) * U[i] - Pt[i - 1] - Pt[i]) / R(4.0);
+  Span<R> fP(-G - 1, n + G), dP(-G - 1, n + G), aP(-G - 1, n + G), kP(-G - 1, n + G);
+  Span<R> fC(-G, n + G), dC(-G, n + G), aC(-G, n + G), kC(-G, n + G), fU(-G, n + G), aU(-G, n + G);
+  for (int j = -G - 1; j < n + G; ++j) {
+    fP[j] = flux<R>(m, 0, Pt[j]); dP[j] = dflux<R>(m, 0, Pt[j]); aP[j] = apot<R>(m, Pt[j]);
+    if (p.nodc) kP[j] = kappa<R>(m, Pt[j]);
+  }
+  for (int i = -G; i < n + G; ++i) {
     fC[i] = flux<R>(m, 0, c[i]); dC[i] = dflux<R>(m, 0, c[i]); aC[i] = apot<R>(m, c[i]);
-    fU[i] = flux<R>(m, 0, ub[i]); aU[i] = apot<R>(m, ub[i]);
+    if (p.nodc) kC[i] = kappa<R>(m, c[i]);
+    fU[i] = flux<R>(m, 0, U[i]); aU[i] = apot<R>(m, U[i]);
   }
-  // high-order flux f(u_{i+1/2}) and DC potential a^_i = (-a_{i-1/2} + 8 a_i - a_{i+1/2})/6
-  std::vector<R> FH(n), AH(n), RH(n);
-  for (int i = 0; i < n; ++i) {
-    FH[i] = fP[i];
-    AH[i] = (-aP[I(i - 1)] + R(8.0) * aC[i] - aP[i]) / R(6.0);
-  }
-  // point residual at x_{i+1/2}: line [u_{i-1/2}, u_i, u_{i+1/2}, u_{i+1}, u_{i+3/2}]
-  for (int i = 0; i < n; ++i) {
-    int ip = I(i + 1);
-    R z[5] = {P[I(i - 1)], c[i], P[i], c[ip], P[ip]};
-    R f[5] = {fP[I(i - 1)], fC[i], fP[i], fC[ip], fP[ip]};
-    R d[5] = {dP[I(i - 1)], dC[i], dP[i], dC[ip], dP[ip]};
-    R a[5] = {aP[I(i - 1)], aC[i], aP[i], aC[ip], aP[ip]};
-    RH[i] = line_residual<R>(z, f, d, a, h);
+  // high-order flux f(u_{i+1/2}) on faces -1..n-1 and DC potential
+  // a^_i = (-a_{i-1/2} + 8 a_i - a_{i+1/2})/6 on cells -1..n
+  Span<R> FH(-1, n), AH(-1, n + 1), RH(jlo, n);
+  for (int f = -1; f < n; ++f) FH[f] = fP[f];
+  for (int i = -1; i <= n; ++i) AH[i] = (-aP[i - 1] + R(8.0) * aC[i] - aP[i]) / R(6.0);
+  // point residual at x_{j+1/2}: line [u_{j-1/2}, u_j, u_{j+1/2}, u_{j+1}, u_{j+3/2}]
+  for (int j = jlo; j < n; ++j) {
+    R z[5] = {Pt[j - 1], c[j], Pt[j], c[j + 1], Pt[j + 1]};
+    R f[5] = {fP[j - 1], fC[j], fP[j], fC[j + 1], fP[j + 1]};
+    R d[5] = {dP[j - 1], dC[j], dP[j], dC[j + 1], dP[j + 1]};
+    if (!p.nodc) {
+      R a[5] = {aP[j - 1], aC[j], aP[j], aC[j + 1], aP[j + 1]};
+      RH[j] = line_residual<R>(z, f, d, a, h);
+    } else {
+      // convection part of the same line (a = 0) plus the compact operator of
+      // Appendix A: 4/h^2 sum_{m,n} b_mn kappa(z_m) z_n
+      R a0[5] = {R(0.0), R(0.0), R(0.0), R(0.0), R(0.0)};
+      R k[5] = {kP[j - 1], kC[j], kP[j], kC[j + 1], kP[j + 1]};
+      R D2 = R(0.0);
+      for (int r = 0; r < 5; ++r)
+        for (int s = 0; s < 5; ++s) D2 = D2 + R(nodc_b(r, s)) * k[r] * z[s];
+      RH[j] = line_residual<R>(z, f, d, a0, h) + R(4.0) * D2 / (h * h);
+    }
   }
   const R mu = tau / h, nu = tau / (h * h);
-  // low-order LLF scheme and its directional states u^{L,+-} (Lemma 5.1)
-  std::vector<R> FL(n), ULp(n), ULm(n);
-  for (int i = 0; i < n; ++i) {
-    int ip = I(i + 1);
-    R al = alpha_interval<R>(m, 0, ub[i], ub[ip]);
-    FL[i] = R(0.5) * (fU[i] + fU[ip]) - R(0.5) * al * (ub[ip] - ub[i]);
+  // low-order LLF scheme on faces -2..n and its directional states u^{L,+-} (Lemma 5.1)
+  Span<R> FL(-2, n + 1), ULp(-2, n + 1), ULm(-1, n + 2);
+  for (int f = -2; f <= n; ++f) {
+    R al = alpha_interval<R>(m, 0, U[f], U[f + 1]);
+    FL[f] = R(0.5) * (fU[f] + fU[f + 1]) - R(0.5) * al * (U[f + 1] - U[f]);
   }
-  for (int i = 0; i < n; ++i) {
-    int ip = I(i + 1), im = I(i - 1);
-    ULp[i] = ub[i] - R(2.0) * mu * (FL[i] - fU[i]) + R(2.0) * nu * (aU[ip] - aU[i]);
-    ULm[i] = ub[i] - R(2.0) * mu * (fU[i] - FL[im]) - R(2.0) * nu * (aU[i] - aU[im]);
-  }
+  for (int i = -2; i <= n; ++i) ULp[i] = U[i] - R(2.0) * mu * (FL[i] - fU[i]) + R(2.0) * nu * (aU[i + 1] - aU[i]);
+  for (int i = -1; i <= n + 1; ++i) ULm[i] = U[i] - R(2.0) * mu * (fU[i] - FL[i - 1]) - R(2.0) * nu * (aU[i] - aU[i - 1]);
   // optional smoothness blend (Section 5.1.3), applied before the limiter
-  std::vector<R> Fh(FH), Ah(AH), R_(RH), thcs(n, R(1.0));
+  Span<R> Fh(-1, n), Ah(-1, n + 1), R_(jlo, n), thcs(-1, n);
+  for (int f = -1; f < n; ++f) { Fh[f] = FH[f]; thcs[f] = R(1.0); }
+  for (int i = -1; i <= n; ++i) Ah[i] = AH[i];
+  for (int j = jlo; j < n; ++j) R_[j] = RH[j];
   if (p.blend) {
-    std::vector<R> st(n), s(n), thds(n);
+    Span<R> st(-2, n + 2), s(-1, n + 1), thds(-1, n + 1);
     if (p.blend == 1) {
-      for (int i = 0; i < n; ++i) st[i] = s_tilde<R>(ub[I(i - 1)], ub[i], ub[I(i + 1)]);
-      for (int i = 0; i < n; ++i) s[i] = (st[I(i - 1)] + R(4.0) * st[i] + st[I(i + 1)]) / R(6.0);
+      for (int i = -2; i < n + 2; ++i) st[i] = s_tilde<R>(U[i - 1], U[i], U[i + 1]);
+      for (int i = -1; i <= n; ++i) s[i] = (st[i - 1] + R(4.0) * st[i] + st[i + 1]) / R(6.0);
     } else {
-      for (int i = 0; i < n; ++i) s[i] = s_ext[i];
+      for (int i = -1; i <= n; ++i) s[i] = s_ext[wrap(i, n)];
     }
-    for (int i = 0; i < n; ++i) {
-      thcs[i] = exp_(-R(p.gamma) * (R(0.5) * (s[i] + s[I(i + 1)])));
-      thds[i] = exp_(-R(p.gamma) * s[i]);
-    }
-    for (int i = 0; i < n; ++i) {
-      Fh[i] = thcs[i] * FH[i] + (R(1.0) - thcs[i]) * FL[i];
-      Ah[i] = thds[i] * AH[i] + (R(1.0) - thds[i]) * aU[i];
-      R RL = low_point_residual<R>(m, 0, ub[i], P[i], ub[I(i + 1)], h);
-      R_[i] = thcs[i] * RH[i] + (R(1.0) - thcs[i]) * RL;
+    for (int f = -1; f < n; ++f) thcs[f] = exp_(-R(p.gamma) * (R(0.5) * (s[f] + s[f + 1])));
+    for (int i = -1; i <= n; ++i) thds[i] = exp_(-R(p.gamma) * s[i]);
+    for (int f = -1; f < n; ++f) Fh[f] = thcs[f] * FH[f] + (R(1.0) - thcs[f]) * FL[f];
+    for (int i = -1; i <= n; ++i) Ah[i] = thds[i] * AH[i] + (R(1.0) - thds[i]) * aU[i];
+    for (int j = jlo; j < n; ++j) {
+      R RL = low_point_residual<R>(m, 0, U[j], Pt[j], U[j + 1], h);
+      R_[j] = thcs[j] * RH[j] + (R(1.0) - thcs[j]) * RL;
     }
   }
-  // monolithic convex limiter (eqs. 1d_convection_limiting_parameter and
-  // 1d_diffusion_limiting_parameter), limited average (eq. 1d_limited_average)
-  std::vector<R> Flim(Fh), Alim(Ah);
-  if (p.limiter) {
-    for (int i = 0; i < n; ++i) {
-      int ip = I(i + 1);
-      R dF = Fh[i] - FL[i];
-      R t = minr(Theta<R>(m, ULp[i], ULp[i] - R(6.0) * mu * dF),
-                 Theta<R>(m, ULm[ip], ULm[ip] + R(6.0) * mu * dF));
-      Flim[i] = (t == R(1.0)) ? Fh[i] : FL[i] + t * dF;
+  if (!p.nodc) {
+    // monolithic convex limiter (eqs. 1d_convection_limiting_parameter and
+    // 1d_diffusion_limiting_parameter), limited average (eq. 1d_limited_average)
+    Span<R> Flim(-1, n), Alim(-1, n + 1);
+    for (int f = -1; f < n; ++f) Flim[f] = Fh[f];
+    for (int i = -1; i <= n; ++i) Alim[i] = Ah[i];
+    if (p.limiter) {
+      for (int f = -1; f < n; ++f) {
+        R dF = Fh[f] - FL[f];
+        R t = minr(Theta<R>(m, ULp[f], ULp[f] - R(6.0) * mu * dF),
+                   Theta<R>(m, ULm[f + 1], ULm[f + 1] + R(6.0) * mu * dF));
+        Flim[f] = (t == R(1.0)) ? Fh[f] : FL[f] + t * dF;
+      }
+      for (int i = -1; i <= n; ++i) {
+        R dA = Ah[i] - aU[i];
+        R t = minr(minr(Theta<R>(m, ULp[i - 1], ULp[i - 1] + R(6.0) * nu * dA),
+                        Theta<R>(m, ULp[i], ULp[i] - R(6.0) * nu * dA)),
+                   minr(Theta<R>(m, ULm[i], ULm[i] - R(6.0) * nu * dA),
+                        Theta<R>(m, ULm[i + 1], ULm[i + 1] + R(6.0) * nu * dA)));
+        Alim[i] = (t == R(1.0)) ? Ah[i] : aU[i] + t * dA;
+      }
     }
-    for (int i = 0; i < n; ++i) {
-      int ip = I(i + 1), im = I(i - 1);
-      R dA = Ah[i] - aU[i];
-      R t = minr(minr(Theta<R>(m, ULp[im], ULp[im] + R(6.0) * nu * dA),
-                      Theta<R>(m, ULp[i], ULp[i] - R(6.0) * nu * dA)),
-                 minr(Theta<R>(m, ULm[i], ULm[i] - R(6.0) * nu * dA),
-                      Theta<R>(m, ULm[ip], ULm[ip] + R(6.0) * nu * dA)));
-      Alim[i] = (t == R(1.0)) ? Ah[i] : aU[i] + t * dA;
+    for (int i = 0; i < n; ++i)
+      ub_o[i] = ub[i] - mu * (Flim[i] - Flim[i - 1]) + nu * (Alim[i + 1] - R(2.0) * Alim[i] + Alim[i - 1]);
+  } else {
+    // Appendix A: total face flux G = f(u_{i+1/2}) - kappa(u_{i+1/2}) D_c(u)_{i+1/2},
+    // D_c(u)_{i+1/2} = (u_{i-1/2} - 8 u_i + 8 u_{i+1} - u_{i+3/2}) / (6h); low-order
+    // counterpart G^L = F^L - (a(ub_{i+1}) - a(ub_i)) / h
+    Span<R> GH(-1, n), GL(-1, n), Glim(-1, n);
+    for (int f = -1; f < n; ++f) {
+      R Dc = (Pt[f - 1] - R(8.0) * c[f] + R(8.0) * c[f + 1] - Pt[f + 1]) / (R(6.0) * h);
+      GH[f] = fP[f] - kP[f] * Dc;
+      GL[f] = FL[f] - (aU[f + 1] - aU[f]) / h;
+      Glim[f] = GH[f];
     }
+    if (p.limiter) {
+      for (int f = -1; f < n; ++f) {
+        R dG = GH[f] - GL[f];
+        R t = minr(Theta<R>(m, ULp[f], ULp[f] - R(2.0) * mu * dG),
+                   Theta<R>(m, ULm[f + 1], ULm[f + 1] + R(2.0) * mu * dG));
+        Glim[f] = (t == R(1.0)) ? GH[f] : GL[f] + t * dG;
+      }
+    }
+    for (int i = 0; i < n; ++i) ub_o[i] = ub[i] - mu * (Glim[i] - Glim[i - 1]);
   }
-  for (int i = 0; i < n; ++i) {
-    int ip = I(i + 1), im = I(i - 1);
-    ub_o[i] = ub[i] - mu * (Flim[i] - Flim[im]) + nu * (Alim[ip] - R(2.0) * Alim[i] + Alim[im]);
-  }
-  // point values: high-order update, then projection onto [umin, umax] (Section 5.1.2)
-  for (int i = 0; i < n; ++i) {
-    R v = P[i] + tau * R_[i];
+  // point values: high-order update, then projection onto [umin, umax] (Section 5.1.2);
+  // Dirichlet boundary points keep the boundary value
+  for (int j = jlo; j < n; ++j) {
+    R v = Pt[j] + tau * R_[j];
     if (p.limiter) v = minr(maxr(v, R(p.umin)), R(p.umax));
-    P_o[i] = v;
+    if (p.bc == 1 && j == -1) v = R(p.bc_left);
+    if (p.bc == 1 && j == n - 1) v = R(p.bc_right);
+    P_o[bounded ? j + 1 : j] = v;
   }
 }
 
@@ -662,11 +781,29 @@ struct State {
 
 int ncomp(const ao_problem& p) { return p.dim == 1 ? 2 : 4; }
 size_t ncell(const ao_problem& p) { return (size_t)p.nx * (p.dim == 1 ? 1 : p.ny); }
+// values in component c: a bounded 1D mesh has n+1 point values
+size_t comp_size(const ao_problem& p, int c) { return ncell(p) + (p.dim == 1 && p.bc != 0 && c == 1 ? 1 : 0); }
+
+// combinations the oracle implements: boundaries and Appendix A in 1D only, an
+// external indicator only on a periodic mesh, Appendix A without the blend
+bool supported(const ao_problem& p) {
+  if ((p.bc != 0 || p.nodc) && p.dim != 1) return false;
+  if (p.bc < 0 || p.bc > 2) return false;
+  if (p.bc != 0 && (p.nx < 4 || p.blend == 2)) return false;
+  if (p.nodc && p.blend) return false;
+  return true;
+}
+
+// Dirichlet boundary point values stay at the boundary data through every combination
+void hold_dirichlet(const ao_problem& p, std::vector<double>* a) {
+  if (p.dim != 1 || p.bc != 1) return;
+  a[1][0] = p.bc_left;
+  a[1][p.nx] = p.bc_right;
+}
 
 void fe(const Model& m, const State& in, double tau, const double* s_ext, State& out) {
   const ao_problem& p = m.p;
-  size_t n = ncell(p);
-  for (int c = 0; c < ncomp(p); ++c) out.a[c].assign(n, 0.0);
+  for (int c = 0; c < ncomp(p); ++c) out.a[c].assign(comp_size(p, c), 0.0);
   if (p.dim == 1)
     fe1d<double>(m, in.a[0].data(), in.a[1].data(), tau, s_ext, out.a[0].data(), out.a[1].data());
   else
@@ -696,6 +833,7 @@ State combine(const ao_problem& p, double a, const State& x, double b, const Sta
     r.a[c].resize(x.a[c].size());
     for (size_t k = 0; k < x.a[c].size(); ++k) r.a[c][k] = a * x.a[c][k] + b * y.a[c][k];
   }
+  hold_dirichlet(p, r.a);
   return r;
 }
 
@@ -708,8 +846,7 @@ Model make_model(const ao_problem* p) {
 
 State load(const ao_problem& p, double* const* arr) {
   State s;
-  size_t n = ncell(p);
-  for (int c = 0; c < ncomp(p); ++c) s.a[c].assign(arr[c], arr[c] + n);
+  for (int c = 0; c < ncomp(p); ++c) s.a[c].assign(arr[c], arr[c] + comp_size(p, c));
   return s;
 }
 void store(const ao_problem& p, const State& s, double* const* arr) {
@@ -724,6 +861,7 @@ extern "C" {
 // in *p. Arrays: dim 1 -> {ub, P}; dim 2 -> {ub, V, X, Y}. s_ext: per-cell indicator
 // (blend == 2) or NULL.
 int ao_fe(const ao_problem* p, double* const* in, double tau, const double* s_ext, double* const* out) {
+  if (!supported(*p)) return -2;
   Model m = make_model(p);
   State a = load(*p, in), b;
   fe(m, a, tau, s_ext, b);
@@ -731,9 +869,13 @@ int ao_fe(const ao_problem* p, double* const* in, double tau, const double* s_ex
   return 0;
 }
 
+}  // extern "C"
+
+namespace {
+
 // One full time step with rk = 3 (SSP-RK3) or 54 (SSP-RK(5,4)); state updated in place.
-int ao_step(const ao_problem* p, int rk, double* const* state, double dt, const double* s_ext, ao_stats* st) {
-  Model m = make_model(p);
+int step_model(const Model& m, int rk, double* const* state, double dt, const double* s_ext, ao_stats* st) {
+  const ao_problem* p = &m.p;
   State u0 = load(*p, state), t;
   if (rk == 3) {
     fe(m, u0, dt, s_ext, t);
@@ -778,16 +920,30 @@ int ao_step(const ao_problem* p, int rk, double* const* state, double dt, const 
   return -1;
 }
 
+}  // namespace
+
+extern "C" {
+
+int ao_step(const ao_problem* p, int rk, double* const* state, double dt, const double* s_ext, ao_stats* st) {
+  if (!supported(*p)) return -2;
+  return step_model(make_model(p), rk, state, dt, s_ext, st);
+}
+
+}  // extern "C"
+
+namespace {
+
 // CFL time step dt = C / max_{faces,l} (alpha_face / h_l + kappa_max / h_l^2)
 // (eq. multid_av_pp_dt; 1D eq. 1d_av_pp_dt), additionally capped by the linear
 // stability of the unlimited high-order scheme for diffusion, dt <= Cd h_l^2 / kappa_max
-// (cfl_diff <= 0 disables the cap).
-double ao_dt(const ao_problem* p, const double* ub, double cfl, double cfl_diff) {
-  Model m = make_model(p);
-  double km = kappa_max(m), worst = 0.0;
+// (cfl_diff <= 0 disables the cap). A bounded 1D mesh has faces -1..n-1, the two end
+// faces between a boundary cell and its ghost cell included. km = kappa_max(m).
+double dt_model(const Model& m, const double* ub, double cfl, double cfl_diff, double km) {
+  const ao_problem* p = &m.p;
+  double worst = 0.0;
   if (p->dim == 1) {
-    for (int i = 0; i < p->nx; ++i) {
-      double a = alpha_interval<double>(m, 0, ub[i], ub[wrap(i + 1, p->nx)]);
+    for (int f = p->bc != 0 ? -1 : 0; f < p->nx; ++f) {
+      double a = alpha_interval<double>(m, 0, cell_at<double>(*p, ub, f), cell_at<double>(*p, ub, f + 1));
       worst = std::max(worst, a / p->dx + km / (p->dx * p->dx));
     }
   } else {
@@ -806,6 +962,75 @@ double ao_dt(const ao_problem* p, const double* ub, double cfl, double cfl_diff)
     rate = std::max(rate, km / (hmin * hmin) / cfl_diff);
   }
   return rate > 0.0 ? 1.0 / rate : INFINITY;
+}
+
+}  // namespace
+
+extern "C" {
+
+double ao_dt(const ao_problem* p, const double* ub, double cfl, double cfl_diff) {
+  Model m = make_model(p);
+  return dt_model(m, ub, cfl, cfl_diff, kappa_max(m));
+}
+
+// Steps with the CFL time step until time T: each step is clipped to the time left,
+// and stepping ends once less than T * 1e-14 is left. *nsteps = steps taken.
+int ao_run(const ao_problem* p, int rk, double* const* state, double T, double cfl, double cfl_diff,
+           long long* nsteps, ao_stats* st) {
+  if (!supported(*p)) return -2;
+  Model m = make_model(p);
+  const double km = kappa_max(m);
+  double t = 0.0;
+  long long k = 0;
+  while (T - t > T * 1e-14) {
+    double dt = std::min(dt_model(m, state[0], cfl, cfl_diff, km), T - t);
+    int rc = step_model(m, rk, state, dt, nullptr, st);
+    if (rc) return rc;
+    t += dt;
+    ++k;
+  }
+  if (nsteps) *nsteps = k;
+  return 0;
+}
+
+// First-order reference scheme for the cell averages alone (the kind of scheme the
+// paper's reference solutions of Section 6 come from): forward Euler with the LLF
+// flux (interval wave speed) and the central second difference of a,
+//   ub_i <- ub_i - mu (F_{i+1/2} - F_{i-1/2}) + nu (a(ub_{i+1}) - 2 a(ub_i) + a(ub_{i-1})),
+// ghost cells by the boundary rule, dt = cfl / max_faces(alpha/h + 2 kappa_max/h^2)
+// (monotone for cfl <= 1), the last step clipped to T. 1D only.
+int ao_first_order_run(const ao_problem* p, double* ub, double T, double cfl, long long* nsteps) {
+  if (p->dim != 1 || !supported(*p)) return -2;
+  Model m = make_model(p);
+  const int n = p->nx;
+  const double h = p->dx, km = kappa_max(m);
+  std::vector<double> F(n + 1), un(n);
+  double t = 0.0;
+  long long k = 0;
+  while (T - t > T * 1e-14) {
+    double worst = 0.0;
+    for (int f = -1; f < n; ++f) {
+      double a = alpha_interval<double>(m, 0, cell_at<double>(*p, ub, f), cell_at<double>(*p, ub, f + 1));
+      worst = std::max(worst, a / h + 2.0 * km / (h * h));
+    }
+    double dt = std::min(cfl / worst, T - t);
+    const double mu = dt / h, nu = dt / (h * h);
+    for (int f = -1; f < n; ++f) {
+      double ul = cell_at<double>(*p, ub, f), ur = cell_at<double>(*p, ub, f + 1);
+      double a = alpha_interval<double>(m, 0, ul, ur);
+      F[f + 1] = 0.5 * (flux<double>(m, 0, ul) + flux<double>(m, 0, ur)) - 0.5 * a * (ur - ul);
+    }
+    for (int i = 0; i < n; ++i) {
+      double am = apot<double>(m, cell_at<double>(*p, ub, i - 1)), a0 = apot<double>(m, ub[i]),
+             ap = apot<double>(m, cell_at<double>(*p, ub, i + 1));
+      un[i] = ub[i] - mu * (F[i + 1] - F[i]) + nu * (ap - 2.0 * a0 + am);
+    }
+    std::copy(un.begin(), un.end(), ub);
+    t += dt;
+    ++k;
+  }
+  if (nsteps) *nsteps = k;
+  return 0;
 }
 
 double ao_kappa_max(const ao_problem* p) { return kappa_max(make_model(p)); }
@@ -836,8 +1061,8 @@ void ao_flop_count(const ao_problem* p, double* const* in, double tau, const dou
   size_t n = ncell(*p);
   std::vector<Cnt> a[4], b[4], se;
   for (int c = 0; c < ncomp(*p); ++c) {
-    a[c].resize(n); b[c].resize(n);
-    for (size_t k = 0; k < n; ++k) a[c][k] = Cnt(in[c][k]);
+    a[c].resize(comp_size(*p, c)); b[c].resize(comp_size(*p, c));
+    for (size_t k = 0; k < a[c].size(); ++k) a[c][k] = Cnt(in[c][k]);
   }
   if (s_ext) { se.resize(n); for (size_t k = 0; k < n; ++k) se[k] = Cnt(s_ext[k]); }
   if (p->dim == 1)
