@@ -39,6 +39,13 @@ BYTES_PER_CELL_STAGE = {"fp64": 85.33, "fp32_mixed": 53.33}
 # SSP-RK(5,4) in the stage layout of the library: 2 + 3 + 3 + 5 + 3 = 16 state passes
 # over 5 stages (the fourth stage reads U3, U0, U2 and writes U1, U2), 3.2 per stage.
 BYTES_PER_CELL_STAGE_RK54 = {"fp64": 102.4, "fp32_mixed": 64.0}
+# 1D interval with Dirichlet ends (Example 6.5): algorithmic flops of one limited
+# forward-Euler evaluation per cell (oracle count on its initial data at 65536 cells) for
+# the doubly conservative form and the form without double conservation, and the bytes
+# a stage must move per cell (SSP-RK3: (2 + 3 + 3) / 3 passes over ub and one point
+# value per cell).
+FLOPS_PER_CELL_STAGE_1D = {"dc": 135.12, "nodc": 209.05}
+BYTES_PER_CELL_STAGE_1D = {"fp64": 42.67, "fp32_mixed": 32.0}
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch (SSP-RK3 stage 2) from
 # the ncu captures summarised in profiles/stage2d_fp64_degenerate_burgers_1024.md and
 # profiles/stage2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
@@ -355,6 +362,10 @@ def forms(args, headline_value, peaks):
         res.update(_form_batch(args, stream, headline_value, peaks))
     if "bl" in sel:
         res.update(_form_bl(args, stream, peaks))
+    if "bounded1d" in sel:
+        res.update(_form_bounded1d(args, stream, peaks))
+    if "ex65" in sel:
+        res.update(_form_ex65())
     return res
 
 
@@ -416,6 +427,64 @@ def _form_pme(args, stream, peaks):
         "roofline": _hbm_roof("fp32_mixed", spec.cells, r32["stage_ms_avg"], peaks)}
     s32.close()
     del st
+    return res
+
+
+def _form_ex65():
+    """Example 6.5 (1D, Dirichlet ends) as the paper runs it: 200 cells to T = 1
+    through af_run, with and without double conservation (launch-bound: time to
+    solution)."""
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import Solver
+    small = {}
+    for form in ("dc", "nodc"):
+        spec = ai.evje_karlsen(200, diffusion_form=form)
+        st = [a.numpy() for a in ai.initial_state(spec)]
+        with Solver(spec, precision="fp64") as s:
+            s.set_state(st)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n = s.run(spec.T)
+            torch.cuda.synchronize()
+            small[form] = {"steps": n, "seconds": round(time.perf_counter() - t0, 3)}
+    return {"evje_karlsen_200_to_T1": small}
+
+
+def _form_bounded1d(args, stream, peaks):
+    """Example 6.5's problem (1D, Dirichlet ends) on 2^24 cells: the 1D stage kernel's
+    throughput, doubly conservative (FP64, FP32-mixed) and without double conservation
+    (FP64)."""
+    import dataclasses
+    import af_inputs as ai
+    res = {}
+    n = args.n1d
+    big = ai.evje_karlsen(n)
+    sd = ai.state_1d(ai.evje_karlsen_fn, big, device="cuda", sub=2, order=3)
+    out = {"cells": n}
+    r = {}
+    for prec, form in (("fp64", "dc"), ("fp64", "nodc"), ("fp32_mixed", "dc")):
+        spec = dataclasses.replace(big, diffusion_form=form)
+        s, rr = _single_form(spec, prec, args.form_steps, 3, sd, stream)
+        r[(prec, form)] = (s, rr)
+        stage_s = rr["stage_ms_avg"] / 1e3
+        e = {"value": round(rr["value"], 1), "stage_ms_avg": round(rr["stage_ms_avg"], 5),
+             "hbm_gbs": round(BYTES_PER_CELL_STAGE_1D[prec] * n / stage_s / 1e9, 1),
+             "hbm_frac": round(BYTES_PER_CELL_STAGE_1D[prec] * n / stage_s / 1e9 / peaks["hbm_gbs"], 4)}
+        if prec == "fp64":
+            tf = FLOPS_PER_CELL_STAGE_1D[form] * n / stage_s / 1e12
+            e["roofline"] = {"bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                             "frac": round(tf / FP64_PEAK_TFLOPS, 4),
+                             "flops_per_cell_stage": FLOPS_PER_CELL_STAGE_1D[form]}
+        out[f"{prec}_{form}"] = e
+    a64 = r[("fp64", "dc")][0].device_tensors()
+    a32 = r[("fp32_mixed", "dc")][0].device_tensors()
+    out["fp32_mixed_dc"]["l1_vs_fp64"] = max(float((x.double() - y.double()).abs().mean()) for x, y in zip(a32, a64))
+    out["fp32_mixed_dc"]["speedup_vs_fp64"] = round(out["fp32_mixed_dc"]["value"] / out["fp64_dc"]["value"], 2)
+    for s, _ in r.values():
+        s.close()
+    del sd, a64, a32
+    res[f"bounded1d_evje_karlsen_{n}"] = out
     return res
 
 
@@ -610,9 +679,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/batched/learned forms")
     ap.add_argument("--form-steps", type=int, default=5)
-    ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl",
+    ap.add_argument("--n1d", type=int, default=1 << 24, help="cells of the bounded1d form")
+    ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl,bounded1d,ex65",
                     help="comma list of forms to run: fp32 (Burgers 1024^2), rk54 (Burgers 1024^2 with "
-                         "SSP-RK(5,4)), pme (4096^2), batch (256), bl (4096^2)")
+                         "SSP-RK(5,4)), pme (4096^2), batch (256), bl (4096^2), bounded1d (Example 6.5's "
+                         "problem on 2^24 cells, with and without double conservation), ex65 (Example 6.5 "
+                         "as printed: 200 cells to T = 1)")
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)

@@ -5,7 +5,8 @@
  *
  *      u_t + div f(u) = Laplace a(u),   a(u) = int kappa,  kappa >= 0      (Section 1)
  *
- * on periodic Cartesian meshes in 1D and 2D (arXiv 2510.11527).
+ * on periodic Cartesian meshes in 1D and 2D, and on 1D intervals with Dirichlet or
+ * outflow ends (arXiv 2510.11527).
  *
  * Degrees of freedom (Section 2 for 1D, Section 4 / Fig. 2 for 2D). All arrays are
  * row-major [ny][nx] with i fastest; a periodic mesh stores nx*ny of each kind:
@@ -14,7 +15,9 @@
  *   X [j][i]  point value at the midpoint of the vertical edge (x_{i+1/2}, y_j)
  *   Y [j][i]  point value at the midpoint of the horizontal edge (x_i, y_{j+1/2})
  * In 1D only ub[i] and P[i] = u(x_{i+1/2}) exist; they are passed in the ub and V
- * slots, and X, Y are ignored (may be NULL).
+ * slots, and X, Y are ignored (may be NULL). A 1D interval with Dirichlet or outflow
+ * ends (grid->bc) has nx+1 point values, P[k] = u(x0 + k dx), k = 0..nx, from the left
+ * to the right end; ub keeps nx values.
  *
  * Conventions
  *   - Every call returns an af_status. On error the context is left unchanged and
@@ -60,14 +63,39 @@ enum {
   AF_DIFF_CONST = 1,      /* a = p0 u                                                       */
   AF_DIFF_PWL = 2,        /* a = p0 min(u - p1, 0) + p2 max(u - p3, 0)  (degenerate band)   */
   AF_DIFF_PME = 3,        /* a = u^p0, p0 integer >= 1 (porous medium)                      */
-  AF_DIFF_CUBIC = 4       /* a = p0 u + p1 u^2 + p2 u^3                                     */
+  AF_DIFF_CUBIC = 4,      /* a = p0 u + p1 u^2 + p2 u^3                                     */
+  AF_DIFF_RAMP = 5        /* a = 0 (u <= p1), p0 (u-p1)^2/(2 p2) (p1 < u < p1+p2),
+                             p0 (u - p1 - p2/2) (u >= p1+p2): kappa rises linearly from 0
+                             to p0 over [p1, p1+p2], p2 > 0 (Example 6.5: p = 1, 0.5, 0.1) */
 };
+
+/* Ends of a 1D interval (Section 6 uses Dirichlet and outflow ends; their discrete
+ * form is this library's reading): ghost cells and ghost points beyond each end.
+ * DIRICHLET: every ghost value is the boundary value (bc_left / bc_right) and the two
+ * end point values are held at it. OUTFLOW: the DoFs are reflected evenly about the
+ * end point (zero gradient); the end point values evolve like interior ones. The CFL
+ * maximum includes the two end faces. 2D meshes are periodic. */
+enum { AF_BC_PERIODIC = 0, AF_BC_DIRICHLET = 1, AF_BC_OUTFLOW = 2 };
+
+/* Discretisation of the diffusion term. DC: the doubly conservative form (Section
+ * 2.2; the default). NODC: the compact form without double conservation of Appendix A
+ * (1D, blend off): the cell average receives the face flux kappa(u) D_c(u) at x_{i+1/2},
+ * the point value 4/dx^2 sum_{m,n} b_mn kappa(u_m) u_n on its 5-point line; with the
+ * limiter on, the total face flux is blended with the low-order face flux
+ * F^L - (a(ub_{i+1}) - a(ub_i))/dx by Theta with factor 2. */
+enum { AF_FORM_DC = 0, AF_FORM_NODC = 1 };
 
 enum { AF_PREC_FP64 = 0, AF_PREC_FP32_MIXED = 1 };   /* FP32 points/stencils, FP64 averages */
 enum { AF_RK_SSP3 = 3, AF_RK_SSP54 = 54 };
 enum { AF_BLEND_OFF = 0, AF_BLEND_PLAIN = 1, AF_BLEND_EXTERNAL = 2 };
 
-typedef struct { int dim; int nx, ny; double x0, x1, y0, y1; } af_grid;  /* periodic only */
+typedef struct {
+  int dim;
+  int nx, ny;
+  double x0, x1, y0, y1;
+  int bc;                 /* AF_BC_*; anything but AF_BC_PERIODIC needs dim = 1, nx >= 4     */
+  double bc_left, bc_right; /* Dirichlet values at x0 and x1                               */
+} af_grid;
 typedef struct { int kind; double p[4]; } af_flux;
 typedef struct { int kind; double p[4]; } af_diff;
 typedef struct { double umin, umax; int from_initial_data; } af_bounds_t;
@@ -80,12 +108,15 @@ typedef struct {
   int limiter;            /* 1: monolithic convex limiter + point projection (Section 5)    */
   int blend;              /* AF_BLEND_*: smoothness-indicator blend (Section 5.1.3)         */
   double gamma;           /* blend strength gamma (1 in the paper's examples)               */
+  int diffusion_form;     /* AF_FORM_DC or AF_FORM_NODC                                     */
 } af_opts;
 
-/* Create a solver for one periodic mesh. Allocates all device buffers (4 state copies
- * for SSP-RK(5,4), 3 for SSP-RK3). bounds->from_initial_data = 1 defers umin/umax to
- * the min/max of the first af_set_state. Returns AF_E_ARG for nx,ny < 1, dim not 1/2,
- * unknown kinds, umin >= umax; AF_E_OOM if allocation fails. */
+/* Create a solver for one mesh. Allocates all device buffers (4 state copies for
+ * SSP-RK(5,4), 3 for SSP-RK3). bounds->from_initial_data = 1 defers umin/umax to the
+ * min/max of the first af_set_state. Returns AF_E_ARG for nx,ny < 1, dim not 1/2,
+ * unknown kinds, umin >= umax, a bounded interval with nx < 4; AF_E_UNSUPPORTED for
+ * non-periodic ends or AF_FORM_NODC in 2D, AF_FORM_NODC with a blend, and the external
+ * indicator on a bounded interval; AF_E_OOM if allocation fails. */
 af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* diff,
                     const af_bounds_t* bounds, const af_opts* opts, af_ctx** out);
 af_status af_destroy(af_ctx* ctx);
@@ -96,19 +127,20 @@ const char* af_last_error(const af_ctx* ctx);
 af_status af_set_stream(af_ctx* ctx, void* stream);
 
 /* Copy a host state in (doubles, caller-owned, nx*ny values each, row-major; X and Y
- * ignored in 1D). The arrays are copied to the device and checked there; FP32-mixed
+ * ignored in 1D; V holds nx+1 values on a bounded 1D interval). The arrays are copied to the device and checked there; FP32-mixed
  * contexts then round the point values to nearest float. AF_E_STATE if any value is NaN
  * or, with the limiter on, outside [umin, umax]; the current state is then unchanged.
  * Page-locked host memory copies fastest. Returns after the host arrays have been read
  * (the caller may reuse them). */
 af_status af_set_state(af_ctx* ctx, const double* ub, const double* V, const double* X, const double* Y);
 /* Copy the current state out into caller-owned doubles (FP32 point values widened
- * exactly). Synchronous with the context's stream. */
+ * exactly; the same array lengths as af_set_state). Synchronous with the context's
+ * stream. */
 af_status af_get_state(af_ctx* ctx, double* ub, double* V, double* X, double* Y);
 
 /* Borrowed device pointers of the current state (ub, V, X, Y). dtype[0] is 8 (ub is
  * always FP64); dtype[1] is 8 or 4 for the point arrays. Valid until the next call that
- * steps or destroys the context. */
+ * steps or destroys the context (a bounded 1D interval: nx+1 point values). */
 af_status af_device_ptrs(af_ctx* ctx, void* ptrs[4], int dtype[2]);
 
 /* Per-cell external smoothness indicator s (nx*ny doubles, host) used when
@@ -158,7 +190,8 @@ af_status af_stats(af_ctx* ctx, long long* clamps, long long* errors, double* ma
 /* ---- batches of independent meshes -------------------------------------------------
  * A batch holds n independent periodic 2D meshes (uneven sizes; per-instance flux and
  * diffusion parameters and bounds) that share the flux kind, precision, RK scheme,
- * limiter and CFL options of *opts (blend must be off). One persistent launch per RK
+ * limiter and CFL options of *opts (blend off, AF_FORM_DC; grids periodic, else
+ * AF_E_UNSUPPORTED). One persistent launch per RK
  * stage walks the (instance, tile) work list with the same tile computation as the
  * single-mesh kernel, so every instance evolves as a single-mesh context with the same
  * options does (bit for bit with SSP-RK3; to a few ulp with SSP-RK(5,4), where the two

@@ -16,17 +16,23 @@ __all__ = ["Solver", "capi", "AfError"]
 
 
 class Solver:
-    """One periodic mesh behind an af_ctx.
+    """One mesh behind an af_ctx.
 
     spec: any object with the attributes dim, nx, ny, x0, x1, y0, y1, flux=(kind, params),
-    diff=(kind, params), umin, umax, limiter, blend, gamma (e.g. af_inputs.Spec).
+    diff=(kind, params), umin, umax, limiter, blend, gamma and optionally bc ("periodic",
+    "dirichlet", "outflow"), bc_values and diffusion_form ("dc", "nodc") (e.g.
+    af_inputs.Spec). A 1D interval with Dirichlet or outflow ends has nx + 1 point values.
     """
 
     def __init__(self, spec, precision="fp64", rk=3, cfl=0.0, cfl_diff=0.0, bounds_from_data=False):
         self.spec = spec
         self.dim = spec.dim
         self.n = spec.nx * (spec.ny if spec.dim == 2 else 1)
-        g = af_grid(spec.dim, spec.nx, spec.ny if spec.dim == 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1)
+        bc = getattr(spec, "bc", "periodic")
+        gl, gr = getattr(spec, "bc_values", (0.0, 0.0))
+        self.npts = self.n + (1 if spec.dim == 1 and bc != "periodic" else 0)
+        g = af_grid(spec.dim, spec.nx, spec.ny if spec.dim == 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1,
+                    capi.BC[bc], float(gl), float(gr))
         f = af_flux()
         f.kind = capi.FLUX[spec.flux[0]]
         for k, v in enumerate(spec.flux[1]):
@@ -37,7 +43,7 @@ class Solver:
             d.p[k] = float(v)
         b = af_bounds_t(float(spec.umin), float(spec.umax), 1 if bounds_from_data else 0)
         o = af_opts(capi.PREC[precision], int(rk), float(cfl), float(cfl_diff), int(bool(spec.limiter)),
-                    capi.BLEND[spec.blend], float(spec.gamma))
+                    capi.BLEND[spec.blend], float(spec.gamma), capi.FORM[getattr(spec, "diffusion_form", "dc")])
         self.precision = precision
         self.ctx = capi.af_create(g, f, d, b, o)
 
@@ -62,14 +68,17 @@ class Solver:
     def set_state(self, state):
         arrs = [np.asarray(a, dtype=np.float64) for a in state]
         if self.dim == 1:
-            capi.af_set_state(self.ctx, self.n, arrs[0], arrs[1])
+            capi.af_set_state(self.ctx, self.n, arrs[0], arrs[1], npts=self.npts)
         else:
             capi.af_set_state(self.ctx, self.n, *arrs)
 
     def get_state(self, out=None):
         """Host copy of (ub, V, X, Y); `out` may supply the destination float64 arrays
         (for instance views of pinned host memory, which copy fastest)."""
-        shape = (self.spec.ny, self.spec.nx) if self.dim == 2 else (self.spec.nx,)
+        if self.dim == 1:
+            flat = None if out is None else [np.asarray(a).reshape(-1) for a in out]
+            return capi.af_get_state(self.ctx, self.n, 1, flat, npts=self.npts)
+        shape = (self.spec.ny, self.spec.nx)
         flat = None if out is None else [np.asarray(a).reshape(-1) for a in out]
         res = capi.af_get_state(self.ctx, self.n, self.dim, flat)
         return [a.reshape(shape) for a in res]
@@ -85,9 +94,10 @@ class Solver:
             if p is None:
                 continue
             typestr = "<f8" if (k == 0 or d1 == 8) else "<f4"
+            shp = (self.npts,) if (self.dim == 1 and k > 0) else shape
 
             class _View:
-                __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (p, False), "version": 3}
+                __cuda_array_interface__ = {"shape": shp, "typestr": typestr, "data": (p, False), "version": 3}
 
             out.append(torch.as_tensor(_View(), device="cuda"))
         return out

@@ -15,7 +15,9 @@ AF_OK, AF_E_ARG, AF_E_CUDA, AF_E_OOM, AF_E_STATE, AF_E_CFL, AF_E_TIMEOUT, AF_E_U
 STATUS_NAMES = {0: "AF_OK", -1: "AF_E_ARG", -2: "AF_E_CUDA", -3: "AF_E_OOM", -4: "AF_E_STATE", -5: "AF_E_CFL",
                 -6: "AF_E_TIMEOUT", -7: "AF_E_UNSUPPORTED"}
 FLUX = {"zero": 0, "linear": 1, "burgers": 2, "bl": 3}
-DIFF = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4}
+DIFF = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4, "ramp": 5}
+BC = {"periodic": 0, "dirichlet": 1, "outflow": 2}
+FORM = {"dc": 0, "nodc": 1}
 PREC = {"fp64": 0, "fp32_mixed": 1}
 BLEND = {"off": 0, "plain": 1, "external": 2}
 
@@ -28,7 +30,8 @@ class AfError(RuntimeError):
 
 class af_grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x0", ctypes.c_double),
-                ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double)]
+                ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("bc", ctypes.c_int),
+                ("bc_left", ctypes.c_double), ("bc_right", ctypes.c_double)]
 
 
 class af_flux(ctypes.Structure):
@@ -46,7 +49,7 @@ class af_bounds_t(ctypes.Structure):
 class af_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rk", ctypes.c_int), ("cfl", ctypes.c_double),
                 ("cfl_diff", ctypes.c_double), ("limiter", ctypes.c_int), ("blend", ctypes.c_int),
-                ("gamma", ctypes.c_double)]
+                ("gamma", ctypes.c_double), ("diffusion_form", ctypes.c_int)]
 
 
 _lib = None
@@ -340,22 +343,27 @@ def af_set_stream(ctx, stream_handle):
     _check(ctx, lib().af_set_stream(ctx, _V(stream_handle)))
 
 
-def af_set_state(ctx, n, ub, V, X=None, Y=None):
-    arrs = [_host(ub, n), _host(V, n), None if X is None else _host(X, n), None if Y is None else _host(Y, n)]
+def af_set_state(ctx, n, ub, V, X=None, Y=None, npts=None):
+    """npts: values per point array (default n; n + 1 on a bounded 1D interval)."""
+    m = n if npts is None else npts
+    arrs = [_host(ub, n), _host(V, m), None if X is None else _host(X, m), None if Y is None else _host(Y, m)]
     _check(ctx, lib().af_set_state(ctx, *[_dp(a) for a in arrs]))
 
 
-def af_get_state(ctx, n, dim, out=None):
-    """Copy the state to host float64 arrays: `out` (C-contiguous float64 arrays of n
-    values each, e.g. views of pinned memory) or new arrays."""
+def af_get_state(ctx, n, dim, out=None, npts=None):
+    """Copy the state to host float64 arrays: `out` (C-contiguous float64 arrays, e.g.
+    views of pinned memory) or new arrays; n averages, npts (default n) point values
+    per point array."""
     k = 4 if dim == 2 else 2
+    m = n if npts is None else npts
+    sizes = [n] + [m] * (k - 1)
     if out is None:
-        out = [np.empty(n) for _ in range(k)]
+        out = [np.empty(z) for z in sizes]
     else:
         out = list(out)
-        if len(out) != k or any(not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.size == n and
-                                     a.flags.c_contiguous) for a in out):
-            raise ValueError(f"out must be {k} C-contiguous float64 arrays of {n} values")
+        if len(out) != k or any(not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.size == z and
+                                     a.flags.c_contiguous) for a, z in zip(out, sizes)):
+            raise ValueError(f"out must be {k} C-contiguous float64 arrays of {sizes} values")
     full = out + ([None, None] if dim == 1 else [])
     _check(ctx, lib().af_get_state(ctx, *[_dp(a) for a in full]))
     return out

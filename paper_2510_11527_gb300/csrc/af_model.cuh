@@ -166,6 +166,43 @@ __device__ __forceinline__ T apot(const DevModel& m, T u) {
     }
     case AF_DIFF_CUBIC:
       return ((par<T>(d, f, 2) * u + par<T>(d, f, 1)) * u + par<T>(d, f, 0)) * u;
+    case AF_DIFF_RAMP: {
+      // 0 below p1, p0 (u-p1)^2 / (2 p2) on the ramp, p0 (u - p1 - p2/2) above it
+      const T k = par<T>(d, f, 0), lo = par<T>(d, f, 1), w = par<T>(d, f, 2), r = u - lo;
+      if (!tlt(lo, u)) return T(0);
+      if (tlt(u, lo + w)) return k * r * r / (T(2) * w);
+      return k * (r - T(0.5) * w);
+    }
+    default:
+      return T(0);
+  }
+}
+
+// kappa(u) = a'(u), read by the diffusion form without double conservation; at a kink
+// the one-sided value on the degenerate side (0 at u = p1, p3 of AF_DIFF_PWL)
+template <class T>
+__device__ __forceinline__ T kappa_fn(const DevModel& m, T u) {
+  const double* d = m.dp;
+  const float* f = m.dpf;
+  switch (m.diff_kind) {
+    case AF_DIFF_CONST:
+      return par<T>(d, f, 0);
+    case AF_DIFF_PWL:
+      return (tlt(u, par<T>(d, f, 1)) ? par<T>(d, f, 0) : T(0)) + (tlt(par<T>(d, f, 3), u) ? par<T>(d, f, 2) : T(0));
+    case AF_DIFF_PME: {
+      const int e = (int)m.dpf[0];
+      T r = T(e);
+      for (int k = 1; k < e; ++k) r *= u;
+      return r;
+    }
+    case AF_DIFF_CUBIC:
+      return par<T>(d, f, 0) + (T(2) * par<T>(d, f, 1) + T(3) * par<T>(d, f, 2) * u) * u;
+    case AF_DIFF_RAMP: {
+      const T k = par<T>(d, f, 0), lo = par<T>(d, f, 1), w = par<T>(d, f, 2);
+      if (!tlt(lo, u)) return T(0);
+      if (tlt(u, lo + w)) return k * (u - lo) / w;
+      return k;
+    }
     default:
       return T(0);
   }

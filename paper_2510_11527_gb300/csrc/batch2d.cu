@@ -86,6 +86,8 @@ __device__ __forceinline__ void batch_stage_body(const BatchInst* __restrict__ i
     A.gamma = 0.0;
     A.tol = I.tol;
     A.stats = stats;
+    A.bc = AF_BC_PERIODIC;
+    A.nodc = 0;
     }
     __syncthreads();
     // element-wise halo loads: the paired path's extra registers spill in this kernel
@@ -407,12 +409,14 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return AF_E_UNSUPPORTED;
   if (opts->precision != AF_PREC_FP64 && opts->precision != AF_PREC_FP32_MIXED) return AF_E_ARG;
   if (opts->rk != AF_RK_SSP3 && opts->rk != AF_RK_SSP54) return AF_E_ARG;
-  if (opts->blend != AF_BLEND_OFF) return AF_E_UNSUPPORTED;
+  if (opts->blend != AF_BLEND_OFF || opts->diffusion_form != AF_FORM_DC) return AF_E_UNSUPPORTED;
   for (int k = 0; k < n; ++k) {
     if (grids[k].dim != 2 || grids[k].nx < 1 || grids[k].ny < 1) return AF_E_ARG;
+    if (grids[k].bc != AF_BC_PERIODIC) return AF_E_UNSUPPORTED;
     if (!(grids[k].x1 > grids[k].x0) || !(grids[k].y1 > grids[k].y0)) return AF_E_ARG;
     if (fluxes[k].kind != fluxes[0].kind || fluxes[k].kind < 0 || fluxes[k].kind > AF_FLUX_BL) return AF_E_ARG;
-    if (diffs[k].kind < AF_DIFF_NONE || diffs[k].kind > AF_DIFF_CUBIC) return AF_E_ARG;
+    if (diffs[k].kind < AF_DIFF_NONE || diffs[k].kind > AF_DIFF_RAMP) return AF_E_ARG;
+    if (diffs[k].kind == AF_DIFF_RAMP && !(diffs[k].p[2] > 0.0)) return AF_E_ARG;
     if (bounds[k].from_initial_data || !(bounds[k].umax > bounds[k].umin)) return AF_E_ARG;
   }
   af_batch* b = new (std::nothrow) af_batch;

@@ -71,6 +71,10 @@ StageArgs2D<PT> base_args(af_ctx* c, int in) {
   a.gamma = c->opts.gamma;
   a.tol = c->tol;
   a.stats = c->stats;
+  a.bc = c->grid.bc;
+  a.bc_left = c->grid.bc_left;
+  a.bc_right = c->grid.bc_right;
+  a.nodc = c->opts.diffusion_form == AF_FORM_NODC;
   return a;
 }
 
@@ -190,7 +194,8 @@ template <int FLUX>
 cudaError_t launch_rate(af_ctx* c) {
   const int blocks = 152 * 4;
   af::dt_rate_kernel<FLUX><<<blocks, af::RED_THREADS, 0, c->stream>>>(c->m, c->dim, c->nx, c->ny, c->inv_h1,
-                                                                       c->inv_h2, c->kmax, c->ub[0], c->rate_bits);
+                                                                       c->inv_h2, c->kmax, c->ub[0], c->rate_bits,
+                                                                       c->grid.bc, c->grid.bc_left, c->grid.bc_right);
   return cudaGetLastError();
 }
 
@@ -219,9 +224,9 @@ af_status read_scalar(af_ctx* c, const double* dev, double* out) {
 }
 
 template <class S>
-af_status reduce_array(af_ctx* c, const S* x, int op, double init, double* out_dev, int accumulate) {
-  const int blocks = (int)std::min<size_t>(af::RED_MAX_BLOCKS, (c->n + af::RED_THREADS - 1) / af::RED_THREADS);
-  af::partial_kernel<S><<<blocks, af::RED_THREADS, 0, c->stream>>>(x, c->n, op, init, c->partial);
+af_status reduce_array(af_ctx* c, const S* x, size_t count, int op, double init, double* out_dev, int accumulate) {
+  const int blocks = (int)std::min<size_t>(af::RED_MAX_BLOCKS, (count + af::RED_THREADS - 1) / af::RED_THREADS);
+  af::partial_kernel<S><<<blocks, af::RED_THREADS, 0, c->stream>>>(x, count, op, init, c->partial);
   CK(c, cudaGetLastError());
   af::finalize_kernel<<<1, af::RED_THREADS, 0, c->stream>>>(c->partial, blocks, op, out_dev, accumulate);
   CK(c, cudaGetLastError());
@@ -248,8 +253,15 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   if (grid->nx < 1 || (grid->dim == 2 && grid->ny < 1)) return AF_E_ARG;
   if (!(grid->x1 > grid->x0) || (grid->dim == 2 && !(grid->y1 > grid->y0))) return AF_E_ARG;
   if (flux->kind < AF_FLUX_ZERO || flux->kind > AF_FLUX_BL) return AF_E_ARG;
-  if (diff->kind < AF_DIFF_NONE || diff->kind > AF_DIFF_CUBIC) return AF_E_ARG;
+  if (diff->kind < AF_DIFF_NONE || diff->kind > AF_DIFF_RAMP) return AF_E_ARG;
   if (diff->kind == AF_DIFF_PME && (diff->p[0] < 1.0 || diff->p[0] != std::floor(diff->p[0]))) return AF_E_ARG;
+  if (diff->kind == AF_DIFF_RAMP && !(diff->p[2] > 0.0)) return AF_E_ARG;
+  if (grid->bc < AF_BC_PERIODIC || grid->bc > AF_BC_OUTFLOW) return AF_E_ARG;
+  if (opts->diffusion_form != AF_FORM_DC && opts->diffusion_form != AF_FORM_NODC) return AF_E_ARG;
+  if (grid->bc != AF_BC_PERIODIC && grid->dim != 1) return AF_E_UNSUPPORTED;
+  if (grid->bc != AF_BC_PERIODIC && grid->nx < 4) return AF_E_ARG;
+  if (opts->diffusion_form == AF_FORM_NODC && (grid->dim != 1 || opts->blend != AF_BLEND_OFF)) return AF_E_UNSUPPORTED;
+  if (grid->bc != AF_BC_PERIODIC && opts->blend == AF_BLEND_EXTERNAL) return AF_E_UNSUPPORTED;
   if (!bounds->from_initial_data && !(bounds->umax > bounds->umin)) return AF_E_ARG;
   if (opts->precision != AF_PREC_FP64 && opts->precision != AF_PREC_FP32_MIXED) return AF_E_ARG;
   if (opts->rk != AF_RK_SSP3 && opts->rk != AF_RK_SSP54) return AF_E_ARG;
@@ -266,6 +278,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->nx = grid->nx;
   c->ny = grid->dim == 2 ? grid->ny : 1;
   c->n = (size_t)c->nx * c->ny;
+  c->np = c->n + (grid->dim == 1 && grid->bc != AF_BC_PERIODIC ? 1 : 0);
   c->prec = opts->precision;
   c->nbuf = opts->rk == AF_RK_SSP54 ? 4 : 3;
   c->dx = (grid->x1 - grid->x0) / grid->nx;
@@ -289,7 +302,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   // one device allocation: nbuf states + scratch
   const size_t ps = pt_size(c);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t per_state = al(c->n * 8) + 3 * al(c->n * ps);
+  const size_t per_state = al(c->n * 8) + 3 * al(c->np * ps);
   const size_t scratch = al(8) * 2 + al(8 * 8) + al(8 * af::RED_MAX_BLOCKS) + al(8) + al(sizeof(DevStats)) + al(c->n * 8);
   const size_t total = per_state * c->nbuf + scratch;
   if (cudaMalloc(&c->block, total) != cudaSuccess) {
@@ -300,9 +313,9 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   unsigned char* p = c->block;
   for (int b = 0; b < c->nbuf; ++b) {
     c->ub[b] = (double*)p; p += al(c->n * 8);
-    c->pv[b] = p; p += al(c->n * ps);
-    c->px[b] = p; p += al(c->n * ps);
-    c->py[b] = p; p += al(c->n * ps);
+    c->pv[b] = p; p += al(c->np * ps);
+    c->px[b] = p; p += al(c->np * ps);
+    c->py[b] = p; p += al(c->np * ps);
   }
   c->dt_dev = (double*)p; p += al(8);
   c->t_dev = (double*)p; p += al(8);
@@ -345,13 +358,15 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
   const int na = c->dim == 2 ? 4 : 2;
   const double* src[4] = {ub, V, X, Y};
-  const size_t n = c->n;
-  // staging: the RK temporaries (buffers 1..nbuf-1, contiguous, >= 40 n bytes >= 8 na n)
+  const size_t n = c->n, np = c->np, total = n + (na - 1) * np;
+  // staging: the RK temporaries (buffers 1..nbuf-1, contiguous, >= 8 n + 12 np bytes
+  // >= 8 total), ub then the point arrays back to back
   double* stg = c->ub[1];
-  for (int a = 0; a < na; ++a)
-    CK(c, cudaMemcpyAsync(stg + a * n, src[a], n * 8, cudaMemcpyHostToDevice, c->stream));
-  const int nb = (int)std::min<size_t>(af::STATE_IO_BLOCKS, (na * n + af::RED_THREADS - 1) / af::RED_THREADS);
-  af::validate_partial_kernel<<<nb, af::RED_THREADS, 0, c->stream>>>(stg, na * n, (unsigned long long*)c->partial);
+  CK(c, cudaMemcpyAsync(stg, ub, n * 8, cudaMemcpyHostToDevice, c->stream));
+  for (int a = 1; a < na; ++a)
+    CK(c, cudaMemcpyAsync(stg + n + (a - 1) * np, src[a], np * 8, cudaMemcpyHostToDevice, c->stream));
+  const int nb = (int)std::min<size_t>(af::STATE_IO_BLOCKS, (total + af::RED_THREADS - 1) / af::RED_THREADS);
+  af::validate_partial_kernel<<<nb, af::RED_THREADS, 0, c->stream>>>(stg, total, (unsigned long long*)c->partial);
   CK(c, cudaGetLastError());
   af::validate_final_kernel<<<1, af::RED_THREADS, 0, c->stream>>>((const unsigned long long*)c->partial, nb, c->red + 5);
   CK(c, cudaGetLastError());
@@ -370,13 +385,13 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
   } else if (c->opts.limiter && (lo < c->m.umin || hi > c->m.umax)) {
     FAIL(c, AF_E_STATE, "input outside [umin, umax]: [%g, %g]", lo, hi);
   }
-  const int grid = (int)std::min<size_t>(152 * 8, (n + af::RED_THREADS - 1) / af::RED_THREADS);
+  const int grid = (int)std::min<size_t>(152 * 8, (np + af::RED_THREADS - 1) / af::RED_THREADS);
   if (c->prec == AF_PREC_FP64)
     af::scatter_state_kernel<double><<<grid, af::RED_THREADS, 0, c->stream>>>(
-        stg, n, na, c->ub[0], (double*)c->pv[0], (double*)c->px[0], (double*)c->py[0]);
+        stg, n, np, na, c->ub[0], (double*)c->pv[0], (double*)c->px[0], (double*)c->py[0]);
   else
     af::scatter_state_kernel<float><<<grid, af::RED_THREADS, 0, c->stream>>>(
-        stg, n, na, c->ub[0], (float*)c->pv[0], (float*)c->px[0], (float*)c->py[0]);
+        stg, n, np, na, c->ub[0], (float*)c->pv[0], (float*)c->px[0], (float*)c->py[0]);
   CK(c, cudaGetLastError());
   return AF_OK;
 }
@@ -384,21 +399,21 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
 af_status af_get_state(af_ctx* c, double* ub, double* V, double* X, double* Y) {
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
   const int na = c->dim == 2 ? 4 : 2;
-  const size_t n = c->n;
+  const size_t n = c->n, np = c->np;
   double* dst[4] = {ub, V, X, Y};
   CK(c, cudaMemcpyAsync(ub, c->ub[0], n * 8, cudaMemcpyDeviceToHost, c->stream));
   if (c->prec == AF_PREC_FP64) {
     void* src[3] = {c->pv[0], c->px[0], c->py[0]};
-    for (int a = 1; a < na; ++a) CK(c, cudaMemcpyAsync(dst[a], src[a - 1], n * 8, cudaMemcpyDeviceToHost, c->stream));
+    for (int a = 1; a < na; ++a) CK(c, cudaMemcpyAsync(dst[a], src[a - 1], np * 8, cudaMemcpyDeviceToHost, c->stream));
   } else {
     // FP32 points widened on the device into the staging area, then copied
     double* stg = c->ub[1];
-    const int grid = (int)std::min<size_t>(152 * 8, (n + af::RED_THREADS - 1) / af::RED_THREADS);
+    const int grid = (int)std::min<size_t>(152 * 8, (np + af::RED_THREADS - 1) / af::RED_THREADS);
     af::gather_points_kernel<<<grid, af::RED_THREADS, 0, c->stream>>>(
-        (const float*)c->pv[0], (const float*)c->px[0], (const float*)c->py[0], n, na, stg);
+        (const float*)c->pv[0], (const float*)c->px[0], (const float*)c->py[0], np, na, stg);
     CK(c, cudaGetLastError());
     for (int a = 1; a < na; ++a)
-      CK(c, cudaMemcpyAsync(dst[a], stg + (a - 1) * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
+      CK(c, cudaMemcpyAsync(dst[a], stg + (a - 1) * np, np * 8, cudaMemcpyDeviceToHost, c->stream));
   }
   CK(c, cudaStreamSynchronize(c->stream));
   return AF_OK;
@@ -528,7 +543,7 @@ af_status af_time(af_ctx* c, double* t) {
 
 af_status af_mass(af_ctx* c, double* mass) {
   if (!c || !mass) return AF_E_ARG;
-  af_status s = reduce_array<double>(c, c->ub[0], 0, 0.0, c->red + 1, 0);
+  af_status s = reduce_array<double>(c, c->ub[0], c->n, 0, 0.0, c->red + 1, 0);
   if (s != AF_OK) return s;
   double v;
   s = read_scalar(c, c->red + 1, &v);
@@ -546,9 +561,9 @@ af_status af_bounds(af_ctx* c, double* umin, double* umax) {
       af_status s;
       const double init = op == 1 ? INFINITY : -INFINITY;
       if (a == 0 || c->prec == AF_PREC_FP64)
-        s = reduce_array<double>(c, (const double*)arrs[a], op, init, c->red + 1 + op, a > 0);
+        s = reduce_array<double>(c, (const double*)arrs[a], a == 0 ? c->n : c->np, op, init, c->red + 1 + op, a > 0);
       else
-        s = reduce_array<float>(c, (const float*)arrs[a], op, init, c->red + 1 + op, a > 0);
+        s = reduce_array<float>(c, (const float*)arrs[a], c->np, op, init, c->red + 1 + op, a > 0);
       if (s != AF_OK) return s;
     }
   }

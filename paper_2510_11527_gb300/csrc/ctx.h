@@ -15,6 +15,7 @@ struct af_ctx {
   af::DevModel m;
   int dim = 2, nx = 1, ny = 1, prec = AF_PREC_FP64, nbuf = 3;
   size_t n = 0;
+  size_t np = 0;                      // point values per point array (n, or n + 1 on a bounded 1D interval)
   double dx = 1, dy = 1, inv_h1 = 1, inv_h2 = 1, kmax = 0, cfl = 0.165, cfl_diff = 0, tol = 0;
   bool bounds_pending = false;
   unsigned char* block = nullptr;     // one allocation for every device buffer

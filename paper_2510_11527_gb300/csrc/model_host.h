@@ -90,6 +90,7 @@ inline double kappa_of(const af_diff& df, double u) {
     case AF_DIFF_PWL: return (u < df.p[1] ? df.p[0] : 0.0) + (u > df.p[3] ? df.p[2] : 0.0);
     case AF_DIFF_PME: return df.p[0] * std::pow(u, df.p[0] - 1.0);
     case AF_DIFF_CUBIC: return df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u;
+    case AF_DIFF_RAMP: return u <= df.p[1] ? 0.0 : (u < df.p[1] + df.p[2] ? df.p[0] * (u - df.p[1]) / df.p[2] : df.p[0]);
     default: return 0.0;
   }
 }

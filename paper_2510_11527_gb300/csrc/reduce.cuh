@@ -19,6 +19,9 @@ constexpr int RED_MAX_BLOCKS = 1024;   // partial-result slots per reduction
 // that lies strictly inside some face interval. The kernel reduces the first term into
 // rate_bits[0] (non-negative doubles order like their bit patterns) and flags the
 // extrema met (bit 8 l + k) in rate_bits[1]; dt_finalize_kernel adds their terms.
+// A bounded 1D interval (bc != AF_BC_PERIODIC) has no wrap-around face; its two end
+// faces join the end cells to their ghosts: the Dirichlet values gl / gr are then face
+// end points too, while an outflow ghost repeats the end cell (nothing new).
 template <int FLUX>
 __device__ __forceinline__ unsigned crit_flags(const DevModel& m, int dir, double a, double b) {
   unsigned f = 0u;
@@ -34,7 +37,8 @@ template <int FLUX>
 __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, int dim, int nx, int ny,
                                                                double inv_h1, double inv_h2, double kmax,
                                                                const double* __restrict__ ub,
-                                                               unsigned long long* rate_bits) {
+                                                               unsigned long long* rate_bits, int bc, double gl,
+                                                               double gr) {
   const size_t n = (size_t)nx * ny;
   double best = 0.0;
   unsigned flags = 0u;
@@ -47,7 +51,11 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
       a1 = r.d[0];
       a2 = r.d[1];
       const int i = (int)(k % nx), j = (int)(k / nx);
-      flags |= crit_flags<FLUX>(m, 0, u, ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)]);
+      const double un = (dim == 1 && bc != AF_BC_PERIODIC && i + 1 == nx)
+                            ? (bc == AF_BC_DIRICHLET ? gr : u)
+                            : ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)];
+      flags |= crit_flags<FLUX>(m, 0, u, un);
+      if (dim == 1 && bc == AF_BC_DIRICHLET && k == 0) flags |= crit_flags<FLUX>(m, 0, gl, u);
       if (dim == 2) flags |= crit_flags<FLUX>(m, 1, u, ub[(size_t)(j + 1 == ny ? 0 : j + 1) * nx + i]) << 8;
     } else {
       a1 = alpha_interval<FLUX, double>(m, 0, u, u);
@@ -55,6 +63,15 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
     }
     best = tmax(best, a1 * inv_h1 + kd1);
     if (dim == 2) best = tmax(best, a2 * inv_h2 + kd2);
+  }
+  if (dim == 1 && bc == AF_BC_DIRICHLET && blockIdx.x == 0 && threadIdx.x == 0) {
+    const double gv[2] = {gl, gr};
+    for (int s = 0; s < 2; ++s) {
+      double d;
+      if constexpr (FLUX == FLUX_BL) d = bl_eval<double>(m, gv[s]).d[0];
+      else d = alpha_interval<FLUX, double>(m, 0, gv[s], gv[s]);
+      best = tmax(best, d * inv_h1 + kd1);
+    }
   }
   for (int o = 16; o > 0; o >>= 1) best = tmax(best, __shfl_xor_sync(0xffffffffu, best, o));
   flags = __reduce_or_sync(0xffffffffu, flags);

@@ -1,12 +1,20 @@
 // Fused 1D stage kernel of the compact fourth-order doubly conservative active flux
-// method (arXiv 2510.11527, Sections 2 and 5.1). Same structure as the 2D kernel:
-// each CTA owns TX cells (cell average ub_i and the point value P_i = u_{i+1/2}) and
-// stages a +-3 cell halo in shared memory.
+// method (arXiv 2510.11527, Sections 2 and 5.1; Appendix A for the diffusion form
+// without double conservation). Same structure as the 2D kernel: each CTA owns TX cells
+// (cell average ub_i and the point value P_i = u_{i+1/2}) and stages a +-3 cell halo
+// in shared memory.
 //   centre          u_i = (6 ub_i - u_{i-1/2} - u_{i+1/2}) / 4
 //   point residual  5-point line [P_{i-1}, c_i, P_i, c_{i+1}, P_{i+1}]
 //   DC potential    a^_i = (-a(P_{i-1}) + 8 a(c_i) - a(P_i)) / 6   (Proposition 2.1)
 //   low order       LLF with interval wave speed, states u^{L,+-} with factor 2
 //   limiter         theta^c (2 states) and theta^d (4 states) with factor 6
+// Without double conservation (Appendix A) the face flux is f(P_i) - kappa(P_i) D_c(u),
+// D_c(u) = (P_{i-1} - 8 c_i + 8 c_{i+1} - P_{i+1}) / (6 dx), the point value takes
+// 4/dx^2 sum_{m,n} b_mn kappa(z_m) z_n on its line, and the limiter blends the total
+// face flux with F^L - (a(ub_{i+1}) - a(ub_i))/dx by Theta with factor 2.
+// A bounded interval (Dirichlet / outflow ends) reads ghost cells and points from the
+// boundary rule, updates the extra left end point u_{-1/2} in CTA 0, and holds
+// Dirichlet end points at the boundary values.
 #pragma once
 #include "stage2d.cuh"
 
@@ -17,11 +25,47 @@ struct Tile1D {
   static constexpr int TX = 256, NT = TX, H = 3, BX = TX + 2 * H;
 };
 
+// Cell average ub_i and point value u_{j+1/2} at any index: stored values inside, the
+// boundary rule outside (periodic image; Dirichlet value; even reflection about the
+// end point for outflow). Indices far beyond an end (never read by an owned output)
+// are clamped to the first H ghosts so that every load stays inside the arrays.
+template <class PT>
+__device__ __forceinline__ double cell1d(const StageArgs2D<PT>& A, int i, int H) {
+  const int n = A.nx;
+  if (A.bc == AF_BC_PERIODIC) return A.ub[wrapi(i, n)];
+  if (i >= 0 && i < n) return A.ub[i];
+  if (A.bc == AF_BC_DIRICHLET) return i < 0 ? A.bc_left : A.bc_right;
+  i = i < -H ? -H : (i >= n + H ? n + H - 1 : i);
+  return A.ub[i < 0 ? -1 - i : 2 * n - 1 - i];
+}
+template <class PT>
+__device__ __forceinline__ PT point1d(const StageArgs2D<PT>& A, int j, int H) {
+  const int n = A.nx;
+  if (A.bc == AF_BC_PERIODIC) return A.V[wrapi(j, n)];
+  if (j >= -1 && j <= n - 1) return A.V[j + 1];
+  if (A.bc == AF_BC_DIRICHLET) return PT(j < -1 ? A.bc_left : A.bc_right);
+  j = j < -H - 1 ? -H - 1 : (j >= n + H ? n + H - 1 : j);
+  return A.V[(j < -1 ? -2 - j : 2 * (n - 1) - j) + 1];
+}
+
+// 4 sum_{m,n} b_mn k_m z_n of Appendix A, B = [0 0; 0 M] - [M 0; 0 0] written out row
+// by row (each row sums to zero)
+template <class T>
+__device__ __forceinline__ T nodc_d2(const T z[5], const T k[5]) {
+  const T r0 = T(-1.0 / 8) * z[0] + T(1.0 / 6) * z[1] - T(1.0 / 24) * z[2];
+  const T r1 = T(1.0 / 6) * z[0] + T(0.5) * z[1] - T(5.0 / 6) * z[2] + T(1.0 / 6) * z[3];
+  const T r2 = T(-1.0 / 8) * (z[0] + z[4]) + T(0.5) * (z[1] + z[3]) - T(0.75) * z[2];
+  const T r3 = T(1.0 / 6) * z[1] - T(5.0 / 6) * z[2] + T(0.5) * z[3] + T(1.0 / 6) * z[4];
+  const T r4 = T(-1.0 / 24) * z[2] + T(1.0 / 6) * z[3] - T(1.0 / 8) * z[4];
+  return T(4) * ((k[0] * r0 + k[1] * r1) + (k[2] * r2 + (k[3] * r3 + k[4] * r4)));
+}
+
 template <int FLUX, class T, class PT>
 __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const StageArgs2D<PT> A) {
   using L = Tile1D<FLUX, T>;
   constexpr int TX = L::TX, NT = L::NT, H = L::H, BX = L::BX;
   __shared__ T sU[BX], sP[BX], sC[BX];
+  // aP / aC hold kappa instead of a without double conservation (no DC potential)
   __shared__ T fP[BX], aP[BX], fC[BX], aC[BX], dP[BX], dC[BX], fU[BX], aU[BX];
   __shared__ T sFH[BX], sAH[BX], sFL[BX], sULp[BX], sULm[BX], sFlim[BX], sAlim[BX];
   __shared__ T sS[BX], sTC[BX], sTD[BX];
@@ -34,11 +78,13 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   const T umin = T(m.umin), umax = T(m.umax);
   const bool blend = A.blend != 0;
   const bool ext = A.blend == 2;
+  const bool nodc = A.nodc != 0;
+  const bool bounded = A.bc != AF_BC_PERIODIC;
+  const int poff = bounded ? 1 : 0;   // point u_{j+1/2} is stored at index j + poff
 
   for (int k = tid; k < BX; k += NT) {
-    const size_t g = (size_t)wrapi(i0 - H + k, nx);
-    sU[k] = T(A.ub[g]);
-    sP[k] = T(A.V[g]);
+    sU[k] = T(cell1d(A, i0 - H + k, H));
+    sP[k] = T(point1d(A, i0 - H + k, H));
   }
   __syncthreads();
   for (int b = tid; b < BX; b += NT) {
@@ -48,13 +94,13 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
     const T p = sP[b];
     fP[b] = flux<FLUX, T>(m, 0, p);
     dP[b] = dflux_abs<FLUX, T>(m, 0, p);
-    aP[b] = apot<T>(m, p);
+    aP[b] = nodc ? kappa_fn<T>(m, p) : apot<T>(m, p);
     if (b >= 1) {
       const T c = (T(6) * u - sP[b - 1] - p) * T(0.25);
       sC[b] = c;
       fC[b] = flux<FLUX, T>(m, 0, c);
       dC[b] = dflux_abs<FLUX, T>(m, 0, c);
-      aC[b] = apot<T>(m, c);
+      aC[b] = nodc ? kappa_fn<T>(m, c) : apot<T>(m, c);
     }
     if (blend && !ext && b >= 1 && b < BX - 1) {
       const T um = sU[b - 1], up = sU[b + 1];
@@ -64,20 +110,41 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   __syncthreads();
   const T ih = T(A.inv_h1);
   const T i6h = T(A.inv_h1 / 6.0), i3h2 = T(A.inv_h1 * A.inv_h1 / 3.0);
-  const int bo = H + tid;
-  // high-order point residual of the owned point
-  T rH;
-  {
-    const int b = bo;
+  // points updated by this thread: its own u_{i+1/2} and, in CTA 0 of a bounded
+  // interval, thread 0 also the left end point u_{-1/2} (held at the boundary value
+  // when the end is Dirichlet)
+  const bool extra = bounded && blockIdx.x == 0 && tid == 0;
+  const int nq = extra ? 2 : 1;
+  const int bq[2] = {H + tid, H - 1};
+  // high-order point residual
+  T rH[2] = {T(0), T(0)};
+  for (int q = 0; q < nq; ++q) {
+    const int b = bq[q];
     const T alpha = tmax(tmax(tmax(dP[b - 1], dC[b]), tmax(dC[b + 1], dP[b + 1])), dP[b]);
-    rH = line_res<T>(sP[b - 1], sC[b], sP[b], sC[b + 1], sP[b + 1], fP[b - 1], fC[b], fC[b + 1], fP[b + 1], alpha,
-                     aP[b - 1], aC[b], aP[b], aC[b + 1], aP[b + 1], i6h, i3h2);
+    if (!nodc) {
+      rH[q] = line_res<T>(sP[b - 1], sC[b], sP[b], sC[b + 1], sP[b + 1], fP[b - 1], fC[b], fC[b + 1], fP[b + 1],
+                          alpha, aP[b - 1], aC[b], aP[b], aC[b + 1], aP[b + 1], i6h, i3h2);
+    } else {
+      const T z[5] = {sP[b - 1], sC[b], sP[b], sC[b + 1], sP[b + 1]};
+      const T k[5] = {aP[b - 1], aC[b], aP[b], aC[b + 1], aP[b + 1]};
+      rH[q] = line_res<T>(z[0], z[1], z[2], z[3], z[4], fP[b - 1], fC[b], fC[b + 1], fP[b + 1], alpha, T(0), T(0),
+                          T(0), T(0), T(0), i6h, i3h2) +
+              nodc_d2<T>(z, k) * (T(3) * i3h2);
+    }
   }
   for (int b = H - 2 + tid; b <= H + TX; b += NT) {
-    if (b >= H - 1 && b < H + TX) sFH[b] = fP[b];
-    if (b >= H - 1) sAH[b] = (T(8) * aC[b] - aP[b - 1] - aP[b]) * T(1.0 / 6.0);
     const T ul = sU[b], ur = sU[b + 1];
-    sFL[b] = T(0.5) * (fU[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, 0, ul, ur) * (ur - ul);
+    const T fl = T(0.5) * (fU[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, 0, ul, ur) * (ur - ul);
+    if (!nodc) {
+      if (b >= H - 1 && b < H + TX) sFH[b] = fP[b];
+      if (b >= H - 1) sAH[b] = (T(8) * aC[b] - aP[b - 1] - aP[b]) * T(1.0 / 6.0);
+      sFL[b] = fl;
+    } else {
+      // total face fluxes: f(P) - kappa(P) D_c(u) and F^L - (a(ub_{i+1}) - a(ub_i)) / dx
+      if (b >= H - 1 && b < H + TX)
+        sFH[b] = fP[b] - aP[b] * (((sP[b - 1] - sP[b + 1]) + T(8) * (sC[b + 1] - sC[b])) * i6h);
+      sFL[b] = fl - (aU[b + 1] - aU[b]) * ih;
+    }
   }
   if (blend) {
     for (int b = H - 1 + tid; b <= H + TX; b += NT) {
@@ -85,7 +152,7 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
     }
   }
   __syncthreads();
-  T rP = rH;
+  T rP[2] = {rH[0], rH[1]};
   if (blend) {
     const T g = T(A.gamma);
     for (int b = H - 1 + tid; b <= H + TX; b += NT) {
@@ -97,13 +164,13 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
       if (b < H + TX) sFH[b] = sTC[b] * sFH[b] + (T(1) - sTC[b]) * sFL[b];
       sAH[b] = sTD[b] * sAH[b] + (T(1) - sTD[b]) * aU[b];
     }
-    {
-      const int b = bo;
+    for (int q = 0; q < nq; ++q) {
+      const int b = bq[q];
       const T zm = sU[b], z0 = sP[b], zp = sU[b + 1];
       const T Fr = T(0.5) * (fP[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, 0, z0, zp) * (zp - z0);
       const T Fl = T(0.5) * (fU[b] + fP[b]) - T(0.5) * alpha_interval<FLUX, T>(m, 0, zm, z0) * (z0 - zm);
       const T RL = (aU[b + 1] - T(2) * aP[b] + aU[b]) * (T(4) * ih * ih) - (Fr - Fl) * (T(2) * ih);
-      rP = sTC[b] * rH + (T(1) - sTC[b]) * RL;
+      rP[q] = sTC[b] * rH[q] + (T(1) - sTC[b]) * RL;
     }
     __syncthreads();
   }
@@ -118,11 +185,19 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
       const T m2 = T(2.0 * mu), n2 = T(2.0 * nu);
       for (int b = H - 2 + tid; b <= H + TX + 1; b += NT) {
         const T u = sU[b], f = fU[b], a = aU[b];
-        if (b <= H + TX) sULp[b] = u - m2 * (sFL[b] - f) + n2 * (aU[b + 1] - a);
-        if (b >= H - 1) sULm[b] = u - m2 * (f - sFL[b - 1]) - n2 * (a - aU[b - 1]);
+        if (!nodc) {
+          if (b <= H + TX) sULp[b] = u - m2 * (sFL[b] - f) + n2 * (aU[b + 1] - a);
+          if (b >= H - 1) sULm[b] = u - m2 * (f - sFL[b - 1]) - n2 * (a - aU[b - 1]);
+        } else {
+          // sFL already holds the total low-order face flux (diffusion included)
+          if (b <= H + TX) sULp[b] = u - m2 * (sFL[b] - f);
+          if (b >= H - 1) sULm[b] = u - m2 * (f - sFL[b - 1]);
+        }
       }
       __syncthreads();
-      const T k6 = T(6.0 * mu), q6 = T(6.0 * nu);
+      // the total face flux of the form without double conservation takes factor 2
+      // (the average is the mean of u^{L,+} and u^{L,-}, one face correction each)
+      const T k6 = T((nodc ? 2.0 : 6.0) * mu), q6 = T(6.0 * nu);
       for (int b = H - 1 + tid; b <= H + TX; b += NT) {
         if (b < H + TX) {
           const T fh = sFH[b], fl = sFL[b], dF = fh - fl;
@@ -130,37 +205,41 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
           const T t = tmin(theta_fn<T>(zp, zp - k6 * dF, umin, umax), theta_fn<T>(zm, zm + k6 * dF, umin, umax));
           sFlim[b] = is_one(t) ? fh : fl + t * dF;
         }
-        const T ah = sAH[b], al = aU[b], d = q6 * (ah - al);
-        const T t = tmin(tmin(theta_fn<T>(sULp[b - 1], sULp[b - 1] + d, umin, umax),
-                              theta_fn<T>(sULp[b], sULp[b] - d, umin, umax)),
-                         tmin(theta_fn<T>(sULm[b], sULm[b] - d, umin, umax),
-                              theta_fn<T>(sULm[b + 1], sULm[b + 1] + d, umin, umax)));
-        sAlim[b] = is_one(t) ? ah : al + t * (ah - al);
+        if (!nodc) {
+          const T ah = sAH[b], al = aU[b], d = q6 * (ah - al);
+          const T t = tmin(tmin(theta_fn<T>(sULp[b - 1], sULp[b - 1] + d, umin, umax),
+                                theta_fn<T>(sULp[b], sULp[b] - d, umin, umax)),
+                           tmin(theta_fn<T>(sULm[b], sULm[b] - d, umin, umax),
+                                theta_fn<T>(sULm[b + 1], sULm[b + 1] + d, umin, umax)));
+          sAlim[b] = is_one(t) ? ah : al + t * (ah - al);
+        }
       }
       __syncthreads();
     }
     if (own) {
-      const int b = bo;
+      const int b = H + tid;
       const size_t g = (size_t)gi;
-      const double ubfe = A.ub[g] - mu * ((double)Flim[b] - (double)Flim[b - 1]) +
-                          nu * (((double)Alim[b + 1] - 2.0 * (double)Alim[b]) + (double)Alim[b - 1]);
-      T p = sP[b] + T(tau) * rP;
-      if (A.limiter) p = tmin(tmax(p, umin), umax);
+      double ubfe = A.ub[g] - mu * ((double)Flim[b] - (double)Flim[b - 1]);
+      if (!nodc) ubfe += nu * (((double)Alim[b + 1] - 2.0 * (double)Alim[b]) + (double)Alim[b - 1]);
       const double cA = A.cA[o], cF = A.cF[o];
-      double ubo;
-      PT po;
-      if (cA != 0.0) {
-        ubo = rk_comb(cA, A.Aub[o][g], cF, ubfe);
-        po = PT(rk_comb(T(cA), T(A.AV[o][g]), T(cF), p));
-      } else {
-        ubo = rk_scale(cF, ubfe);
-        po = PT(rk_scale(T(cF), p));
-      }
-      if (A.limiter && A.sg[o]) {
-        ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
-        po = safeguard<PT>(po, PT(m.umin), PT(m.umax), A.tol, A.stats);
-      }
+      double ubo = cA != 0.0 ? rk_comb(cA, A.Aub[o][g], cF, ubfe) : rk_scale(cF, ubfe);
+      if (A.limiter && A.sg[o]) ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
       A.Oub[o][g] = ubo;
+    }
+    for (int q = 0; q < nq; ++q) {
+      const int gj = q == 0 ? gi : -1;   // point index j of u_{j+1/2}
+      if (gj >= nx) continue;
+      const size_t g = (size_t)(gj + poff);
+      PT po;
+      if (A.bc == AF_BC_DIRICHLET && (gj == -1 || gj == nx - 1)) {
+        po = PT(gj == -1 ? A.bc_left : A.bc_right);
+      } else {
+        T p = sP[bq[q]] + T(tau) * rP[q];
+        if (A.limiter) p = tmin(tmax(p, umin), umax);
+        const double cA = A.cA[o], cF = A.cF[o];
+        po = cA != 0.0 ? PT(rk_comb(T(cA), T(A.AV[o][g]), T(cF), p)) : PT(rk_scale(T(cF), p));
+        if (A.limiter && A.sg[o]) po = safeguard<PT>(po, PT(m.umin), PT(m.umax), A.tol, A.stats);
+      }
       A.OV[o][g] = po;
     }
     if (o + 1 < A.nout) __syncthreads();

@@ -59,6 +59,11 @@ struct StageArgs2D {
   double gamma;
   double tol;                        // safeguard tolerance (absolute)
   DevStats* stats;
+  // 1D only: ends of the interval (AF_BC_*) and the diffusion form (AF_FORM_*). On a
+  // bounded interval the point arrays hold nx+1 values, index k <-> u(x0 + k dx).
+  int bc;
+  double bc_left, bc_right;
+  int nodc;
 };
 
 // Per flux kind: which pointwise quantities are stored per point and per cell average

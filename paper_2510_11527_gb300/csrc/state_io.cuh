@@ -83,22 +83,24 @@ static __global__ void __launch_bounds__(RED_THREADS) validate_final_kernel(cons
   }
 }
 
-// staged doubles (na arrays of n, back to back) -> state buffers (points rounded to
-// nearest when stored in FP32)
+// staged doubles (ub: n values, then na - 1 point arrays of np >= n values, back to
+// back) -> state buffers (points rounded to nearest when stored in FP32)
 template <class PT>
-__global__ void __launch_bounds__(RED_THREADS) scatter_state_kernel(const double* __restrict__ stg, size_t n, int na,
-                                                                    double* ub, PT* V, PT* X, PT* Y) {
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
-    ub[k] = stg[k];
+__global__ void __launch_bounds__(RED_THREADS) scatter_state_kernel(const double* __restrict__ stg, size_t n,
+                                                                    size_t np, int na, double* ub, PT* V, PT* X,
+                                                                    PT* Y) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < np; k += (size_t)gridDim.x * blockDim.x) {
+    if (k < n) ub[k] = stg[k];
     V[k] = (PT)stg[n + k];
     if (na == 4) {
-      X[k] = (PT)stg[2 * n + k];
-      Y[k] = (PT)stg[3 * n + k];
+      X[k] = (PT)stg[n + np + k];
+      Y[k] = (PT)stg[n + 2 * np + k];
     }
   }
 }
 
-// FP32 point arrays -> staged doubles (exact widening) for the copy to the host
+// FP32 point arrays (np values each) -> staged doubles (exact widening) for the copy to
+// the host
 __global__ void __launch_bounds__(RED_THREADS) gather_points_kernel(const float* __restrict__ V,
                                                                     const float* __restrict__ X,
                                                                     const float* __restrict__ Y, size_t n, int na,

@@ -32,3 +32,22 @@ def test_bytes_per_cell_stage():
     arrays54 = (2 + 3 + 3 + 5 + 3) / 5
     assert np.isclose(bench.BYTES_PER_CELL_STAGE_RK54["fp64"], arrays54 * 4 * 8)
     assert np.isclose(bench.BYTES_PER_CELL_STAGE_RK54["fp32_mixed"], arrays54 * (8 + 3 * 4))
+
+
+def test_flops_per_cell_stage_1d_match_oracle_count():
+    import af_inputs as ai
+    import bench
+    import oracle
+    for form in ("dc", "nodc"):
+        spec = ai.evje_karlsen(65536, diffusion_form=form)
+        st = [a.numpy() for a in ai.initial_state(spec)]
+        fc = oracle.flop_count(spec, st, 0.3 * oracle.dt_cfl(spec, st[0]))
+        per_cell = (fc["add"] + fc["mul"] + fc["div"] + fc["exp"]) / spec.cells
+        assert abs(per_cell - bench.FLOPS_PER_CELL_STAGE_1D[form]) < 0.01
+
+
+def test_bytes_per_cell_stage_1d():
+    import bench
+    arrays = (2 + 3 + 3) / 3     # SSP-RK3 state passes per stage; a cell owns ub and one point
+    assert np.isclose(bench.BYTES_PER_CELL_STAGE_1D["fp64"], round(arrays * 2 * 8, 2), atol=0.01)
+    assert np.isclose(bench.BYTES_PER_CELL_STAGE_1D["fp32_mixed"], arrays * (8 + 4))
