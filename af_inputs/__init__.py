@@ -8,7 +8,9 @@ it produces, so the two sides always start from identical inputs.
 Layout of a 2D state (periodic, row-major [ny][nx], i fastest):
   ub[j,i] cell average, V[j,i] at (x_{i+1/2}, y_{j+1/2}), X[j,i] at (x_{i+1/2}, y_j),
   Y[j,i] at (x_i, y_{j+1/2}).  A 1D state is (ub[i], P[i] = u(x_{i+1/2})); on a 1D
-  interval with Dirichlet or outflow ends P has nx+1 entries, P[k] = u(x0 + k dx).
+  interval with Dirichlet or outflow ends P has nx+1 entries, P[k] = u(x0 + k dx). A 2D
+  rectangle with outflow ends has V [ny+1][nx+1] at (x0 + k dx, y0 + l dy), X [ny][nx+1]
+  at (x0 + k dx, y_j) and Y [ny+1][nx] at (x_i, y0 + l dy).
 
 Cell averages use a tensor Gauss-Legendre rule on sub-cells (exact closed forms for
 single Fourier modes); point values are exact evaluations. Disc indicators use the
@@ -36,7 +38,7 @@ class Spec:
           ("ramp", (k, lo, w)) for a = 0 (u <= lo), k (u-lo)^2/(2w) (lo < u < lo+w),
           k (u - lo - w/2) (u >= lo+w).
     blend: "off", "plain" (smoothness indicator) or "external" (per-cell indicator input).
-    bc: "periodic", or in 1D "dirichlet" (end values bc_values) or "outflow".
+    bc: "periodic", "outflow" (1D or 2D), or in 1D "dirichlet" (end values bc_values).
     diffusion_form: "dc" (doubly conservative) or, in 1D, "nodc" (the diffusion
           discretization without double conservation of Appendix A).
     """
@@ -129,13 +131,17 @@ def cell_average_1d(func: Callable, spec: Spec, sub: int = 4, order: int = 5, de
 
 
 def points_2d(func: Callable, spec: Spec, device="cpu"):
-    """Exact point values (V, X, Y) of func(x, y)."""
+    """Exact point values (V, X, Y) of func(x, y) (a rectangle with ends also holds the
+    values on its left and bottom sides)."""
     i = torch.arange(spec.nx, dtype=torch.float64, device=device)
     j = torch.arange(spec.ny, dtype=torch.float64, device=device)
     xc = spec.x0 + (i + 0.5) * spec.dx   # x_i
     xf = spec.x0 + (i + 1.0) * spec.dx   # x_{i+1/2}
     yc = spec.y0 + (j + 0.5) * spec.dy
     yf = spec.y0 + (j + 1.0) * spec.dy
+    if spec.bc != "periodic":
+        xf = spec.x0 + torch.arange(spec.nx + 1, dtype=torch.float64, device=device) * spec.dx
+        yf = spec.y0 + torch.arange(spec.ny + 1, dtype=torch.float64, device=device) * spec.dy
     V = func(xf[None, :], yf[:, None])
     X = func(xf[None, :], yc[:, None])
     Y = func(xc[None, :], yf[:, None])
@@ -273,6 +279,28 @@ def strongly_degenerate_fn(x):
     return torch.where((x + r).abs() < 0.4, one, torch.where((x - r).abs() < 0.4, -one, torch.zeros_like(x)))
 
 
+def buckley_leverett_2d_outflow(n: int = 100, limiter: bool = True) -> Spec:
+    """Example 6.7: f = u^2/(u^2+(1-u)^2), g = f (1 - 5(1-u)^2), a = 0.01 u on
+    [-1.5, 1.5]^2 with outflow ends, u0 = 1 on x^2 + y^2 < 1/2, T = 0.5."""
+    return Spec(dim=2, nx=n, ny=n, x0=-1.5, x1=1.5, y0=-1.5, y1=1.5, flux=("bl", (5.0,)), diff=("const", (0.01,)),
+                umin=0.0, umax=1.0, limiter=limiter, rk=3, T=0.5, name="buckley_leverett2d_outflow", bc="outflow")
+
+
+def strongly_degenerate_2d(n: int = 100, blend: str = "plain") -> Spec:
+    """Example 6.9: f = g = u^2, a = 0.1 (u - 1/4) (u > 1/4), 0.1 (u + 1/4) (u < -1/4), 0
+    otherwise, on [-1.5, 1.5]^2 with outflow ends, discs +-1 of radius 2/5 about
+    (-1/2, -1/2) / (1/2, 1/2), T = 0.5."""
+    return Spec(dim=2, nx=n, ny=n, x0=-1.5, x1=1.5, y0=-1.5, y1=1.5, flux=("burgers", (1.0,)),
+                diff=("pwl", (0.1, -0.25, 0.1, 0.25)), umin=-1.0, umax=1.0, limiter=True, blend=blend, gamma=1.0,
+                rk=3, T=0.5, name="strongly_degenerate2d", bc="outflow")
+
+
+def strongly_degenerate_2d_fn(x, y):
+    r1 = (x + 0.5) ** 2 + (y + 0.5) ** 2
+    r2 = (x - 0.5) ** 2 + (y - 0.5) ** 2
+    return (r1 < 4.0 / 25.0).to(torch.float64) - (r2 < 4.0 / 25.0).to(torch.float64)
+
+
 def config2(n: int = 1024) -> Spec:
     """2D strongly degenerate Burgers: f = u^2/2, kappa = 0.1 [u > 0.5], discs +-1."""
     return Spec(dim=2, nx=n, ny=n, x0=-1.5, x1=1.5, y0=-1.5, y1=1.5, flux=("burgers", (0.5,)),
@@ -307,6 +335,10 @@ def initial_state(spec: Spec, device="cpu", sub: int = 4, order: int = 5):
         return state_2d(lambda x, y: barenblatt(x, y, 1.0), spec, device=device, sub=sub, order=order)
     if spec.name == "buckley_leverett2d":
         return state_2d(bl_disc_fn, spec, device=device, sub=sub, order=order)
+    if spec.name == "buckley_leverett2d_outflow":
+        return state_2d(lambda x, y: bl_disc_fn(x, y, math.sqrt(0.5)), spec, device=device, sub=sub, order=order)
+    if spec.name == "strongly_degenerate2d":
+        return state_2d(strongly_degenerate_2d_fn, spec, device=device, sub=sub, order=order)
     raise KeyError(spec.name)
 
 
@@ -370,8 +402,10 @@ def random_state_2d(spec: Spec, seed: int, lo: float | None = None, hi: float | 
     g = torch.Generator(device="cpu").manual_seed(seed)
     lo = spec.umin if lo is None else lo
     hi = spec.umax if hi is None else hi
-    shape = (spec.ny, spec.nx)
-    return [(lo + (hi - lo) * torch.rand(shape, generator=g, dtype=torch.float64)).to(device) for _ in range(4)]
+    shapes = [(spec.ny, spec.nx)] * 4
+    if spec.bc != "periodic":
+        shapes = [(spec.ny, spec.nx), (spec.ny + 1, spec.nx + 1), (spec.ny, spec.nx + 1), (spec.ny + 1, spec.nx)]
+    return [(lo + (hi - lo) * torch.rand(sh, generator=g, dtype=torch.float64)).to(device) for sh in shapes]
 
 
 def random_state_1d(spec: Spec, seed: int, lo: float | None = None, hi: float | None = None):

@@ -112,9 +112,13 @@ def _prep(spec, state):
     n = 2 if spec.dim == 1 else 4
     assert len(state) == n
     out = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)).copy() for a in state]
-    npts = spec.nx + 1 if spec.dim == 1 and getattr(spec, "bc", "periodic") != "periodic" else None
-    if npts is not None:
-        assert out[0].size == spec.nx and out[1].size == npts, "bounded 1D state: nx averages, nx+1 points"
+    bounded = getattr(spec, "bc", "periodic") != "periodic"
+    if bounded and spec.dim == 1:
+        assert out[0].size == spec.nx and out[1].size == spec.nx + 1, "bounded 1D state: nx averages, nx+1 points"
+    if bounded and spec.dim == 2:
+        nx, ny = spec.nx, spec.ny
+        want = [nx * ny, (nx + 1) * (ny + 1), (nx + 1) * ny, nx * (ny + 1)]
+        assert [a.size for a in out] == want, "2D rectangle with ends: ub, V, X, Y sizes"
     return out
 
 

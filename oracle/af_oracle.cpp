@@ -21,6 +21,9 @@
 // 1D (Section 2): ub[i] and P[i] = u_{i+1/2}; periodic, so u_{1/2} = u_{N+1/2}.
 // 1D with a Dirichlet or outflow boundary: P[j+1] = u_{j+1/2}, j = -1..N-1 (N+1 values
 // from the left to the right end of the interval).
+// 2D rectangle with outflow ends: ub [ny][nx]; V [ny+1][nx+1] (corners, from the
+// bottom-left corner); X [ny][nx+1] (vertical edges, from the left side); Y [ny+1][nx]
+// (horizontal edges, from the bottom side).
 //
 // Readings where the paper is silent (also listed in the design notes):
 //   * 2D factors: directional split 1/(2d)=1/4, limiter factor 3*2d = 12, MPP CFL 1/4
@@ -41,7 +44,9 @@
 //     every ghost DoF holds the boundary value and the boundary point value is held
 //     at it. Outflow: even reflection of the DoFs about the boundary point (a
 //     zero-gradient extension); the boundary point values evolve like interior ones.
-//     The CFL maximum also runs over the two boundary faces.
+//     The CFL maximum also runs over the two boundary faces. A 2D rectangle takes
+//     outflow ends only (the paper's 2D examples with ends use outflow): the periodic
+//     step on the rectangle padded with reflected ghost layers, restricted to it.
 //   * AF method without double conservation (Appendix A, 1D): the cell average
 //     receives the face flux f(u_{i+1/2}) - kappa(u_{i+1/2}) D_c(u)_{i+1/2}; the point
 //     value the compact operator 4/h^2 sum b_mn kappa(z_m) z_n on its 5-point line.
@@ -105,7 +110,7 @@ extern "C" {
 //            4 cubic a = p0*u + p1*u^2 + p2*u^3,
 //            5 ramp a = 0 (u <= p1), p0 (u-p1)^2 / (2 p2) (p1 < u < p1+p2),
 //              p0 (u - p1 - p2/2) (u >= p1+p2)  (kappa rises linearly from 0 to p0).
-// bc: 0 periodic, 1 Dirichlet (bc_left, bc_right), 2 outflow -- 1D only.
+// bc: 0 periodic, 1 Dirichlet (bc_left, bc_right; 1D only), 2 outflow (1D or 2D).
 // nodc: 1 selects the AF method without double conservation of Appendix A (1D only,
 //       blend off).
 typedef struct {
@@ -782,16 +787,33 @@ struct State {
 int ncomp(const ao_problem& p) { return p.dim == 1 ? 2 : 4; }
 size_t ncell(const ao_problem& p) { return (size_t)p.nx * (p.dim == 1 ? 1 : p.ny); }
 // values in component c: a bounded 1D mesh has n+1 point values
-size_t comp_size(const ao_problem& p, int c) { return ncell(p) + (p.dim == 1 && p.bc != 0 && c == 1 ? 1 : 0); }
+size_t comp_size(const ao_problem& p, int c) {
+  if (p.bc == 0 || c == 0) return ncell(p);
+  if (p.dim == 1) return ncell(p) + 1;
+  const size_t nx = p.nx, ny = p.ny;
+  return c == 1 ? (nx + 1) * (ny + 1) : (c == 2 ? (nx + 1) * ny : nx * (ny + 1));
+}
 
 // combinations the oracle implements: boundaries and Appendix A in 1D only, an
 // external indicator only on a periodic mesh, Appendix A without the blend
 bool supported(const ao_problem& p) {
-  if ((p.bc != 0 || p.nodc) && p.dim != 1) return false;
+  if ((p.bc == 1 || p.nodc) && p.dim != 1) return false;
   if (p.bc < 0 || p.bc > 2) return false;
-  if (p.bc != 0 && (p.nx < 4 || p.blend == 2)) return false;
+  if (p.bc != 0 && (p.nx < 4 || (p.dim == 2 && p.ny < 4) || p.blend == 2)) return false;
   if (p.nodc && p.blend) return false;
   return true;
+}
+
+// Even extension of a bounded direction with n cells, periodic with period 2n: the cell
+// index i (cell i spans [x_{i-1/2}, x_{i+1/2}]) and the face index k = j + 1 of the point
+// u_{j+1/2} (k = 0 .. n from end to end) mapped into the stored range.
+inline int reflect_cell(int i, int n) {
+  int r = ((i % (2 * n)) + 2 * n) % (2 * n);
+  return r < n ? r : 2 * n - 1 - r;
+}
+inline int reflect_face(int k, int n) {
+  int r = ((k % (2 * n)) + 2 * n) % (2 * n);
+  return r <= n ? r : 2 * n - r;
 }
 
 // Dirichlet boundary point values stay at the boundary data through every combination
@@ -801,10 +823,50 @@ void hold_dirichlet(const ao_problem& p, std::vector<double>* a) {
   a[1][p.nx] = p.bc_right;
 }
 
+// Forward-Euler step on a 2D rectangle with outflow ends: the periodic step on the
+// rectangle padded with G ghost layers on every side (every DoF kind evenly reflected
+// about the boundary lines), restricted to the rectangle's DoFs. Each output reads
+// inputs at most 3 cells away, so the wrap of the padded periodic mesh never reaches
+// the rectangle's DoFs.
+void fe2d_outflow(const Model& m, const State& in, double tau, State& out) {
+  const ao_problem& p = m.p;
+  const int nx = p.nx, ny = p.ny, G = 5, NX = nx + 2 * G, NY = ny + 2 * G;
+  Model mp = m;
+  mp.p.nx = NX;
+  mp.p.ny = NY;
+  mp.p.bc = 0;
+  const size_t N = (size_t)NX * NY;
+  std::vector<double> ub(N), V(N), X(N), Y(N), ubo(N), Vo(N), Xo(N), Yo(N);
+  for (int J = 0; J < NY; ++J)
+    for (int I = 0; I < NX; ++I) {
+      const int i = I - G, j = J - G;   // cell (i, j); its corner V_{ij}, edges X_{ij}, Y_{ij}
+      const int ci = reflect_cell(i, nx), cj = reflect_cell(j, ny);
+      const int fi = reflect_face(i + 1, nx), fj = reflect_face(j + 1, ny);
+      const size_t g = (size_t)J * NX + I;
+      ub[g] = in.a[0][(size_t)cj * nx + ci];
+      V[g] = in.a[1][(size_t)fj * (nx + 1) + fi];
+      X[g] = in.a[2][(size_t)cj * (nx + 1) + fi];
+      Y[g] = in.a[3][(size_t)fj * nx + ci];
+    }
+  fe2d<double>(mp, ub.data(), V.data(), X.data(), Y.data(), tau, nullptr, ubo.data(), Vo.data(), Xo.data(),
+               Yo.data());
+  auto P = [&](int i, int j) { return (size_t)(j + G) * NX + (i + G); };
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) out.a[0][(size_t)j * nx + i] = ubo[P(i, j)];
+  for (int j = -1; j < ny; ++j)
+    for (int i = -1; i < nx; ++i) out.a[1][(size_t)(j + 1) * (nx + 1) + (i + 1)] = Vo[P(i, j)];
+  for (int j = 0; j < ny; ++j)
+    for (int i = -1; i < nx; ++i) out.a[2][(size_t)j * (nx + 1) + (i + 1)] = Xo[P(i, j)];
+  for (int j = -1; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) out.a[3][(size_t)(j + 1) * nx + i] = Yo[P(i, j)];
+}
+
 void fe(const Model& m, const State& in, double tau, const double* s_ext, State& out) {
   const ao_problem& p = m.p;
   for (int c = 0; c < ncomp(p); ++c) out.a[c].assign(comp_size(p, c), 0.0);
-  if (p.dim == 1)
+  if (p.dim == 2 && p.bc != 0)
+    fe2d_outflow(m, in, tau, out);
+  else if (p.dim == 1)
     fe1d<double>(m, in.a[0].data(), in.a[1].data(), tau, s_ext, out.a[0].data(), out.a[1].data());
   else
     fe2d<double>(m, in.a[0].data(), in.a[1].data(), in.a[2].data(), in.a[3].data(), tau, s_ext,
@@ -950,8 +1012,12 @@ double dt_model(const Model& m, const double* ub, double cfl, double cfl_diff, d
     for (int j = 0; j < p->ny; ++j)
       for (int i = 0; i < p->nx; ++i) {
         double u = ub[(size_t)j * p->nx + i];
-        double a1 = alpha_interval<double>(m, 0, u, ub[(size_t)j * p->nx + wrap(i + 1, p->nx)]);
-        double a2 = alpha_interval<double>(m, 1, u, ub[(size_t)wrap(j + 1, p->ny) * p->nx + i]);
+        // the neighbour across the right / top face (an outflow ghost repeats the cell)
+        double ur = ub[(size_t)j * p->nx + wrap(i + 1, p->nx)], ut = ub[(size_t)wrap(j + 1, p->ny) * p->nx + i];
+        if (p->bc != 0 && i + 1 == p->nx) ur = u;
+        if (p->bc != 0 && j + 1 == p->ny) ut = u;
+        double a1 = alpha_interval<double>(m, 0, u, ur);
+        double a2 = alpha_interval<double>(m, 1, u, ut);
         worst = std::max(worst, a1 / p->dx + km / (p->dx * p->dx));
         worst = std::max(worst, a2 / p->dy + km / (p->dy * p->dy));
       }
@@ -1056,6 +1122,8 @@ void ao_rk54_coefs(double* alpha, double* beta) {
 // Flop count of one FE evaluation on the given state (counting scalar; every
 // +,-,*,/ and exp counts one). out[0..4] = add, mul, div, exp, cmp.
 void ao_flop_count(const ao_problem* p, double* const* in, double tau, const double* s_ext, long long* out) {
+  for (int k = 0; k < 5; ++k) out[k] = 0;
+  if (!supported(*p) || (p->dim == 2 && p->bc != 0)) return;   // periodic 2D and all 1D forms
   Model m = make_model(p);
   g_flops = FlopCounter();
   size_t n = ncell(*p);
