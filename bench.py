@@ -366,6 +366,8 @@ def forms(args, headline_value, peaks):
         res.update(_form_bounded1d(args, stream, peaks))
     if "ex65" in sel:
         res.update(_form_ex65())
+    if "rect2d" in sel:
+        res.update(_form_rect2d(args, stream, flush, peaks))
     return res
 
 
@@ -449,6 +451,51 @@ def _form_ex65():
             torch.cuda.synchronize()
             small[form] = {"steps": n, "seconds": round(time.perf_counter() - t0, 3)}
     return {"evje_karlsen_200_to_T1": small}
+
+
+def _form_rect2d(args, stream, flush, peaks):
+    """2D rectangles with outflow ends: Examples 6.7 and 6.9 as printed (100^2 to
+    T = 0.5 through af_run: time to solution), and Example 6.9's problem on 2048^2 with
+    outflow ends against the same mesh periodic (the cost of the ends), FP64 and
+    FP32-mixed."""
+    import dataclasses
+    import statistics as st_
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import Solver
+    res = {}
+    small = {}
+    for name, spec in (("ex67_bl", ai.buckley_leverett_2d_outflow(100)), ("ex69_blend", ai.strongly_degenerate_2d(100))):
+        st = [a.numpy() for a in ai.initial_state(spec)]
+        with Solver(spec, precision="fp64") as s:
+            s.set_state(st)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n = s.run(spec.T)
+            torch.cuda.synchronize()
+            small[name] = {"steps": n, "seconds": round(time.perf_counter() - t0, 3)}
+    res["rect2d_examples_100_to_T"] = small
+    n = 2048
+    big = dataclasses.replace(ai.strongly_degenerate_2d(n), blend="off")
+    host_rect = [a.cpu().numpy() for a in ai.initial_state(big, device="cuda", sub=2, order=3)]
+    per = dataclasses.replace(big, bc="periodic")
+    host_per = [host_rect[0], host_rect[1][1:, 1:].copy(), host_rect[2][:, 1:].copy(), host_rect[3][1:, :].copy()]
+    out = {"cells": n * n}
+    for prec in ("fp64", "fp32_mixed"):
+        e = {}
+        for tag, spec, st in (("outflow", big, host_rect), ("periodic", per, host_per)):
+            s = Solver(spec, precision=prec)
+            s.set_stream(stream)
+            s.set_state(st)
+            torch.cuda.synchronize()
+            step_ms, stage_ms = _time_steps(_solver_stepper(s, stream), s.num_stages, args.form_steps, 3, stream, flush)
+            e[tag] = {"value": round(spec.cells * s.num_stages * args.form_steps / (sum(step_ms) / 1e3), 1),
+                      "stage_ms_avg": round(st_.mean(stage_ms), 5)}
+            s.close()
+        e["outflow_vs_periodic"] = round(e["outflow"]["value"] / e["periodic"]["value"], 3)
+        out[prec] = e
+    res["rect2d_strongly_degenerate_2048"] = out
+    return res
 
 
 def _form_bounded1d(args, stream, peaks):
@@ -680,11 +727,12 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/batched/learned forms")
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--n1d", type=int, default=1 << 24, help="cells of the bounded1d form")
-    ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl,bounded1d,ex65",
+    ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl,bounded1d,ex65,rect2d",
                     help="comma list of forms to run: fp32 (Burgers 1024^2), rk54 (Burgers 1024^2 with "
                          "SSP-RK(5,4)), pme (4096^2), batch (256), bl (4096^2), bounded1d (Example 6.5's "
                          "problem on 2^24 cells, with and without double conservation), ex65 (Example 6.5 "
-                         "as printed: 200 cells to T = 1)")
+                         "as printed: 200 cells to T = 1), rect2d (Examples 6.7 / 6.9 at 100^2 to T and "
+                         "Example 6.9's problem on 2048^2 with outflow ends vs periodic)")
     args = ap.parse_args()
     if args.impl == "reference":
         res = run_reference(args)

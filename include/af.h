@@ -5,8 +5,8 @@
  *
  *      u_t + div f(u) = Laplace a(u),   a(u) = int kappa,  kappa >= 0      (Section 1)
  *
- * on periodic Cartesian meshes in 1D and 2D, and on 1D intervals with Dirichlet or
- * outflow ends (arXiv 2510.11527).
+ * on periodic Cartesian meshes in 1D and 2D, on 1D intervals with Dirichlet or outflow
+ * ends and on 2D rectangles with outflow ends (arXiv 2510.11527).
  *
  * Degrees of freedom (Section 2 for 1D, Section 4 / Fig. 2 for 2D). All arrays are
  * row-major [ny][nx] with i fastest; a periodic mesh stores nx*ny of each kind:
@@ -17,7 +17,9 @@
  * In 1D only ub[i] and P[i] = u(x_{i+1/2}) exist; they are passed in the ub and V
  * slots, and X, Y are ignored (may be NULL). A 1D interval with Dirichlet or outflow
  * ends (grid->bc) has nx+1 point values, P[k] = u(x0 + k dx), k = 0..nx, from the left
- * to the right end; ub keeps nx values.
+ * to the right end; ub keeps nx values. A 2D rectangle with outflow ends has
+ * V [ny+1][nx+1] at (x0 + k dx, y0 + l dy), X [ny][nx+1] at (x0 + k dx, y_j) and
+ * Y [ny+1][nx] at (x_i, y0 + l dy); ub keeps [ny][nx].
  *
  * Conventions
  *   - Every call returns an af_status. On error the context is left unchanged and
@@ -74,7 +76,8 @@ enum {
  * DIRICHLET: every ghost value is the boundary value (bc_left / bc_right) and the two
  * end point values are held at it. OUTFLOW: the DoFs are reflected evenly about the
  * end point (zero gradient); the end point values evolve like interior ones. The CFL
- * maximum includes the two end faces. 2D meshes are periodic. */
+ * maximum includes the two end faces. A 2D rectangle takes OUTFLOW on all four sides
+ * (each DoF kind reflected about the side lines) or is periodic. */
 enum { AF_BC_PERIODIC = 0, AF_BC_DIRICHLET = 1, AF_BC_OUTFLOW = 2 };
 
 /* Discretisation of the diffusion term. DC: the doubly conservative form (Section
@@ -93,7 +96,7 @@ typedef struct {
   int dim;
   int nx, ny;
   double x0, x1, y0, y1;
-  int bc;                 /* AF_BC_*; anything but AF_BC_PERIODIC needs dim = 1, nx >= 4     */
+  int bc;                 /* AF_BC_*: DIRICHLET needs dim = 1; OUTFLOW dim 1 or 2; nx, ny >= 4 */
   double bc_left, bc_right; /* Dirichlet values at x0 and x1                               */
 } af_grid;
 typedef struct { int kind; double p[4]; } af_flux;
@@ -114,9 +117,10 @@ typedef struct {
 /* Create a solver for one mesh. Allocates all device buffers (4 state copies for
  * SSP-RK(5,4), 3 for SSP-RK3). bounds->from_initial_data = 1 defers umin/umax to the
  * min/max of the first af_set_state. Returns AF_E_ARG for nx,ny < 1, dim not 1/2,
- * unknown kinds, umin >= umax, a bounded interval with nx < 4; AF_E_UNSUPPORTED for
- * non-periodic ends or AF_FORM_NODC in 2D, AF_FORM_NODC with a blend, and the external
- * indicator on a bounded interval; AF_E_OOM if allocation fails. */
+ * unknown kinds, umin >= umax, non-periodic ends with nx (or, in 2D, ny) < 4;
+ * AF_E_UNSUPPORTED for Dirichlet ends or AF_FORM_NODC in 2D, AF_FORM_NODC with a
+ * blend, and the external indicator with non-periodic ends; AF_E_OOM if allocation
+ * fails. */
 af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* diff,
                     const af_bounds_t* bounds, const af_opts* opts, af_ctx** out);
 af_status af_destroy(af_ctx* ctx);
@@ -127,7 +131,8 @@ const char* af_last_error(const af_ctx* ctx);
 af_status af_set_stream(af_ctx* ctx, void* stream);
 
 /* Copy a host state in (doubles, caller-owned, nx*ny values each, row-major; X and Y
- * ignored in 1D; V holds nx+1 values on a bounded 1D interval). The arrays are copied to the device and checked there; FP32-mixed
+ * ignored in 1D; V holds nx+1 values on a bounded 1D interval; a 2D rectangle with
+ * ends takes the V, X, Y shapes given at the top of this file). The arrays are copied to the device and checked there; FP32-mixed
  * contexts then round the point values to nearest float. AF_E_STATE if any value is NaN
  * or, with the limiter on, outside [umin, umax]; the current state is then unchanged.
  * Page-locked host memory copies fastest. Returns after the host arrays have been read
@@ -140,7 +145,11 @@ af_status af_get_state(af_ctx* ctx, double* ub, double* V, double* X, double* Y)
 
 /* Borrowed device pointers of the current state (ub, V, X, Y). dtype[0] is 8 (ub is
  * always FP64); dtype[1] is 8 or 4 for the point arrays. Valid until the next call that
- * steps or destroys the context (a bounded 1D interval: nx+1 point values). */
+ * steps or destroys the context (a bounded 1D interval: nx+1 point values; a 2D
+ * rectangle with ends: its padded device layout, (nx+1) x (ny+1) entries per array,
+ * entry (I, J) holding the average of cell (I-1, J-1) and the corner / edge values at
+ * that cell's top-right; the averages in row and column 0, X in row 0 and Y in column 0
+ * are not DoFs). */
 af_status af_device_ptrs(af_ctx* ctx, void* ptrs[4], int dtype[2]);
 
 /* Per-cell external smoothness indicator s (nx*ny doubles, host) used when

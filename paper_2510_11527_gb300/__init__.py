@@ -21,7 +21,8 @@ class Solver:
     spec: any object with the attributes dim, nx, ny, x0, x1, y0, y1, flux=(kind, params),
     diff=(kind, params), umin, umax, limiter, blend, gamma and optionally bc ("periodic",
     "dirichlet", "outflow"), bc_values and diffusion_form ("dc", "nodc") (e.g.
-    af_inputs.Spec). A 1D interval with Dirichlet or outflow ends has nx + 1 point values.
+    af_inputs.Spec). A 1D interval with Dirichlet or outflow ends has nx + 1 point values;
+    a 2D rectangle with outflow ends has V [ny+1][nx+1], X [ny][nx+1], Y [ny+1][nx].
     """
 
     def __init__(self, spec, precision="fp64", rk=3, cfl=0.0, cfl_diff=0.0, bounds_from_data=False):
@@ -31,6 +32,10 @@ class Solver:
         bc = getattr(spec, "bc", "periodic")
         gl, gr = getattr(spec, "bc_values", (0.0, 0.0))
         self.npts = self.n + (1 if spec.dim == 1 and bc != "periodic" else 0)
+        nx, ny = spec.nx, (spec.ny if spec.dim == 2 else 1)
+        self.rect = spec.dim == 2 and bc != "periodic"
+        self.shapes = ([(ny, nx), (ny + 1, nx + 1), (ny, nx + 1), (ny + 1, nx)] if self.rect
+                       else [(ny, nx)] * 4 if spec.dim == 2 else [(nx,), (self.npts,)])
         g = af_grid(spec.dim, spec.nx, spec.ny if spec.dim == 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1,
                     capi.BC[bc], float(gl), float(gr))
         f = af_flux()
@@ -70,7 +75,7 @@ class Solver:
         if self.dim == 1:
             capi.af_set_state(self.ctx, self.n, arrs[0], arrs[1], npts=self.npts)
         else:
-            capi.af_set_state(self.ctx, self.n, *arrs)
+            capi.af_set_state(self.ctx, self.n, *arrs, sizes=[int(np.prod(s)) for s in self.shapes])
 
     def get_state(self, out=None):
         """Host copy of (ub, V, X, Y); `out` may supply the destination float64 arrays
@@ -78,17 +83,20 @@ class Solver:
         if self.dim == 1:
             flat = None if out is None else [np.asarray(a).reshape(-1) for a in out]
             return capi.af_get_state(self.ctx, self.n, 1, flat, npts=self.npts)
-        shape = (self.spec.ny, self.spec.nx)
         flat = None if out is None else [np.asarray(a).reshape(-1) for a in out]
-        res = capi.af_get_state(self.ctx, self.n, self.dim, flat)
-        return [a.reshape(shape) for a in res]
+        res = capi.af_get_state(self.ctx, self.n, self.dim, flat, sizes=[int(np.prod(s)) for s in self.shapes])
+        return [a.reshape(sh) for a, sh in zip(res, self.shapes)]
 
     def device_tensors(self):
-        """Zero-copy torch views of the current device state (ub, V, X, Y)."""
+        """Zero-copy torch views of the current device state (ub, V, X, Y); a 2D rectangle
+        with ends gives its padded device layout, [ny+1][nx+1] per array (entry (I, J):
+        average of cell (I-1, J-1), corner / edge values at its top-right)."""
         import torch
 
         ptrs, (d0, d1) = capi.af_device_ptrs(self.ctx)
         shape = (self.spec.ny, self.spec.nx) if self.dim == 2 else (self.spec.nx,)
+        if self.rect:
+            shape = (self.spec.ny + 1, self.spec.nx + 1)
         out = []
         for k, p in enumerate(ptrs):
             if p is None:

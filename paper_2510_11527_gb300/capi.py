@@ -343,20 +343,23 @@ def af_set_stream(ctx, stream_handle):
     _check(ctx, lib().af_set_stream(ctx, _V(stream_handle)))
 
 
-def af_set_state(ctx, n, ub, V, X=None, Y=None, npts=None):
-    """npts: values per point array (default n; n + 1 on a bounded 1D interval)."""
+def af_set_state(ctx, n, ub, V, X=None, Y=None, npts=None, sizes=None):
+    """npts: values per point array (default n; n + 1 on a bounded 1D interval); sizes:
+    the values of ub, V, X, Y one by one (a 2D rectangle with ends)."""
     m = n if npts is None else npts
-    arrs = [_host(ub, n), _host(V, m), None if X is None else _host(X, m), None if Y is None else _host(Y, m)]
+    sz = sizes if sizes is not None else [n, m, m, m]
+    arrs = [_host(ub, sz[0]), _host(V, sz[1]), None if X is None else _host(X, sz[2]),
+            None if Y is None else _host(Y, sz[3])]
     _check(ctx, lib().af_set_state(ctx, *[_dp(a) for a in arrs]))
 
 
-def af_get_state(ctx, n, dim, out=None, npts=None):
+def af_get_state(ctx, n, dim, out=None, npts=None, sizes=None):
     """Copy the state to host float64 arrays: `out` (C-contiguous float64 arrays, e.g.
     views of pinned memory) or new arrays; n averages, npts (default n) point values
-    per point array."""
+    per point array, or the values of each array in `sizes`."""
     k = 4 if dim == 2 else 2
     m = n if npts is None else npts
-    sizes = [n] + [m] * (k - 1)
+    sizes = list(sizes[:k]) if sizes is not None else [n] + [m] * (k - 1)
     if out is None:
         out = [np.empty(z) for z in sizes]
     else:

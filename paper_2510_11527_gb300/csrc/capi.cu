@@ -51,12 +51,28 @@ namespace {
 
 size_t pt_size(const af_ctx* c) { return c->prec == AF_PREC_FP64 ? sizeof(double) : sizeof(float); }
 
+// a 2D rectangle with ends (padded device layout)
+bool is_rect(const af_ctx* c) { return c->dim == 2 && c->grid.bc != AF_BC_PERIODIC; }
+
+// values per host array of af_set_state / af_get_state: ub, V, X, Y
+void host_sizes(const af_ctx* c, size_t sz[4]) {
+  const size_t nx = c->nx, ny = c->ny;
+  sz[0] = c->n;
+  if (is_rect(c)) {
+    sz[1] = (nx + 1) * (ny + 1);
+    sz[2] = (nx + 1) * ny;
+    sz[3] = nx * (ny + 1);
+  } else {
+    sz[1] = sz[2] = sz[3] = c->np;
+  }
+}
+
 template <class PT>
 StageArgs2D<PT> base_args(af_ctx* c, int in) {
   StageArgs2D<PT> a;
   std::memset(&a, 0, sizeof(a));
-  a.nx = c->nx;
-  a.ny = c->ny;
+  a.nx = c->pnx;   // the stage kernels tile the padded layout of a 2D rectangle with ends
+  a.ny = c->pny;
   a.inv_h1 = c->inv_h1;
   a.inv_h2 = c->inv_h2;
   a.ub = c->ub[in];
@@ -113,6 +129,7 @@ cudaError_t launch<double>(af_ctx* c, const StageArgs2D<double>& a) {
   cudaError_t e = run_indicator(c, a);
   if (e != cudaSuccess) return e;
   if (c->dim == 1) return af::launch_stage1d_f64(c->flux.kind, c->m, a, c->stream);
+  if (is_rect(c)) return af::launch_stage2d_rect_f64(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
   return af::launch_stage2d_f64(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
 }
 template <>
@@ -120,6 +137,7 @@ cudaError_t launch<float>(af_ctx* c, const StageArgs2D<float>& a) {
   cudaError_t e = run_indicator(c, a);
   if (e != cudaSuccess) return e;
   if (c->dim == 1) return af::launch_stage1d_f32(c->flux.kind, c->m, a, c->stream);
+  if (is_rect(c)) return af::launch_stage2d_rect_f32(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
   return af::launch_stage2d_f32(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
 }
 
@@ -193,7 +211,7 @@ af_status stage_any(af_ctx* c, int k) {
 template <int FLUX>
 cudaError_t launch_rate(af_ctx* c) {
   const int blocks = 152 * 4;
-  af::dt_rate_kernel<FLUX><<<blocks, af::RED_THREADS, 0, c->stream>>>(c->m, c->dim, c->nx, c->ny, c->inv_h1,
+  af::dt_rate_kernel<FLUX><<<blocks, af::RED_THREADS, 0, c->stream>>>(c->m, c->dim, c->pnx, c->pny, c->inv_h1,
                                                                        c->inv_h2, c->kmax, c->ub[0], c->rate_bits,
                                                                        c->grid.bc, c->grid.bc_left, c->grid.bc_right);
   return cudaGetLastError();
@@ -223,10 +241,17 @@ af_status read_scalar(af_ctx* c, const double* dev, double* out) {
   return AF_OK;
 }
 
+// reduction of x[0, count) (op 0 sum, 1 min, 2 max); with w > 0 only the entries whose
+// column (of rows of width w) is >= ilo and row >= jlo
 template <class S>
-af_status reduce_array(af_ctx* c, const S* x, size_t count, int op, double init, double* out_dev, int accumulate) {
+af_status reduce_array(af_ctx* c, const S* x, size_t count, int op, double init, double* out_dev, int accumulate,
+                       int w = 0, int ilo = 0, int jlo = 0) {
   const int blocks = (int)std::min<size_t>(af::RED_MAX_BLOCKS, (count + af::RED_THREADS - 1) / af::RED_THREADS);
-  af::partial_kernel<S><<<blocks, af::RED_THREADS, 0, c->stream>>>(x, count, op, init, c->partial);
+  if (w > 0)
+    af::partial_masked_kernel<S><<<blocks, af::RED_THREADS, 0, c->stream>>>(x, count, w, ilo, jlo, op, init,
+                                                                            c->partial);
+  else
+    af::partial_kernel<S><<<blocks, af::RED_THREADS, 0, c->stream>>>(x, count, op, init, c->partial);
   CK(c, cudaGetLastError());
   af::finalize_kernel<<<1, af::RED_THREADS, 0, c->stream>>>(c->partial, blocks, op, out_dev, accumulate);
   CK(c, cudaGetLastError());
@@ -258,8 +283,8 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   if (diff->kind == AF_DIFF_RAMP && !(diff->p[2] > 0.0)) return AF_E_ARG;
   if (grid->bc < AF_BC_PERIODIC || grid->bc > AF_BC_OUTFLOW) return AF_E_ARG;
   if (opts->diffusion_form != AF_FORM_DC && opts->diffusion_form != AF_FORM_NODC) return AF_E_ARG;
-  if (grid->bc != AF_BC_PERIODIC && grid->dim != 1) return AF_E_UNSUPPORTED;
-  if (grid->bc != AF_BC_PERIODIC && grid->nx < 4) return AF_E_ARG;
+  if (grid->bc == AF_BC_DIRICHLET && grid->dim != 1) return AF_E_UNSUPPORTED;
+  if (grid->bc != AF_BC_PERIODIC && (grid->nx < 4 || (grid->dim == 2 && grid->ny < 4))) return AF_E_ARG;
   if (opts->diffusion_form == AF_FORM_NODC && (grid->dim != 1 || opts->blend != AF_BLEND_OFF)) return AF_E_UNSUPPORTED;
   if (grid->bc != AF_BC_PERIODIC && opts->blend == AF_BLEND_EXTERNAL) return AF_E_UNSUPPORTED;
   if (!bounds->from_initial_data && !(bounds->umax > bounds->umin)) return AF_E_ARG;
@@ -279,6 +304,10 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->ny = grid->dim == 2 ? grid->ny : 1;
   c->n = (size_t)c->nx * c->ny;
   c->np = c->n + (grid->dim == 1 && grid->bc != AF_BC_PERIODIC ? 1 : 0);
+  const bool rect = grid->dim == 2 && grid->bc != AF_BC_PERIODIC;
+  c->pnx = c->nx + (rect ? 1 : 0);
+  c->pny = c->ny + (rect ? 1 : 0);
+  c->pn = (size_t)c->pnx * c->pny;
   c->prec = opts->precision;
   c->nbuf = opts->rk == AF_RK_SSP54 ? 4 : 3;
   c->dx = (grid->x1 - grid->x0) / grid->nx;
@@ -302,7 +331,8 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   // one device allocation: nbuf states + scratch
   const size_t ps = pt_size(c);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
-  const size_t per_state = al(c->n * 8) + 3 * al(c->np * ps);
+  const size_t ulen = rect ? c->pn : c->n, plen = rect ? c->pn : c->np;
+  const size_t per_state = al(ulen * 8) + 3 * al(plen * ps);
   const size_t scratch = al(8) * 2 + al(8 * 8) + al(8 * af::RED_MAX_BLOCKS) + al(8) + al(sizeof(DevStats)) + al(c->n * 8);
   const size_t total = per_state * c->nbuf + scratch;
   if (cudaMalloc(&c->block, total) != cudaSuccess) {
@@ -312,10 +342,10 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   }
   unsigned char* p = c->block;
   for (int b = 0; b < c->nbuf; ++b) {
-    c->ub[b] = (double*)p; p += al(c->n * 8);
-    c->pv[b] = p; p += al(c->np * ps);
-    c->px[b] = p; p += al(c->np * ps);
-    c->py[b] = p; p += al(c->np * ps);
+    c->ub[b] = (double*)p; p += al(ulen * 8);
+    c->pv[b] = p; p += al(plen * ps);
+    c->px[b] = p; p += al(plen * ps);
+    c->py[b] = p; p += al(plen * ps);
   }
   c->dt_dev = (double*)p; p += al(8);
   c->t_dev = (double*)p; p += al(8);
@@ -358,13 +388,15 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
   const int na = c->dim == 2 ? 4 : 2;
   const double* src[4] = {ub, V, X, Y};
-  const size_t n = c->n, np = c->np, total = n + (na - 1) * np;
-  // staging: the RK temporaries (buffers 1..nbuf-1, contiguous, >= 8 n + 12 np bytes
-  // >= 8 total), ub then the point arrays back to back
+  size_t sz[4], off[5] = {0, 0, 0, 0, 0};
+  host_sizes(c, sz);
+  for (int a = 0; a < na; ++a) off[a + 1] = off[a] + sz[a];
+  const size_t total = off[na];
+  // staging: the RK temporaries (buffers 1..nbuf-1, contiguous, >= 8 total bytes), the
+  // host arrays back to back
   double* stg = c->ub[1];
-  CK(c, cudaMemcpyAsync(stg, ub, n * 8, cudaMemcpyHostToDevice, c->stream));
-  for (int a = 1; a < na; ++a)
-    CK(c, cudaMemcpyAsync(stg + n + (a - 1) * np, src[a], np * 8, cudaMemcpyHostToDevice, c->stream));
+  for (int a = 0; a < na; ++a)
+    CK(c, cudaMemcpyAsync(stg + off[a], src[a], sz[a] * 8, cudaMemcpyHostToDevice, c->stream));
   const int nb = (int)std::min<size_t>(af::STATE_IO_BLOCKS, (total + af::RED_THREADS - 1) / af::RED_THREADS);
   af::validate_partial_kernel<<<nb, af::RED_THREADS, 0, c->stream>>>(stg, total, (unsigned long long*)c->partial);
   CK(c, cudaGetLastError());
@@ -385,13 +417,24 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
   } else if (c->opts.limiter && (lo < c->m.umin || hi > c->m.umax)) {
     FAIL(c, AF_E_STATE, "input outside [umin, umax]: [%g, %g]", lo, hi);
   }
-  const int grid = (int)std::min<size_t>(152 * 8, (np + af::RED_THREADS - 1) / af::RED_THREADS);
-  if (c->prec == AF_PREC_FP64)
-    af::scatter_state_kernel<double><<<grid, af::RED_THREADS, 0, c->stream>>>(
-        stg, n, np, na, c->ub[0], (double*)c->pv[0], (double*)c->px[0], (double*)c->py[0]);
-  else
-    af::scatter_state_kernel<float><<<grid, af::RED_THREADS, 0, c->stream>>>(
-        stg, n, np, na, c->ub[0], (float*)c->pv[0], (float*)c->px[0], (float*)c->py[0]);
+  if (is_rect(c)) {
+    const int grid = (int)std::min<size_t>(152 * 8, (c->pn + af::RED_THREADS - 1) / af::RED_THREADS);
+    if (c->prec == AF_PREC_FP64)
+      af::scatter_rect_kernel<double><<<grid, af::RED_THREADS, 0, c->stream>>>(
+          stg, c->nx, c->ny, c->ub[0], (double*)c->pv[0], (double*)c->px[0], (double*)c->py[0]);
+    else
+      af::scatter_rect_kernel<float><<<grid, af::RED_THREADS, 0, c->stream>>>(
+          stg, c->nx, c->ny, c->ub[0], (float*)c->pv[0], (float*)c->px[0], (float*)c->py[0]);
+  } else {
+    const size_t n = c->n, np = c->np;
+    const int grid = (int)std::min<size_t>(152 * 8, (np + af::RED_THREADS - 1) / af::RED_THREADS);
+    if (c->prec == AF_PREC_FP64)
+      af::scatter_state_kernel<double><<<grid, af::RED_THREADS, 0, c->stream>>>(
+          stg, n, np, na, c->ub[0], (double*)c->pv[0], (double*)c->px[0], (double*)c->py[0]);
+    else
+      af::scatter_state_kernel<float><<<grid, af::RED_THREADS, 0, c->stream>>>(
+          stg, n, np, na, c->ub[0], (float*)c->pv[0], (float*)c->px[0], (float*)c->py[0]);
+  }
   CK(c, cudaGetLastError());
   return AF_OK;
 }
@@ -399,8 +442,27 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
 af_status af_get_state(af_ctx* c, double* ub, double* V, double* X, double* Y) {
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
   const int na = c->dim == 2 ? 4 : 2;
-  const size_t n = c->n, np = c->np;
   double* dst[4] = {ub, V, X, Y};
+  if (is_rect(c)) {
+    // padded device layout -> the caller's layout, as doubles in the staging area
+    size_t sz[4], off[5] = {0, 0, 0, 0, 0};
+    host_sizes(c, sz);
+    for (int a = 0; a < na; ++a) off[a + 1] = off[a] + sz[a];
+    double* stg = c->ub[1];
+    const int grid = (int)std::min<size_t>(152 * 8, (c->pn + af::RED_THREADS - 1) / af::RED_THREADS);
+    if (c->prec == AF_PREC_FP64)
+      af::gather_rect_kernel<double><<<grid, af::RED_THREADS, 0, c->stream>>>(
+          c->ub[0], (const double*)c->pv[0], (const double*)c->px[0], (const double*)c->py[0], c->nx, c->ny, stg);
+    else
+      af::gather_rect_kernel<float><<<grid, af::RED_THREADS, 0, c->stream>>>(
+          c->ub[0], (const float*)c->pv[0], (const float*)c->px[0], (const float*)c->py[0], c->nx, c->ny, stg);
+    CK(c, cudaGetLastError());
+    for (int a = 0; a < na; ++a)
+      CK(c, cudaMemcpyAsync(dst[a], stg + off[a], sz[a] * 8, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return AF_OK;
+  }
+  const size_t n = c->n, np = c->np;
   CK(c, cudaMemcpyAsync(ub, c->ub[0], n * 8, cudaMemcpyDeviceToHost, c->stream));
   if (c->prec == AF_PREC_FP64) {
     void* src[3] = {c->pv[0], c->px[0], c->py[0]};
@@ -457,10 +519,11 @@ af_status af_forward_euler(af_ctx* c, double tau) {
     set_out<float>(c, a, 0, 1, 0.0, -1, 1.0, 1.0, 0);
     CK(c, launch<float>(c, a));
   }
-  std::swap(c->ub[0], c->ub[1]);
-  std::swap(c->pv[0], c->pv[1]);
-  std::swap(c->px[0], c->px[1]);
-  std::swap(c->py[0], c->py[1]);
+  // the result goes back into buffer 0 (one copy of the state's span), so the state
+  // always lives there and buffers 1.. stay the contiguous staging area of
+  // af_set_state / af_get_state
+  const size_t span = (size_t)((unsigned char*)c->ub[1] - (unsigned char*)c->ub[0]);
+  CK(c, cudaMemcpyAsync(c->ub[0], c->ub[1], span, cudaMemcpyDeviceToDevice, c->stream));
   return AF_OK;
 }
 
@@ -543,7 +606,8 @@ af_status af_time(af_ctx* c, double* t) {
 
 af_status af_mass(af_ctx* c, double* mass) {
   if (!c || !mass) return AF_E_ARG;
-  af_status s = reduce_array<double>(c, c->ub[0], c->n, 0, 0.0, c->red + 1, 0);
+  af_status s = is_rect(c) ? reduce_array<double>(c, c->ub[0], c->pn, 0, 0.0, c->red + 1, 0, c->pnx, 1, 1)
+                           : reduce_array<double>(c, c->ub[0], c->n, 0, 0.0, c->red + 1, 0);
   if (s != AF_OK) return s;
   double v;
   s = read_scalar(c, c->red + 1, &v);
@@ -560,10 +624,14 @@ af_status af_bounds(af_ctx* c, double* umin, double* umax) {
     for (int a = 0; a < na; ++a) {
       af_status s;
       const double init = op == 1 ? INFINITY : -INFINITY;
+      // DoFs of the padded rectangle: ub from (1, 1), V everywhere, X from row 1, Y from column 1
+      const bool r = is_rect(c);
+      const int w = r ? c->pnx : 0, ilo = r && (a == 0 || a == 3) ? 1 : 0, jlo = r && (a == 0 || a == 2) ? 1 : 0;
+      const size_t cnt = r ? c->pn : (a == 0 ? c->n : c->np);
       if (a == 0 || c->prec == AF_PREC_FP64)
-        s = reduce_array<double>(c, (const double*)arrs[a], a == 0 ? c->n : c->np, op, init, c->red + 1 + op, a > 0);
+        s = reduce_array<double>(c, (const double*)arrs[a], cnt, op, init, c->red + 1 + op, a > 0, w, ilo, jlo);
       else
-        s = reduce_array<float>(c, (const float*)arrs[a], c->np, op, init, c->red + 1 + op, a > 0);
+        s = reduce_array<float>(c, (const float*)arrs[a], cnt, op, init, c->red + 1 + op, a > 0, w, ilo, jlo);
       if (s != AF_OK) return s;
     }
   }

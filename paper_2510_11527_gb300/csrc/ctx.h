@@ -16,6 +16,13 @@ struct af_ctx {
   int dim = 2, nx = 1, ny = 1, prec = AF_PREC_FP64, nbuf = 3;
   size_t n = 0;
   size_t np = 0;                      // point values per point array (n, or n + 1 on a bounded 1D interval)
+  // device layout: a 2D rectangle with outflow ends is stored padded, (nx + 1) x (ny + 1)
+  // entries per array, padded cell (I, J) holding the average of cell (I - 1, J - 1) and
+  // the corner V, vertical-edge X and horizontal-edge Y values at its top-right; row 0
+  // and column 0 hold the bottom / left side points (the averages there, X in row 0
+  // and Y in column 0 are not DoFs). Otherwise pnx = nx, pny = ny.
+  int pnx = 1, pny = 1;
+  size_t pn = 0;                      // pnx * pny entries per device array (1D: max(n, np))
   double dx = 1, dy = 1, inv_h1 = 1, inv_h2 = 1, kmax = 0, cfl = 0.165, cfl_diff = 0, tol = 0;
   bool bounds_pending = false;
   unsigned char* block = nullptr;     // one allocation for every device buffer

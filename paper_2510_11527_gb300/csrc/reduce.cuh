@@ -21,7 +21,9 @@ constexpr int RED_MAX_BLOCKS = 1024;   // partial-result slots per reduction
 // extrema met (bit 8 l + k) in rate_bits[1]; dt_finalize_kernel adds their terms.
 // A bounded 1D interval (bc != AF_BC_PERIODIC) has no wrap-around face; its two end
 // faces join the end cells to their ghosts: the Dirichlet values gl / gr are then face
-// end points too, while an outflow ghost repeats the end cell (nothing new).
+// end points too, while an outflow ghost repeats the end cell (nothing new). A 2D
+// rectangle with outflow ends arrives in its padded layout (nx, ny = padded sizes): row
+// and column 0 are skipped, and its last column / row has no face beyond.
 template <int FLUX>
 __device__ __forceinline__ unsigned crit_flags(const DevModel& m, int dir, double a, double b) {
   unsigned f = 0u;
@@ -43,20 +45,25 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
   double best = 0.0;
   unsigned flags = 0u;
   const double kd1 = kmax * inv_h1 * inv_h1, kd2 = kmax * inv_h2 * inv_h2;
+  const bool rect = dim == 2 && bc != AF_BC_PERIODIC;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(k % nx), j = (int)(k / nx);
+    if (rect && (i == 0 || j == 0)) continue;
     const double u = ub[k];
     double a1, a2;
     if constexpr (FLUX == FLUX_BL) {
       const BLVals<double> r = bl_eval<double>(m, u);
       a1 = r.d[0];
       a2 = r.d[1];
-      const int i = (int)(k % nx), j = (int)(k / nx);
-      const double un = (dim == 1 && bc != AF_BC_PERIODIC && i + 1 == nx)
-                            ? (bc == AF_BC_DIRICHLET ? gr : u)
-                            : ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)];
+      double un = ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)];
+      if (dim == 1 && bc != AF_BC_PERIODIC && i + 1 == nx) un = bc == AF_BC_DIRICHLET ? gr : u;
+      if (rect && i + 1 == nx) un = u;
       flags |= crit_flags<FLUX>(m, 0, u, un);
       if (dim == 1 && bc == AF_BC_DIRICHLET && k == 0) flags |= crit_flags<FLUX>(m, 0, gl, u);
-      if (dim == 2) flags |= crit_flags<FLUX>(m, 1, u, ub[(size_t)(j + 1 == ny ? 0 : j + 1) * nx + i]) << 8;
+      if (dim == 2) {
+        const double ut = (rect && j + 1 == ny) ? u : ub[(size_t)(j + 1 == ny ? 0 : j + 1) * nx + i];
+        flags |= crit_flags<FLUX>(m, 1, u, ut) << 8;
+      }
     } else {
       a1 = alpha_interval<FLUX, double>(m, 0, u, u);
       a2 = alpha_interval<FLUX, double>(m, 1, u, u);
@@ -147,6 +154,27 @@ __global__ void __launch_bounds__(RED_THREADS) partial_kernel(const S* __restric
   const size_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
   double acc = init;
   for (size_t k = beg + threadIdx.x; k < end; k += RED_THREADS) acc = red_op(op, acc, (double)x[k]);
+  __shared__ double sm[RED_THREADS];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sm[threadIdx.x] = red_op(op, sm[threadIdx.x], sm[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partial[blockIdx.x] = sm[0];
+}
+
+// the same over the entries of a row-major array with rows of width w whose column is
+// >= ilo and row >= jlo (the DoFs of a padded 2D rectangle)
+template <class S>
+__global__ void __launch_bounds__(RED_THREADS) partial_masked_kernel(const S* __restrict__ x, size_t n, int w,
+                                                                     int ilo, int jlo, int op, double init,
+                                                                     double* partial) {
+  const size_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const size_t beg = blockIdx.x * chunk, end = beg + chunk < n ? beg + chunk : n;
+  double acc = init;
+  for (size_t k = beg + threadIdx.x; k < end; k += RED_THREADS)
+    if ((int)(k % w) >= ilo && (int)(k / w) >= jlo) acc = red_op(op, acc, (double)x[k]);
   __shared__ double sm[RED_THREADS];
   sm[threadIdx.x] = acc;
   __syncthreads();

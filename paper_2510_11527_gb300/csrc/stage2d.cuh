@@ -170,10 +170,25 @@ __device__ __forceinline__ T line_res(T z0, T z1, T z2, T z3, T z4, T f0, T f1, 
   return da * i3h2 - (cf + alpha * dz) * i6h;
 }
 
+// Padded index of a 2D rectangle with outflow ends (n cells in this direction, padded
+// index I = cell index + 1): the evenly reflected source of a cell-type entry (ub; X in
+// y; Y in x) and of a face-type entry (V; X in x; Y in y). Indices further out than any
+// owned output reads are clamped first, so every load stays inside the arrays (n >= 4).
+__device__ __forceinline__ int rect_cell(int I, int n) {
+  I = I < -3 ? -3 : (I > n + 4 ? n + 4 : I);
+  return I < 1 ? 1 - I : (I > n ? 2 * n + 1 - I : I);
+}
+__device__ __forceinline__ int rect_face(int I, int n) {
+  I = I < -3 ? -3 : (I > n + 4 ? n + 4 : I);
+  return I < 0 ? -I : (I > n ? 2 * n - I : I);
+}
+
 // One TX x TY tile with origin (i0, j0) of one mesh: all phases P0-P5. Every thread of
 // the CTA must call it (it contains __syncthreads); smem_raw holds Tile2D::SMEM bytes.
-// PAIRED enables the paired vector loads of interior halo boxes (P0).
-template <int FLUX, class T, class PT, bool BLEND, int TX_ = 32, int TY_ = 8, bool PAIRED = true>
+// PAIRED enables the paired vector loads of interior halo boxes (P0). RECT selects a 2D
+// rectangle with outflow ends in its padded layout (reflected ghost loads, masked stores);
+// periodic meshes compile without any of it.
+template <int FLUX, class T, class PT, bool BLEND, int TX_ = 32, int TY_ = 8, bool PAIRED = true, bool RECT = false>
 __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<PT>& A, const int i0, const int j0,
                                            unsigned char* smem_raw) {
   using L = Tile2D<FLUX, T, BLEND, TX_, TY_>;
@@ -238,8 +253,10 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   // ---- P0: load the halo box --------------------------------------------------------
   // Tiles whose halo box lies inside an even-width mesh load the box as aligned pairs
   // (8- or 16-byte vector loads; rows start at the even column i0 - 2); other tiles
-  // (periodic wrap, odd widths, the +-3 blend halo) load element by element. In both,
-  // all loads of a thread are issued before its first store, so their latencies overlap.
+  // (periodic wrap, odd widths, the +-3 blend halo, the sides of a rectangle with
+  // outflow ends) load element by element. In both, all loads of a thread are issued
+  // before its first store, so their latencies overlap. A rectangle (A.bc) is tiled in
+  // its padded layout: a paired box never reaches row or column 0 or beyond the last.
   bool paired = false;
   if constexpr (H == 2 && PAIRED) {
     paired = (nx % 2 == 0) && i0 - H >= 0 && i0 + TX + H <= nx && j0 - H >= 0 && j0 + TY + H <= ny;
@@ -284,12 +301,22 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
       const int k = tid + it * NT;
       if (k < BN) {
         const int bx = k % BX, by = k / BX;
-        const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
-        const size_t g = (size_t)gj * nx + gi;
-        ldU[it] = A.ub[g];
-        ldV[it] = A.V[g];
-        ldX[it] = A.X[g];
-        ldY[it] = A.Y[g];
+        if constexpr (RECT) {
+          // cell-type and face-type source indices in the padded layout
+          const int ci = rect_cell(i0 - H + bx, nx - 1), fi = rect_face(i0 - H + bx, nx - 1);
+          const int cj = rect_cell(j0 - H + by, ny - 1), fj = rect_face(j0 - H + by, ny - 1);
+          ldU[it] = A.ub[(size_t)cj * nx + ci];
+          ldV[it] = A.V[(size_t)fj * nx + fi];
+          ldX[it] = A.X[(size_t)cj * nx + fi];
+          ldY[it] = A.Y[(size_t)fj * nx + ci];
+        } else {
+          const int gi = wrapi(i0 - H + bx, nx), gj = wrapi(j0 - H + by, ny);
+          const size_t g = (size_t)gj * nx + gi;
+          ldU[it] = A.ub[g];
+          ldV[it] = A.V[g];
+          ldX[it] = A.X[g];
+          ldY[it] = A.Y[g];
+        }
       }
     }
 #pragma unroll
@@ -710,37 +737,52 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
         xo = PT(rk_scale(cFt, x));
         yo = PT(rk_scale(cFt, y));
       }
-      if (A.limiter && A.sg[o]) {
-        ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
-        vo = safeguard<PT>(vo, PT(umin), PT(umax), A.tol, A.stats);
-        xo = safeguard<PT>(xo, PT(umin), PT(umax), A.tol, A.stats);
-        yo = safeguard<PT>(yo, PT(umin), PT(umax), A.tol, A.stats);
+      if constexpr (RECT) {
+        // the padded rectangle stores the average from (1, 1), X from row 1, Y from column 1
+        const bool wU = gi > 0 && gj > 0, wX = gj > 0, wY = gi > 0;
+        if (A.limiter && A.sg[o]) {
+          if (wU) ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
+          vo = safeguard<PT>(vo, PT(umin), PT(umax), A.tol, A.stats);
+          if (wX) xo = safeguard<PT>(xo, PT(umin), PT(umax), A.tol, A.stats);
+          if (wY) yo = safeguard<PT>(yo, PT(umin), PT(umax), A.tol, A.stats);
+        }
+        if (wU) A.Oub[o][g] = ubo;
+        A.OV[o][g] = vo;
+        if (wX) A.OX[o][g] = xo;
+        if (wY) A.OY[o][g] = yo;
+      } else {
+        if (A.limiter && A.sg[o]) {
+          ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
+          vo = safeguard<PT>(vo, PT(umin), PT(umax), A.tol, A.stats);
+          xo = safeguard<PT>(xo, PT(umin), PT(umax), A.tol, A.stats);
+          yo = safeguard<PT>(yo, PT(umin), PT(umax), A.tol, A.stats);
+        }
+        A.Oub[o][g] = ubo;
+        A.OV[o][g] = vo;
+        A.OX[o][g] = xo;
+        A.OY[o][g] = yo;
       }
-      A.Oub[o][g] = ubo;
-      A.OV[o][g] = vo;
-      A.OX[o][g] = xo;
-      A.OY[o][g] = yo;
     }
     if (o + 1 < A.nout) __syncthreads();
   }
 }
 
 // One CTA per 32 x 8 tile of a single mesh (row-major tile index in blockIdx.x).
-template <int FLUX, class T, class PT, bool BLEND>
+template <int FLUX, class T, class PT, bool BLEND, bool RECT = false>
 __global__ void __launch_bounds__(256) stage2d_kernel(const DevModel m, const StageArgs2D<PT> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tiles_x = (A.nx + 31) / 32, t = blockIdx.x;   // 1D grid: no 65535 limit on rows
-  stage_tile<FLUX, T, PT, BLEND, 32, 8>(m, A, (t % tiles_x) * 32, (t / tiles_x) * 8, smem_raw);
+  stage_tile<FLUX, T, PT, BLEND, 32, 8, true, RECT>(m, A, (t % tiles_x) * 32, (t / tiles_x) * 8, smem_raw);
 }
 
 // The same for the FP32 stencils without the blend, compiled for 6 resident CTAs per SM
 // (<= 40 registers; its 36 KB of shared memory allow 6): measured 8% faster than the
 // compiler's own 48-register choice at 5 CTAs per SM.
-template <int FLUX>
+template <int FLUX, bool RECT = false>
 __global__ void __launch_bounds__(256, 6) stage2d_kernel_f32occ6(const DevModel m, const StageArgs2D<float> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int tiles_x = (A.nx + 31) / 32, t = blockIdx.x;
-  stage_tile<FLUX, float, float, false, 32, 8>(m, A, (t % tiles_x) * 32, (t / tiles_x) * 8, smem_raw);
+  stage_tile<FLUX, float, float, false, 32, 8, true, RECT>(m, A, (t % tiles_x) * 32, (t / tiles_x) * 8, smem_raw);
 }
 
 }  // namespace af

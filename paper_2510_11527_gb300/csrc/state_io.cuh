@@ -99,6 +99,10 @@ __global__ void __launch_bounds__(RED_THREADS) scatter_state_kernel(const double
   }
 }
 
+// exact widening of a stored point value
+__device__ __forceinline__ double wide(double v) { return v; }
+__device__ __forceinline__ double wide(float v) { return f2d_exact(v); }
+
 // FP32 point arrays (np values each) -> staged doubles (exact widening) for the copy to
 // the host
 __global__ void __launch_bounds__(RED_THREADS) gather_points_kernel(const float* __restrict__ V,
@@ -111,6 +115,42 @@ __global__ void __launch_bounds__(RED_THREADS) gather_points_kernel(const float*
       stg[n + k] = f2d_exact(X[k]);
       stg[2 * n + k] = f2d_exact(Y[k]);
     }
+  }
+}
+
+// 2D rectangle with ends: the caller's layout (ub [ny][nx], V [ny+1][nx+1],
+// X [ny][nx+1], Y [ny+1][nx], staged back to back as doubles) <-> the padded device
+// layout ((nx+1) x (ny+1) per array; entry (I, J) holds ub(I-1, J-1), V(I-1, J-1),
+// X(I-1, J-1), Y(I-1, J-1) in cell / point indices, i.e. corner and edges of padded cell
+// (I, J)). Padded entries that are not DoFs (ub in row / column 0, X in row 0, Y in
+// column 0) are written as 0 and never read as data.
+template <class PT>
+__global__ void __launch_bounds__(RED_THREADS) scatter_rect_kernel(const double* __restrict__ stg, int nx, int ny,
+                                                                   double* ub, PT* V, PT* X, PT* Y) {
+  const int NX = nx + 1, NY = ny + 1;
+  const size_t pn = (size_t)NX * NY, oV = (size_t)nx * ny, oX = oV + pn, oY = oX + (size_t)NX * ny;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pn; k += (size_t)gridDim.x * blockDim.x) {
+    const int I = (int)(k % NX), J = (int)(k / NX);
+    ub[k] = (I > 0 && J > 0) ? stg[(size_t)(J - 1) * nx + (I - 1)] : 0.0;
+    V[k] = (PT)stg[oV + k];
+    X[k] = J > 0 ? (PT)stg[oX + (size_t)(J - 1) * NX + I] : PT(0);
+    Y[k] = I > 0 ? (PT)stg[oY + (size_t)J * nx + (I - 1)] : PT(0);
+  }
+}
+
+template <class PT>
+__global__ void __launch_bounds__(RED_THREADS) gather_rect_kernel(const double* __restrict__ ub,
+                                                                  const PT* __restrict__ V, const PT* __restrict__ X,
+                                                                  const PT* __restrict__ Y, int nx, int ny,
+                                                                  double* stg) {
+  const int NX = nx + 1, NY = ny + 1;
+  const size_t pn = (size_t)NX * NY, oV = (size_t)nx * ny, oX = oV + pn, oY = oX + (size_t)NX * ny;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < pn; k += (size_t)gridDim.x * blockDim.x) {
+    const int I = (int)(k % NX), J = (int)(k / NX);
+    if (I > 0 && J > 0) stg[(size_t)(J - 1) * nx + (I - 1)] = ub[k];
+    stg[oV + k] = wide(V[k]);
+    if (J > 0) stg[oX + (size_t)(J - 1) * NX + I] = wide(X[k]);
+    if (I > 0) stg[oY + (size_t)J * nx + (I - 1)] = wide(Y[k]);
   }
 }
 

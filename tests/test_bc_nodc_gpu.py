@@ -240,7 +240,7 @@ def test_bounded_state_sizes_and_device_views():
 def test_unsupported_combinations_are_rejected():
     from paper_2510_11527_gb300 import AfError
     bad = [
-        ai.Spec(dim=2, nx=8, ny=8, bc="outflow", flux=("burgers", (0.5,))),
+        ai.Spec(dim=2, nx=8, ny=8, bc="dirichlet", flux=("burgers", (0.5,))),
         ai.Spec(dim=2, nx=8, ny=8, diffusion_form="nodc", diff=("const", (0.1,))),
         spec1d(16, "outflow", "nodc", blend="plain"),
         spec1d(16, "dirichlet", blend="external"),
