@@ -63,6 +63,9 @@ class Spec:
     bc: str = "periodic"
     bc_values: Tuple[float, float] = (0.0, 0.0)
     diffusion_form: str = "dc"
+    nz: int = 1
+    z0: float = 0.0
+    z1: float = 1.0
 
     @property
     def dx(self) -> float:
@@ -73,11 +76,16 @@ class Spec:
         return (self.y1 - self.y0) / self.ny if self.dim == 2 else 1.0
 
     @property
-    def cells(self) -> int:
-        return self.nx * (self.ny if self.dim == 2 else 1)
+    def dz(self) -> float:
+        return (self.z1 - self.z0) / self.nz if self.dim == 3 else 1.0
 
-    def with_size(self, nx: int, ny: int | None = None) -> "Spec":
-        return dataclasses.replace(self, nx=nx, ny=(ny if ny is not None else (nx if self.dim == 2 else 1)))
+    @property
+    def cells(self) -> int:
+        return self.nx * (self.ny if self.dim >= 2 else 1) * (self.nz if self.dim == 3 else 1)
+
+    def with_size(self, nx: int, ny: int | None = None, nz: int | None = None) -> "Spec":
+        return dataclasses.replace(self, nx=nx, ny=(ny if ny is not None else (nx if self.dim >= 2 else 1)),
+                                   nz=(nz if nz is not None else (nx if self.dim == 3 else 1)))
 
 
 # ----------------------------------------------------------------------------------
@@ -406,6 +414,40 @@ def random_state_2d(spec: Spec, seed: int, lo: float | None = None, hi: float | 
     if spec.bc != "periodic":
         shapes = [(spec.ny, spec.nx), (spec.ny + 1, spec.nx + 1), (spec.ny, spec.nx + 1), (spec.ny + 1, spec.nx)]
     return [(lo + (hi - lo) * torch.rand(sh, generator=g, dtype=torch.float64)).to(device) for sh in shapes]
+
+
+# 3D (periodic, [nz][ny][nx]): 8 arrays ordered by kind s = sx + 2 sy + 4 sz of the location
+# (i + sx/2, j + sy/2, k + sz/2): ub, x-face, y-face, xy-edge, z-face, xz-edge, yz-edge,
+# corner.
+def kind_offsets_3d():
+    return [((s >> 0) & 1, (s >> 1) & 1, (s >> 2) & 1) for s in range(8)]
+
+
+def random_state_3d(spec: Spec, seed: int, lo: float | None = None, hi: float | None = None):
+    g = torch.Generator(device="cpu").manual_seed(seed)
+    lo = spec.umin if lo is None else lo
+    hi = spec.umax if hi is None else hi
+    shape = (spec.nz, spec.ny, spec.nx)
+    return [lo + (hi - lo) * torch.rand(shape, generator=g, dtype=torch.float64) for _ in range(8)]
+
+
+def mode_3d_state(spec: Spec, k: float, shift: float = 1.0, amp: float = 1.0):
+    """u0 = shift + amp sin(k (x + y + z)): closed-form cell averages (the product of the
+    three 1D averaging factors) and exact point values at every kind's location."""
+    i = torch.arange(spec.nx, dtype=torch.float64)
+    j = torch.arange(spec.ny, dtype=torch.float64)
+    kk = torch.arange(spec.nz, dtype=torch.float64)
+    fac = 1.0
+    for h in (spec.dx, spec.dy, spec.dz):
+        fac *= math.sin(k * h / 2) / (k * h / 2)
+    out = []
+    for s, (sx, sy, sz) in enumerate(kind_offsets_3d()):
+        x = spec.x0 + (i + 0.5 + 0.5 * sx) * spec.dx
+        y = spec.y0 + (j + 0.5 + 0.5 * sy) * spec.dy
+        z = spec.z0 + (kk + 0.5 + 0.5 * sz) * spec.dz
+        ph = k * (x[None, None, :] + y[None, :, None] + z[:, None, None])
+        out.append(shift + amp * (fac if s == 0 else 1.0) * torch.sin(ph))
+    return out
 
 
 def random_state_1d(spec: Spec, seed: int, lo: float | None = None, hi: float | None = None):

@@ -38,7 +38,7 @@ class Problem(ctypes.Structure):
         ("limiter", ctypes.c_int), ("blend", ctypes.c_int), ("gamma", ctypes.c_double),
         ("clamp_tol", ctypes.c_double),
         ("bc", ctypes.c_int), ("bc_left", ctypes.c_double), ("bc_right", ctypes.c_double),
-        ("nodc", ctypes.c_int),
+        ("nodc", ctypes.c_int), ("nz", ctypes.c_int), ("dz", ctypes.c_double),
     ]
 
 
@@ -70,6 +70,7 @@ def lib():
         _lib.ao_theta.restype = ctypes.c_double
         _lib.ao_rk54_coefs.argtypes = [dpp, dpp]
         _lib.ao_flop_count.argtypes = [P, arr, ctypes.c_double, dpp, ctypes.POINTER(ctypes.c_longlong)]
+        _lib.ao_fe_generic.argtypes = [P, arr, ctypes.c_double, dpp, arr]
         _lib.ao_run.argtypes = [P, ctypes.c_int, arr, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                 ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(Stats)]
         _lib.ao_first_order_run.argtypes = [P, dpp, ctypes.c_double, ctypes.c_double,
@@ -82,9 +83,11 @@ def make_problem(spec) -> Problem:
     p = Problem()
     p.dim = spec.dim
     p.nx = spec.nx
-    p.ny = spec.ny if spec.dim == 2 else 1
+    p.ny = spec.ny if spec.dim >= 2 else 1
     p.dx = (spec.x1 - spec.x0) / spec.nx
-    p.dy = (spec.y1 - spec.y0) / spec.ny if spec.dim == 2 else 1.0
+    p.dy = (spec.y1 - spec.y0) / spec.ny if spec.dim >= 2 else 1.0
+    p.nz = getattr(spec, "nz", 1) if spec.dim == 3 else 1
+    p.dz = (spec.z1 - spec.z0) / spec.nz if spec.dim == 3 else 1.0
     p.flux_kind = FLUX_KINDS[spec.flux[0]]
     for k, v in enumerate(spec.flux[1]):
         p.flux_p[k] = float(v)
@@ -109,7 +112,7 @@ def _ptrs(arrays):
 
 
 def _prep(spec, state):
-    n = 2 if spec.dim == 1 else 4
+    n = 1 << spec.dim
     assert len(state) == n
     out = [np.ascontiguousarray(np.asarray(a, dtype=np.float64)).copy() for a in state]
     bounded = getattr(spec, "bc", "periodic") != "periodic"
@@ -140,6 +143,43 @@ def fe(spec, state, tau, s_ext=None):
     return out
 
 
+def fe_generic(spec, state, tau, s_ext=None):
+    """The dimension-generic fine-grid evaluation of a periodic state (arrays in the
+    library's order); for 1D and 2D it restates fe() in another form."""
+    p = make_problem(spec)
+    a = _prep(spec, state)
+    out = [np.zeros_like(x) for x in a]
+    s, sp = _sext(s_ext)
+    if lib().ao_fe_generic(ctypes.byref(p), _ptrs(a), float(tau), sp, _ptrs(out)) == -2:
+        raise ValueError("combination not supported by the oracle")
+    return out
+
+
+def diffusion_spectral_radius(dim, n=4):
+    """Spectral radius (in units of kappa / h^2) of the unlimited scheme's semi-discrete
+    operator for a = u on a periodic mesh of n cells per direction with h = 1, assembled
+    column by column from the oracle's forward-Euler step (the scheme is linear, so
+    FE(u, 1) - u is the operator applied to u)."""
+    import af_inputs
+    kw = dict(dim=dim, nx=n, x0=0.0, x1=float(n), flux=("zero", ()), diff=("const", (1.0,)), umin=-1e9,
+              umax=1e9, limiter=False)
+    if dim >= 2:
+        kw.update(ny=n, y0=0.0, y1=float(n))
+    if dim == 3:
+        kw.update(nz=n, z0=0.0, z1=float(n))
+    spec = af_inputs.Spec(**kw)
+    cells = n ** dim
+    nk = 1 << dim
+    size = cells * nk
+    A = np.zeros((size, size))
+    for col in range(size):
+        st = [np.zeros(cells) for _ in range(nk)]
+        st[col // cells][col % cells] = 1.0
+        out = fe(spec, st, 1.0)
+        A[:, col] = np.concatenate([o.ravel() - x.ravel() for o, x in zip(out, st)])
+    return float(np.max(np.abs(np.linalg.eigvals(A))))
+
+
 def step(spec, rk, state, dt, s_ext=None):
     """One SSP-RK time step (rk = 3 or 54). Returns (new_state, stats dict)."""
     p = make_problem(spec)
@@ -156,8 +196,11 @@ def step(spec, rk, state, dt, s_ext=None):
 
 # 0.9 x the linear (von Neumann) stability limit of the unlimited scheme for pure
 # diffusion, kappa dt / h^2: 1D from Table 1 (0.157, 0.333), 2D from the 4x4 symbol
-# (spectral radius 40.78 kappa/h^2 -> 0.0616 for SSP-RK3, 0.1307 for SSP-RK(5,4)).
-DIFF_CAP = {(1, 3): 0.9 * 0.157, (1, 54): 0.9 * 0.333, (2, 3): 0.9 * 0.0616, (2, 54): 0.9 * 0.1307}
+# (spectral radius 40.78 kappa/h^2 -> 0.0616 for SSP-RK3, 0.1307 for SSP-RK(5,4)), 3D
+# from the 8x8 symbol (63.335 kappa/h^2; the stability intervals of SSP-RK3 and
+# SSP-RK(5,4) on the negative real axis reach 2.5127 and 5.330).
+DIFF_CAP = {(1, 3): 0.9 * 0.157, (1, 54): 0.9 * 0.333, (2, 3): 0.9 * 0.0616, (2, 54): 0.9 * 0.1307,
+            (3, 3): 0.9 * 2.5127 / 63.335, (3, 54): 0.9 * 5.330 / 63.335}
 
 
 def dt_cfl(spec, ub, cfl=None, cfl_diff=None):

@@ -21,6 +21,9 @@
 // 1D (Section 2): ub[i] and P[i] = u_{i+1/2}; periodic, so u_{1/2} = u_{N+1/2}.
 // 1D with a Dirichlet or outflow boundary: P[j+1] = u_{j+1/2}, j = -1..N-1 (N+1 values
 // from the left to the right end of the interval).
+// 3D (periodic, [nz][ny][nx], i fastest): 8 arrays ordered by kind s = sx + 2 sy + 4 sz
+// of the location (i + sx/2, j + sy/2, k + sz/2): ub, then the x-face, y-face, xy-edge,
+// z-face, xz-edge, yz-edge and corner values.
 // 2D rectangle with outflow ends: ub [ny][nx]; V [ny+1][nx+1] (corners, from the
 // bottom-left corner); X [ny][nx+1] (vertical edges, from the left side); Y [ny+1][nx]
 // (horizontal edges, from the bottom side).
@@ -103,7 +106,7 @@ inline int wrap(int i, int n) { return ((i % n) + n) % n; }
 extern "C" {
 
 // Problem description shared with the Python side through ctypes.
-// flux_kind: 0 zero, 1 linear f1=p0*u f2=p1*u, 2 Burgers f1=f2=p0*u^2,
+// flux_kind: 0 zero, 1 linear f1=p0*u f2=p1*u (f3=p2*u), 2 Burgers f_l=p0*u^2,
 //            3 Buckley-Leverett f1=u^2/(u^2+(1-u)^2), f2=f1*(1-p0*(1-u)^2).
 // diff_kind: 0 none, 1 constant a=p0*u, 2 piecewise linear
 //            a = p0*min(u-p1,0) + p2*max(u-p3,0), 3 porous medium a=u^p0 (integer p0>=1),
@@ -129,6 +132,8 @@ typedef struct {
   int bc;               // 0 periodic, 1 Dirichlet, 2 outflow (1D)
   double bc_left, bc_right;
   int nodc;             // 1: Appendix A discretization of the diffusion term
+  int nz;               // 3D: cells along z (periodic)
+  double dz;
 } ao_problem;
 
 typedef struct {
@@ -148,13 +153,13 @@ namespace {
 struct Model {
   ao_problem p;
   // interior local extrema of f_l' (Buckley-Leverett only), found once at set-up
-  std::vector<double> crit[2];
+  std::vector<double> crit[3];
 };
 
 template <class R> R flux(const Model& m, int dir, R u) {
   const ao_problem& p = m.p;
   switch (p.flux_kind) {
-    case 1: return R(dir == 0 ? p.flux_p[0] : p.flux_p[1]) * u;
+    case 1: return R(dir == 0 ? p.flux_p[0] : (dir == 1 ? p.flux_p[1] : p.flux_p[2])) * u;
     case 2: return R(p.flux_p[0]) * u * u;
     case 3: {
       R v = R(1.0) - u;
@@ -169,7 +174,7 @@ template <class R> R flux(const Model& m, int dir, R u) {
 template <class R> R dflux(const Model& m, int dir, R u) {
   const ao_problem& p = m.p;
   switch (p.flux_kind) {
-    case 1: return R(dir == 0 ? p.flux_p[0] : p.flux_p[1]);
+    case 1: return R(dir == 0 ? p.flux_p[0] : (dir == 1 ? p.flux_p[1] : p.flux_p[2]));
     case 2: return R(2.0 * p.flux_p[0]) * u;
     case 3: {
       // f1 = u^2/D, D = u^2 + (1-u)^2, f1' = 2u(1-u)/D^2
@@ -257,7 +262,7 @@ double kappa_max(const Model& m) {
 // Interior local extrema of f_l' on [-1, 2] by sampling and golden-section refinement
 // (the value of f' at an extremum is insensitive to the location error).
 void find_crit(Model& m) {
-  for (int d = 0; d < 2; ++d) m.crit[d].clear();
+  for (int d = 0; d < 3; ++d) m.crit[d].clear();
   if (m.p.flux_kind != 3) return;
   for (int d = 0; d < 2; ++d) {
     const double a = -1.0, b = 2.0;
@@ -530,6 +535,299 @@ void fe1d(const Model& m, const R* ub, const R* P, R tau, const R* s_ext, R* ub_
 }
 
 // ---------------------------------------------------------------------------------
+// Dimension-generic forward-Euler evaluation (Sections 4 and 5.2; d = 1, 2, 3) on the
+// fine grid of half-cell spacing: the DoF at (i + s_0/2, j + s_1/2, k + s_2/2), s_l in
+// {0, 1}, has fine index (2i + s_0, 2j + s_1, 2k + s_2). Its kind is s = s_0 + 2 s_1 +
+// 4 s_2: kind 0 is the cell centre (recovered, not a DoF), kinds 1 .. 2^d - 1 are the
+// point values (3D: 1 x-face, 2 y-face, 3 xy-edge, 4 z-face, 5 xz-edge, 6 yz-edge,
+// 7 corner; 2D: 1 = X, 2 = Y, 3 = V). Every 5-point line of the paper is then the fine
+// points p - 2e, p - e, p, p + e, p + 2e along one axis, and every Simpson average
+// takes weights 1, 4, 1 (/6) per axis. Periodic in every direction.
+template <class R>
+void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R* const* P, R tau,
+          const R* s_ext, R* ub_o, R* const* P_o) {
+  const ao_problem& p = m.p;
+  const int nk = 1 << d;
+  int nn[3] = {1, 1, 1};
+  for (int l = 0; l < d; ++l) nn[l] = n[l];
+  const size_t N = (size_t)nn[0] * nn[1] * nn[2];
+  auto cell = [&](const int* c) {   // periodic cell index -> linear
+    int w[3];
+    for (int l = 0; l < 3; ++l) w[l] = wrap(c[l], nn[l]);
+    return ((size_t)w[2] * nn[1] + w[1]) * nn[0] + w[0];
+  };
+  auto decode = [&](size_t q, int* c) {
+    c[0] = (int)(q % nn[0]);
+    c[1] = (int)((q / nn[0]) % nn[1]);
+    c[2] = (int)(q / ((size_t)nn[0] * nn[1]));
+  };
+  // fine index f -> (kind, cell)
+  auto split = [&](const int* f, int& kind, size_t& q) {
+    int c[3] = {0, 0, 0};
+    kind = 0;
+    for (int l = 0; l < d; ++l) {
+      const int w = wrap(f[l], 2 * nn[l]);
+      c[l] = w >> 1;
+      kind |= (w & 1) << l;
+    }
+    q = cell(c);
+  };
+  const R w1[3] = {R(1.0), R(4.0), R(1.0)};   // Simpson weights (/6) for offsets -1, 0, +1
+
+  // (1) centre value from the tensor Simpson rule for the cell average:
+  //     ub = sum_m (prod_l w1(m_l)/6) z(2i + m)  ->  solved for the centre m = 0
+  std::vector<R> C(N);
+  for (size_t q = 0; q < N; ++q) {
+    int c[3];
+    decode(q, c);
+    R acc = R(0.0);
+    for (int o = 0; o < 27; ++o) {
+      int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      bool skip = false, centre = true;
+      for (int l = 0; l < 3; ++l) {
+        if (l >= d && mm[l] != 0) skip = true;
+        if (mm[l] != 0) centre = false;
+      }
+      if (skip || centre) continue;
+      R wgt = R(1.0);
+      int f[3] = {0, 0, 0};
+      for (int l = 0; l < d; ++l) { wgt = wgt * w1[mm[l] + 1]; f[l] = 2 * c[l] + mm[l]; }
+      int kind;
+      size_t qq;
+      split(f, kind, qq);
+      acc = acc + wgt * P[kind][qq];
+    }
+    R w0 = R(1.0), tot = R(1.0);
+    for (int l = 0; l < d; ++l) { w0 = w0 * R(4.0); tot = tot * R(6.0); }
+    C[q] = (tot * ub[q] - acc) / w0;
+  }
+  auto Z = [&](const int* f) {
+    int kind;
+    size_t qq;
+    split(f, kind, qq);
+    return kind == 0 ? C[qq] : P[kind][qq];
+  };
+  std::vector<R> fU[3], aU(N);
+  for (int l = 0; l < d; ++l) fU[l].resize(N);
+  for (size_t q = 0; q < N; ++q) {
+    for (int l = 0; l < d; ++l) fU[l][q] = flux<R>(m, l, ub[q]);
+    aU[q] = apot<R>(m, ub[q]);
+  }
+  // transverse Simpson offsets of a face / a cell: all m with m_l = 0 along the axis l
+  auto transverse = [&](int l, auto&& fn) {
+    for (int o = 0; o < 27; ++o) {
+      int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
+      bool skip = mm[l] != 0;
+      for (int t = d; t < 3; ++t) if (mm[t] != 0) skip = true;
+      if (skip) continue;
+      R wgt = R(1.0), tot = R(1.0);
+      for (int t = 0; t < d; ++t)
+        if (t != l) { wgt = wgt * w1[mm[t] + 1]; tot = tot * R(6.0); }
+      fn(mm, wgt, tot);
+    }
+  };
+
+  // (2) high-order face fluxes F^H_l (Simpson face average of f_l) and cell potentials
+  //     A^H_l (transverse Simpson average of the 1D DC potential along l)
+  std::vector<R> FH[3], AH[3];
+  for (int l = 0; l < d; ++l) {
+    FH[l].resize(N);
+    AH[l].resize(N);
+    for (size_t q = 0; q < N; ++q) {
+      int c[3];
+      decode(q, c);
+      R fs = R(0.0), as = R(0.0), tot6 = R(1.0);
+      transverse(l, [&](const int* mm, R wgt, R tot) {
+        int f[3] = {0, 0, 0}, fm[3], fp[3];
+        for (int t = 0; t < d; ++t) f[t] = 2 * c[t] + mm[t];
+        for (int t = 0; t < 3; ++t) { fm[t] = f[t]; fp[t] = f[t]; }
+        fm[l] -= 1;
+        fp[l] += 1;
+        fs = fs + wgt * flux<R>(m, l, Z(fp));   // face point at fine 2i + 1 along l
+        R ahat = (-apot<R>(m, Z(fm)) + R(8.0) * apot<R>(m, Z(f)) - apot<R>(m, Z(fp))) / R(6.0);
+        as = as + wgt * ahat;
+        tot6 = tot;
+      });
+      FH[l][q] = fs / tot6;
+      AH[l][q] = as / tot6;
+    }
+  }
+
+  // (3) high-order point residuals, one 5-point line per axis
+  std::vector<R> RH[8][3];
+  for (int s = 1; s < nk; ++s)
+    for (int l = 0; l < d; ++l) {
+      RH[s][l].resize(N);
+      for (size_t q = 0; q < N; ++q) {
+        int c[3];
+        decode(q, c);
+        int f0[3] = {0, 0, 0};
+        for (int t = 0; t < d; ++t) f0[t] = 2 * c[t] + ((s >> t) & 1);
+        R z[5], fl[5], df[5], a[5];
+        for (int t = 0; t < 5; ++t) {
+          int f[3] = {f0[0], f0[1], f0[2]};
+          f[l] += t - 2;
+          z[t] = Z(f);
+          fl[t] = flux<R>(m, l, z[t]);
+          df[t] = dflux<R>(m, l, z[t]);
+          a[t] = apot<R>(m, z[t]);
+        }
+        RH[s][l][q] = line_residual<R>(z, fl, df, a, h[l]);
+      }
+    }
+
+  // (4) low-order LLF fluxes and directional states u^{L,+-}_l with factor 2d
+  R mu[3], nu[3];
+  std::vector<R> FL[3], ULp[3], ULm[3];
+  const R twod = R(2.0 * d);
+  auto nb = [&](size_t q, int l, int step) {
+    int c[3];
+    decode(q, c);
+    c[l] += step;
+    return cell(c);
+  };
+  for (int l = 0; l < d; ++l) {
+    mu[l] = tau / h[l];
+    nu[l] = tau / (h[l] * h[l]);
+    FL[l].resize(N);
+    ULp[l].resize(N);
+    ULm[l].resize(N);
+    for (size_t q = 0; q < N; ++q) {
+      size_t qp = nb(q, l, 1);
+      R al = alpha_interval<R>(m, l, ub[q], ub[qp]);
+      FL[l][q] = R(0.5) * (fU[l][q] + fU[l][qp]) - R(0.5) * al * (ub[qp] - ub[q]);
+    }
+    for (size_t q = 0; q < N; ++q) {
+      size_t qp = nb(q, l, 1), qm = nb(q, l, -1);
+      ULp[l][q] = ub[q] - twod * mu[l] * (FL[l][q] - fU[l][q]) + twod * nu[l] * (aU[qp] - aU[q]);
+      ULm[l][q] = ub[q] - twod * mu[l] * (fU[l][q] - FL[l][qm]) - twod * nu[l] * (aU[q] - aU[qm]);
+    }
+  }
+
+  // (5) optional smoothness blend, axis by axis (Section 5.2.3)
+  std::vector<R> Fh[3], Ah[3], RP[8];
+  for (int l = 0; l < d; ++l) { Fh[l] = FH[l]; Ah[l] = AH[l]; }
+  for (int s = 1; s < nk; ++s) {
+    RP[s].assign(N, R(0.0));
+    for (size_t q = 0; q < N; ++q) {
+      R acc = RH[s][0][q];
+      for (int l = 1; l < d; ++l) acc = acc + RH[s][l][q];
+      RP[s][q] = acc;
+    }
+  }
+  if (p.blend) {
+    std::vector<R> sl[3], tc[3], td[3];
+    const R g = R(p.gamma);
+    for (int l = 0; l < d; ++l) {
+      sl[l].resize(N);
+      tc[l].resize(N);
+      td[l].resize(N);
+      if (p.blend == 1) {
+        std::vector<R> st(N);
+        for (size_t q = 0; q < N; ++q) st[q] = s_tilde<R>(ub[nb(q, l, -1)], ub[q], ub[nb(q, l, 1)]);
+        for (size_t q = 0; q < N; ++q) sl[l][q] = (st[nb(q, l, -1)] + R(4.0) * st[q] + st[nb(q, l, 1)]) / R(6.0);
+      } else {
+        for (size_t q = 0; q < N; ++q) sl[l][q] = s_ext[q];
+      }
+      for (size_t q = 0; q < N; ++q) {
+        tc[l][q] = exp_(-g * (R(0.5) * (sl[l][q] + sl[l][nb(q, l, 1)])));
+        td[l][q] = exp_(-g * sl[l][q]);
+      }
+      for (size_t q = 0; q < N; ++q) {
+        Fh[l][q] = tc[l][q] * FH[l][q] + (R(1.0) - tc[l][q]) * FL[l][q];
+        Ah[l][q] = td[l][q] * AH[l][q] + (R(1.0) - td[l][q]) * aU[q];
+      }
+    }
+    // point weight along l: on an l-face (s_l = 1), the min of theta^{c,s}_l over the
+    // l-faces holding the point; otherwise the min of theta^{d,s}_l over the cells
+    // holding it. Low-order residual on the +-h/2 neighbours, a centre replaced by its
+    // cell average.
+    for (int s = 1; s < nk; ++s)
+      for (size_t q = 0; q < N; ++q) {
+        int c[3];
+        decode(q, c);
+        int f0[3] = {0, 0, 0};
+        for (int t = 0; t < d; ++t) f0[t] = 2 * c[t] + ((s >> t) & 1);
+        R acc = R(0.0);
+        for (int l = 0; l < d; ++l) {
+          R w = R(2.0);
+          const bool onface = (s >> l) & 1;
+          // cells holding the point: along l its own cell c_l; across t, c_t and, on an
+          // odd coordinate, c_t + 1
+          for (int o = 0; o < 8; ++o) {
+            int cc[3] = {c[0], c[1], c[2]};
+            bool ok = true;
+            for (int t = 0; t < 3; ++t) {
+              const int bit = (o >> t) & 1;
+              if (!bit) continue;
+              if (t == l || t >= d || !((s >> t) & 1)) { ok = false; break; }
+              cc[t] += 1;
+            }
+            if (!ok) continue;
+            const size_t qq = cell(cc);
+            const R v = onface ? tc[l][qq] : td[l][qq];
+            w = (w == R(2.0)) ? v : minr(w, v);
+          }
+          R zz[3];
+          for (int t = 0; t < 3; ++t) {
+            int f[3] = {f0[0], f0[1], f0[2]};
+            f[l] += t - 1;
+            int kind;
+            size_t qq;
+            split(f, kind, qq);
+            zz[t] = kind == 0 ? ub[qq] : P[kind][qq];
+          }
+          R RL = low_point_residual<R>(m, l, zz[0], zz[1], zz[2], h[l]);
+          acc = (l == 0) ? (w * RH[s][l][q] + (R(1.0) - w) * RL) : acc + (w * RH[s][l][q] + (R(1.0) - w) * RL);
+        }
+        RP[s][q] = acc;
+      }
+  }
+
+  // (6) monolithic convex limiter with factor 3 * 2d
+  std::vector<R> Fl[3], Al[3];
+  for (int l = 0; l < d; ++l) { Fl[l] = Fh[l]; Al[l] = Ah[l]; }
+  if (p.limiter) {
+    const R kf = R(6.0 * d);
+    for (int l = 0; l < d; ++l) {
+      for (size_t q = 0; q < N; ++q) {
+        size_t qp = nb(q, l, 1);
+        R dF = Fh[l][q] - FL[l][q];
+        R t = minr(Theta<R>(m, ULp[l][q], ULp[l][q] - kf * mu[l] * dF),
+                   Theta<R>(m, ULm[l][qp], ULm[l][qp] + kf * mu[l] * dF));
+        Fl[l][q] = (t == R(1.0)) ? Fh[l][q] : FL[l][q] + t * dF;
+      }
+      for (size_t q = 0; q < N; ++q) {
+        size_t qm = nb(q, l, -1), qp = nb(q, l, 1);
+        R dA = Ah[l][q] - aU[q];
+        R t = minr(minr(Theta<R>(m, ULp[l][qm], ULp[l][qm] + kf * nu[l] * dA),
+                        Theta<R>(m, ULp[l][q], ULp[l][q] - kf * nu[l] * dA)),
+                   minr(Theta<R>(m, ULm[l][q], ULm[l][q] - kf * nu[l] * dA),
+                        Theta<R>(m, ULm[l][qp], ULm[l][qp] + kf * nu[l] * dA)));
+        Al[l][q] = (t == R(1.0)) ? Ah[l][q] : aU[q] + t * dA;
+      }
+    }
+  }
+
+  // (7) limited cell-average update and point values with projection
+  for (size_t q = 0; q < N; ++q) {
+    R v = ub[q];
+    for (int l = 0; l < d; ++l) {
+      size_t qm = nb(q, l, -1), qp = nb(q, l, 1);
+      v = v - mu[l] * (Fl[l][q] - Fl[l][qm]) + nu[l] * (Al[l][qp] - R(2.0) * Al[l][q] + Al[l][qm]);
+    }
+    ub_o[q] = v;
+  }
+  const R umin = R(p.umin), umax = R(p.umax);
+  for (int s = 1; s < nk; ++s)
+    for (size_t q = 0; q < N; ++q) {
+      R v = P[s][q] + tau * RP[s][q];
+      if (p.limiter) v = minr(maxr(v, umin), umax);
+      P_o[s][q] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------------
 // 2D forward-Euler evaluation (Sections 4 and 5.2 with d = 2).
 template <class R>
 void fe2d(const Model& m, const R* ub, const R* V, const R* X, const R* Y, R tau, const R* s_ext,
@@ -781,11 +1079,13 @@ const double RK54_B[5][5] = {
     {0, 0, 0, 0.063692468666290, 0.226007483236906}};
 
 struct State {
-  std::vector<double> a[4];
+  std::vector<double> a[8];
 };
 
-int ncomp(const ao_problem& p) { return p.dim == 1 ? 2 : 4; }
-size_t ncell(const ao_problem& p) { return (size_t)p.nx * (p.dim == 1 ? 1 : p.ny); }
+int ncomp(const ao_problem& p) { return 1 << p.dim; }
+size_t ncell(const ao_problem& p) {
+  return (size_t)p.nx * (p.dim >= 2 ? p.ny : 1) * (p.dim == 3 ? p.nz : 1);
+}
 // values in component c: a bounded 1D mesh has n+1 point values
 size_t comp_size(const ao_problem& p, int c) {
   if (p.bc == 0 || c == 0) return ncell(p);
@@ -797,6 +1097,8 @@ size_t comp_size(const ao_problem& p, int c) {
 // combinations the oracle implements: boundaries and Appendix A in 1D only, an
 // external indicator only on a periodic mesh, Appendix A without the blend
 bool supported(const ao_problem& p) {
+  if (p.dim < 1 || p.dim > 3) return false;
+  if (p.dim == 3 && (p.bc != 0 || p.flux_kind == 3)) return false;   // 3D: periodic, no Buckley-Leverett
   if ((p.bc == 1 || p.nodc) && p.dim != 1) return false;
   if (p.bc < 0 || p.bc > 2) return false;
   if (p.bc != 0 && (p.nx < 4 || (p.dim == 2 && p.ny < 4) || p.blend == 2)) return false;
@@ -864,7 +1166,14 @@ void fe2d_outflow(const Model& m, const State& in, double tau, State& out) {
 void fe(const Model& m, const State& in, double tau, const double* s_ext, State& out) {
   const ao_problem& p = m.p;
   for (int c = 0; c < ncomp(p); ++c) out.a[c].assign(comp_size(p, c), 0.0);
-  if (p.dim == 2 && p.bc != 0)
+  if (p.dim == 3) {
+    const int n[3] = {p.nx, p.ny, p.nz};
+    const double h[3] = {p.dx, p.dy, p.dz};
+    const double* P[8];
+    double* Po[8];
+    for (int c = 1; c < 8; ++c) { P[c] = in.a[c].data(); Po[c] = out.a[c].data(); }
+    fend<double>(m, 3, n, h, in.a[0].data(), P, tau, s_ext, out.a[0].data(), Po);
+  } else if (p.dim == 2 && p.bc != 0)
     fe2d_outflow(m, in, tau, out);
   else if (p.dim == 1)
     fe1d<double>(m, in.a[0].data(), in.a[1].data(), tau, s_ext, out.a[0].data(), out.a[1].data());
@@ -1003,7 +1312,20 @@ namespace {
 double dt_model(const Model& m, const double* ub, double cfl, double cfl_diff, double km) {
   const ao_problem* p = &m.p;
   double worst = 0.0;
-  if (p->dim == 1) {
+  if (p->dim == 3) {
+    const int n[3] = {p->nx, p->ny, p->nz};
+    const double h[3] = {p->dx, p->dy, p->dz};
+    for (int k = 0; k < n[2]; ++k)
+      for (int j = 0; j < n[1]; ++j)
+        for (int i = 0; i < n[0]; ++i) {
+          const double u = ub[((size_t)k * n[1] + j) * n[0] + i];
+          const double un[3] = {ub[((size_t)k * n[1] + j) * n[0] + wrap(i + 1, n[0])],
+                                ub[((size_t)k * n[1] + wrap(j + 1, n[1])) * n[0] + i],
+                                ub[((size_t)wrap(k + 1, n[2]) * n[1] + j) * n[0] + i]};
+          for (int l = 0; l < 3; ++l)
+            worst = std::max(worst, alpha_interval<double>(m, l, u, un[l]) / h[l] + km / (h[l] * h[l]));
+        }
+  } else if (p->dim == 1) {
     for (int f = p->bc != 0 ? -1 : 0; f < p->nx; ++f) {
       double a = alpha_interval<double>(m, 0, cell_at<double>(*p, ub, f), cell_at<double>(*p, ub, f + 1));
       worst = std::max(worst, a / p->dx + km / (p->dx * p->dx));
@@ -1025,6 +1347,7 @@ double dt_model(const Model& m, const double* ub, double cfl, double cfl_diff, d
   double rate = worst / cfl;
   if (cfl_diff > 0.0 && km > 0.0) {
     double hmin = p->dim == 1 ? p->dx : std::min(p->dx, p->dy);
+    if (p->dim == 3) hmin = std::min(hmin, p->dz);
     rate = std::max(rate, km / (hmin * hmin) / cfl_diff);
   }
   return rate > 0.0 ? 1.0 / rate : INFINITY;
@@ -1101,6 +1424,28 @@ int ao_first_order_run(const ao_problem* p, double* ub, double T, double cfl, lo
 
 double ao_kappa_max(const ao_problem* p) { return kappa_max(make_model(p)); }
 
+// The dimension-generic fine-grid evaluation applied to a periodic 1D, 2D or 3D state in
+// the library's array order (1D: ub, P; 2D: ub, V, X, Y; 3D: by kind). For 1D and 2D it
+// restates the dedicated evaluations in another form; the two must agree.
+int ao_fe_generic(const ao_problem* p, double* const* in, double tau, const double* s_ext, double* const* out) {
+  if (!supported(*p) || p->bc != 0 || p->nodc) return -2;
+  Model m = make_model(p);
+  const int d = p->dim;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  const double h[3] = {p->dx, p->dy, p->dz};
+  const double* P[8] = {nullptr};
+  double* Po[8] = {nullptr};
+  // kind of each array after ub: 1D P -> 1; 2D V, X, Y -> 3, 1, 2; 3D by kind
+  const int kind2[4] = {0, 3, 1, 2};
+  for (int c = 1; c < (1 << d); ++c) {
+    const int k = d == 2 ? kind2[c] : c;
+    P[k] = in[c];
+    Po[k] = out[c];
+  }
+  fend<double>(m, d, n, h, in[0], P, tau, s_ext, out[0], Po);
+  return 0;
+}
+
 double ao_alpha_interval(const ao_problem* p, int dir, double a, double b) {
   return alpha_interval<double>(make_model(p), dir, a, b);
 }
@@ -1123,17 +1468,24 @@ void ao_rk54_coefs(double* alpha, double* beta) {
 // +,-,*,/ and exp counts one). out[0..4] = add, mul, div, exp, cmp.
 void ao_flop_count(const ao_problem* p, double* const* in, double tau, const double* s_ext, long long* out) {
   for (int k = 0; k < 5; ++k) out[k] = 0;
-  if (!supported(*p) || (p->dim == 2 && p->bc != 0)) return;   // periodic 2D and all 1D forms
+  if (!supported(*p) || (p->dim == 2 && p->bc != 0)) return;   // periodic 2D / 3D and all 1D forms
   Model m = make_model(p);
   g_flops = FlopCounter();
   size_t n = ncell(*p);
-  std::vector<Cnt> a[4], b[4], se;
+  std::vector<Cnt> a[8], b[8], se;
   for (int c = 0; c < ncomp(*p); ++c) {
     a[c].resize(comp_size(*p, c)); b[c].resize(comp_size(*p, c));
     for (size_t k = 0; k < a[c].size(); ++k) a[c][k] = Cnt(in[c][k]);
   }
   if (s_ext) { se.resize(n); for (size_t k = 0; k < n; ++k) se[k] = Cnt(s_ext[k]); }
-  if (p->dim == 1)
+  if (p->dim == 3) {
+    const int n[3] = {p->nx, p->ny, p->nz};
+    const Cnt h[3] = {Cnt(p->dx), Cnt(p->dy), Cnt(p->dz)};
+    const Cnt* P[8];
+    Cnt* Po[8];
+    for (int c = 1; c < 8; ++c) { P[c] = a[c].data(); Po[c] = b[c].data(); }
+    fend<Cnt>(m, 3, n, h, a[0].data(), P, Cnt(tau), s_ext ? se.data() : nullptr, b[0].data(), Po);
+  } else if (p->dim == 1)
     fe1d<Cnt>(m, a[0].data(), a[1].data(), Cnt(tau), s_ext ? se.data() : nullptr, b[0].data(), b[1].data());
   else
     fe2d<Cnt>(m, a[0].data(), a[1].data(), a[2].data(), a[3].data(), Cnt(tau), s_ext ? se.data() : nullptr,
