@@ -333,6 +333,8 @@ def initial_state(spec: Spec, device="cpu", sub: int = 4, order: int = 5):
     """Initial DoFs for the named workloads."""
     if spec.name == "linear1d":
         return sine_1d_state(spec, device=device)
+    if spec.name == "pme3d":
+        return state_3d(lambda x, y, z: barenblatt_3d(x, y, z, 1.0), spec, sub=sub, order=order)
     if spec.name == "evje_karlsen":
         return state_1d(evje_karlsen_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "strongly_degenerate1d":
@@ -448,6 +450,50 @@ def mode_3d_state(spec: Spec, k: float, shift: float = 1.0, amp: float = 1.0):
         ph = k * (x[None, None, :] + y[None, :, None] + z[:, None, None])
         out.append(shift + amp * (fac if s == 0 else 1.0) * torch.sin(ph))
     return out
+
+
+def state_3d(func: Callable, spec: Spec, sub: int = 2, order: int = 3) -> List[torch.Tensor]:
+    """Cell averages of func(x, y, z) by a tensor Gauss-Legendre rule on sub^3 sub-cells and
+    exact point values at every kind's location (8 arrays by kind, [nz][ny][nx])."""
+    gx, gw = _gauss(order)
+    offs, wts = [], []
+    for s_ in range(sub):
+        for q in range(order):
+            offs.append((s_ + 0.5 + 0.5 * gx[q]) / sub)
+            wts.append(gw[q] / (2 * sub))
+    i = torch.arange(spec.nx, dtype=torch.float64)
+    j = torch.arange(spec.ny, dtype=torch.float64)
+    k = torch.arange(spec.nz, dtype=torch.float64)
+    ub = torch.zeros((spec.nz, spec.ny, spec.nx), dtype=torch.float64)
+    for oz, wz in zip(offs, wts):
+        z = spec.z0 + (k + oz) * spec.dz
+        for oy, wy in zip(offs, wts):
+            y = spec.y0 + (j + oy) * spec.dy
+            for ox, wx in zip(offs, wts):
+                x = spec.x0 + (i + ox) * spec.dx
+                ub += wx * wy * wz * func(x[None, None, :], y[None, :, None], z[:, None, None])
+    out = [ub]
+    for s_, (sx, sy, sz) in enumerate(kind_offsets_3d()):
+        if s_ == 0:
+            continue
+        x = spec.x0 + (i + 0.5 + 0.5 * sx) * spec.dx
+        y = spec.y0 + (j + 0.5 + 0.5 * sy) * spec.dy
+        z = spec.z0 + (k + 0.5 + 0.5 * sz) * spec.dz
+        out.append(func(x[None, None, :], y[None, :, None], z[:, None, None]).expand(spec.nz, spec.ny, spec.nx).clone())
+    return out
+
+
+def barenblatt_3d(x, y, z, t: float):
+    """Barenblatt solution of u_t = Lap(u^2) in 3D: t^(-3/5) max(0, 1 - |x|^2 t^(-2/5) / 20)."""
+    r2 = x * x + y * y + z * z
+    return t ** (-0.6) * torch.clamp(1.0 - r2 * t ** (-0.4) / 20.0, min=0.0)
+
+
+def pme_3d(n: int = 32) -> Spec:
+    """Porous medium a = u^2 in 3D on [-6, 6]^3 (periodic; the Barenblatt support stays
+    inside), from the Barenblatt profile at t = 1."""
+    return Spec(dim=3, nx=n, ny=n, nz=n, x0=-6.0, x1=6.0, y0=-6.0, y1=6.0, z0=-6.0, z1=6.0, flux=("zero", ()),
+                diff=("pme", (2,)), umin=0.0, umax=1.0, limiter=True, rk=3, name="pme3d")
 
 
 def random_state_1d(spec: Spec, seed: int, lo: float | None = None, hi: float | None = None):

@@ -5,8 +5,8 @@
  *
  *      u_t + div f(u) = Laplace a(u),   a(u) = int kappa,  kappa >= 0      (Section 1)
  *
- * on periodic Cartesian meshes in 1D and 2D, on 1D intervals with Dirichlet or outflow
- * ends and on 2D rectangles with outflow ends (arXiv 2510.11527).
+ * on periodic Cartesian meshes in 1D, 2D and 3D, on 1D intervals with Dirichlet or
+ * outflow ends and on 2D rectangles with outflow ends (arXiv 2510.11527).
  *
  * Degrees of freedom (Section 2 for 1D, Section 4 / Fig. 2 for 2D). All arrays are
  * row-major [ny][nx] with i fastest; a periodic mesh stores nx*ny of each kind:
@@ -20,6 +20,11 @@
  * to the right end; ub keeps nx values. A 2D rectangle with outflow ends has
  * V [ny+1][nx+1] at (x0 + k dx, y0 + l dy), X [ny][nx+1] at (x0 + k dx, y_j) and
  * Y [ny+1][nx] at (x_i, y0 + l dy); ub keeps [ny][nx].
+ * 3D (periodic, [nz][ny][nx], i fastest; Section 4): 8 arrays ordered by the kind
+ * s = sx + 2 sy + 4 sz of the location (i + sx/2, j + sy/2, k + sz/2): the cell average
+ * (s = 0), then the x-face, y-face, xy-edge, z-face, xz-edge, yz-edge and corner values.
+ * They are passed through the *_arrays calls below (FP64; SSP-RK3 / SSP-RK(5,4); zero,
+ * linear (p0, p1, p2 velocities) or Burgers flux; blend off or plain).
  *
  * Conventions
  *   - Every call returns an af_status. On error the context is left unchanged and
@@ -93,11 +98,13 @@ enum { AF_RK_SSP3 = 3, AF_RK_SSP54 = 54 };
 enum { AF_BLEND_OFF = 0, AF_BLEND_PLAIN = 1, AF_BLEND_EXTERNAL = 2 };
 
 typedef struct {
-  int dim;
+  int dim;                /* 1, 2 or 3                                                     */
   int nx, ny;
   double x0, x1, y0, y1;
   int bc;                 /* AF_BC_*: DIRICHLET needs dim = 1; OUTFLOW dim 1 or 2; nx, ny >= 4 */
   double bc_left, bc_right; /* Dirichlet values at x0 and x1                               */
+  int nz;                 /* 3D: cells along z                                              */
+  double z0, z1;
 } af_grid;
 typedef struct { int kind; double p[4]; } af_flux;
 typedef struct { int kind; double p[4]; } af_diff;
@@ -119,8 +126,9 @@ typedef struct {
  * min/max of the first af_set_state. Returns AF_E_ARG for nx,ny < 1, dim not 1/2,
  * unknown kinds, umin >= umax, non-periodic ends with nx (or, in 2D, ny) < 4;
  * AF_E_UNSUPPORTED for Dirichlet ends or AF_FORM_NODC in 2D, AF_FORM_NODC with a
- * blend, and the external indicator with non-periodic ends; AF_E_OOM if allocation
- * fails. */
+ * blend, the external indicator with non-periodic ends, and in 3D anything but a
+ * periodic FP64 mesh with the zero, linear or Burgers flux, AF_FORM_DC and the blend off
+ * or plain; AF_E_OOM if allocation fails. */
 af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* diff,
                     const af_bounds_t* bounds, const af_opts* opts, af_ctx** out);
 af_status af_destroy(af_ctx* ctx);
@@ -142,6 +150,13 @@ af_status af_set_state(af_ctx* ctx, const double* ub, const double* V, const dou
  * exactly; the same array lengths as af_set_state). Synchronous with the context's
  * stream. */
 af_status af_get_state(af_ctx* ctx, double* ub, double* V, double* X, double* Y);
+
+/* The state as 2^dim arrays (narr must be 1 << dim): 1D ub, P; 2D ub, V, X, Y (as
+ * af_set_state); 3D the 8 arrays by kind. Same checks and ownership as af_set_state /
+ * af_get_state / af_device_ptrs; these are the only state calls of a 3D context. */
+af_status af_set_state_arrays(af_ctx* ctx, int narr, const double* const* arrays);
+af_status af_get_state_arrays(af_ctx* ctx, int narr, double* const* arrays);
+af_status af_device_ptrs_arrays(af_ctx* ctx, int narr, void** ptrs, int dtype[2]);
 
 /* Borrowed device pointers of the current state (ub, V, X, Y). dtype[0] is 8 (ub is
  * always FP64); dtype[1] is 8 or 4 for the point arrays. Valid until the next call that

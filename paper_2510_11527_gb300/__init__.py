@@ -28,16 +28,19 @@ class Solver:
     def __init__(self, spec, precision="fp64", rk=3, cfl=0.0, cfl_diff=0.0, bounds_from_data=False):
         self.spec = spec
         self.dim = spec.dim
-        self.n = spec.nx * (spec.ny if spec.dim == 2 else 1)
+        self.n = spec.nx * (spec.ny if spec.dim >= 2 else 1) * (spec.nz if spec.dim == 3 else 1)
         bc = getattr(spec, "bc", "periodic")
         gl, gr = getattr(spec, "bc_values", (0.0, 0.0))
         self.npts = self.n + (1 if spec.dim == 1 and bc != "periodic" else 0)
-        nx, ny = spec.nx, (spec.ny if spec.dim == 2 else 1)
+        nx, ny = spec.nx, (spec.ny if spec.dim >= 2 else 1)
         self.rect = spec.dim == 2 and bc != "periodic"
         self.shapes = ([(ny, nx), (ny + 1, nx + 1), (ny, nx + 1), (ny + 1, nx)] if self.rect
                        else [(ny, nx)] * 4 if spec.dim == 2 else [(nx,), (self.npts,)])
-        g = af_grid(spec.dim, spec.nx, spec.ny if spec.dim == 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1,
-                    capi.BC[bc], float(gl), float(gr))
+        if spec.dim == 3:
+            self.shapes = [(spec.nz, ny, nx)] * 8
+        g = af_grid(spec.dim, spec.nx, spec.ny if spec.dim >= 2 else 1, spec.x0, spec.x1, spec.y0, spec.y1,
+                    capi.BC[bc], float(gl), float(gr), spec.nz if spec.dim == 3 else 1,
+                    getattr(spec, "z0", 0.0), getattr(spec, "z1", 1.0))
         f = af_flux()
         f.kind = capi.FLUX[spec.flux[0]]
         for k, v in enumerate(spec.flux[1]):
@@ -72,6 +75,9 @@ class Solver:
     # state I/O
     def set_state(self, state):
         arrs = [np.asarray(a, dtype=np.float64) for a in state]
+        if self.dim == 3:
+            capi.af_set_state_arrays(self.ctx, arrs, [int(np.prod(s)) for s in self.shapes])
+            return
         if self.dim == 1:
             capi.af_set_state(self.ctx, self.n, arrs[0], arrs[1], npts=self.npts)
         else:
@@ -80,6 +86,10 @@ class Solver:
     def get_state(self, out=None):
         """Host copy of (ub, V, X, Y); `out` may supply the destination float64 arrays
         (for instance views of pinned host memory, which copy fastest)."""
+        if self.dim == 3:
+            flat = None if out is None else [np.asarray(a).reshape(-1) for a in out]
+            res = capi.af_get_state_arrays(self.ctx, [int(np.prod(s)) for s in self.shapes], flat)
+            return [a.reshape(sh) for a, sh in zip(res, self.shapes)]
         if self.dim == 1:
             flat = None if out is None else [np.asarray(a).reshape(-1) for a in out]
             return capi.af_get_state(self.ctx, self.n, 1, flat, npts=self.npts)
@@ -93,10 +103,15 @@ class Solver:
         average of cell (I-1, J-1), corner / edge values at its top-right)."""
         import torch
 
-        ptrs, (d0, d1) = capi.af_device_ptrs(self.ctx)
+        if self.dim == 3:
+            ptrs, (d0, d1) = capi.af_device_ptrs_arrays(self.ctx, 8)
+        else:
+            ptrs, (d0, d1) = capi.af_device_ptrs(self.ctx)
         shape = (self.spec.ny, self.spec.nx) if self.dim == 2 else (self.spec.nx,)
         if self.rect:
             shape = (self.spec.ny + 1, self.spec.nx + 1)
+        if self.dim == 3:
+            shape = (self.spec.nz, self.spec.ny, self.spec.nx)
         out = []
         for k, p in enumerate(ptrs):
             if p is None:

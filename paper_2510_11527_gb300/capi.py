@@ -31,7 +31,8 @@ class AfError(RuntimeError):
 class af_grid(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("x0", ctypes.c_double),
                 ("x1", ctypes.c_double), ("y0", ctypes.c_double), ("y1", ctypes.c_double), ("bc", ctypes.c_int),
-                ("bc_left", ctypes.c_double), ("bc_right", ctypes.c_double)]
+                ("bc_left", ctypes.c_double), ("bc_right", ctypes.c_double), ("nz", ctypes.c_int),
+                ("z0", ctypes.c_double), ("z1", ctypes.c_double)]
 
 
 class af_flux(ctypes.Structure):
@@ -73,6 +74,9 @@ def lib():
         "af_set_state": [_V, _D, _D, _D, _D],
         "af_get_state": [_V, _D, _D, _D, _D],
         "af_device_ptrs": [_V, ctypes.POINTER(_V), ctypes.POINTER(ctypes.c_int)],
+        "af_set_state_arrays": [_V, ctypes.c_int, ctypes.POINTER(_D)],
+        "af_get_state_arrays": [_V, ctypes.c_int, ctypes.POINTER(_D)],
+        "af_device_ptrs_arrays": [_V, ctypes.c_int, ctypes.POINTER(_V), ctypes.POINTER(ctypes.c_int)],
         "af_set_indicator": [_V, _D],
         "af_set_indicator_device": [_V, _V],
         "af_forward_euler": [_V, ctypes.c_double],
@@ -146,7 +150,7 @@ def lib():
 def exported_symbols():
     """Names of the entry points declared in include/af.h (for the export test)."""
     return ["af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_state", "af_get_state",
-            "af_device_ptrs", "af_set_indicator", "af_set_indicator_device", "af_forward_euler", "af_stage", "af_dt_device",
+            "af_device_ptrs", "af_set_state_arrays", "af_get_state_arrays", "af_device_ptrs_arrays", "af_set_indicator", "af_set_indicator_device", "af_forward_euler", "af_stage", "af_dt_device",
             "af_num_stages", "af_step", "af_run", "af_time", "af_mass", "af_bounds", "af_dt_cfl", "af_stats",
             "af_mass_noalloc", "af_batch_create", "af_batch_destroy", "af_batch_last_error", "af_batch_set_stream",
             "af_batch_info", "af_batch_set_tile", "af_batch_autotune", "af_batch_set_state", "af_batch_get_state",
@@ -370,6 +374,30 @@ def af_get_state(ctx, n, dim, out=None, npts=None, sizes=None):
     full = out + ([None, None] if dim == 1 else [])
     _check(ctx, lib().af_get_state(ctx, *[_dp(a) for a in full]))
     return out
+
+
+def af_set_state_arrays(ctx, arrays, sizes):
+    """The state as 2^dim host arrays (3D: the 8 arrays by kind), `sizes` values each."""
+    hs = [_host(a, n) for a, n in zip(arrays, sizes)]
+    ptrs = (_D * len(hs))(*[_dp(a) for a in hs])
+    _check(ctx, lib().af_set_state_arrays(ctx, len(hs), ptrs))
+
+
+def af_get_state_arrays(ctx, sizes, out=None):
+    out = [np.empty(n) for n in sizes] if out is None else list(out)
+    for a, n in zip(out, sizes):
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.size == n and a.flags.c_contiguous):
+            raise ValueError(f"out arrays must be C-contiguous float64 with {sizes} values")
+    ptrs = (_D * len(out))(*[_dp(a) for a in out])
+    _check(ctx, lib().af_get_state_arrays(ctx, len(out), ptrs))
+    return out
+
+
+def af_device_ptrs_arrays(ctx, narr):
+    ptrs = (_V * narr)()
+    dt = (ctypes.c_int * 2)()
+    _check(ctx, lib().af_device_ptrs_arrays(ctx, narr, ptrs, dt))
+    return [p for p in ptrs], (dt[0], dt[1])
 
 
 def af_device_ptrs(ctx):

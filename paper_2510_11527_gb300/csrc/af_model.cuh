@@ -121,7 +121,7 @@ __device__ __forceinline__ BLVals<T> bl_eval(const DevModel& m, T u) {
 template <int FLUX, class T>
 __device__ __forceinline__ T flux(const DevModel& m, int dir, T u) {
   if constexpr (FLUX == FLUX_LINEAR) {
-    return par<T>(m.fp, m.fpf, dir == 0 ? 0 : 1) * u;
+    return par<T>(m.fp, m.fpf, dir) * u;
   } else if constexpr (FLUX == FLUX_BURGERS) {
     return par<T>(m.fp, m.fpf, 0) * u * u;
   } else if constexpr (FLUX == FLUX_BL) {
@@ -135,7 +135,7 @@ __device__ __forceinline__ T flux(const DevModel& m, int dir, T u) {
 template <int FLUX, class T>
 __device__ __forceinline__ T dflux_abs(const DevModel& m, int dir, T u) {
   if constexpr (FLUX == FLUX_LINEAR) {
-    return tabs(par<T>(m.fp, m.fpf, dir == 0 ? 0 : 1));
+    return tabs(par<T>(m.fp, m.fpf, dir));
   } else if constexpr (FLUX == FLUX_BURGERS) {
     return tabs(T(2) * par<T>(m.fp, m.fpf, 0) * u);
   } else if constexpr (FLUX == FLUX_BL) {
@@ -214,7 +214,7 @@ __device__ __forceinline__ T kappa_fn(const DevModel& m, T u) {
 template <int FLUX, class T>
 __device__ __forceinline__ T alpha_interval_pre(const DevModel& m, int dir, T a, T b, T da, T db) {
   if constexpr (FLUX == FLUX_LINEAR) {
-    return tabs(par<T>(m.fp, m.fpf, dir == 0 ? 0 : 1));
+    return tabs(par<T>(m.fp, m.fpf, dir));
   } else if constexpr (FLUX == FLUX_BURGERS) {
     return tabs(T(2) * par<T>(m.fp, m.fpf, 0)) * tmax(tabs(a), tabs(b));
   } else if constexpr (FLUX == FLUX_BL) {

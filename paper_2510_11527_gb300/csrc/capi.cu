@@ -25,9 +25,12 @@ namespace {
 // 0.9 x the linear stability limit kappa dt / h^2 of the unlimited scheme for pure
 // diffusion: 1D from the von Neumann analysis of Section 3.2 (0.157 SSP-RK3, 0.333
 // SSP-RK(5,4)); 2D from the 4x4 Fourier symbol of the 2D scheme, whose spectral radius
-// is 40.78 kappa/h^2 (0.0616 SSP-RK3, 0.1307 SSP-RK(5,4)).
+// is 40.78 kappa/h^2 (0.0616 SSP-RK3, 0.1307 SSP-RK(5,4)); 3D from its 8x8 symbol.
 double default_cfl_diff(int dim, int rk) {
   if (dim == 1) return 0.9 * (rk == AF_RK_SSP54 ? 0.333 : 0.157);
+  // 3D: spectral radius 63.335 kappa/h^2 of the 8x8 symbol; SSP-RK3 / SSP-RK(5,4)
+  // stability intervals 2.5127 / 5.330 on the negative real axis
+  if (dim == 3) return 0.9 * (rk == AF_RK_SSP54 ? 5.330 : 2.5127) / 63.335;
   return 0.9 * (rk == AF_RK_SSP54 ? 0.1307 : 0.0616);
 }
 
@@ -141,70 +144,109 @@ cudaError_t launch<float>(af_ctx* c, const StageArgs2D<float>& a) {
   return af::launch_stage2d_f32(c->flux.kind, c->opts.blend != AF_BLEND_OFF, c->m, a, c->stream);
 }
 
-// stage k of the configured scheme (buffer roles in the comments of af_stage)
-template <class PT>
-af_status stage_impl(af_ctx* c, int k) {
-  const int sg = 1;
+// Buffer roles of stage k of the configured scheme (see af_stage): the input buffer and
+// one or two outputs out = cA * U[aidx] + cF * FE(U[in], tcoef * dt) -> U[oidx]; sg:
+// apply the post-stage safeguard. Returns the number of outputs (0: k out of range).
+struct OutSpec {
+  int oidx;
+  double cA;
+  int aidx;
+  double cF, tcoef;
+  int sg;
+};
+int stage_plan(const af_ctx* c, int k, int* in, OutSpec out[2]) {
   if (c->opts.rk == AF_RK_SSP3) {
-    if (k == 0) {
-      auto a = base_args<PT>(c, 0);
-      set_out<PT>(c, a, 0, 1, 0.0, -1, 1.0, 1.0, sg);
-      CK(c, launch<PT>(c, a));
-    } else if (k == 1) {
-      auto a = base_args<PT>(c, 1);
-      set_out<PT>(c, a, 0, 2, 0.75, 0, 0.25, 1.0, sg);
-      CK(c, launch<PT>(c, a));
-    } else if (k == 2) {
-      auto a = base_args<PT>(c, 2);
-      set_out<PT>(c, a, 0, 0, 1.0 / 3.0, 0, 2.0 / 3.0, 1.0, sg);
-      CK(c, launch<PT>(c, a));
-    } else {
-      FAIL(c, AF_E_ARG, "stage %d out of range", k);
-    }
-    return AF_OK;
+    if (k == 0) { *in = 0; out[0] = {1, 0.0, -1, 1.0, 1.0, 1}; return 1; }
+    if (k == 1) { *in = 1; out[0] = {2, 0.75, 0, 0.25, 1.0, 1}; return 1; }
+    if (k == 2) { *in = 2; out[0] = {0, 1.0 / 3.0, 0, 2.0 / 3.0, 1.0, 1}; return 1; }
+    return 0;
   }
   const double(*A)[5] = af::kA54;
   const double(*B)[5] = af::kB54;
   switch (k) {
-    case 0: {
-      auto a = base_args<PT>(c, 0);
-      set_out<PT>(c, a, 0, 1, 0.0, -1, A[0][0], B[0][0] / A[0][0], sg);
-      CK(c, launch<PT>(c, a));
-      break;
-    }
-    case 1: {
-      auto a = base_args<PT>(c, 1);
-      set_out<PT>(c, a, 0, 2, A[1][0], 0, A[1][1], B[1][1] / A[1][1], sg);
-      CK(c, launch<PT>(c, a));
-      break;
-    }
-    case 2: {
-      auto a = base_args<PT>(c, 2);
-      set_out<PT>(c, a, 0, 3, A[2][0], 0, A[2][2], B[2][2] / A[2][2], sg);
-      CK(c, launch<PT>(c, a));
-      break;
-    }
-    case 3: {
+    case 0: *in = 0; out[0] = {1, 0.0, -1, A[0][0], B[0][0] / A[0][0], 1}; return 1;
+    case 1: *in = 1; out[0] = {2, A[1][0], 0, A[1][1], B[1][1] / A[1][1], 1}; return 1;
+    case 2: *in = 2; out[0] = {3, A[2][0], 0, A[2][2], B[2][2] / A[2][2], 1}; return 1;
+    case 3:
       // u^(4) = a30 u0 + a33 FE(u3); partial = a42 u2 + a43 FE(u3, own ratio) in place
-      auto a = base_args<PT>(c, 3);
-      set_out<PT>(c, a, 0, 1, A[3][0], 0, A[3][3], B[3][3] / A[3][3], sg);
-      set_out<PT>(c, a, 1, 2, A[4][2], 2, A[4][3], B[4][3] / A[4][3], 0);
-      CK(c, launch<PT>(c, a));
-      break;
-    }
-    case 4: {
-      auto a = base_args<PT>(c, 1);
-      set_out<PT>(c, a, 0, 0, 1.0, 2, A[4][4], B[4][4] / A[4][4], sg);
-      CK(c, launch<PT>(c, a));
-      break;
-    }
-    default:
-      FAIL(c, AF_E_ARG, "stage %d out of range", k);
+      *in = 3;
+      out[0] = {1, A[3][0], 0, A[3][3], B[3][3] / A[3][3], 1};
+      out[1] = {2, A[4][2], 2, A[4][3], B[4][3] / A[4][3], 0};
+      return 2;
+    case 4: *in = 1; out[0] = {0, 1.0, 2, A[4][4], B[4][4] / A[4][4], 1}; return 1;
+    default: return 0;
   }
+}
+
+// stage k of the configured scheme
+template <class PT>
+af_status stage_impl(af_ctx* c, int k) {
+  int in = 0;
+  OutSpec out[2];
+  const int nout = stage_plan(c, k, &in, out);
+  if (nout == 0) FAIL(c, AF_E_ARG, "stage %d out of range", k);
+  auto a = base_args<PT>(c, in);
+  for (int o = 0; o < nout; ++o) set_out<PT>(c, a, o, out[o].oidx, out[o].cA, out[o].aidx, out[o].cF, out[o].tcoef, out[o].sg);
+  CK(c, launch<PT>(c, a));
   return AF_OK;
 }
 
+// the 3D stage arguments for input buffer `in` (outputs added by the caller)
+af::StageArgs3D args3d(af_ctx* c, int in) {
+  af::StageArgs3D a;
+  std::memset(&a, 0, sizeof(a));
+  a.n[0] = c->nx;
+  a.n[1] = c->ny;
+  a.n[2] = c->nz;
+  a.inv_h[0] = c->inv_h1;
+  a.inv_h[1] = c->inv_h2;
+  a.inv_h[2] = c->inv_h3;
+  for (int s = 0; s < 8; ++s) a.in[s] = c->k3[in][s];
+  a.dt = c->dt_dev;
+  a.limiter = c->opts.limiter;
+  a.blend = c->opts.blend;
+  a.gamma = c->opts.gamma;
+  a.tol = c->tol;
+  a.stats = c->stats;
+  a.C = c->scr3[0];
+  for (int l = 0; l < 3; ++l) {
+    a.FH[l] = c->scr3[1 + l];
+    a.AH[l] = c->scr3[4 + l];
+    a.FL[l] = c->scr3[7 + l];
+    a.S[l] = c->scr3[10 + l];
+    a.Flim[l] = c->scr3[13 + l];
+    a.Alim[l] = c->scr3[16 + l];
+  }
+  return a;
+}
+
+af_status stage3d_out(af_ctx* c, int in, const OutSpec* out, int nout) {
+  af::StageArgs3D a = args3d(c, in);
+  a.nout = nout;
+  for (int o = 0; o < nout; ++o) {
+    a.tcoef[o] = out[o].tcoef;
+    a.cA[o] = out[o].cA;
+    a.cF[o] = out[o].cF;
+    a.sg[o] = out[o].sg;
+    for (int s = 0; s < 8; ++s) {
+      a.A[o][s] = out[o].aidx >= 0 ? c->k3[out[o].aidx][s] : nullptr;
+      a.O[o][s] = c->k3[out[o].oidx][s];
+    }
+  }
+  CK(c, af::launch_stage3d_f64(c->flux.kind, c->m, a, c->stream));
+  return AF_OK;
+}
+
+af_status stage3d_impl(af_ctx* c, int k) {
+  int in = 0;
+  OutSpec out[2];
+  const int nout = stage_plan(c, k, &in, out);
+  if (nout == 0) FAIL(c, AF_E_ARG, "stage %d out of range", k);
+  return stage3d_out(c, in, out, nout);
+}
+
 af_status stage_any(af_ctx* c, int k) {
+  if (c->dim == 3) return stage3d_impl(c, k);
   return c->prec == AF_PREC_FP64 ? stage_impl<double>(c, k) : stage_impl<float>(c, k);
 }
 
@@ -220,6 +262,15 @@ cudaError_t launch_rate(af_ctx* c) {
 // device CFL step -> *dst (no host round trip); t_acc: advance the device time
 af_status dt_device(af_ctx* c, double* dst, double* t_acc, double t_end = -1.0, double* count = nullptr) {
   cudaError_t e;
+  if (c->dim == 3) {
+    CK(c, af::launch_rate3d(c->flux.kind, c->m, args3d(c, 0), c->kmax, c->rate_bits, c->stream));
+    const double hmin = std::min(c->dx, std::min(c->dy, c->dz));
+    // no interior extrema of f_l' in 3D: the finalize step adds no extremum terms (dim 0)
+    af::dt_finalize_kernel<<<1, 1, 0, c->stream>>>(c->rate_bits, c->m, 0, c->inv_h1, c->inv_h2, c->cfl, c->cfl_diff,
+                                                   c->kmax, 1.0 / (hmin * hmin), dst, t_acc, t_end, count);
+    CK(c, cudaGetLastError());
+    return AF_OK;
+  }
   switch (c->flux.kind) {
     case AF_FLUX_ZERO: e = launch_rate<af::FLUX_ZERO>(c); break;
     case AF_FLUX_LINEAR: e = launch_rate<af::FLUX_LINEAR>(c); break;
@@ -274,9 +325,11 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   *out = nullptr;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return AF_E_UNSUPPORTED;
-  if (grid->dim != 1 && grid->dim != 2) return AF_E_ARG;
-  if (grid->nx < 1 || (grid->dim == 2 && grid->ny < 1)) return AF_E_ARG;
-  if (!(grid->x1 > grid->x0) || (grid->dim == 2 && !(grid->y1 > grid->y0))) return AF_E_ARG;
+  if (grid->dim < 1 || grid->dim > 3) return AF_E_ARG;
+  if (grid->nx < 1 || (grid->dim >= 2 && grid->ny < 1) || (grid->dim == 3 && grid->nz < 1)) return AF_E_ARG;
+  if (!(grid->x1 > grid->x0) || (grid->dim >= 2 && !(grid->y1 > grid->y0)) ||
+      (grid->dim == 3 && !(grid->z1 > grid->z0)))
+    return AF_E_ARG;
   if (flux->kind < AF_FLUX_ZERO || flux->kind > AF_FLUX_BL) return AF_E_ARG;
   if (diff->kind < AF_DIFF_NONE || diff->kind > AF_DIFF_RAMP) return AF_E_ARG;
   if (diff->kind == AF_DIFF_PME && (diff->p[0] < 1.0 || diff->p[0] != std::floor(diff->p[0]))) return AF_E_ARG;
@@ -287,6 +340,9 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   if (grid->bc != AF_BC_PERIODIC && (grid->nx < 4 || (grid->dim == 2 && grid->ny < 4))) return AF_E_ARG;
   if (opts->diffusion_form == AF_FORM_NODC && (grid->dim != 1 || opts->blend != AF_BLEND_OFF)) return AF_E_UNSUPPORTED;
   if (grid->bc != AF_BC_PERIODIC && opts->blend == AF_BLEND_EXTERNAL) return AF_E_UNSUPPORTED;
+  if (grid->dim == 3 && (grid->bc != AF_BC_PERIODIC || flux->kind == AF_FLUX_BL || opts->precision != AF_PREC_FP64 ||
+                         opts->blend == AF_BLEND_EXTERNAL || opts->diffusion_form != AF_FORM_DC))
+    return AF_E_UNSUPPORTED;
   if (!bounds->from_initial_data && !(bounds->umax > bounds->umin)) return AF_E_ARG;
   if (opts->precision != AF_PREC_FP64 && opts->precision != AF_PREC_FP32_MIXED) return AF_E_ARG;
   if (opts->rk != AF_RK_SSP3 && opts->rk != AF_RK_SSP54) return AF_E_ARG;
@@ -301,8 +357,9 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->opts = *opts;
   c->dim = grid->dim;
   c->nx = grid->nx;
-  c->ny = grid->dim == 2 ? grid->ny : 1;
-  c->n = (size_t)c->nx * c->ny;
+  c->ny = grid->dim >= 2 ? grid->ny : 1;
+  c->nz = grid->dim == 3 ? grid->nz : 1;
+  c->n = (size_t)c->nx * c->ny * c->nz;
   c->np = c->n + (grid->dim == 1 && grid->bc != AF_BC_PERIODIC ? 1 : 0);
   const bool rect = grid->dim == 2 && grid->bc != AF_BC_PERIODIC;
   c->pnx = c->nx + (rect ? 1 : 0);
@@ -311,9 +368,11 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->prec = opts->precision;
   c->nbuf = opts->rk == AF_RK_SSP54 ? 4 : 3;
   c->dx = (grid->x1 - grid->x0) / grid->nx;
-  c->dy = grid->dim == 2 ? (grid->y1 - grid->y0) / grid->ny : 1.0;
+  c->dy = grid->dim >= 2 ? (grid->y1 - grid->y0) / grid->ny : 1.0;
+  c->dz = grid->dim == 3 ? (grid->z1 - grid->z0) / grid->nz : 1.0;
   c->inv_h1 = 1.0 / c->dx;
-  c->inv_h2 = grid->dim == 2 ? 1.0 / c->dy : 0.0;
+  c->inv_h2 = grid->dim >= 2 ? 1.0 / c->dy : 0.0;
+  c->inv_h3 = grid->dim == 3 ? 1.0 / c->dz : 0.0;
   c->cfl = opts->cfl > 0.0 ? opts->cfl : 0.33 / grid->dim;
   c->cfl_diff = opts->cfl_diff > 0.0 ? opts->cfl_diff : (opts->cfl_diff < 0.0 ? 0.0 : default_cfl_diff(c->dim, opts->rk));
   std::memset(&c->m, 0, sizeof(c->m));
@@ -332,9 +391,12 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   const size_t ps = pt_size(c);
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t ulen = rect ? c->pn : c->n, plen = rect ? c->pn : c->np;
-  const size_t per_state = al(ulen * 8) + 3 * al(plen * ps);
+  const bool d3 = grid->dim == 3;
+  // 3D: 8 FP64 arrays per state and 19 scratch arrays of the 3D stage
+  const size_t per_state = d3 ? 8 * al(c->n * 8) : al(ulen * 8) + 3 * al(plen * ps);
+  const size_t scr3 = d3 ? 19 * al(c->n * 8) : 0;
   const size_t scratch = al(8) * 2 + al(8 * 8) + al(8 * af::RED_MAX_BLOCKS) + al(8) + al(sizeof(DevStats)) + al(c->n * 8);
-  const size_t total = per_state * c->nbuf + scratch;
+  const size_t total = per_state * c->nbuf + scratch + scr3;
   if (cudaMalloc(&c->block, total) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -342,6 +404,14 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   }
   unsigned char* p = c->block;
   for (int b = 0; b < c->nbuf; ++b) {
+    if (d3) {
+      for (int s = 0; s < 8; ++s) { c->k3[b][s] = (double*)p; p += al(c->n * 8); }
+      c->ub[b] = c->k3[b][0];
+      c->pv[b] = c->k3[b][1];
+      c->px[b] = c->k3[b][2];
+      c->py[b] = c->k3[b][3];
+      continue;
+    }
     c->ub[b] = (double*)p; p += al(ulen * 8);
     c->pv[b] = p; p += al(plen * ps);
     c->px[b] = p; p += al(plen * ps);
@@ -354,6 +424,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->rate_bits = (unsigned long long*)p; p += al(16);
   c->stats = (DevStats*)p; p += al(sizeof(DevStats));
   c->s_ext = (double*)p; p += al(c->n * 8);
+  for (int k = 0; d3 && k < 19; ++k) { c->scr3[k] = (double*)p; p += al(c->n * 8); }
   if (cudaMemset(c->block, 0, total) != cudaSuccess || cudaMallocHost(&c->host_pinned, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->block);
@@ -386,6 +457,7 @@ int af_num_stages(const af_ctx* c) { return !c ? 0 : (c->opts.rk == AF_RK_SSP54 
 
 af_status af_set_state(af_ctx* c, const double* ub, const double* V, const double* X, const double* Y) {
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
+  if (c->dim == 3) FAIL(c, AF_E_ARG, "a 3D state has 8 arrays: use af_set_state_arrays");
   const int na = c->dim == 2 ? 4 : 2;
   const double* src[4] = {ub, V, X, Y};
   size_t sz[4], off[5] = {0, 0, 0, 0, 0};
@@ -441,6 +513,7 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
 
 af_status af_get_state(af_ctx* c, double* ub, double* V, double* X, double* Y) {
   if (!c || !ub || !V || (c->dim == 2 && (!X || !Y))) return AF_E_ARG;
+  if (c->dim == 3) FAIL(c, AF_E_ARG, "a 3D state has 8 arrays: use af_get_state_arrays");
   const int na = c->dim == 2 ? 4 : 2;
   double* dst[4] = {ub, V, X, Y};
   if (is_rect(c)) {
@@ -481,6 +554,67 @@ af_status af_get_state(af_ctx* c, double* ub, double* V, double* X, double* Y) {
   return AF_OK;
 }
 
+af_status af_set_state_arrays(af_ctx* c, int narr, const double* const* arrays) {
+  if (!c || !arrays || narr != (1 << c->dim)) return AF_E_ARG;
+  for (int a = 0; a < narr; ++a)
+    if (!arrays[a]) return AF_E_ARG;
+  if (c->dim == 1) return af_set_state(c, arrays[0], arrays[1], nullptr, nullptr);
+  if (c->dim == 2) return af_set_state(c, arrays[0], arrays[1], arrays[2], arrays[3]);
+  // 3D (FP64): stage the 8 arrays in the RK temporaries, check them there, then copy
+  const size_t n = c->n;
+  double* stg = c->k3[1][0];   // buffers 1.. are contiguous: 8 n doubles per buffer
+  for (int a = 0; a < 8; ++a)
+    CK(c, cudaMemcpyAsync(stg + a * n, arrays[a], n * 8, cudaMemcpyHostToDevice, c->stream));
+  const size_t total = 8 * n;
+  const int nb = (int)std::min<size_t>(af::STATE_IO_BLOCKS, (total + af::RED_THREADS - 1) / af::RED_THREADS);
+  af::validate_partial_kernel<<<nb, af::RED_THREADS, 0, c->stream>>>(stg, total, (unsigned long long*)c->partial);
+  CK(c, cudaGetLastError());
+  af::validate_final_kernel<<<1, af::RED_THREADS, 0, c->stream>>>((const unsigned long long*)c->partial, nb, c->red + 5);
+  CK(c, cudaGetLastError());
+  CK(c, cudaMemcpyAsync(c->host_pinned, c->red + 5, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  const double nan = c->host_pinned[0], lo = c->host_pinned[1], hi = c->host_pinned[2];
+  if (nan > 0.0) FAIL(c, AF_E_STATE, "NaN in the input arrays (%.0f values)", nan);
+  if (c->bounds_pending) {
+    if (!(hi > lo)) FAIL(c, AF_E_STATE, "bounds from initial data need max > min");
+    c->m.umin = lo;
+    c->m.umax = hi;
+    c->kmax = af::kappa_max_of(c->diff, lo, hi);
+    c->tol = 8.0 * 2.220446049250313e-16 * std::max(std::fabs(lo), std::fabs(hi));
+    c->bounds_pending = false;
+  } else if (c->opts.limiter && (lo < c->m.umin || hi > c->m.umax)) {
+    FAIL(c, AF_E_STATE, "input outside [umin, umax]: [%g, %g]", lo, hi);
+  }
+  for (int a = 0; a < 8; ++a)
+    CK(c, cudaMemcpyAsync(c->k3[0][a], stg + a * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  return AF_OK;
+}
+
+af_status af_get_state_arrays(af_ctx* c, int narr, double* const* arrays) {
+  if (!c || !arrays || narr != (1 << c->dim)) return AF_E_ARG;
+  for (int a = 0; a < narr; ++a)
+    if (!arrays[a]) return AF_E_ARG;
+  if (c->dim == 1) return af_get_state(c, arrays[0], arrays[1], nullptr, nullptr);
+  if (c->dim == 2) return af_get_state(c, arrays[0], arrays[1], arrays[2], arrays[3]);
+  for (int a = 0; a < 8; ++a)
+    CK(c, cudaMemcpyAsync(arrays[a], c->k3[0][a], c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  return AF_OK;
+}
+
+af_status af_device_ptrs_arrays(af_ctx* c, int narr, void** ptrs, int dtype[2]) {
+  if (!c || !ptrs || narr != (1 << c->dim)) return AF_E_ARG;
+  if (c->dim < 3) {
+    void* p4[4];
+    af_status s = af_device_ptrs(c, p4, dtype);
+    for (int a = 0; a < narr; ++a) ptrs[a] = p4[a];
+    return s;
+  }
+  for (int a = 0; a < 8; ++a) ptrs[a] = c->k3[0][a];
+  if (dtype) { dtype[0] = 8; dtype[1] = 8; }
+  return AF_OK;
+}
+
 af_status af_device_ptrs(af_ctx* c, void* ptrs[4], int dtype[2]) {
   if (!c || !ptrs) return AF_E_ARG;
   ptrs[0] = c->ub[0];
@@ -510,7 +644,11 @@ af_status af_forward_euler(af_ctx* c, double tau) {
   if (c->bounds_pending) FAIL(c, AF_E_STATE, "state not set");
   af_status s = set_dt(c, tau, false);
   if (s != AF_OK) return s;
-  if (c->prec == AF_PREC_FP64) {
+  if (c->dim == 3) {
+    const OutSpec out = {1, 0.0, -1, 1.0, 1.0, 0};
+    s = stage3d_out(c, 0, &out, 1);
+    if (s != AF_OK) return s;
+  } else if (c->prec == AF_PREC_FP64) {
     auto a = base_args<double>(c, 0);
     set_out<double>(c, a, 0, 1, 0.0, -1, 1.0, 1.0, 0);
     CK(c, launch<double>(c, a));
@@ -612,12 +750,22 @@ af_status af_mass(af_ctx* c, double* mass) {
   double v;
   s = read_scalar(c, c->red + 1, &v);
   if (s != AF_OK) return s;
-  *mass = v * c->dx * c->dy;
+  *mass = v * c->dx * c->dy * c->dz;   // dz = 1 below 3D
   return AF_OK;
 }
 
 af_status af_bounds(af_ctx* c, double* umin, double* umax) {
   if (!c || !umin || !umax) return AF_E_ARG;
+  if (c->dim == 3) {
+    for (int op = 1; op <= 2; ++op)
+      for (int a = 0; a < 8; ++a) {
+        af_status s = reduce_array<double>(c, c->k3[0][a], c->n, op, op == 1 ? INFINITY : -INFINITY, c->red + 1 + op, a > 0);
+        if (s != AF_OK) return s;
+      }
+    af_status s = read_scalar(c, c->red + 2, umin);
+    if (s != AF_OK) return s;
+    return read_scalar(c, c->red + 3, umax);
+  }
   const int na = c->dim == 2 ? 4 : 2;
   void* arrs[4] = {c->ub[0], c->pv[0], c->px[0], c->py[0]};
   for (int op = 1; op <= 2; ++op) {
@@ -660,7 +808,7 @@ af_status af_stats(af_ctx* c, long long* clamps, long long* errors, double* max_
     std::memcpy(&v, &st.max_excess_bits, sizeof(v));
     *max_excess = v;
   }
-  if (mass_adjust) *mass_adjust = st.ub_adjust * c->dx * c->dy;
+  if (mass_adjust) *mass_adjust = st.ub_adjust * c->dx * c->dy * c->dz;
   return AF_OK;
 }
 

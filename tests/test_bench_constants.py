@@ -51,3 +51,15 @@ def test_bytes_per_cell_stage_1d():
     arrays = (2 + 3 + 3) / 3     # SSP-RK3 state passes per stage; a cell owns ub and one point
     assert np.isclose(bench.BYTES_PER_CELL_STAGE_1D["fp64"], round(arrays * 2 * 8, 2), atol=0.01)
     assert np.isclose(bench.BYTES_PER_CELL_STAGE_1D["fp32_mixed"], arrays * (8 + 4))
+
+
+def test_constants_3d():
+    import af_inputs as ai
+    import bench
+    import oracle
+    assert np.isclose(bench.BYTES_PER_CELL_STAGE_3D, round((2 + 3 + 3) / 3 * 8 * 8, 2), atol=0.01)
+    spec = ai.pme_3d(24)
+    st = [a.numpy() for a in ai.initial_state(spec, sub=2, order=3)]
+    fc = oracle.flop_count(spec, st, 0.3 * oracle.dt_cfl(spec, st[0]))
+    per_cell = (fc["add"] + fc["mul"] + fc["div"] + fc["exp"]) / spec.cells
+    assert abs(per_cell - bench.FLOPS_PER_CELL_STAGE_3D_ORACLE) < 0.01
