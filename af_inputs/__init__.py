@@ -73,7 +73,7 @@ class Spec:
 
     @property
     def dy(self) -> float:
-        return (self.y1 - self.y0) / self.ny if self.dim == 2 else 1.0
+        return (self.y1 - self.y0) / self.ny if self.dim >= 2 else 1.0
 
     @property
     def dz(self) -> float:

@@ -607,6 +607,23 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
     split(f, kind, qq);
     return kind == 0 ? C[qq] : P[kind][qq];
   };
+  // pointwise nonlinearities at every fine location, evaluated once: f_l, f_l', a per
+  // kind (kind 0: at the recovered centres)
+  std::vector<R> Pf[8][3], Pd[8][3], Pa[8];
+  for (int s = 0; s < nk; ++s) {
+    const R* z = s == 0 ? C.data() : P[s];
+    Pa[s].resize(N);
+    for (int l = 0; l < d; ++l) { Pf[s][l].resize(N); Pd[s][l].resize(N); }
+    for (size_t q = 0; q < N; ++q) {
+      Pa[s][q] = apot<R>(m, z[q]);
+      for (int l = 0; l < d; ++l) { Pf[s][l][q] = flux<R>(m, l, z[q]); Pd[s][l][q] = dflux<R>(m, l, z[q]); }
+    }
+  }
+  auto at = [&](const int* f, int& kind) {
+    size_t qq;
+    split(f, kind, qq);
+    return qq;
+  };
   std::vector<R> fU[3], aU(N);
   for (int l = 0; l < d; ++l) fU[l].resize(N);
   for (size_t q = 0; q < N; ++q) {
@@ -643,8 +660,10 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
         for (int t = 0; t < 3; ++t) { fm[t] = f[t]; fp[t] = f[t]; }
         fm[l] -= 1;
         fp[l] += 1;
-        fs = fs + wgt * flux<R>(m, l, Z(fp));   // face point at fine 2i + 1 along l
-        R ahat = (-apot<R>(m, Z(fm)) + R(8.0) * apot<R>(m, Z(f)) - apot<R>(m, Z(fp))) / R(6.0);
+        int kp, km, k0;
+        const size_t qp = at(fp, kp), qm = at(fm, km), q0 = at(f, k0);
+        fs = fs + wgt * Pf[kp][l][qp];   // face point at fine 2i + 1 along l
+        R ahat = (-Pa[km][qm] + R(8.0) * Pa[k0][q0] - Pa[kp][qp]) / R(6.0);
         as = as + wgt * ahat;
         tot6 = tot;
       });
@@ -667,10 +686,12 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
         for (int t = 0; t < 5; ++t) {
           int f[3] = {f0[0], f0[1], f0[2]};
           f[l] += t - 2;
+          int kt;
+          const size_t qt = at(f, kt);
           z[t] = Z(f);
-          fl[t] = flux<R>(m, l, z[t]);
-          df[t] = dflux<R>(m, l, z[t]);
-          a[t] = apot<R>(m, z[t]);
+          fl[t] = Pf[kt][l][qt];
+          df[t] = Pd[kt][l][qt];
+          a[t] = Pa[kt][qt];
         }
         RH[s][l][q] = line_residual<R>(z, fl, df, a, h[l]);
       }
