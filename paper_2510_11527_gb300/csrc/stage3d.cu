@@ -43,33 +43,27 @@ __device__ __forceinline__ size_t shift3(const StageArgs3D& A, size_t q, int l, 
   return cell3(A, c);
 }
 
-// kind and cell of a fine index
-__device__ __forceinline__ int split3(const StageArgs3D& A, const int* f, size_t& q) {
-  int c[3], kind = 0;
-  for (int l = 0; l < 3; ++l) {
-    const int w = wrapi(f[l], 2 * A.n[l]);
-    c[l] = w >> 1;
-    kind |= (w & 1) << l;
-  }
-  q = ((size_t)c[2] * A.n[1] + c[1]) * A.n[0] + c[0];
-  return kind;
-}
-
-// value at a fine index: the recovered centre for kind 0, else the point value
-__device__ __forceinline__ double zfine(const StageArgs3D& A, const int* f) {
-  size_t q;
-  const int kind = split3(A, f, q);
-  return kind == 0 ? A.C[q] : A.in[kind][q];
-}
-
-// the same with a centre replaced by its cell average (kind 0 of the input is ub)
-__device__ __forceinline__ double zfine_avg(const StageArgs3D& A, const int* f) {
-  size_t q;
-  const int kind = split3(A, f, q);
-  return A.in[kind][q];
-}
-
 __device__ __forceinline__ double w1(int m) { return m == 0 ? 4.0 : 1.0; }
+
+// The wrapped fine coordinates of offsets -2 .. +3 from the cell's fine origin 2c along
+// each axis, formed once per cell: a fine access is then two shifts and a lookup.
+struct FineAxes {
+  int f[3][6];
+};
+__device__ __forceinline__ FineAxes fine_axes(const StageArgs3D& A, const int* c) {
+  FineAxes fa;
+  for (int l = 0; l < 3; ++l)
+    for (int o = 0; o < 6; ++o) fa.f[l][o] = wrapi(2 * c[l] + o - 2, 2 * A.n[l]);
+  return fa;
+}
+// fine value at offsets (ox, oy, oz) in [-2, 3] from 2c: kind 0 is the recovered centre,
+// or the cell average when avg is set (the low-order neighbours of the blend)
+__device__ __forceinline__ double zoff(const StageArgs3D& A, const FineAxes& fa, int ox, int oy, int oz, bool avg = false) {
+  const int fx = fa.f[0][ox + 2], fy = fa.f[1][oy + 2], fz = fa.f[2][oz + 2];
+  const int kind = (fx & 1) | ((fy & 1) << 1) | ((fz & 1) << 2);
+  const size_t q = ((size_t)(fz >> 1) * A.n[1] + (fy >> 1)) * A.n[0] + (fx >> 1);
+  return (kind == 0 && !avg) ? A.C[q] : A.in[kind][q];
+}
 
 __global__ void __launch_bounds__(T3) centre3d_kernel(const StageArgs3D A) {
   if (*A.dt == 0.0) return;
@@ -77,13 +71,13 @@ __global__ void __launch_bounds__(T3) centre3d_kernel(const StageArgs3D A) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N; q += (size_t)gridDim.x * blockDim.x) {
     int c[3];
     decode3(A, q, c);
+    const FineAxes fa = fine_axes(A, c);
     double acc = 0.0;
     for (int o = 0; o < 27; ++o) {
       const int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
       if (mm[0] == 0 && mm[1] == 0 && mm[2] == 0) continue;
       const double w = (1.0 * w1(mm[0])) * w1(mm[1]) * w1(mm[2]);
-      const int f[3] = {2 * c[0] + mm[0], 2 * c[1] + mm[1], 2 * c[2] + mm[2]};
-      acc = acc + w * zfine(A, f);
+      acc = acc + w * zoff(A, fa, mm[0], mm[1], mm[2]);
     }
     A.C[q] = (216.0 * A.in[0][q] - acc) / 64.0;
   }
@@ -97,7 +91,16 @@ __global__ void __launch_bounds__(T3) cellq3d_kernel(const DevModel m, const Sta
     int c[3];
     decode3(A, q, c);
     const double u = A.in[0][q];
+    // the cell's Simpson block: fine offsets {-1, 0, 1}^3 around 2c (index o = mx + 1 +
+    // 3 (my + 1) + 9 (mz + 1)), with a(z) evaluated once per location
+    const FineAxes fa = fine_axes(A, c);
+    double zb[27], ab[27];
+    for (int o = 0; o < 27; ++o) {
+      zb[o] = zoff(A, fa, o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1);
+      ab[o] = apot<double>(m, zb[o]);
+    }
     for (int l = 0; l < 3; ++l) {
+      const int st = l == 0 ? 1 : (l == 1 ? 3 : 9);
       double fs = 0.0, as = 0.0;
       for (int o = 0; o < 27; ++o) {
         const int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
@@ -105,13 +108,8 @@ __global__ void __launch_bounds__(T3) cellq3d_kernel(const DevModel m, const Sta
         double w = 1.0;
         for (int t = 0; t < 3; ++t)
           if (t != l) w = w * w1(mm[t]);
-        int f[3] = {2 * c[0] + mm[0], 2 * c[1] + mm[1], 2 * c[2] + mm[2]};
-        int fm[3] = {f[0], f[1], f[2]}, fp[3] = {f[0], f[1], f[2]};
-        fm[l] -= 1;
-        fp[l] += 1;
-        const double zp = zfine(A, fp);
-        fs = fs + w * flux<FLUX, double>(m, l, zp);
-        const double ahat = (-apot<double>(m, zfine(A, fm)) + 8.0 * apot<double>(m, zfine(A, f)) - apot<double>(m, zp)) / 6.0;
+        fs = fs + w * flux<FLUX, double>(m, l, zb[o + st]);
+        const double ahat = (-ab[o - st] + 8.0 * ab[o] - ab[o + st]) / 6.0;
         as = as + w * ahat;
       }
       A.FH[l][q] = fs / 36.0;
@@ -193,6 +191,7 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N; q += (size_t)gridDim.x * blockDim.x) {
     int c[3];
     decode3(A, q, c);
+    const FineAxes fa = fine_axes(A, c);
     // limited cell-average update (eq. multid_limited_average)
     double v = A.in[0][q];
     for (int l = 0; l < 3; ++l) {
@@ -205,7 +204,7 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
     A.O[o][0][q] = ubo;
     // point values owned by the cell: kinds 1..7 at fine 2c + s
     for (int s = 1; s < 8; ++s) {
-      const int p[3] = {2 * c[0] + (s & 1), 2 * c[1] + ((s >> 1) & 1), 2 * c[2] + ((s >> 2) & 1)};
+      const int p[3] = {s & 1, (s >> 1) & 1, (s >> 2) & 1};   // offsets from 2c
       double acc = 0.0;
       for (int l = 0; l < 3; ++l) {
         const double ih = A.inv_h[l];
@@ -213,7 +212,7 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
         for (int t = 0; t < 5; ++t) {
           int f[3] = {p[0], p[1], p[2]};
           f[l] += t - 2;
-          z[t] = zfine(A, f);
+          z[t] = zoff(A, fa, f[0], f[1], f[2]);
           fz[t] = flux<FLUX, double>(m, l, z[t]);
           dz[t] = dflux_abs<FLUX, double>(m, l, z[t]);
           az[t] = apot<double>(m, z[t]);
@@ -245,7 +244,8 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
           int fm[3] = {p[0], p[1], p[2]}, fp[3] = {p[0], p[1], p[2]};
           fm[l] -= 1;
           fp[l] += 1;
-          const double zm = zfine_avg(A, fm), z0 = z[2], zp = zfine_avg(A, fp);
+          const double zm = zoff(A, fa, fm[0], fm[1], fm[2], true), z0 = z[2],
+                       zp = zoff(A, fa, fp[0], fp[1], fp[2], true);
           const double Fr = 0.5 * (flux<FLUX, double>(m, l, z0) + flux<FLUX, double>(m, l, zp)) -
                             0.5 * alpha_interval<FLUX, double>(m, l, z0, zp) * (zp - z0);
           const double Fl = 0.5 * (flux<FLUX, double>(m, l, zm) + flux<FLUX, double>(m, l, z0)) -
