@@ -201,6 +201,10 @@ af::StageArgs3D args3d(af_ctx* c, int in) {
   a.inv_h[0] = c->inv_h1;
   a.inv_h[1] = c->inv_h2;
   a.inv_h[2] = c->inv_h3;
+  for (int l = 0; l < 3; ++l) {
+    a.i6h[l] = a.inv_h[l] / 6.0;
+    a.i3h2[l] = a.inv_h[l] * a.inv_h[l] / 3.0;
+  }
   for (int s = 0; s < 8; ++s) a.in[s] = c->k3[in][s];
   a.dt = c->dt_dev;
   a.limiter = c->opts.limiter;

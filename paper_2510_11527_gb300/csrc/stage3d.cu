@@ -43,7 +43,15 @@ __device__ __forceinline__ size_t shift3(const StageArgs3D& A, size_t q, int l, 
   return cell3(A, c);
 }
 
-__device__ __forceinline__ double w1(int m) { return m == 0 ? 4.0 : 1.0; }
+// Simpson weights 1, 4, 1 per axis as exact tables (no FP64 multiplies per term): the
+// full 3D weight of offset o = mx + 1 + 3 (my + 1) + 9 (mz + 1), and the transverse 2D
+// weight for each axis l (the factor along l is 1)
+__constant__ double kW27[27] = {1, 4, 1, 4, 16, 4, 1, 4, 1, 4, 16, 4, 16, 64, 16, 4, 16, 4, 1, 4, 1, 4, 16, 4, 1, 4, 1};
+__device__ __forceinline__ double wtrans(int o, int l) {
+  // drop the factor of axis l from the 3D weight: divide by its 1D weight (4 or 1)
+  const int ml = l == 0 ? o % 3 : (l == 1 ? (o / 3) % 3 : o / 9);
+  return ml == 1 ? kW27[o] * 0.25 : kW27[o];
+}
 
 // The wrapped fine coordinates of offsets -2 .. +3 from the cell's fine origin 2c along
 // each axis, formed once per cell: a fine access is then two shifts and a lookup.
@@ -76,8 +84,7 @@ __global__ void __launch_bounds__(T3) centre3d_kernel(const StageArgs3D A) {
     for (int o = 0; o < 27; ++o) {
       const int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
       if (mm[0] == 0 && mm[1] == 0 && mm[2] == 0) continue;
-      const double w = (1.0 * w1(mm[0])) * w1(mm[1]) * w1(mm[2]);
-      acc = acc + w * zoff(A, fa, mm[0], mm[1], mm[2]);
+      acc = acc + kW27[o] * zoff(A, fa, mm[0], mm[1], mm[2]);
     }
     A.C[q] = (216.0 * A.in[0][q] - acc) / 64.0;
   }
@@ -105,15 +112,13 @@ __global__ void __launch_bounds__(T3) cellq3d_kernel(const DevModel m, const Sta
       for (int o = 0; o < 27; ++o) {
         const int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
         if (mm[l] != 0) continue;
-        double w = 1.0;
-        for (int t = 0; t < 3; ++t)
-          if (t != l) w = w * w1(mm[t]);
+        const double w = wtrans(o, l);
         fs = fs + w * flux<FLUX, double>(m, l, zb[o + st]);
-        const double ahat = (-ab[o - st] + 8.0 * ab[o] - ab[o + st]) / 6.0;
+        const double ahat = (-ab[o - st] + 8.0 * ab[o] - ab[o + st]) * (1.0 / 6.0);
         as = as + w * ahat;
       }
-      A.FH[l][q] = fs / 36.0;
-      A.AH[l][q] = as / 36.0;
+      A.FH[l][q] = fs * (1.0 / 36.0);
+      A.AH[l][q] = as * (1.0 / 36.0);
       const double un = A.in[0][shift3(A, q, l, 1)];
       const double al = alpha_interval<FLUX, double>(m, l, u, un);
       A.FL[l][q] = 0.5 * (flux<FLUX, double>(m, l, u) + flux<FLUX, double>(m, l, un)) - 0.5 * al * (un - u);
@@ -123,7 +128,7 @@ __global__ void __launch_bounds__(T3) cellq3d_kernel(const DevModel m, const Sta
         auto st = [](double a, double b, double cc) {
           return tabs(a - 2.0 * b + cc) / (tabs(a) + 2.0 * tabs(b) + tabs(cc) + 1e-13);
         };
-        A.S[l][q] = (st(v[0], v[1], v[2]) + 4.0 * st(v[1], v[2], v[3]) + st(v[2], v[3], v[4])) / 6.0;
+        A.S[l][q] = (st(v[0], v[1], v[2]) + 4.0 * st(v[1], v[2], v[3]) + st(v[2], v[3], v[4])) * (1.0 / 6.0);
       }
     }
   }
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
         }
         const double alpha = tmax(tmax(tmax(dz[0], dz[1]), tmax(dz[3], dz[4])), dz[2]);
         const double rh = line_res<double>(z[0], z[1], z[2], z[3], z[4], fz[0], fz[1], fz[3], fz[4], alpha, az[0], az[1],
-                                           az[2], az[3], az[4], ih / 6.0, ih * ih / 3.0);
+                                           az[2], az[3], az[4], A.i6h[l], A.i3h2[l]);
         double r = rh;
         if (A.blend) {
           // weight: min of theta^{c,s}_l over the l-faces holding the point (s_l = 1),

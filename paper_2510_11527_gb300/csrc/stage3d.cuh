@@ -13,6 +13,7 @@ namespace af {
 struct StageArgs3D {
   int n[3];                          // cells per direction
   double inv_h[3];                   // 1/dx, 1/dy, 1/dz
+  double i6h[3], i3h2[3];            // 1/(6 h_l), 1/(3 h_l^2)
   const double* in[8];               // FE input state, by kind
   int nout;                          // 1 or 2 limited FE evaluations of the same input
   double tcoef[2];                   // tau_k = tcoef_k * (*dt)
