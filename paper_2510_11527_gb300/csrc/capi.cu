@@ -344,6 +344,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   if (grid->bc != AF_BC_PERIODIC && (grid->nx < 4 || (grid->dim == 2 && grid->ny < 4))) return AF_E_ARG;
   if (opts->diffusion_form == AF_FORM_NODC && (grid->dim != 1 || opts->blend != AF_BLEND_OFF)) return AF_E_UNSUPPORTED;
   if (grid->bc != AF_BC_PERIODIC && opts->blend == AF_BLEND_EXTERNAL) return AF_E_UNSUPPORTED;
+  if (grid->dim == 3 && (double)grid->nx * grid->ny * grid->nz >= 2147483648.0) return AF_E_ARG;   // 32-bit cell index
   if (grid->dim == 3 && (grid->bc != AF_BC_PERIODIC || flux->kind == AF_FLUX_BL || opts->precision != AF_PREC_FP64 ||
                          opts->blend == AF_BLEND_EXTERNAL || opts->diffusion_form != AF_FORM_DC))
     return AF_E_UNSUPPORTED;

@@ -25,10 +25,13 @@ constexpr int T3 = 256;
 
 __device__ __forceinline__ size_t cells3(const StageArgs3D& A) { return (size_t)A.n[0] * A.n[1] * A.n[2]; }
 
+// cell coordinates of a linear index (32-bit: meshes hold < 2^31 cells)
 __device__ __forceinline__ void decode3(const StageArgs3D& A, size_t q, int* c) {
-  c[0] = (int)(q % A.n[0]);
-  c[1] = (int)((q / A.n[0]) % A.n[1]);
-  c[2] = (int)(q / ((size_t)A.n[0] * A.n[1]));
+  const unsigned qq = (unsigned)q, n0 = (unsigned)A.n[0], n1 = (unsigned)A.n[1];
+  const unsigned r = qq / n0;
+  c[0] = (int)(qq - r * n0);
+  c[1] = (int)(r % n1);
+  c[2] = (int)(r / n1);
 }
 
 // periodic cell index
@@ -36,11 +39,14 @@ __device__ __forceinline__ size_t cell3(const StageArgs3D& A, const int* c) {
   return ((size_t)wrapi(c[2], A.n[2]) * A.n[1] + wrapi(c[1], A.n[1])) * A.n[0] + wrapi(c[0], A.n[0]);
 }
 
-__device__ __forceinline__ size_t shift3(const StageArgs3D& A, size_t q, int l, int step) {
-  int c[3];
-  decode3(A, q, c);
-  c[l] += step;
-  return cell3(A, c);
+// neighbour step cells along l of the cell at coordinates c (|step| <= 2, no division)
+__device__ __forceinline__ size_t nbr3(const StageArgs3D& A, const int* c, int l, int step) {
+  int d[3] = {c[0], c[1], c[2]};
+  d[l] += step;
+  if (d[l] < 0) d[l] += A.n[l];
+  if (d[l] >= A.n[l]) d[l] -= A.n[l];
+  if (d[l] < 0 || d[l] >= A.n[l]) d[l] = wrapi(d[l], A.n[l]);   // meshes thinner than the step
+  return ((size_t)d[2] * A.n[1] + d[1]) * A.n[0] + d[0];
 }
 
 // Simpson weights 1, 4, 1 per axis as exact tables (no FP64 multiplies per term): the
@@ -119,12 +125,12 @@ __global__ void __launch_bounds__(T3) cellq3d_kernel(const DevModel m, const Sta
       }
       A.FH[l][q] = fs * (1.0 / 36.0);
       A.AH[l][q] = as * (1.0 / 36.0);
-      const double un = A.in[0][shift3(A, q, l, 1)];
+      const double un = A.in[0][nbr3(A, c, l, 1)];
       const double al = alpha_interval<FLUX, double>(m, l, u, un);
       A.FL[l][q] = 0.5 * (flux<FLUX, double>(m, l, u) + flux<FLUX, double>(m, l, un)) - 0.5 * al * (un - u);
       if (A.blend) {
         double v[5];
-        for (int t = 0; t < 5; ++t) v[t] = A.in[0][shift3(A, q, l, t - 2)];
+        for (int t = 0; t < 5; ++t) v[t] = A.in[0][nbr3(A, c, l, t - 2)];
         auto st = [](double a, double b, double cc) {
           return tabs(a - 2.0 * b + cc) / (tabs(a) + 2.0 * tabs(b) + tabs(cc) + 1e-13);
         };
@@ -135,14 +141,16 @@ __global__ void __launch_bounds__(T3) cellq3d_kernel(const DevModel m, const Sta
 }
 
 // low-order directional states of cell q along l (Lemma 5.1 with factor 2d = 6)
+// (q: the cell, qp / qm: its neighbour after / before it along l)
 template <int FLUX>
-__device__ __forceinline__ double ulp3(const DevModel& m, const StageArgs3D& A, size_t q, int l, double mu, double nu) {
-  const double u = A.in[0][q], un = A.in[0][shift3(A, q, l, 1)];
+__device__ __forceinline__ double ulp3(const DevModel& m, const StageArgs3D& A, size_t q, size_t qp, int l, double mu,
+                                       double nu) {
+  const double u = A.in[0][q], un = A.in[0][qp];
   return u - 6.0 * mu * (A.FL[l][q] - flux<FLUX, double>(m, l, u)) + 6.0 * nu * (apot<double>(m, un) - apot<double>(m, u));
 }
 template <int FLUX>
-__device__ __forceinline__ double ulm3(const DevModel& m, const StageArgs3D& A, size_t q, int l, double mu, double nu) {
-  const size_t qm = shift3(A, q, l, -1);
+__device__ __forceinline__ double ulm3(const DevModel& m, const StageArgs3D& A, size_t q, size_t qm, int l, double mu,
+                                       double nu) {
   const double u = A.in[0][q], um = A.in[0][qm];
   return u - 6.0 * mu * (flux<FLUX, double>(m, l, u) - A.FL[l][qm]) - 6.0 * nu * (apot<double>(m, u) - apot<double>(m, um));
 }
@@ -154,10 +162,12 @@ __global__ void __launch_bounds__(T3) limit3d_kernel(const DevModel m, const Sta
   const double tau = A.tcoef[o] * dtv;
   const size_t N = cells3(A);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N; q += (size_t)gridDim.x * blockDim.x) {
+    int c[3];
+    decode3(A, q, c);
     const double u = A.in[0][q], au = apot<double>(m, u);
     for (int l = 0; l < 3; ++l) {
       const double mu = tau * A.inv_h[l], nu = mu * A.inv_h[l];
-      const size_t qp = shift3(A, q, l, 1), qm = shift3(A, q, l, -1);
+      const size_t qp = nbr3(A, c, l, 1), qm = nbr3(A, c, l, -1);
       double fh = A.FH[l][q], ah = A.AH[l][q];
       const double fl = A.FL[l][q];
       if (A.blend) {
@@ -171,11 +181,11 @@ __global__ void __launch_bounds__(T3) limit3d_kernel(const DevModel m, const Sta
         const double umin = m.umin, umax = m.umax;
         const double k = 18.0 * mu, kd = 18.0 * nu;
         const double dF = fh - fl;
-        const double zp = ulp3<FLUX>(m, A, q, l, mu, nu), zm = ulm3<FLUX>(m, A, qp, l, mu, nu);
+        const double zp = ulp3<FLUX>(m, A, q, qp, l, mu, nu), zm = ulm3<FLUX>(m, A, qp, q, l, mu, nu);
         const double tcl = tmin(theta_fn<double>(zp, zp - k * dF, umin, umax), theta_fn<double>(zm, zm + k * dF, umin, umax));
         flim = is_one(tcl) ? fh : fl + tcl * dF;
         const double dA = ah - au;
-        const double p0 = ulp3<FLUX>(m, A, qm, l, mu, nu), q0 = ulm3<FLUX>(m, A, q, l, mu, nu);
+        const double p0 = ulp3<FLUX>(m, A, qm, q, l, mu, nu), q0 = ulm3<FLUX>(m, A, q, qm, l, mu, nu);
         const double td = tmin(tmin(theta_fn<double>(p0, p0 + kd * dA, umin, umax), theta_fn<double>(zp, zp - kd * dA, umin, umax)),
                                tmin(theta_fn<double>(q0, q0 - kd * dA, umin, umax), theta_fn<double>(zm, zm + kd * dA, umin, umax)));
         alim = is_one(td) ? ah : au + td * dA;
@@ -201,7 +211,7 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
     double v = A.in[0][q];
     for (int l = 0; l < 3; ++l) {
       const double mu = tau * A.inv_h[l], nu = mu * A.inv_h[l];
-      const size_t qm = shift3(A, q, l, -1), qp = shift3(A, q, l, 1);
+      const size_t qm = nbr3(A, c, l, -1), qp = nbr3(A, c, l, 1);
       v = v - mu * (A.Flim[l][q] - A.Flim[l][qm]) + nu * (A.Alim[l][qp] - 2.0 * A.Alim[l][q] + A.Alim[l][qm]);
     }
     double ubo = cA != 0.0 ? rk_comb(cA, A.A[o][0][q], cF, v) : rk_scale(cF, v);
@@ -237,12 +247,12 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
             for (int t = 0; t < 3; ++t) {
               if (!((bits >> t) & 1)) continue;
               if (t == l || !((s >> t) & 1)) { ok = false; break; }
-              cc[t] += 1;
+              cc[t] = cc[t] + 1 == A.n[t] ? 0 : cc[t] + 1;   // periodic, so nbr3 below sees wrapped coordinates
             }
             if (!ok) continue;
             const size_t qq = cell3(A, cc);
             const double sv = A.S[l][qq];
-            const double wv = onface ? exp(-A.gamma * (0.5 * (sv + A.S[l][shift3(A, qq, l, 1)]))) : exp(-A.gamma * sv);
+            const double wv = onface ? exp(-A.gamma * (0.5 * (sv + A.S[l][nbr3(A, cc, l, 1)]))) : exp(-A.gamma * sv);
             w = (w == 2.0) ? wv : tmin(w, wv);
           }
           // low-order residual on the +-h/2 neighbours (a centre replaced by its average)
