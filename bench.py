@@ -463,13 +463,19 @@ def _form_ex65():
 
 def _form_pme3d(args, stream, peaks):
     """3D porous medium (a = u^2) from the Barenblatt profile on n3d^3 cells (default
-    128^3), FP64: the four-kernel 3D stage."""
+    128^3): the four-kernel 3D stage in FP64, and the FP32-mixed form against it."""
     import statistics as st_
     import af_inputs as ai
     from paper_2510_11527_gb300 import Solver
     n = args.n3d
     spec = ai.pme_3d(n)
     host = [a.numpy() for a in ai.initial_state(spec, sub=2, order=3)]
+    # the FP32-mixed form on the same workload (its L1 difference from FP64 after the
+    # same timed steps)
+    s32 = Solver(spec, precision="fp32_mixed")
+    s32.set_stream(stream)
+    s32.set_state(host)
+    step32, stage32 = _time_steps(_solver_stepper(s32, stream), s32.num_stages, args.form_steps, 3, stream)
     s = Solver(spec, precision="fp64")
     s.set_stream(stream)
     s.set_state(host)
@@ -478,6 +484,11 @@ def _form_pme3d(args, stream, peaks):
     cells = spec.cells
     out = {"cells": cells, "value": round(cells * s.num_stages * args.form_steps / (sum(step_ms) / 1e3), 1),
            "stage_ms_avg": round(st_.mean(stage_ms), 5)}
+    v32 = cells * s32.num_stages * args.form_steps / (sum(step32) / 1e3)
+    l1 = max(float((a.double() - b.double()).abs().mean()) for a, b in zip(s32.device_tensors(), s.device_tensors()))
+    out["fp32_mixed"] = {"value": round(v32, 1), "stage_ms_avg": round(st_.mean(stage32), 5),
+                         "speedup_vs_fp64": round(v32 / out["value"], 2), "l1_vs_fp64": l1}
+    s32.close()
     tf = FLOPS_PER_CELL_STAGE_3D * cells / stage_s / 1e12
     gbs = BYTES_PER_CELL_STAGE_3D * cells / stage_s / 1e9
     out["roofline"] = {"bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

@@ -23,8 +23,10 @@
  * 3D (periodic, [nz][ny][nx], i fastest; Section 4): 8 arrays ordered by the kind
  * s = sx + 2 sy + 4 sz of the location (i + sx/2, j + sy/2, k + sz/2): the cell average
  * (s = 0), then the x-face, y-face, xy-edge, z-face, xz-edge, yz-edge and corner values.
- * They are passed through the *_arrays calls below (FP64; SSP-RK3 / SSP-RK(5,4); zero,
- * linear (p0, p1, p2 velocities) or Burgers flux; blend off or plain).
+ * They are passed through the *_arrays calls below as FP64 (SSP-RK3 / SSP-RK(5,4); zero,
+ * linear (p0, p1, p2 velocities) or Burgers flux; blend off or plain). FP32-mixed keeps
+ * the averages in FP64 and the 7 point arrays in FP32 on the device (af_device_ptrs_arrays
+ * reports the element sizes).
  *
  * Conventions
  *   - Every call returns an af_status. On error the context is left unchanged and
@@ -127,8 +129,8 @@ typedef struct {
  * unknown kinds, umin >= umax, non-periodic ends with nx (or, in 2D, ny) < 4;
  * AF_E_UNSUPPORTED for Dirichlet ends or AF_FORM_NODC in 2D, AF_FORM_NODC with a
  * blend, the external indicator with non-periodic ends, and in 3D anything but a
- * periodic FP64 mesh with the zero, linear or Burgers flux, AF_FORM_DC and the blend off
- * or plain; AF_E_OOM if allocation fails. */
+ * periodic mesh (FP64 or FP32-mixed) with the zero, linear or Burgers flux, AF_FORM_DC
+ * and the blend off or plain; AF_E_OOM if allocation fails. */
 af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* diff,
                     const af_bounds_t* bounds, const af_opts* opts, af_ctx** out);
 af_status af_destroy(af_ctx* ctx);

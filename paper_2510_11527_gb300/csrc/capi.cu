@@ -191,9 +191,11 @@ af_status stage_impl(af_ctx* c, int k) {
   return AF_OK;
 }
 
-// the 3D stage arguments for input buffer `in` (outputs added by the caller)
-af::StageArgs3D args3d(af_ctx* c, int in) {
-  af::StageArgs3D a;
+// the 3D stage arguments for input buffer `in` (outputs added by the caller); T is the
+// context's point / stencil precision
+template <class T>
+af::StageArgs3D<T> args3d(af_ctx* c, int in) {
+  af::StageArgs3D<T> a;
   std::memset(&a, 0, sizeof(a));
   a.n[0] = c->nx;
   a.n[1] = c->ny;
@@ -205,40 +207,52 @@ af::StageArgs3D args3d(af_ctx* c, int in) {
     a.i6h[l] = a.inv_h[l] / 6.0;
     a.i3h2[l] = a.inv_h[l] * a.inv_h[l] / 3.0;
   }
-  for (int s = 0; s < 8; ++s) a.in[s] = c->k3[in][s];
+  a.ub = (const double*)c->k3[in][0];
+  for (int s = 1; s < 8; ++s) a.pt[s] = (const T*)c->k3[in][s];
   a.dt = c->dt_dev;
   a.limiter = c->opts.limiter;
   a.blend = c->opts.blend;
   a.gamma = c->opts.gamma;
   a.tol = c->tol;
   a.stats = c->stats;
-  a.C = c->scr3[0];
+  a.C = (T*)c->scr3[0];
   for (int l = 0; l < 3; ++l) {
-    a.FH[l] = c->scr3[1 + l];
-    a.AH[l] = c->scr3[4 + l];
-    a.FL[l] = c->scr3[7 + l];
-    a.S[l] = c->scr3[10 + l];
-    a.Flim[l] = c->scr3[13 + l];
-    a.Alim[l] = c->scr3[16 + l];
+    a.FH[l] = (T*)c->scr3[1 + l];
+    a.AH[l] = (T*)c->scr3[4 + l];
+    a.FL[l] = (T*)c->scr3[7 + l];
+    a.S[l] = (T*)c->scr3[10 + l];
+    a.Flim[l] = (T*)c->scr3[13 + l];
+    a.Alim[l] = (T*)c->scr3[16 + l];
   }
   return a;
 }
 
-af_status stage3d_out(af_ctx* c, int in, const OutSpec* out, int nout) {
-  af::StageArgs3D a = args3d(c, in);
+template <class T>
+af_status stage3d_typed(af_ctx* c, int in, const OutSpec* out, int nout) {
+  af::StageArgs3D<T> a = args3d<T>(c, in);
   a.nout = nout;
   for (int o = 0; o < nout; ++o) {
     a.tcoef[o] = out[o].tcoef;
     a.cA[o] = out[o].cA;
     a.cF[o] = out[o].cF;
     a.sg[o] = out[o].sg;
-    for (int s = 0; s < 8; ++s) {
-      a.A[o][s] = out[o].aidx >= 0 ? c->k3[out[o].aidx][s] : nullptr;
-      a.O[o][s] = c->k3[out[o].oidx][s];
+    a.Aub[o] = out[o].aidx >= 0 ? (const double*)c->k3[out[o].aidx][0] : nullptr;
+    a.Oub[o] = (double*)c->k3[out[o].oidx][0];
+    for (int s = 1; s < 8; ++s) {
+      a.Apt[o][s] = out[o].aidx >= 0 ? (const T*)c->k3[out[o].aidx][s] : nullptr;
+      a.Opt[o][s] = (T*)c->k3[out[o].oidx][s];
     }
   }
-  CK(c, af::launch_stage3d_f64(c->flux.kind, c->m, a, c->stream));
+  if constexpr (sizeof(T) == 8) {
+    CK(c, af::launch_stage3d_f64(c->flux.kind, c->m, a, c->stream));
+  } else {
+    CK(c, af::launch_stage3d_f32(c->flux.kind, c->m, a, c->stream));
+  }
   return AF_OK;
+}
+
+af_status stage3d_out(af_ctx* c, int in, const OutSpec* out, int nout) {
+  return c->prec == AF_PREC_FP64 ? stage3d_typed<double>(c, in, out, nout) : stage3d_typed<float>(c, in, out, nout);
 }
 
 af_status stage3d_impl(af_ctx* c, int k) {
@@ -267,7 +281,9 @@ cudaError_t launch_rate(af_ctx* c) {
 af_status dt_device(af_ctx* c, double* dst, double* t_acc, double t_end = -1.0, double* count = nullptr) {
   cudaError_t e;
   if (c->dim == 3) {
-    CK(c, af::launch_rate3d(c->flux.kind, c->m, args3d(c, 0), c->kmax, c->rate_bits, c->stream));
+    const int n3[3] = {c->nx, c->ny, c->nz};
+    const double ih3[3] = {c->inv_h1, c->inv_h2, c->inv_h3};
+    CK(c, af::launch_rate3d(c->flux.kind, c->m, n3, (const double*)c->k3[0][0], ih3, c->kmax, c->rate_bits, c->stream));
     const double hmin = std::min(c->dx, std::min(c->dy, c->dz));
     // no interior extrema of f_l' in 3D: the finalize step adds no extremum terms (dim 0)
     af::dt_finalize_kernel<<<1, 1, 0, c->stream>>>(c->rate_bits, c->m, 0, c->inv_h1, c->inv_h2, c->cfl, c->cfl_diff,
@@ -345,7 +361,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   if (opts->diffusion_form == AF_FORM_NODC && (grid->dim != 1 || opts->blend != AF_BLEND_OFF)) return AF_E_UNSUPPORTED;
   if (grid->bc != AF_BC_PERIODIC && opts->blend == AF_BLEND_EXTERNAL) return AF_E_UNSUPPORTED;
   if (grid->dim == 3 && (double)grid->nx * grid->ny * grid->nz >= 2147483648.0) return AF_E_ARG;   // 32-bit cell index
-  if (grid->dim == 3 && (grid->bc != AF_BC_PERIODIC || flux->kind == AF_FLUX_BL || opts->precision != AF_PREC_FP64 ||
+  if (grid->dim == 3 && (grid->bc != AF_BC_PERIODIC || flux->kind == AF_FLUX_BL ||
                          opts->blend == AF_BLEND_EXTERNAL || opts->diffusion_form != AF_FORM_DC))
     return AF_E_UNSUPPORTED;
   if (!bounds->from_initial_data && !(bounds->umax > bounds->umin)) return AF_E_ARG;
@@ -397,8 +413,9 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t ulen = rect ? c->pn : c->n, plen = rect ? c->pn : c->np;
   const bool d3 = grid->dim == 3;
-  // 3D: 8 FP64 arrays per state and 19 scratch arrays of the 3D stage
-  const size_t per_state = d3 ? 8 * al(c->n * 8) : al(ulen * 8) + 3 * al(plen * ps);
+  // 3D: the FP64 averages and 7 point arrays per state, and 19 scratch arrays of the 3D
+  // stage (sized for FP64)
+  const size_t per_state = d3 ? al(c->n * 8) + 7 * al(c->n * ps) : al(ulen * 8) + 3 * al(plen * ps);
   const size_t scr3 = d3 ? 19 * al(c->n * 8) : 0;
   const size_t scratch = al(8) * 2 + al(8 * 8) + al(8 * af::RED_MAX_BLOCKS) + al(8) + al(sizeof(DevStats)) + al(c->n * 8);
   const size_t total = per_state * c->nbuf + scratch + scr3;
@@ -410,8 +427,8 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   unsigned char* p = c->block;
   for (int b = 0; b < c->nbuf; ++b) {
     if (d3) {
-      for (int s = 0; s < 8; ++s) { c->k3[b][s] = (double*)p; p += al(c->n * 8); }
-      c->ub[b] = c->k3[b][0];
+      for (int s = 0; s < 8; ++s) { c->k3[b][s] = p; p += al(c->n * (s == 0 ? 8 : ps)); }
+      c->ub[b] = (double*)c->k3[b][0];
       c->pv[b] = c->k3[b][1];
       c->px[b] = c->k3[b][2];
       c->py[b] = c->k3[b][3];
@@ -429,7 +446,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->rate_bits = (unsigned long long*)p; p += al(16);
   c->stats = (DevStats*)p; p += al(sizeof(DevStats));
   c->s_ext = (double*)p; p += al(c->n * 8);
-  for (int k = 0; d3 && k < 19; ++k) { c->scr3[k] = (double*)p; p += al(c->n * 8); }
+  for (int k = 0; d3 && k < 19; ++k) { c->scr3[k] = p; p += al(c->n * 8); }
   if (cudaMemset(c->block, 0, total) != cudaSuccess || cudaMallocHost(&c->host_pinned, 8 * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     cudaFree(c->block);
@@ -565,9 +582,10 @@ af_status af_set_state_arrays(af_ctx* c, int narr, const double* const* arrays) 
     if (!arrays[a]) return AF_E_ARG;
   if (c->dim == 1) return af_set_state(c, arrays[0], arrays[1], nullptr, nullptr);
   if (c->dim == 2) return af_set_state(c, arrays[0], arrays[1], arrays[2], arrays[3]);
-  // 3D (FP64): stage the 8 arrays in the RK temporaries, check them there, then copy
+  // 3D: stage the 8 arrays in the RK temporaries (buffers 1.., contiguous, >= 64 n
+  // bytes), check them there, then copy (FP32-mixed: round the points to nearest)
   const size_t n = c->n;
-  double* stg = c->k3[1][0];   // buffers 1.. are contiguous: 8 n doubles per buffer
+  double* stg = (double*)c->k3[1][0];
   for (int a = 0; a < 8; ++a)
     CK(c, cudaMemcpyAsync(stg + a * n, arrays[a], n * 8, cudaMemcpyHostToDevice, c->stream));
   const size_t total = 8 * n;
@@ -585,13 +603,22 @@ af_status af_set_state_arrays(af_ctx* c, int narr, const double* const* arrays) 
     c->m.umin = lo;
     c->m.umax = hi;
     c->kmax = af::kappa_max_of(c->diff, lo, hi);
-    c->tol = 8.0 * 2.220446049250313e-16 * std::max(std::fabs(lo), std::fabs(hi));
+    c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) *
+             std::max(std::fabs(lo), std::fabs(hi));
     c->bounds_pending = false;
   } else if (c->opts.limiter && (lo < c->m.umin || hi > c->m.umax)) {
     FAIL(c, AF_E_STATE, "input outside [umin, umax]: [%g, %g]", lo, hi);
   }
-  for (int a = 0; a < 8; ++a)
-    CK(c, cudaMemcpyAsync(c->k3[0][a], stg + a * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  CK(c, cudaMemcpyAsync(c->k3[0][0], stg, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+  const int grid = (int)std::min<size_t>(152 * 8, (n + af::RED_THREADS - 1) / af::RED_THREADS);
+  for (int a = 1; a < 8; ++a) {
+    if (c->prec == AF_PREC_FP64) {
+      CK(c, cudaMemcpyAsync(c->k3[0][a], stg + a * n, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      af::narrow_kernel<<<grid, af::RED_THREADS, 0, c->stream>>>(stg + a * n, (float*)c->k3[0][a], n);
+      CK(c, cudaGetLastError());
+    }
+  }
   return AF_OK;
 }
 
@@ -601,8 +628,21 @@ af_status af_get_state_arrays(af_ctx* c, int narr, double* const* arrays) {
     if (!arrays[a]) return AF_E_ARG;
   if (c->dim == 1) return af_get_state(c, arrays[0], arrays[1], nullptr, nullptr);
   if (c->dim == 2) return af_get_state(c, arrays[0], arrays[1], arrays[2], arrays[3]);
-  for (int a = 0; a < 8; ++a)
-    CK(c, cudaMemcpyAsync(arrays[a], c->k3[0][a], c->n * 8, cudaMemcpyDeviceToHost, c->stream));
+  const size_t n = c->n;
+  if (c->prec == AF_PREC_FP64) {
+    for (int a = 0; a < 8; ++a)
+      CK(c, cudaMemcpyAsync(arrays[a], c->k3[0][a], n * 8, cudaMemcpyDeviceToHost, c->stream));
+  } else {
+    // FP32 points widened on the device into the staging area, then copied
+    double* stg = (double*)c->k3[1][0];
+    const int grid = (int)std::min<size_t>(152 * 8, (n + af::RED_THREADS - 1) / af::RED_THREADS);
+    CK(c, cudaMemcpyAsync(arrays[0], c->k3[0][0], n * 8, cudaMemcpyDeviceToHost, c->stream));
+    for (int a = 1; a < 8; ++a) {
+      af::widen_kernel<<<grid, af::RED_THREADS, 0, c->stream>>>((const float*)c->k3[0][a], stg + a * n, n);
+      CK(c, cudaGetLastError());
+      CK(c, cudaMemcpyAsync(arrays[a], stg + a * n, n * 8, cudaMemcpyDeviceToHost, c->stream));
+    }
+  }
   CK(c, cudaStreamSynchronize(c->stream));
   return AF_OK;
 }
@@ -616,7 +656,7 @@ af_status af_device_ptrs_arrays(af_ctx* c, int narr, void** ptrs, int dtype[2]) 
     return s;
   }
   for (int a = 0; a < 8; ++a) ptrs[a] = c->k3[0][a];
-  if (dtype) { dtype[0] = 8; dtype[1] = 8; }
+  if (dtype) { dtype[0] = 8; dtype[1] = (int)pt_size(c); }
   return AF_OK;
 }
 
@@ -764,7 +804,10 @@ af_status af_bounds(af_ctx* c, double* umin, double* umax) {
   if (c->dim == 3) {
     for (int op = 1; op <= 2; ++op)
       for (int a = 0; a < 8; ++a) {
-        af_status s = reduce_array<double>(c, c->k3[0][a], c->n, op, op == 1 ? INFINITY : -INFINITY, c->red + 1 + op, a > 0);
+        const double init = op == 1 ? INFINITY : -INFINITY;
+        af_status s = (a == 0 || c->prec == AF_PREC_FP64)
+                          ? reduce_array<double>(c, (const double*)c->k3[0][a], c->n, op, init, c->red + 1 + op, a > 0)
+                          : reduce_array<float>(c, (const float*)c->k3[0][a], c->n, op, init, c->red + 1 + op, a > 0);
         if (s != AF_OK) return s;
       }
     af_status s = read_scalar(c, c->red + 2, umin);

@@ -22,12 +22,13 @@ struct af_ctx {
   // and column 0 hold the bottom / left side points (the averages there, X in row 0
   // and Y in column 0 are not DoFs). Otherwise pnx = nx, pny = ny.
   int pnx = 1, pny = 1;
-  // 3D: cells along z, the 8 arrays of each buffer by kind (k3[b][0] == ub[b]) and the
-  // stage scratch (centres; per direction FH, AH, FL, s, limited F and A)
+  // 3D: cells along z, the 8 arrays of each buffer by kind (k3[b][0] == ub[b]; points
+  // in the context's precision) and the stage scratch (centres; per direction FH, AH,
+  // FL, s, limited F and A)
   int nz = 1;
   double dz = 1, inv_h3 = 0;
-  double* k3[4][8] = {};
-  double* scr3[19] = {};
+  void* k3[4][8] = {};                // [b][0]: FP64 averages; [b][1..7]: points (FP64 or FP32)
+  void* scr3[19] = {};                // stencil precision
   size_t pn = 0;                      // pnx * pny entries per device array (1D: max(n, np))
   double dx = 1, dy = 1, inv_h1 = 1, inv_h2 = 1, kmax = 0, cfl = 0.165, cfl_diff = 0, tol = 0;
   bool bounds_pending = false;

@@ -16,9 +16,10 @@ cudaError_t launch_stage2d_rect_f64(int flux, bool blend, const DevModel& m, con
                                     cudaStream_t s);
 cudaError_t launch_stage2d_rect_f32(int flux, bool blend, const DevModel& m, const StageArgs2D<float>& a,
                                     cudaStream_t s);
-cudaError_t launch_stage3d_f64(int flux, const DevModel& m, const StageArgs3D& a, cudaStream_t s);
-cudaError_t launch_rate3d(int flux, const DevModel& m, const StageArgs3D& a, double kmax, unsigned long long* rate_bits,
-                          cudaStream_t s);
+cudaError_t launch_stage3d_f64(int flux, const DevModel& m, const StageArgs3D<double>& a, cudaStream_t s);
+cudaError_t launch_stage3d_f32(int flux, const DevModel& m, const StageArgs3D<float>& a, cudaStream_t s);
+cudaError_t launch_rate3d(int flux, const DevModel& m, const int* n, const double* ub, const double* inv_h, double kmax,
+                          unsigned long long* rate_bits, cudaStream_t s);
 cudaError_t launch_stage1d_f64(int flux, const DevModel& m, const StageArgs2D<double>& a, cudaStream_t s);
 cudaError_t launch_stage1d_f32(int flux, const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s);
 

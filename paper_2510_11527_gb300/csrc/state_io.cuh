@@ -118,6 +118,16 @@ __global__ void __launch_bounds__(RED_THREADS) gather_points_kernel(const float*
   }
 }
 
+// dst[k] = src[k] rounded to nearest float / widened exactly (3D FP32-mixed point arrays)
+__global__ void __launch_bounds__(RED_THREADS) narrow_kernel(const double* __restrict__ src, float* dst, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = (float)src[k];
+}
+__global__ void __launch_bounds__(RED_THREADS) widen_kernel(const float* __restrict__ src, double* dst, size_t n) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x)
+    dst[k] = f2d_exact(src[k]);
+}
+
 // 2D rectangle with ends: the caller's layout (ub [ny][nx], V [ny+1][nx+1],
 // X [ny][nx+1], Y [ny+1][nx], staged back to back as doubles) <-> the padded device
 // layout ((nx+1) x (ny+1) per array; entry (I, J) holds ub(I-1, J-1), V(I-1, J-1),

@@ -23,9 +23,9 @@ def _built():
     build.build()
 
 
-def solver(spec, rk=3, **kw):
+def solver(spec, rk=3, prec="fp64", **kw):
     from paper_2510_11527_gb300 import Solver
-    return Solver(spec, precision="fp64", rk=rk, **kw)
+    return Solver(spec, precision=prec, rk=rk, **kw)
 
 
 def relerr(a, b):
@@ -131,5 +131,47 @@ def test_3d_rejects_what_it_does_not_support():
             setattr(spec, k, v)
         with pytest.raises(AfError):
             solver(spec)
-    with pytest.raises(AfError):
-        Solver(box("burgers_pwl", (6, 6, 6)), precision="fp32_mixed")
+
+
+@pytest.mark.parametrize("name,blend", [("burgers_pwl", "plain"), ("linear_const", "off"), ("pme", "off")])
+def test_fp32_mixed_3d_vs_oracle(name, blend):
+    spec = box(name, (13, 9, 6), blend=blend)
+    st = [a.numpy() for a in ai.random_state_3d(spec, seed=11)]
+    tau = oracle.dt_cfl(spec, st[0])
+    want = oracle.fe(spec, st, tau)
+    with solver(spec, prec="fp32_mixed") as s:
+        s.set_state(st)
+        s.forward_euler(tau)
+        got = s.get_state()
+        lo, hi = s.bounds()
+    assert max(np.max(np.abs(g - w)) for g, w in zip(got, want)) <= 1e-5
+    assert max(np.mean(np.abs(g - w)) for g, w in zip(got, want)) <= 1e-6
+    assert lo >= 0.0 and hi <= 1.0
+
+
+def test_fp32_mixed_3d_run_vs_fp64():
+    spec = ai.pme_3d(20)
+    st = [a.numpy() for a in ai.initial_state(spec, sub=2, order=3)]
+    res = {}
+    for prec in ("fp64", "fp32_mixed"):
+        with solver(spec, prec=prec) as s:
+            s.set_state(st)
+            s.run(0.03)
+            res[prec] = (s.get_state(), s.mass(), s.bounds(), s.stats())
+    (g64, m64, _, _), (g32, m32, (lo, hi), stats) = res["fp64"], res["fp32_mixed"]
+    assert stats["errors"] == 0 and lo >= 0.0 and hi <= 1.0
+    assert m32 == pytest.approx(float(np.sum(st[0])) * spec.dx * spec.dy * spec.dz, rel=1e-12)
+    assert max(np.mean(np.abs(a - b)) for a, b in zip(g32, g64)) < 1e-6
+
+
+def test_fp32_mixed_3d_state_io():
+    spec = box("burgers_pwl", (6, 5, 4))
+    st = [a.numpy() for a in ai.random_state_3d(spec, seed=8)]
+    with solver(spec, prec="fp32_mixed") as s:
+        s.set_state(st)
+        got = s.get_state()
+        views = s.device_tensors()
+    assert np.array_equal(got[0], st[0])
+    for a, b in zip(got[1:], st[1:]):
+        assert np.array_equal(a, b.astype(np.float32).astype(np.float64))
+    assert str(views[0].dtype) == "torch.float64" and str(views[1].dtype) == "torch.float32"
