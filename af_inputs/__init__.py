@@ -483,10 +483,13 @@ def state_3d(func: Callable, spec: Spec, sub: int = 2, order: int = 3) -> List[t
     return out
 
 
-def barenblatt_3d(x, y, z, t: float):
-    """Barenblatt solution of u_t = Lap(u^2) in 3D: t^(-3/5) max(0, 1 - |x|^2 t^(-2/5) / 20)."""
+def barenblatt_3d(x, y, z, t: float, m: int = 2):
+    """Barenblatt solution of u_t = Lap(u^m) in 3D (Example 6.3 with d = 3); for m = 2,
+    t^(-3/5) max(0, 1 - |x|^2 t^(-2/5) / 20)."""
+    alpha = 1.0 / (m - 1 + 2.0 / 3.0)
     r2 = x * x + y * y + z * z
-    return t ** (-0.6) * torch.clamp(1.0 - r2 * t ** (-0.4) / 20.0, min=0.0)
+    core = 1.0 - alpha * (m - 1) / (6.0 * m) * r2 / (t ** (2 * alpha / 3))
+    return t ** (-alpha) * torch.clamp(core, min=0.0) ** (1.0 / (m - 1))
 
 
 def pme_3d(n: int = 32) -> Spec:
