@@ -31,12 +31,14 @@ class Spec:
     """Problem description: mesh, flux, diffusion potential, bounds, options.
 
     flux: ("zero", ()), ("linear", (cx, cy)), ("burgers", (coef,)) for f = coef*u^2 in
-          every direction, ("bl", (g,)) for f1 = u^2/(u^2+(1-u)^2), f2 = f1*(1-g(1-u)^2).
+          every direction, ("bl", (g,)) for f1 = u^2/(u^2+(1-u)^2), f2 = f1*(1-g(1-u)^2)
+          (in 1D, f = f1*(1-g(1-u)^2)).
     diff: ("none", ()), ("const", (k0,)) for a = k0*u,
           ("pwl", (klo, lo, khi, hi)) for a = klo*min(u-lo,0) + khi*max(u-hi,0),
           ("pme", (m,)) for a = u^m, ("cubic", (c1, c2, c3)) for a = c1 u + c2 u^2 + c3 u^3,
           ("ramp", (k, lo, w)) for a = 0 (u <= lo), k (u-lo)^2/(2w) (lo < u < lo+w),
-          k (u - lo - w/2) (u >= lo+w).
+          k (u - lo - w/2) (u >= lo+w), ("cubic01", (c1, c2, c3)) for the cubic at
+          min(max(u, 0), 1).
     blend: "off", "plain" (smoothness indicator) or "external" (per-cell indicator input).
     bc: "periodic", "outflow" (1D or 2D), or in 1D "dirichlet" (end values bc_values).
     diffusion_form: "dc" (doubly conservative) or, in 1D, "nodc" (the diffusion
@@ -287,6 +289,29 @@ def strongly_degenerate_fn(x):
     return torch.where((x + r).abs() < 0.4, one, torch.where((x - r).abs() < 0.4, -one, torch.zeros_like(x)))
 
 
+def buckley_leverett_1d(n: int = 100, gravity: bool = False, problem: str = "ibvp") -> Spec:
+    """Example 6.6: f = u^2/(u^2+(1-u)^2), times 1 - 5(1-u)^2 with gravity; a = eps
+    (2u^2 - 4u^3/3) on [0, 1] (0 below, 2 eps/3 above), eps = 0.01; [0, 1] with Dirichlet
+    ends, MPP limiting, T = 1. problem "ibvp": u0 = 1 - 3x on [0, 1/3), 0 otherwise, ends
+    u(0) = 1, u(1) = 0. "rp": u0 = 0 on [0, 1 - 1/sqrt(2)), 1 otherwise; its ends hold the
+    initial data's end values 0 and 1."""
+    eps = 0.01
+    return Spec(dim=1, nx=n, x0=0.0, x1=1.0, flux=("bl", (5.0 if gravity else 0.0,)),
+                diff=("cubic01", (0.0, 2.0 * eps, -4.0 * eps / 3.0)), umin=0.0, umax=1.0, limiter=True, rk=3,
+                T=1.0, name=f"buckley_leverett1d_{problem}", bc="dirichlet",
+                bc_values=(1.0, 0.0) if problem == "ibvp" else (0.0, 1.0))
+
+
+def bl1d_ibvp_fn(x):
+    """1 - 3x on [0, 1/3), 0 otherwise"""
+    return torch.where(x < 1.0 / 3.0, 1.0 - 3.0 * x, torch.zeros_like(x))
+
+
+def bl1d_rp_fn(x):
+    """0 on [0, 1 - 1/sqrt(2)), 1 otherwise"""
+    return torch.where(x < 1.0 - 1.0 / math.sqrt(2.0), torch.zeros_like(x), torch.ones_like(x))
+
+
 def buckley_leverett_2d_outflow(n: int = 100, limiter: bool = True) -> Spec:
     """Example 6.7: f = u^2/(u^2+(1-u)^2), g = f (1 - 5(1-u)^2), a = 0.01 u on
     [-1.5, 1.5]^2 with outflow ends, u0 = 1 on x^2 + y^2 < 1/2, T = 0.5."""
@@ -337,6 +362,10 @@ def initial_state(spec: Spec, device="cpu", sub: int = 4, order: int = 5):
         return state_3d(lambda x, y, z: barenblatt_3d(x, y, z, 1.0), spec, sub=sub, order=order)
     if spec.name == "evje_karlsen":
         return state_1d(evje_karlsen_fn, spec, device=device, sub=sub, order=order)
+    if spec.name == "buckley_leverett1d_ibvp":
+        return state_1d(bl1d_ibvp_fn, spec, device=device, sub=sub, order=order)
+    if spec.name == "buckley_leverett1d_rp":
+        return state_1d(bl1d_rp_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "strongly_degenerate1d":
         return state_1d(strongly_degenerate_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "degenerate_burgers2d":

@@ -23,7 +23,7 @@ import numpy as np
 from .build import build_oracle
 
 FLUX_KINDS = {"zero": 0, "linear": 1, "burgers": 2, "bl": 3}
-DIFF_KINDS = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4, "ramp": 5}
+DIFF_KINDS = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4, "ramp": 5, "cubic01": 6}
 BC_KINDS = {"periodic": 0, "dirichlet": 1, "outflow": 2}
 BLEND_KINDS = {"off": 0, "plain": 1, "external": 2}
 

@@ -107,10 +107,12 @@ extern "C" {
 
 // Problem description shared with the Python side through ctypes.
 // flux_kind: 0 zero, 1 linear f1=p0*u f2=p1*u (f3=p2*u), 2 Burgers f_l=p0*u^2,
-//            3 Buckley-Leverett f1=u^2/(u^2+(1-u)^2), f2=f1*(1-p0*(1-u)^2).
+//            3 Buckley-Leverett f1=u^2/(u^2+(1-u)^2), f2=f1*(1-p0*(1-u)^2); in 1D the
+//              flux is the gravity form f1*(1-p0*(1-u)^2).
 // diff_kind: 0 none, 1 constant a=p0*u, 2 piecewise linear
 //            a = p0*min(u-p1,0) + p2*max(u-p3,0), 3 porous medium a=u^p0 (integer p0>=1),
 //            4 cubic a = p0*u + p1*u^2 + p2*u^3,
+//            6 the cubic of kind 4 at min(max(u, 0), 1) (constant outside [0, 1]),
 //            5 ramp a = 0 (u <= p1), p0 (u-p1)^2 / (2 p2) (p1 < u < p1+p2),
 //              p0 (u - p1 - p2/2) (u >= p1+p2)  (kappa rises linearly from 0 to p0).
 // bc: 0 periodic, 1 Dirichlet (bc_left, bc_right; 1D only), 2 outflow (1D or 2D).
@@ -164,7 +166,9 @@ template <class R> R flux(const Model& m, int dir, R u) {
     case 3: {
       R v = R(1.0) - u;
       R f1 = u * u / (u * u + v * v);
-      if (dir == 0) return f1;
+      // the gravity factor acts along y in 2D and 3D, and along the only axis in 1D
+      // (Example 6.6: f = f1 (1 - 5 (1-u)^2) with gravity, p0 = 0 without)
+      if (dir == 0 && p.dim != 1) return f1;
       return f1 * (R(1.0) - R(p.flux_p[0]) * v * v);
     }
     default: return R(0.0);
@@ -182,7 +186,7 @@ template <class R> R dflux(const Model& m, int dir, R u) {
       R D = u * u + v * v;
       R f1 = u * u / D;
       R d1 = R(2.0) * u * v / (D * D);
-      if (dir == 0) return d1;
+      if (dir == 0 && p.dim != 1) return d1;
       R g = R(p.flux_p[0]);
       // f2 = f1 (1 - g v^2), f2' = f1' (1 - g v^2) + f1 * 2 g v
       return d1 * (R(1.0) - g * v * v) + f1 * R(2.0) * g * v;
@@ -204,6 +208,11 @@ template <class R> R apot(const Model& m, R u) {
       return r;
     }
     case 4: return R(p.diff_p[0]) * u + R(p.diff_p[1]) * u * u + R(p.diff_p[2]) * u * u * u;
+    case 6: {
+      // the cubic of kind 4 on [0, 1], constant outside (Example 6.6)
+      R v = minr(maxr(u, R(0.0)), R(1.0));
+      return R(p.diff_p[0]) * v + R(p.diff_p[1]) * v * v + R(p.diff_p[2]) * v * v * v;
+    }
     case 5: {
       R lo = R(p.diff_p[1]), w = R(p.diff_p[2]);
       if (u <= lo) return R(0.0);
@@ -228,6 +237,9 @@ template <class R> R kappa(const Model& m, R u) {
       return r;
     }
     case 4: return R(p.diff_p[0]) + R(2.0 * p.diff_p[1]) * u + R(3.0 * p.diff_p[2]) * u * u;
+    case 6:
+      if (!(u > R(0.0) && u < R(1.0))) return R(0.0);
+      return R(p.diff_p[0]) + R(2.0 * p.diff_p[1]) * u + R(3.0 * p.diff_p[2]) * u * u;
     case 5: {
       R lo = R(p.diff_p[1]), w = R(p.diff_p[2]);
       if (u <= lo) return R(0.0);
@@ -252,9 +264,15 @@ double kappa_max(const Model& m) {
     if (p.diff_p[1] > lo) best = std::max(best, p.diff_p[0]);
     if (p.diff_p[3] < hi) best = std::max(best, p.diff_p[2]);
   }
-  if (p.diff_kind == 4 && p.diff_p[2] != 0.0) {
+  if ((p.diff_kind == 4 || p.diff_kind == 6) && p.diff_p[2] != 0.0) {
     double uv = -p.diff_p[1] / (3 * p.diff_p[2]);
     if (uv > lo && uv < hi) best = std::max(best, kappa<double>(m, uv));
+  }
+  if (p.diff_kind == 6) {
+    // one-sided limits of kappa at the ends of [0, 1] inside the interval
+    auto k4 = [&](double u) { return p.diff_p[0] + 2.0 * p.diff_p[1] * u + 3.0 * p.diff_p[2] * u * u; };
+    if (lo < 0.0 && hi > 0.0) best = std::max(best, k4(0.0));
+    if (lo < 1.0 && hi > 1.0) best = std::max(best, k4(1.0));
   }
   return best;
 }
