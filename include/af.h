@@ -63,7 +63,8 @@ enum {
   AF_FLUX_ZERO = 0,       /* f = 0                                                          */
   AF_FLUX_LINEAR = 1,     /* f1 = p0 u, f2 = p1 u                                           */
   AF_FLUX_BURGERS = 2,    /* f1 = f2 = p0 u^2                                               */
-  AF_FLUX_BL = 3          /* Buckley-Leverett: f1 = u^2/(u^2+(1-u)^2), f2 = f1 (1 - p0 (1-u)^2) */
+  AF_FLUX_BL = 3          /* Buckley-Leverett: f1 = u^2/(u^2+(1-u)^2), f2 = f1 (1 - p0 (1-u)^2);
+                             in 1D f = f1 (1 - p0 (1-u)^2) (Example 6.6; p0 = 0: no gravity) */
 };
 
 /* Diffusion potential kinds a(u) = int kappa (Section 1). */
@@ -73,9 +74,11 @@ enum {
   AF_DIFF_PWL = 2,        /* a = p0 min(u - p1, 0) + p2 max(u - p3, 0)  (degenerate band)   */
   AF_DIFF_PME = 3,        /* a = u^p0, p0 integer >= 1 (porous medium)                      */
   AF_DIFF_CUBIC = 4,      /* a = p0 u + p1 u^2 + p2 u^3                                     */
-  AF_DIFF_RAMP = 5        /* a = 0 (u <= p1), p0 (u-p1)^2/(2 p2) (p1 < u < p1+p2),
+  AF_DIFF_RAMP = 5,       /* a = 0 (u <= p1), p0 (u-p1)^2/(2 p2) (p1 < u < p1+p2),
                              p0 (u - p1 - p2/2) (u >= p1+p2): kappa rises linearly from 0
                              to p0 over [p1, p1+p2], p2 > 0 (Example 6.5: p = 1, 0.5, 0.1) */
+  AF_DIFF_CUBIC01 = 6     /* a = p0 v + p1 v^2 + p2 v^3 with v = min(max(u, 0), 1): constant
+                             outside [0, 1] (Example 6.6: p = 0, 2 eps, -4 eps / 3)        */
 };
 
 /* Ends of a 1D interval (Section 6 uses Dirichlet and outflow ends; their discrete

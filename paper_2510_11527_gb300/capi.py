@@ -15,7 +15,7 @@ AF_OK, AF_E_ARG, AF_E_CUDA, AF_E_OOM, AF_E_STATE, AF_E_CFL, AF_E_TIMEOUT, AF_E_U
 STATUS_NAMES = {0: "AF_OK", -1: "AF_E_ARG", -2: "AF_E_CUDA", -3: "AF_E_OOM", -4: "AF_E_STATE", -5: "AF_E_CFL",
                 -6: "AF_E_TIMEOUT", -7: "AF_E_UNSUPPORTED"}
 FLUX = {"zero": 0, "linear": 1, "burgers": 2, "bl": 3}
-DIFF = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4, "ramp": 5}
+DIFF = {"none": 0, "const": 1, "pwl": 2, "pme": 3, "cubic": 4, "ramp": 5, "cubic01": 6}
 BC = {"periodic": 0, "dirichlet": 1, "outflow": 2}
 FORM = {"dc": 0, "nodc": 1}
 PREC = {"fp64": 0, "fp32_mixed": 1}

@@ -166,6 +166,11 @@ __device__ __forceinline__ T apot(const DevModel& m, T u) {
     }
     case AF_DIFF_CUBIC:
       return ((par<T>(d, f, 2) * u + par<T>(d, f, 1)) * u + par<T>(d, f, 0)) * u;
+    case AF_DIFF_CUBIC01: {
+      // the cubic at min(max(u, 0), 1): constant outside [0, 1]
+      const T v = tmin(tmax(u, T(0)), T(1));
+      return ((par<T>(d, f, 2) * v + par<T>(d, f, 1)) * v + par<T>(d, f, 0)) * v;
+    }
     case AF_DIFF_RAMP: {
       // 0 below p1, p0 (u-p1)^2 / (2 p2) on the ramp, p0 (u - p1 - p2/2) above it
       const T k = par<T>(d, f, 0), lo = par<T>(d, f, 1), w = par<T>(d, f, 2), r = u - lo;
@@ -196,6 +201,9 @@ __device__ __forceinline__ T kappa_fn(const DevModel& m, T u) {
       return r;
     }
     case AF_DIFF_CUBIC:
+      return par<T>(d, f, 0) + (T(2) * par<T>(d, f, 1) + T(3) * par<T>(d, f, 2) * u) * u;
+    case AF_DIFF_CUBIC01:
+      if (!(tlt(T(0), u) && tlt(u, T(1)))) return T(0);
       return par<T>(d, f, 0) + (T(2) * par<T>(d, f, 1) + T(3) * par<T>(d, f, 2) * u) * u;
     case AF_DIFF_RAMP: {
       const T k = par<T>(d, f, 0), lo = par<T>(d, f, 1), w = par<T>(d, f, 2);

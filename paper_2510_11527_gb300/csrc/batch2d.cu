@@ -415,7 +415,7 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     if (grids[k].bc != AF_BC_PERIODIC) return AF_E_UNSUPPORTED;
     if (!(grids[k].x1 > grids[k].x0) || !(grids[k].y1 > grids[k].y0)) return AF_E_ARG;
     if (fluxes[k].kind != fluxes[0].kind || fluxes[k].kind < 0 || fluxes[k].kind > AF_FLUX_BL) return AF_E_ARG;
-    if (diffs[k].kind < AF_DIFF_NONE || diffs[k].kind > AF_DIFF_RAMP) return AF_E_ARG;
+    if (diffs[k].kind < AF_DIFF_NONE || diffs[k].kind > AF_DIFF_CUBIC01) return AF_E_ARG;
     if (diffs[k].kind == AF_DIFF_RAMP && !(diffs[k].p[2] > 0.0)) return AF_E_ARG;
     if (bounds[k].from_initial_data || !(bounds[k].umax > bounds[k].umin)) return AF_E_ARG;
   }
@@ -463,7 +463,7 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     for (int q = 0; q < 4; ++q) { I.m.fp[q] = fluxes[k].p[q]; I.m.dp[q] = diffs[k].p[q]; }
     I.m.umin = bounds[k].umin;
     I.m.umax = bounds[k].umax;
-    af::finish_model(I.m, fluxes[k].kind);
+    af::finish_model(I.m, fluxes[k].kind, 2);
     I.kmax = af::kappa_max_of(diffs[k], bounds[k].umin, bounds[k].umax);
     const double scale = std::max(std::fabs(bounds[k].umin), std::fabs(bounds[k].umax));
     I.tol = (b->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;

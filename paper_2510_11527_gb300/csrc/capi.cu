@@ -351,7 +351,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
       (grid->dim == 3 && !(grid->z1 > grid->z0)))
     return AF_E_ARG;
   if (flux->kind < AF_FLUX_ZERO || flux->kind > AF_FLUX_BL) return AF_E_ARG;
-  if (diff->kind < AF_DIFF_NONE || diff->kind > AF_DIFF_RAMP) return AF_E_ARG;
+  if (diff->kind < AF_DIFF_NONE || diff->kind > AF_DIFF_CUBIC01) return AF_E_ARG;
   if (diff->kind == AF_DIFF_PME && (diff->p[0] < 1.0 || diff->p[0] != std::floor(diff->p[0]))) return AF_E_ARG;
   if (diff->kind == AF_DIFF_RAMP && !(diff->p[2] > 0.0)) return AF_E_ARG;
   if (grid->bc < AF_BC_PERIODIC || grid->bc > AF_BC_OUTFLOW) return AF_E_ARG;
@@ -403,7 +403,7 @@ af_status af_create(const af_grid* grid, const af_flux* flux, const af_diff* dif
   c->bounds_pending = bounds->from_initial_data != 0;
   c->m.umin = bounds->umin;
   c->m.umax = bounds->umax;
-  af::finish_model(c->m, flux->kind);
+  af::finish_model(c->m, flux->kind, grid->dim);
   if (!c->bounds_pending) c->kmax = af::kappa_max_of(*diff, bounds->umin, bounds->umax);
   const double scale = std::max(std::fabs(bounds->umin), std::fabs(bounds->umax));
   c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;

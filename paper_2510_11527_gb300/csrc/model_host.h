@@ -73,13 +73,24 @@ inline void bl_critical_points(DevModel& m) {
   }
 }
 
-// after fp/dp/umin/umax are set: flux-specific tables and float copies
-inline void finish_model(DevModel& m, int flux_kind) {
+// after fp/dp/umin/umax are set: flux-specific tables and float copies. In 1D the
+// Buckley-Leverett flux is the gravity form f1 (1 - g (1-u)^2), the form of direction 1:
+// its extrema tables are also placed in slot 0, which the 1D wave-speed code reads.
+inline void finish_model(DevModel& m, int flux_kind, int dim) {
   for (int d = 0; d < 2; ++d) {
     m.ncrit[d] = 0;
     for (int k = 0; k < 8; ++k) m.crit[d][k] = m.critv[d][k] = 0.0;
   }
-  if (flux_kind == AF_FLUX_BL) bl_critical_points(m);
+  if (flux_kind == AF_FLUX_BL) {
+    bl_critical_points(m);
+    if (dim == 1) {
+      m.ncrit[0] = m.ncrit[1];
+      for (int k = 0; k < 8; ++k) {
+        m.crit[0][k] = m.crit[1][k];
+        m.critv[0][k] = m.critv[1][k];
+      }
+    }
+  }
   fill_float_params(m);
 }
 
@@ -91,6 +102,8 @@ inline double kappa_of(const af_diff& df, double u) {
     case AF_DIFF_PME: return df.p[0] * std::pow(u, df.p[0] - 1.0);
     case AF_DIFF_CUBIC: return df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u;
     case AF_DIFF_RAMP: return u <= df.p[1] ? 0.0 : (u < df.p[1] + df.p[2] ? df.p[0] * (u - df.p[1]) / df.p[2] : df.p[0]);
+    case AF_DIFF_CUBIC01:
+      return (u > 0.0 && u < 1.0) ? df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u : 0.0;
     default: return 0.0;
   }
 }
@@ -102,9 +115,15 @@ inline double kappa_max_of(const af_diff& df, double lo, double hi) {
     if (lo < df.p[1]) k = std::max(k, df.p[0]);
     if (hi > df.p[3]) k = std::max(k, df.p[2]);
   }
-  if (df.kind == AF_DIFF_CUBIC && df.p[2] != 0.0) {
+  if ((df.kind == AF_DIFF_CUBIC || df.kind == AF_DIFF_CUBIC01) && df.p[2] != 0.0) {
     const double uv = -df.p[1] / (3.0 * df.p[2]);
     if (uv > lo && uv < hi) k = std::max(k, kappa_of(df, uv));
+  }
+  if (df.kind == AF_DIFF_CUBIC01) {
+    // one-sided limits at the ends of [0, 1] inside the interval
+    auto k4 = [&](double u) { return df.p[0] + 2.0 * df.p[1] * u + 3.0 * df.p[2] * u * u; };
+    if (lo < 0.0 && hi > 0.0) k = std::max(k, k4(0.0));
+    if (lo < 1.0 && hi > 1.0) k = std::max(k, k4(1.0));
   }
   return k;
 }

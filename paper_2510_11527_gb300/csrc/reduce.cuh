@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
     double a1, a2;
     if constexpr (FLUX == FLUX_BL) {
       const BLVals<double> r = bl_eval<double>(m, u);
-      a1 = r.d[0];
+      a1 = r.d[dim == 1 ? 1 : 0];   // 1D: the gravity form (its extrema tables sit in slot 0)
       a2 = r.d[1];
       double un = ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)];
       if (dim == 1 && bc != AF_BC_PERIODIC && i + 1 == nx) un = bc == AF_BC_DIRICHLET ? gr : u;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
     const double gv[2] = {gl, gr};
     for (int s = 0; s < 2; ++s) {
       double d;
-      if constexpr (FLUX == FLUX_BL) d = bl_eval<double>(m, gv[s]).d[0];
+      if constexpr (FLUX == FLUX_BL) d = bl_eval<double>(m, gv[s]).d[1];
       else d = alpha_interval<FLUX, double>(m, 0, gv[s], gv[s]);
       best = tmax(best, d * inv_h1 + kd1);
     }

@@ -64,6 +64,9 @@ template <int FLUX, class T, class PT>
 __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const StageArgs2D<PT> A) {
   using L = Tile1D<FLUX, T>;
   constexpr int TX = L::TX, NT = L::NT, H = L::H, BX = L::BX;
+  // flux direction of the model functions: the 1D Buckley-Leverett flux is the gravity
+  // form f1 (1 - g (1-u)^2), which the model keeps as direction 1 (Example 6.6)
+  constexpr int XD = FLUX == FLUX_BL ? 1 : 0;
   __shared__ T sU[BX], sP[BX], sC[BX];
   // aP / aC hold kappa instead of a without double conservation (no DC potential)
   __shared__ T fP[BX], aP[BX], fC[BX], aC[BX], dP[BX], dC[BX], fU[BX], aU[BX];
@@ -89,17 +92,17 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   __syncthreads();
   for (int b = tid; b < BX; b += NT) {
     const T u = sU[b];
-    fU[b] = flux<FLUX, T>(m, 0, u);
+    fU[b] = flux<FLUX, T>(m, XD, u);
     aU[b] = apot<T>(m, u);
     const T p = sP[b];
-    fP[b] = flux<FLUX, T>(m, 0, p);
-    dP[b] = dflux_abs<FLUX, T>(m, 0, p);
+    fP[b] = flux<FLUX, T>(m, XD, p);
+    dP[b] = dflux_abs<FLUX, T>(m, XD, p);
     aP[b] = nodc ? kappa_fn<T>(m, p) : apot<T>(m, p);
     if (b >= 1) {
       const T c = (T(6) * u - sP[b - 1] - p) * T(0.25);
       sC[b] = c;
-      fC[b] = flux<FLUX, T>(m, 0, c);
-      dC[b] = dflux_abs<FLUX, T>(m, 0, c);
+      fC[b] = flux<FLUX, T>(m, XD, c);
+      dC[b] = dflux_abs<FLUX, T>(m, XD, c);
       aC[b] = nodc ? kappa_fn<T>(m, c) : apot<T>(m, c);
     }
     if (blend && !ext && b >= 1 && b < BX - 1) {
@@ -134,7 +137,7 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   }
   for (int b = H - 2 + tid; b <= H + TX; b += NT) {
     const T ul = sU[b], ur = sU[b + 1];
-    const T fl = T(0.5) * (fU[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, 0, ul, ur) * (ur - ul);
+    const T fl = T(0.5) * (fU[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, XD, ul, ur) * (ur - ul);
     if (!nodc) {
       if (b >= H - 1 && b < H + TX) sFH[b] = fP[b];
       if (b >= H - 1) sAH[b] = (T(8) * aC[b] - aP[b - 1] - aP[b]) * T(1.0 / 6.0);
@@ -167,8 +170,8 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
     for (int q = 0; q < nq; ++q) {
       const int b = bq[q];
       const T zm = sU[b], z0 = sP[b], zp = sU[b + 1];
-      const T Fr = T(0.5) * (fP[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, 0, z0, zp) * (zp - z0);
-      const T Fl = T(0.5) * (fU[b] + fP[b]) - T(0.5) * alpha_interval<FLUX, T>(m, 0, zm, z0) * (z0 - zm);
+      const T Fr = T(0.5) * (fP[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, XD, z0, zp) * (zp - z0);
+      const T Fl = T(0.5) * (fU[b] + fP[b]) - T(0.5) * alpha_interval<FLUX, T>(m, XD, zm, z0) * (z0 - zm);
       const T RL = (aU[b + 1] - T(2) * aP[b] + aU[b]) * (T(4) * ih * ih) - (Fr - Fl) * (T(2) * ih);
       rP[q] = sTC[b] * rH[q] + (T(1) - sTC[b]) * RL;
     }
