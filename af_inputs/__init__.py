@@ -230,6 +230,24 @@ def barenblatt(x, y, t: float, m: int = 2, d: int = 2):
     return t ** (-alpha) * torch.clamp(core, min=0.0) ** (1.0 / (m - 1))
 
 
+def two_hills_fn(x, y):
+    """Example 6.4: exp(-1/(6 - r^2)) inside r^2 < 6 about (2, -2) and about (-2, 2), 0
+    elsewhere (the two supports are disjoint)."""
+    out = torch.zeros(torch.broadcast_shapes(x.shape, y.shape), dtype=torch.float64, device=x.device)
+    for cx, cy in ((2.0, -2.0), (-2.0, 2.0)):
+        r2 = (x - cx) ** 2 + (y - cy) ** 2
+        inside = r2 < 6.0
+        out = out + torch.where(inside, torch.exp(-1.0 / torch.where(inside, 6.0 - r2, 1.0)), torch.zeros_like(out))
+    return out
+
+
+def two_hills(n: int = 100, limiter: bool = True) -> Spec:
+    """Example 6.4 (collision of two hills): u_t = Lap(u^2) on the periodic [-10, 10]^2,
+    T = 4; bounds [0, exp(-1/6)], the range of the initial data."""
+    return Spec(dim=2, nx=n, ny=n, x0=-10.0, x1=10.0, y0=-10.0, y1=10.0, flux=("zero", ()), diff=("pme", (2,)),
+                umin=0.0, umax=math.exp(-1.0 / 6.0), limiter=limiter, rk=3, T=4.0, name="two_hills")
+
+
 def bl_disc_fn(x, y, radius: float = 0.5):
     return ((x * x + y * y) < radius * radius).to(torch.float64)
 
@@ -372,6 +390,8 @@ def initial_state(spec: Spec, device="cpu", sub: int = 4, order: int = 5):
         return state_2d(discs_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "pme2d":
         return state_2d(lambda x, y: barenblatt(x, y, 1.0), spec, device=device, sub=sub, order=order)
+    if spec.name == "two_hills":
+        return state_2d(two_hills_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "buckley_leverett2d":
         return state_2d(bl_disc_fn, spec, device=device, sub=sub, order=order)
     if spec.name == "buckley_leverett2d_outflow":
