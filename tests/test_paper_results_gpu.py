@@ -179,3 +179,35 @@ def test_barenblatt_to_t2_vs_closed_form():
         err[prec] = float(np.mean(np.abs(got - ref)))
     assert err["fp64"] < 3e-7, err
     assert abs(err["fp32_mixed"] - err["fp64"]) <= 0.05 * err["fp64"], err
+
+
+def test_two_hills_to_final_time():
+    """Example 6.4 (collision of two hills, 100^2 on the periodic [-10, 10]^2, T = 4):
+    the CUDA path matches the oracle's run; with the MPP limiting the minimum is exactly
+    0 and mass is conserved; without it negative values appear."""
+    import dataclasses
+    import oracle
+    spec = ai.two_hills(100)
+    st = [a.numpy() for a in ai.initial_state(spec)]
+    ref, nref, stats = oracle.run_native(spec, 3, st, spec.T)
+    assert stats["error"] == 0
+    with solver(spec) as s:
+        s.set_state(st)
+        n = s.run(spec.T)
+        got = s.get_state()
+        lo, hi = s.bounds()
+        mass = s.mass()
+        assert s.stats()["errors"] == 0
+    assert n == nref
+    err = max(np.max(np.abs(g - r)) for g, r in zip(got, ref)) / spec.umax
+    print(f"two hills: {n} steps, max relative difference from the oracle {err:.3e}")
+    assert err <= TOL_TWO_HILLS
+    assert lo == 0.0 and hi <= spec.umax
+    assert mass == pytest.approx(float(np.sum(st[0])) * spec.dx * spec.dy, rel=1e-12)
+    with solver(dataclasses.replace(spec, limiter=False)) as s:
+        s.set_state(st)
+        s.run(0.5)
+        assert s.bounds()[0] < -1e-4
+
+
+TOL_TWO_HILLS = 1e-12
