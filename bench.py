@@ -372,6 +372,8 @@ def forms(args, headline_value, peaks):
         res.update(_form_bounded1d(args, stream, peaks))
     if "ex65" in sel:
         res.update(_form_ex65())
+    if "ex64_66" in sel:
+        res.update(_form_examples_64_66())
     if "rect2d" in sel:
         res.update(_form_rect2d(args, stream, flush, peaks))
     if "pme3d" in sel:
@@ -459,6 +461,33 @@ def _form_ex65():
             torch.cuda.synchronize()
             small[form] = {"steps": n, "seconds": round(time.perf_counter() - t0, 3)}
     return {"evje_karlsen_200_to_T1": small}
+
+
+def _form_examples_64_66():
+    """Examples 6.4 (two hills, 100^2 to T = 4) and 6.6 (1D Buckley-Leverett, 100 cells
+    to T = 1, both initial data, with and without gravity) as printed, FP64 through
+    af_run: time to solution."""
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import Solver
+
+    def timed(spec):
+        st = [a.numpy() for a in ai.initial_state(spec)]
+        with Solver(spec, precision="fp64") as s:
+            s.set_state(st)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            n = s.run(spec.T)
+            torch.cuda.synchronize()
+            lo, _ = s.bounds()
+            return {"steps": n, "seconds": round(time.perf_counter() - t0, 3), "min": lo}
+
+    out = {"two_hills_100x100_to_T4": timed(ai.two_hills(100))}
+    for g in (False, True):
+        for p in ("ibvp", "rp"):
+            out[f"buckley_leverett1d_{p}_{'gravity' if g else 'nogravity'}_100_to_T1"] = \
+                timed(ai.buckley_leverett_1d(100, g, p))
+    return out
 
 
 def _form_pme3d(args, stream, peaks):
@@ -776,11 +805,11 @@ def main():
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--n1d", type=int, default=1 << 24, help="cells of the bounded1d form")
     ap.add_argument("--n3d", type=int, default=128, help="cells per direction of the pme3d form")
-    ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl,bounded1d,ex65,rect2d,pme3d",
+    ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl,bounded1d,ex65,ex64_66,rect2d,pme3d",
                     help="comma list of forms to run: fp32 (Burgers 1024^2), rk54 (Burgers 1024^2 with "
                          "SSP-RK(5,4)), pme (4096^2), batch (256), bl (4096^2), bounded1d (Example 6.5's "
                          "problem on 2^24 cells, with and without double conservation), ex65 (Example 6.5 "
-                         "as printed: 200 cells to T = 1), rect2d (Examples 6.7 / 6.9 at 100^2 to T and "
+                         "as printed: 200 cells to T = 1), ex64_66 (Examples 6.4 and 6.6 as printed), rect2d (Examples 6.7 / 6.9 at 100^2 to T and "
                          "Example 6.9's problem on 2048^2 with outflow ends vs periodic), pme3d (3D porous "
                          "medium on 128^3)")
     args = ap.parse_args()
