@@ -206,6 +206,9 @@ af::StageArgs3D<T> args3d(af_ctx* c, int in) {
   for (int l = 0; l < 3; ++l) {
     a.i6h[l] = a.inv_h[l] / 6.0;
     a.i3h2[l] = a.inv_h[l] * a.inv_h[l] / 3.0;
+    a.inv_hT[l] = (T)a.inv_h[l];
+    a.i6hT[l] = (T)a.i6h[l];
+    a.i3h2T[l] = (T)a.i3h2[l];
   }
   a.ub = (const double*)c->k3[in][0];
   for (int s = 1; s < 8; ++s) a.pt[s] = (const T*)c->k3[in][s];

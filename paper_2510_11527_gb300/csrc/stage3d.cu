@@ -176,16 +176,26 @@ __device__ __forceinline__ T ulm3(const DevModel& m, const StageArgs3D<T>& A, si
 template <int FLUX, class T>
 __global__ void __launch_bounds__(T3) limit3d_kernel(const DevModel m, const StageArgs3D<T> A, int o) {
   const double dtv = *A.dt;
-  if (dtv == 0.0) return;
-  const double tau = A.tcoef[o] * dtv;
+  if (dtv == 0.0) return;   // uniform over the grid
+  // per-direction factors of this launch, formed once per block in FP64 and rounded to
+  // the stencil type (a double -> float rounding is an FP64-unit instruction on GB300)
+  __shared__ T sK[3][4];   // 6 mu, 6 nu, 18 mu, 18 nu
+  if (threadIdx.x < 3) {
+    const int l = threadIdx.x;
+    const double mu = A.tcoef[o] * dtv * A.inv_h[l], nu = mu * A.inv_h[l];
+    sK[l][0] = T(6.0 * mu);
+    sK[l][1] = T(6.0 * nu);
+    sK[l][2] = T(18.0 * mu);
+    sK[l][3] = T(18.0 * nu);
+  }
+  __syncthreads();
   const size_t N = cells3(A);
+  const T g = T(A.gamma), umin = T(m.umin), umax = T(m.umax);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N; q += (size_t)gridDim.x * blockDim.x) {
     int c[3];
     decode3(A, q, c);
     const T u = to_stencil<T>(A.ub[q]), au = apot<T>(m, u);
-    const T g = T(A.gamma), umin = T(m.umin), umax = T(m.umax);
     for (int l = 0; l < 3; ++l) {
-      const double mu = tau * A.inv_h[l], nu = mu * A.inv_h[l];
       const size_t qp = nbr3(A, c, l, 1), qm = nbr3(A, c, l, -1);
       T fh = A.FH[l][q], ah = A.AH[l][q];
       const T fl = A.FL[l][q];
@@ -197,8 +207,8 @@ __global__ void __launch_bounds__(T3) limit3d_kernel(const DevModel m, const Sta
       }
       T flim = fh, alim = ah;
       if (A.limiter) {
-        const T mu6 = T(6.0 * mu), nu6 = T(6.0 * nu);
-        const T k = T(18.0 * mu), kd = T(18.0 * nu);
+        const T mu6 = sK[l][0], nu6 = sK[l][1];
+        const T k = sK[l][2], kd = sK[l][3];
         const T dF = fh - fl;
         const T zp = ulp3<FLUX, T>(m, A, q, qp, l, mu6, nu6), zm = ulm3<FLUX, T>(m, A, qp, q, l, mu6, nu6);
         const T tcl = tmin(theta_fn<T>(zp, zp - k * dF, umin, umax), theta_fn<T>(zm, zm + k * dF, umin, umax));
@@ -218,10 +228,19 @@ __global__ void __launch_bounds__(T3) limit3d_kernel(const DevModel m, const Sta
 template <int FLUX, class T>
 __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const StageArgs3D<T> A, int o) {
   const double dtv = *A.dt;
-  if (dtv == 0.0) return;
+  if (dtv == 0.0) return;   // uniform over the grid
   const double tau = A.tcoef[o] * dtv;
   const double cA = A.cA[o], cF = A.cF[o];
+  // mu_l = tau / h_l and nu_l = tau / h_l^2 of this launch, once per block
+  __shared__ double sMu[3], sNu[3];
+  if (threadIdx.x < 3) {
+    const int l = threadIdx.x;
+    sMu[l] = tau * A.inv_h[l];
+    sNu[l] = sMu[l] * A.inv_h[l];
+  }
+  __syncthreads();
   const size_t N = cells3(A);
+  const T taut = T(tau), cAt = T(cA), cFt = T(cF), umin = T(m.umin), umax = T(m.umax), g = T(A.gamma);
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N; q += (size_t)gridDim.x * blockDim.x) {
     int c[3];
     decode3(A, q, c);
@@ -229,7 +248,7 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
     // limited cell-average update (eq. multid_limited_average), in FP64
     double v = A.ub[q];
     for (int l = 0; l < 3; ++l) {
-      const double mu = tau * A.inv_h[l], nu = mu * A.inv_h[l];
+      const double mu = sMu[l], nu = sNu[l];
       const size_t qm = nbr3(A, c, l, -1), qp = nbr3(A, c, l, 1);
       const double f0 = wide(A.Flim[l][q]), fm = wide(A.Flim[l][qm]);
       const double a0 = wide(A.Alim[l][q]), am = wide(A.Alim[l][qm]), ap = wide(A.Alim[l][qp]);
@@ -238,13 +257,12 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
     double ubo = cA != 0.0 ? rk_comb(cA, A.Aub[o][q], cF, v) : rk_scale(cF, v);
     if (A.limiter && A.sg[o]) ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
     A.Oub[o][q] = ubo;
-    const T taut = T(tau), cAt = T(cA), cFt = T(cF), umin = T(m.umin), umax = T(m.umax), g = T(A.gamma);
     // point values owned by the cell: kinds 1..7 at fine 2c + s
     for (int s = 1; s < 8; ++s) {
       const int p[3] = {s & 1, (s >> 1) & 1, (s >> 2) & 1};   // offsets from 2c
       T acc = T(0);
       for (int l = 0; l < 3; ++l) {
-        const T ih = T(A.inv_h[l]);
+        const T ih = A.inv_hT[l];
         T z[5], fz[5], dz[5], az[5];
         for (int t = 0; t < 5; ++t) {
           int f[3] = {p[0], p[1], p[2]};
@@ -256,7 +274,7 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
         }
         const T alpha = tmax(tmax(tmax(dz[0], dz[1]), tmax(dz[3], dz[4])), dz[2]);
         const T rh = line_res<T>(z[0], z[1], z[2], z[3], z[4], fz[0], fz[1], fz[3], fz[4], alpha, az[0], az[1], az[2],
-                                 az[3], az[4], T(A.i6h[l]), T(A.i3h2[l]));
+                                 az[3], az[4], A.i6hT[l], A.i3h2T[l]);
         T r = rh;
         if (A.blend) {
           // weight: min of theta^{c,s}_l over the l-faces holding the point (s_l = 1),

@@ -16,6 +16,7 @@ struct StageArgs3D {
   int n[3];                          // cells per direction
   double inv_h[3];                   // 1/dx, 1/dy, 1/dz
   double i6h[3], i3h2[3];            // 1/(6 h_l), 1/(3 h_l^2)
+  T inv_hT[3], i6hT[3], i3h2T[3];    // the same three, rounded to the stencil type
   const double* ub;                  // FE input: cell averages
   const T* pt[8];                    // FE input: point values by kind (pt[0] unused)
   int nout;                          // 1 or 2 limited FE evaluations of the same input

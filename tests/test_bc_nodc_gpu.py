@@ -327,3 +327,29 @@ def test_example_6_6_fp32_mixed(gravity):
     # measured 7.6e-7 (no gravity) and 4.0e-6 (gravity) after 910 / 1307 steps
     assert err <= 2e-5
     assert lo >= 0.0 and hi <= 1.0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_clipped_cubic_in_2d_and_3d(dim, prec):
+    """the clipped cubic potential on the 2D and 3D paths, with data beyond [0, 1]"""
+    diff = ("cubic01", (0.0, 0.02, -0.04 / 3.0))
+    if dim == 2:
+        spec = ai.Spec(dim=2, nx=45, ny=37, x0=0, x1=1.0, y0=0, y1=0.8, flux=("burgers", (0.5,)), diff=diff,
+                       umin=-0.5, umax=1.5, limiter=True, blend="plain")
+        st = np_state(ai.random_state_2d(spec, seed=3))
+    else:
+        spec = ai.Spec(dim=3, nx=11, ny=9, nz=7, x0=0, x1=1.0, y0=0, y1=0.8, z0=0, z1=0.6, flux=("burgers", (0.5,)),
+                       diff=diff, umin=-0.5, umax=1.5, limiter=True, blend="plain")
+        st = np_state(ai.random_state_3d(spec, seed=3))
+    tau = oracle.dt_cfl(spec, st[0])
+    want = oracle.fe(spec, st, tau)
+    with solver(spec, prec) as s:
+        s.set_state(st)
+        assert s.dt_cfl() == pytest.approx(tau, rel=1e-14)
+        s.forward_euler(tau)
+        got = s.get_state()
+    if prec == "fp64":
+        assert relerr(got, want) <= TOL64
+    else:
+        assert max(np.max(np.abs(g - w)) for g, w in zip(got, want)) <= 1e-5
