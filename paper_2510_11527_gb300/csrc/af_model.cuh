@@ -27,6 +27,7 @@ struct DevModel {
   // the same parameters rounded to float, read by the FP32 stencils (GB300's FP64
   // unit also performs the double->float conversions, so none happen per use)
   float fpf[4], dpf[4], critf[2][8], critvf[2][8];
+  int pme_e;             // AF_DIFF_PME: the integer exponent p0 (no conversion per use)
 };
 
 // parameter k of a double/float pair in the stencil precision T
@@ -39,6 +40,7 @@ inline void fill_float_params(DevModel& m) {
     m.fpf[k] = (float)m.fp[k];
     m.dpf[k] = (float)m.dp[k];
   }
+  m.pme_e = m.diff_kind == AF_DIFF_PME ? (int)m.dp[0] : 0;
   for (int d = 0; d < 2; ++d)
     for (int k = 0; k < 8; ++k) {
       m.critf[d][k] = (float)m.crit[d][k];
@@ -159,7 +161,7 @@ __device__ __forceinline__ T apot(const DevModel& m, T u) {
       if ((__double_as_longlong(d[2]) << 1) == 0) return par<T>(d, f, 0) * tmin(u - par<T>(d, f, 1), T(0));
       return par<T>(d, f, 0) * tmin(u - par<T>(d, f, 1), T(0)) + par<T>(d, f, 2) * tmax(u - par<T>(d, f, 3), T(0));
     case AF_DIFF_PME: {
-      int e = (int)m.dpf[0];
+      const int e = m.pme_e;
       T r = u;
       for (int k = 1; k < e; ++k) r *= u;
       return r;
@@ -195,7 +197,7 @@ __device__ __forceinline__ T kappa_fn(const DevModel& m, T u) {
     case AF_DIFF_PWL:
       return (tlt(u, par<T>(d, f, 1)) ? par<T>(d, f, 0) : T(0)) + (tlt(par<T>(d, f, 3), u) ? par<T>(d, f, 2) : T(0));
     case AF_DIFF_PME: {
-      const int e = (int)m.dpf[0];
+      const int e = m.pme_e;
       T r = T(e);
       for (int k = 1; k < e; ++k) r *= u;
       return r;
