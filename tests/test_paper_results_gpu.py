@@ -211,3 +211,26 @@ def test_two_hills_to_final_time():
 
 
 TOL_TWO_HILLS = 1e-12
+
+
+@pytest.mark.parametrize("m", [2, 3, 5, 8])
+def test_barenblatt_1d_gpu(m):
+    """Example 6.3, 1D (80 cells on [-6, 6], t: 1 -> 2, SSP-RK(5,4)): the CUDA path
+    matches the oracle's runs with and without limiting; the limited minimum is exactly
+    0 and the unlimited one is negative."""
+    import dataclasses
+    import oracle
+    spec = ai.Spec(dim=1, nx=80, x0=-6.0, x1=6.0, flux=("zero", ()), diff=("pme", (m,)), umin=0.0, umax=1.0,
+                   limiter=True)
+    st = [a.numpy() for a in ai.state_1d(lambda x: ai.barenblatt(x, torch.zeros_like(x), 1.0, m=m, d=1), spec)]
+    for lim in (True, False):
+        sp = dataclasses.replace(spec, limiter=lim)
+        ref, nref, _ = oracle.run_native(sp, 54, st, 1.0)
+        with solver(sp, rk=54) as s:
+            s.set_state(st)
+            n = s.run(1.0)
+            got = s.get_state()
+            lo, _ = s.bounds()
+        assert n == nref
+        assert max(np.max(np.abs(g - r)) for g, r in zip(got, ref)) <= 1e-12
+        assert (lo == 0.0) if lim else (lo < 0.0)
