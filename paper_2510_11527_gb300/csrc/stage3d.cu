@@ -105,12 +105,27 @@ __global__ void __launch_bounds__(T3) centre3d_kernel(const StageArgs3D<T> A) {
   for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < N; q += (size_t)gridDim.x * blockDim.x) {
     int c[3];
     decode3(A, q, c);
-    const FineAxes fa = fine_axes(A, c);
+    // the fine point at offset m in {-1, 0, 1}^3 from the centre is of kind
+    // s = [m_x != 0] + 2 [m_y != 0] + 4 [m_z != 0], stored with the cell c - [m = -1]:
+    // the 8 cells of the block c - {0, 1}^3 hold all 26 (same order and weights as
+    // the fine-grid walk)
+    size_t cq[8];
+    {
+      int lo[3];
+      for (int l = 0; l < 3; ++l) lo[l] = c[l] == 0 ? A.n[l] - 1 : c[l] - 1;
+      for (int a = 0; a < 8; ++a) {
+        const int x = (a & 1) ? lo[0] : c[0], y = (a & 2) ? lo[1] : c[1], z = (a & 4) ? lo[2] : c[2];
+        cq[a] = ((size_t)z * A.n[1] + y) * A.n[0] + x;
+      }
+    }
     T acc = T(0);
+#pragma unroll
     for (int o = 0; o < 27; ++o) {
-      const int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
-      if (mm[0] == 0 && mm[1] == 0 && mm[2] == 0) continue;
-      acc = acc + w27<T>(o) * zoff(A, fa, mm[0], mm[1], mm[2]);
+      const int mx = o % 3 - 1, my = (o / 3) % 3 - 1, mz = o / 9 - 1;
+      if (mx == 0 && my == 0 && mz == 0) continue;
+      const int kind = (mx != 0) | ((my != 0) << 1) | ((mz != 0) << 2);
+      const int a = (mx < 0) | ((my < 0) << 1) | ((mz < 0) << 2);
+      acc = acc + w27<T>(o) * A.pt[kind][cq[a]];
     }
     A.C[q] = (T(216) * to_stencil<T>(A.ub[q]) - acc) * T(1.0 / 64.0);
   }
