@@ -15,6 +15,7 @@ What lives here:
 
 Problem descriptions are any object with the attributes of ``af_inputs.Spec``.
 """
+import contextlib
 import ctypes
 import math
 
@@ -53,29 +54,48 @@ _lib = None
 def lib():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build_oracle())
-        P = ctypes.POINTER(Problem)
-        dpp = ctypes.POINTER(ctypes.c_double)
-        arr = ctypes.POINTER(dpp)
-        _lib.ao_fe.argtypes = [P, arr, ctypes.c_double, dpp, arr]
-        _lib.ao_step.argtypes = [P, ctypes.c_int, arr, ctypes.c_double, dpp, ctypes.POINTER(Stats)]
-        _lib.ao_dt.argtypes = [P, dpp, ctypes.c_double, ctypes.c_double]
-        _lib.ao_dt.restype = ctypes.c_double
-        _lib.ao_kappa_max.argtypes = [P]
-        _lib.ao_kappa_max.restype = ctypes.c_double
-        _lib.ao_alpha_interval.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double]
-        _lib.ao_alpha_interval.restype = ctypes.c_double
-        _lib.ao_point_funcs.argtypes = [P, ctypes.c_int, ctypes.c_double, dpp, dpp, dpp]
-        _lib.ao_theta.argtypes = [P, ctypes.c_double, ctypes.c_double]
-        _lib.ao_theta.restype = ctypes.c_double
-        _lib.ao_rk54_coefs.argtypes = [dpp, dpp]
-        _lib.ao_flop_count.argtypes = [P, arr, ctypes.c_double, dpp, ctypes.POINTER(ctypes.c_longlong)]
-        _lib.ao_fe_generic.argtypes = [P, arr, ctypes.c_double, dpp, arr]
-        _lib.ao_run.argtypes = [P, ctypes.c_int, arr, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(Stats)]
-        _lib.ao_first_order_run.argtypes = [P, dpp, ctypes.c_double, ctypes.c_double,
-                                            ctypes.POINTER(ctypes.c_longlong)]
+        _lib = _load(build_oracle())
     return _lib
+
+
+@contextlib.contextmanager
+def planted(**defines):
+    """Run the oracle API on a variant build with a planted mistake (preprocessor
+    macros of af_oracle.cpp), to show that a pin catches it. Restores the oracle on
+    exit."""
+    global _lib
+    saved = lib()
+    _lib = _load(build_oracle(defines=defines))
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def _load(path):
+    lb = ctypes.CDLL(path)
+    P = ctypes.POINTER(Problem)
+    dpp = ctypes.POINTER(ctypes.c_double)
+    arr = ctypes.POINTER(dpp)
+    lb.ao_fe.argtypes = [P, arr, ctypes.c_double, dpp, arr]
+    lb.ao_step.argtypes = [P, ctypes.c_int, arr, ctypes.c_double, dpp, ctypes.POINTER(Stats)]
+    lb.ao_dt.argtypes = [P, dpp, ctypes.c_double, ctypes.c_double]
+    lb.ao_dt.restype = ctypes.c_double
+    lb.ao_kappa_max.argtypes = [P]
+    lb.ao_kappa_max.restype = ctypes.c_double
+    lb.ao_alpha_interval.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_double]
+    lb.ao_alpha_interval.restype = ctypes.c_double
+    lb.ao_point_funcs.argtypes = [P, ctypes.c_int, ctypes.c_double, dpp, dpp, dpp]
+    lb.ao_theta.argtypes = [P, ctypes.c_double, ctypes.c_double]
+    lb.ao_theta.restype = ctypes.c_double
+    lb.ao_rk54_coefs.argtypes = [dpp, dpp]
+    lb.ao_flop_count.argtypes = [P, arr, ctypes.c_double, dpp, ctypes.POINTER(ctypes.c_longlong)]
+    lb.ao_fe_generic.argtypes = [P, arr, ctypes.c_double, dpp, arr]
+    lb.ao_run.argtypes = [P, ctypes.c_int, arr, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                          ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(Stats)]
+    lb.ao_first_order_run.argtypes = [P, dpp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_longlong)]
+    return lb
 
 
 def make_problem(spec) -> Problem:

@@ -31,6 +31,9 @@
 // Readings where the paper is silent (also listed in the design notes):
 //   * 2D factors: directional split 1/(2d)=1/4, limiter factor 3*2d = 12, MPP CFL 1/4
 //     (derived from the 1D factors 2,6 and the 3D factors 6,18 of Section 5).
+//   * Without a diffusion term (a constant) each limited directional state has only
+//     its face correction, so the face limiter factor is 2d instead of 3*2d (Example
+//     6.2's limited results in Table 3 and its fourth-order rate need this factor).
 //   * 2D cell potential A^H_l: tensor Simpson average of the 1D potential a-hat of
 //     Proposition 2.1 along the transverse direction (Section 4, face averages).
 //   * Low-order point residual used by the smoothness blend (Section 5.1.3 defers it):
@@ -249,6 +252,39 @@ template <class R> R kappa(const Model& m, R u) {
     default: return R(0.0);
   }
 }
+
+// Whether the equation has a diffusion term at all: a(u) is constant for kind 0 and
+// for every kind whose coefficients of u are all zero (the porous medium always
+// diffuses).
+bool has_diffusion(const ao_problem& p) {
+  switch (p.diff_kind) {
+    case 1: return p.diff_p[0] != 0.0;
+    case 2: return p.diff_p[0] != 0.0 || p.diff_p[2] != 0.0;
+    case 3: return true;
+    case 4:
+    case 6: return p.diff_p[0] != 0.0 || p.diff_p[1] != 0.0 || p.diff_p[2] != 0.0;
+    case 5: return p.diff_p[0] != 0.0;
+    default: return false;
+  }
+}
+
+// Number of parts in the convex decomposition of each limited directional state
+// u^{Lim,+-} (Section 5.1.1; Section 5.2 per direction). With diffusion each state is
+// the mean of three parts -- the face correction and the two potential corrections --
+// so a face correction enters its part with factor 3 * 2d (6 in 1D, 12 in 2D, 18 in
+// 3D). Without a diffusion term the potential corrections vanish identically and the
+// state consists of the face correction alone, factor 2d (reading of Example 6.2: the
+// pure-convection limiter reproduces Table 3's limited columns and keeps the
+// fourth-order rate only with this factor).
+int lim_parts(const ao_problem& p) { return has_diffusion(p) ? 3 : 1; }
+
+// Planted-mistake hook for the pins' sensitivity tests only (a separate build with
+// -DAO_PLANT_FACE_SCALE=...; the oracle itself is built without it): scales the face
+// limiter factor.
+#ifndef AO_PLANT_FACE_SCALE
+#define AO_PLANT_FACE_SCALE 1.0
+#endif
+double face_factor(const ao_problem& p, int d) { return 2.0 * d * lim_parts(p) * AO_PLANT_FACE_SCALE; }
 
 // kappa_max = max over [umin, umax] of kappa (Section 5.1.1). Plain dense sampling
 // plus the interval end points and the kinks of the piecewise form.
@@ -503,10 +539,12 @@ void fe1d(const Model& m, const R* ub, const R* P, R tau, const R* s_ext, R* ub_
     for (int f = -1; f < n; ++f) Flim[f] = Fh[f];
     for (int i = -1; i <= n; ++i) Alim[i] = Ah[i];
     if (p.limiter) {
+      // face correction factor 2 * parts (6 with diffusion, 2 without)
+      const R kc = R(face_factor(p, 1));
       for (int f = -1; f < n; ++f) {
         R dF = Fh[f] - FL[f];
-        R t = minr(Theta<R>(m, ULp[f], ULp[f] - R(6.0) * mu * dF),
-                   Theta<R>(m, ULm[f + 1], ULm[f + 1] + R(6.0) * mu * dF));
+        R t = minr(Theta<R>(m, ULp[f], ULp[f] - kc * mu * dF),
+                   Theta<R>(m, ULm[f + 1], ULm[f + 1] + kc * mu * dF));
         Flim[f] = (t == R(1.0)) ? Fh[f] : FL[f] + t * dF;
       }
       for (int i = -1; i <= n; ++i) {
@@ -823,17 +861,18 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
       }
   }
 
-  // (6) monolithic convex limiter with factor 3 * 2d
+  // (6) monolithic convex limiter: potential corrections with factor 3 * 2d, face
+  //     corrections with 2d times the number of parts (3 * 2d with diffusion, 2d without)
   std::vector<R> Fl[3], Al[3];
   for (int l = 0; l < d; ++l) { Fl[l] = Fh[l]; Al[l] = Ah[l]; }
   if (p.limiter) {
-    const R kf = R(6.0 * d);
+    const R kf = R(6.0 * d), kc = R(face_factor(p, d));
     for (int l = 0; l < d; ++l) {
       for (size_t q = 0; q < N; ++q) {
         size_t qp = nb(q, l, 1);
         R dF = Fh[l][q] - FL[l][q];
-        R t = minr(Theta<R>(m, ULp[l][q], ULp[l][q] - kf * mu[l] * dF),
-                   Theta<R>(m, ULm[l][qp], ULm[l][qp] + kf * mu[l] * dF));
+        R t = minr(Theta<R>(m, ULp[l][q], ULp[l][q] - kc * mu[l] * dF),
+                   Theta<R>(m, ULm[l][qp], ULm[l][qp] + kc * mu[l] * dF));
         Fl[l][q] = (t == R(1.0)) ? Fh[l][q] : FL[l][q] + t * dF;
       }
       for (size_t q = 0; q < N; ++q) {
@@ -1042,21 +1081,23 @@ void fe2d(const Model& m, const R* ub, const R* V, const R* X, const R* Y, R tau
       }
   }
 
-  // (7) monolithic convex limiter with factor 3*2d = 12 (eqs.
-  //     multid_convection_limiting_parameter, multid_diffusion_limiting_parameter)
+  // (7) monolithic convex limiter (eqs. multid_convection_limiting_parameter,
+  //     multid_diffusion_limiting_parameter): potential corrections with factor
+  //     3*2d = 12, face corrections with 2d times the number of parts (12 with
+  //     diffusion, 4 without)
   std::vector<R> Fl1(Fh1), Fl2(Fh2), Al1(Ah1), Al2(Ah2);
   if (p.limiter) {
-    const R k12 = R(12.0);
+    const R k12 = R(12.0), kc = R(face_factor(p, 2));
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         size_t k = at(i, j), kx = at(i + 1, j), ky = at(i, j + 1);
         R dF1 = Fh1[k] - FL1[k];
-        R t1 = minr(Theta<R>(m, ULp1[k], ULp1[k] - k12 * mu1 * dF1),
-                    Theta<R>(m, ULm1[kx], ULm1[kx] + k12 * mu1 * dF1));
+        R t1 = minr(Theta<R>(m, ULp1[k], ULp1[k] - kc * mu1 * dF1),
+                    Theta<R>(m, ULm1[kx], ULm1[kx] + kc * mu1 * dF1));
         Fl1[k] = (t1 == R(1.0)) ? Fh1[k] : FL1[k] + t1 * dF1;
         R dF2 = Fh2[k] - FL2[k];
-        R t2 = minr(Theta<R>(m, ULp2[k], ULp2[k] - k12 * mu2 * dF2),
-                    Theta<R>(m, ULm2[ky], ULm2[ky] + k12 * mu2 * dF2));
+        R t2 = minr(Theta<R>(m, ULp2[k], ULp2[k] - kc * mu2 * dF2),
+                    Theta<R>(m, ULm2[ky], ULm2[ky] + kc * mu2 * dF2));
         Fl2[k] = (t2 == R(1.0)) ? Fh2[k] : FL2[k] + t2 * dF2;
       }
     for (int j = 0; j < ny; ++j)
