@@ -28,6 +28,11 @@ struct DevModel {
   // unit also performs the double->float conversions, so none happen per use)
   float fpf[4], dpf[4], critf[2][8], critvf[2][8];
   int pme_e;             // AF_DIFF_PME: the integer exponent p0 (no conversion per use)
+  // parts of the convex decomposition of each limited directional state u^{Lim,+-}
+  // (Section 5.1.1, per direction in Section 5.2): 3 -- the face correction and the two
+  // potential corrections -- when the equation diffuses, 1 when a(u) is constant and
+  // only the face correction is present. The face limiter factor is 2d times this.
+  int lim_parts;
 };
 
 // parameter k of a double/float pair in the stencil precision T

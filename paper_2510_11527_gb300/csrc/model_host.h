@@ -76,7 +76,24 @@ inline void bl_critical_points(DevModel& m) {
 // after fp/dp/umin/umax are set: flux-specific tables and float copies. In 1D the
 // Buckley-Leverett flux is the gravity form f1 (1 - g (1-u)^2), the form of direction 1:
 // its extrema tables are also placed in slot 0, which the 1D wave-speed code reads.
+// 1 when the diffusion potential a(u) is constant (no diffusion term: kind NONE, or a
+// kind whose coefficients of u are all zero), else 3; see DevModel::lim_parts.
+inline int limiter_parts(int diff_kind, const double* p) {
+  bool diffuses = false;
+  switch (diff_kind) {
+    case AF_DIFF_CONST: diffuses = p[0] != 0.0; break;
+    case AF_DIFF_PWL: diffuses = p[0] != 0.0 || p[2] != 0.0; break;
+    case AF_DIFF_PME: diffuses = true; break;
+    case AF_DIFF_CUBIC:
+    case AF_DIFF_CUBIC01: diffuses = p[0] != 0.0 || p[1] != 0.0 || p[2] != 0.0; break;
+    case AF_DIFF_RAMP: diffuses = p[0] != 0.0; break;
+    default: diffuses = false;
+  }
+  return diffuses ? 3 : 1;
+}
+
 inline void finish_model(DevModel& m, int flux_kind, int dim) {
+  m.lim_parts = limiter_parts(m.diff_kind, m.dp);
   for (int d = 0; d < 2; ++d) {
     m.ncrit[d] = 0;
     for (int k = 0; k < 8; ++k) m.crit[d][k] = m.critv[d][k] = 0.0;

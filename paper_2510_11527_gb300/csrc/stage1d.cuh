@@ -7,7 +7,8 @@
 //   point residual  5-point line [P_{i-1}, c_i, P_i, c_{i+1}, P_{i+1}]
 //   DC potential    a^_i = (-a(P_{i-1}) + 8 a(c_i) - a(P_i)) / 6   (Proposition 2.1)
 //   low order       LLF with interval wave speed, states u^{L,+-} with factor 2
-//   limiter         theta^c (2 states) and theta^d (4 states) with factor 6
+//   limiter         theta^c (2 states; factor 6, or 2 without a diffusion term) and
+//                   theta^d (4 states; factor 6)
 // Without double conservation (Appendix A) the face flux is f(P_i) - kappa(P_i) D_c(u),
 // D_c(u) = (P_{i-1} - 8 c_i + 8 c_{i+1} - P_{i+1}) / (6 dx), the point value takes
 // 4/dx^2 sum_{m,n} b_mn kappa(z_m) z_n on its line, and the limiter blends the total
@@ -198,9 +199,10 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
         }
       }
       __syncthreads();
-      // the total face flux of the form without double conservation takes factor 2
-      // (the average is the mean of u^{L,+} and u^{L,-}, one face correction each)
-      const T k6 = T((nodc ? 2.0 : 6.0) * mu), q6 = T(6.0 * nu);
+      // face factor 2 * parts (6 with diffusion, 2 without); the total face flux of the
+      // form without double conservation takes factor 2 (the average is the mean of
+      // u^{L,+} and u^{L,-}, one face correction each)
+      const T k6 = T((nodc ? 2.0 : double(2 * m.lim_parts)) * mu), q6 = T(6.0 * nu);
       for (int b = H - 1 + tid; b <= H + TX; b += NT) {
         if (b < H + TX) {
           const T fh = sFH[b], fl = sFL[b], dF = fh - fl;

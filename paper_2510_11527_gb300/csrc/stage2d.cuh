@@ -16,7 +16,8 @@
 //       potentials A^H_l, LLF fluxes F^L_l
 //   P2b/P2c (blend) smoothness s_l, weights theta^{c,s}, theta^{d,s}; blended F, A, R
 //   P3  directional low-order states u^{L,+-}_l (factor 2d = 4)
-//   P4  limiter parameters theta^c (faces), theta^d (cells) with factor 3*2d = 12
+//   P4  limiter parameters theta^c (faces; factor 3*2d = 12, or 2d = 4 without a
+//       diffusion term), theta^d (cells; factor 12)
 //   P5  limited cell-average update (eq. multid_limited_average), point update and
 //       projection, RK combination, safeguard, store.
 //
@@ -241,8 +242,8 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
       sc.n4_1[o] = T(4.0 * nu1);
       sc.m4_2[o] = T(4.0 * mu2);
       sc.n4_2[o] = T(4.0 * nu2);
-      sc.k1[o] = T(12.0 * mu1);
-      sc.k2[o] = T(12.0 * mu2);
+      sc.k1[o] = T(double(4 * m.lim_parts) * mu1);
+      sc.k2[o] = T(double(4 * m.lim_parts) * mu2);
       sc.q1[o] = T(12.0 * nu1);
       sc.q2[o] = T(12.0 * nu2);
       sc.cAt[o] = T(A.cA[o]);

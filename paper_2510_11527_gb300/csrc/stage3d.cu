@@ -1,7 +1,7 @@
 // 3D stage of the compact fourth-order doubly conservative active flux method with the
 // monolithic convex limiter (arXiv 2510.11527, Section 4's 3D DoFs; Section 5.2 with
-// d = 3: directional split 1/6, limiter factor 18). Four kernels per stage, one thread
-// per cell, FP64:
+// d = 3: directional split 1/6, limiter factor 18, face factor 6 without a diffusion
+// term). Four kernels per stage, one thread per cell, FP64:
 //   K1 centre values from the tensor Simpson rule of the cell average;
 //   K2 per direction: high-order face flux (Simpson face average of f_l), DC cell
 //      potential (transverse Simpson average of the 1D potential along l), LLF face
@@ -194,13 +194,13 @@ __global__ void __launch_bounds__(T3) limit3d_kernel(const DevModel m, const Sta
   if (dtv == 0.0) return;   // uniform over the grid
   // per-direction factors of this launch, formed once per block in FP64 and rounded to
   // the stencil type (a double -> float rounding is an FP64-unit instruction on GB300)
-  __shared__ T sK[3][4];   // 6 mu, 6 nu, 18 mu, 18 nu
+  __shared__ T sK[3][4];   // 6 mu, 6 nu, face factor (18 or 6) mu, 18 nu
   if (threadIdx.x < 3) {
     const int l = threadIdx.x;
     const double mu = A.tcoef[o] * dtv * A.inv_h[l], nu = mu * A.inv_h[l];
     sK[l][0] = T(6.0 * mu);
     sK[l][1] = T(6.0 * nu);
-    sK[l][2] = T(18.0 * mu);
+    sK[l][2] = T(double(6 * m.lim_parts) * mu);   // 18 mu, or 6 mu without diffusion
     sK[l][3] = T(18.0 * nu);
   }
   __syncthreads();

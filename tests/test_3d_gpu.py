@@ -41,6 +41,8 @@ MODELS = {
     "linear_const": dict(flux=("linear", (1.0, -0.6, 0.3)), diff=("const", (0.01,))),
     "pme": dict(flux=("zero", ()), diff=("pme", (2,))),
     "burgers_ramp": dict(flux=("burgers", (0.5,)), diff=("ramp", (0.05, 0.4, 0.2))),
+    # pure convection: face limiter factor 2d = 6
+    "burgers_none": dict(flux=("burgers", (0.5,)), diff=("none", ())),
 }
 
 

@@ -171,14 +171,16 @@ def test_batch_cfl_interior_extrema_bl():
 @pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
 def test_batch_tiny_and_ragged_meshes_equal_single_mesh(prec):
     """Meshes smaller than the halo (1x1, 3x2), ragged tile edges (5x7, 33x9) and a
-    non-square mesh in one batch: SSP-RK3 steps agree bit for bit with single-mesh
-    contexts (the periodic wrap takes its modulo path for the smallest ones)."""
+    non-square mesh in one batch, with and without a diffusion term: SSP-RK3 steps agree
+    bit for bit with single-mesh contexts (the periodic wrap takes its modulo path for
+    the smallest ones)."""
     from paper_2510_11527_gb300 import Solver, capi
     sizes = [(1, 1), (3, 2), (5, 7), (33, 9), (40, 17)]
     specs, states = [], []
     for k, (nx, ny) in enumerate(sizes):
+        # every other instance without a diffusion term (face limiter factor 4, not 12)
         s = ai.Spec(dim=2, nx=nx, ny=ny, x0=0.0, x1=0.1 * nx, y0=0.0, y1=0.1 * ny, flux=("burgers", (0.5,)),
-                    diff=("pwl", (0.03, 0.25, 0.03, 0.75)), umin=0.0, umax=1.0)
+                    diff=("pwl", (0.03, 0.25, 0.03, 0.75)) if k % 2 == 0 else ("none", ()), umin=0.0, umax=1.0)
         specs.append(s)
         states.append([a.numpy() for a in ai.random_state_2d(s, seed=40 + k)])
     b = capi.af_batch_create(*_structs(specs, prec, 3))

@@ -48,6 +48,9 @@ PROBLEMS_2D = {
     "pme": dict(flux=("zero", ()), diff=("pme", (2,)), umin=0.0, umax=1.0),
     "linear": dict(flux=("linear", (1.0, -0.6)), diff=("const", (0.01,)), umin=-2.0, umax=2.0),
     "burgers_band": dict(flux=("burgers", (0.5,)), diff=("pwl", (0.03, 0.25, 0.03, 0.75)), umin=0.0, umax=1.0),
+    # pure convection: the face limiter factor is 2d = 4 (no potential corrections)
+    "burgers_none": dict(flux=("burgers", (0.5,)), diff=("none", ()), umin=-1.0, umax=1.0),
+    "bl_none": dict(flux=("bl", (5.0,)), diff=("none", ()), umin=0.0, umax=1.0),
 }
 
 
@@ -172,8 +175,9 @@ def test_config1_linear_1d_matches_oracle_and_exact():
 
 @pytest.mark.parametrize("n", [3, 7, 256, 257, 1000])
 @pytest.mark.parametrize("lim,blend", [(True, "off"), (True, "plain"), (False, "off")])
-def test_forward_euler_1d(n, lim, blend):
-    spec = ai.Spec(dim=1, nx=n, x0=-2, x1=2, flux=("burgers", (1.0,)), diff=("pwl", (0.1, -0.25, 0.1, 0.25)),
+@pytest.mark.parametrize("diff", [("pwl", (0.1, -0.25, 0.1, 0.25)), ("none", ())])
+def test_forward_euler_1d(n, lim, blend, diff):
+    spec = ai.Spec(dim=1, nx=n, x0=-2, x1=2, flux=("burgers", (1.0,)), diff=diff,
                    umin=-1.0, umax=1.0, limiter=lim, blend=blend)
     st = np_state(ai.random_state_1d(spec, seed=n))
     tau = oracle.dt_cfl(spec, st[0])
