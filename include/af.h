@@ -298,17 +298,24 @@ af_status af_set_mlp(af_ctx* ctx, const af_mlp* net);
  * cannot afford the implicit device synchronisation of an allocation, or a plugin host
  * that forbids a library from allocating on its own.
  *   - Scratch: a file-scope device array of AF_MASS_NOALLOC_MAX_CELLS / 2048 partial
- *     sums (512 KiB) plus one result slot, held by every GPU that loads the library until
- *     the process exits. All slots a call uses are overwritten by that call.
- *   - The first call on a device resolves the array's device address (with that device
- *     current); calls that overlap on the GPU (e.g. on two streams) race on the shared
- *     scratch and must be serialised by the caller.
+ *     sums (512 KiB) plus one result slot, held by every GPU that loads the library
+ *     until the process exits. All slots a call uses are overwritten by that call.
+ *   - When the array is allocated: with CUDA's default lazy module loading, when its
+ *     module is loaded on a device -- at the first call on that device (which resolves
+ *     the array's device address, with that device current). A caller whose memory pool
+ *     is about to claim the device should therefore make one call first; after that,
+ *     calls allocate nothing. The address is resolved again on every call, so the entry
+ *     point stays valid after the caller resets the device.
+ *   - Calls that overlap on the GPU (e.g. on two streams) race on the shared scratch and
+ *     must be serialised by the caller.
  *   - The summation order is fixed (2048-cell blocks, then a fixed tree), so repeated
  *     calls on the same data return bit-identical results; the order differs from
  *     af_mass, so the two agree to FP64 round-off.
  *   - Returns AF_E_ARG for NULL pointers, ncells <= 0 or ncells >
- *     AF_MASS_NOALLOC_MAX_CELLS, AF_E_CUDA if a launch or copy fails. Work is issued on
- *     `stream` (NULL: legacy default stream), which is synchronised before returning. */
+ *     AF_MASS_NOALLOC_MAX_CELLS, or a ub_dev that is not device memory of the current
+ *     device (host memory, another GPU's memory); AF_E_CUDA if a launch or copy fails.
+ *     Work is issued on `stream` (NULL: legacy default stream), which is synchronised
+ *     before returning. */
 #define AF_MASS_NOALLOC_MAX_CELLS 134217728LL
 af_status af_mass_noalloc(const double* ub_dev, long long ncells, double cell_area, double* mass, void* stream);
 

@@ -4,8 +4,6 @@
 // callers that cannot allocate device memory (see include/af.h).
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "af.h"
 
 namespace {
@@ -19,11 +17,6 @@ static_assert((long long)kMaxParts * kPerBlock == AF_MASS_NOALLOC_MAX_CELLS, "si
 // Scratch shared by every call on a device: kMaxParts block partials followed by the
 // final sum (512 KiB + 8 B per device that loads the library, held until exit).
 static __device__ __align__(256) double g_mass_scratch[kMaxParts + 1];
-
-// Host-side device addresses of g_mass_scratch, one per device, resolved on first use.
-constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {nullptr};
-std::mutex g_setup_mutex;
 
 // Block b sums cells [b * 2048, (b + 1) * 2048) in a fixed order: each thread adds its
 // 8 strided cells, then a shared-memory tree of halving strides.
@@ -60,22 +53,26 @@ __global__ void __launch_bounds__(1024) mass_final_static(double* parts, int npa
   if (threadIdx.x == 0) parts[kMaxParts] = sm[0];
 }
 
-// Device address of this device's scratch array (the host-side name of the array is
-// only a stand-in and must never be passed to a kernel).
+// Device address of the current device's scratch array, resolved on every call (the
+// host-side name of the array is only a stand-in and must never be passed to a kernel;
+// resolving per call also stays right after the caller resets the device, which
+// reloads the module at a new address). With CUDA's lazy module loading the first
+// resolution on a device loads this module and allocates the array there.
 cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_addr[dev]) {
-    double* p = nullptr;
-    e = cudaGetSymbolAddress((void**)&p, g_mass_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
+  return cudaGetSymbolAddress((void**)out, g_mass_scratch);
+}
+
+// ub_dev must be device (or managed) memory of the current device: a pointer into
+// another device's memory would run the reduction on the wrong GPU.
+bool on_current_device(const void* p) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaPointerAttributes pa;
+  if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+    (void)cudaGetLastError();   // the failed query's own error: the call reports AF_E_ARG
+    return false;
   }
-  *out = g_scratch_addr[dev];
-  return cudaSuccess;
+  return (pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged) && pa.device == dev;
 }
 
 }  // namespace
@@ -84,14 +81,19 @@ extern "C" af_status af_mass_noalloc(const double* ub_dev, long long ncells, dou
                                      void* stream) {
   if (!ub_dev || !mass) return AF_E_ARG;
   if (ncells <= 0 || ncells > AF_MASS_NOALLOC_MAX_CELLS) return AF_E_ARG;
+  if (!on_current_device(ub_dev)) return AF_E_ARG;
   double* scratch = nullptr;
   if (scratch_for_current_device(&scratch) != cudaSuccess) return AF_E_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  const int nparts = (int)((ncells + kPerBlock - 1) / kPerBlock);
-  mass_partial_static<<<nparts, kThreads, 0, s>>>(ub_dev, ncells, scratch);
-  if (cudaGetLastError() != cudaSuccess) return AF_E_CUDA;
-  mass_final_static<<<1, 1024, 0, s>>>(scratch, nparts);
-  if (cudaGetLastError() != cudaSuccess) return AF_E_CUDA;
+  int nparts = (int)((ncells + kPerBlock - 1) / kPerBlock);
+  // launch errors are taken from the launch calls themselves, so an unrelated error
+  // left pending by an earlier call is neither reported here nor cleared
+  void* a1[] = {(void*)&ub_dev, (void*)&ncells, (void*)&scratch};
+  if (cudaLaunchKernel((const void*)mass_partial_static, dim3(nparts), dim3(kThreads), a1, 0, s) != cudaSuccess)
+    return AF_E_CUDA;
+  void* a2[] = {(void*)&scratch, (void*)&nparts};
+  if (cudaLaunchKernel((const void*)mass_final_static, dim3(1), dim3(1024), a2, 0, s) != cudaSuccess)
+    return AF_E_CUDA;
   double sum = 0.0;
   if (cudaMemcpyAsync(&sum, scratch + kMaxParts, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
     return AF_E_CUDA;
