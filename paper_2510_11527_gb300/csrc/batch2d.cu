@@ -428,8 +428,11 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
   b->nbuf = opts->rk == AF_RK_SSP54 ? 4 : 3;
   b->limiter = opts->limiter;
   b->cfl = opts->cfl > 0.0 ? opts->cfl : 0.33 / 2;
+  // default diffusive cap as for a single mesh: none for SSP-RK(5,4) with the limiter
   b->cfl_diff = opts->cfl_diff > 0.0 ? opts->cfl_diff
-                                     : (opts->cfl_diff < 0.0 ? 0.0 : 0.9 * (opts->rk == AF_RK_SSP54 ? 0.1307 : 0.0616));
+                : (opts->cfl_diff < 0.0 || (opts->rk == AF_RK_SSP54 && opts->limiter)
+                       ? 0.0
+                       : 0.9 * (opts->rk == AF_RK_SSP54 ? 0.1307 : 0.0616));
   b->grids.assign(grids, grids + n);
   const size_t ps = b->prec == AF_PREC_FP64 ? 8 : 4;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
