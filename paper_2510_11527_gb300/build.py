@@ -20,6 +20,11 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.
          "-I", CSRC]
 
 
+# Per-file flags: the column-marching kernel forms every face term in two places and
+# needs an arithmetic without compiler contraction (see csrc/stream2d_f32.cu).
+FILE_FLAGS = {"stream2d_f32.cu": ["-fmad=false"]}
+
+
 def _sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
@@ -45,7 +50,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-        cmd = [NVCC] + ARCH + FLAGS + extra + ["-c", src, "-o", obj]
+        cmd = [NVCC] + ARCH + FLAGS + FILE_FLAGS.get(os.path.basename(src), []) + extra + ["-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

@@ -12,6 +12,7 @@ cudaError_t launch_stage2d_f64(int flux, bool blend, const DevModel& m, const St
                                cudaStream_t s);
 cudaError_t launch_stage2d_f32(int flux, bool blend, const DevModel& m, const StageArgs2D<float>& a,
                                cudaStream_t s);
+cudaError_t launch_stream2d_f32(int flux, const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s);
 cudaError_t launch_stage2d_rect_f64(int flux, bool blend, const DevModel& m, const StageArgs2D<double>& a,
                                     cudaStream_t s);
 cudaError_t launch_stage2d_rect_f32(int flux, bool blend, const DevModel& m, const StageArgs2D<float>& a,

@@ -1,9 +1,11 @@
-// Launchers of the fused 2D stage kernels (internal): one CTA per 32 x 8 tile of the
-// mesh, or of the padded layout of a rectangle with ends (RECT). The FP64 form and the
-// blended FP32 form run stage2d_kernel; the FP32 form without the blend runs the
-// 6-CTAs-per-SM compilation. The translation units instantiate the periodic (RECT =
-// false) and the rectangle (RECT = true) launchers separately, so they compile in
-// parallel and the periodic kernels are unaffected by the rectangle's code.
+// Launchers of the fused 2D stage kernels (internal). The FP32-mixed form of a periodic
+// mesh without the blend runs the column-marching kernel (stream2d.cuh). The others run
+// one CTA per 32 x 8 tile of the mesh, or of the padded layout of a rectangle with ends
+// (RECT): the FP64 form and the blended FP32 form stage2d_kernel, the FP32 rectangle
+// without the blend the 6-CTAs-per-SM compilation. The translation units instantiate
+// the periodic (RECT = false) and the rectangle (RECT = true) launchers separately, so
+// they compile in parallel and the periodic kernels are unaffected by the rectangle's
+// code.
 #pragma once
 #include <type_traits>
 
@@ -19,6 +21,7 @@ static auto stage2d_kernel_for() {
 
 template <int FLUX, class T, bool BLEND, bool RECT>
 static cudaError_t stage2d_go(const DevModel& m, const StageArgs2D<T>& a, cudaStream_t s) {
+  if constexpr (std::is_same_v<T, float> && !BLEND && !RECT) return launch_stream2d_f32(FLUX, m, a, s);
   using L = Tile2D<FLUX, T, BLEND>;
   static bool attr = false;
   auto k = stage2d_kernel_for<FLUX, T, BLEND, RECT>();

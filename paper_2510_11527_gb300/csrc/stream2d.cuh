@@ -1,0 +1,484 @@
+// Column-marching 2D stage kernel (periodic meshes, no smoothness blend): the same
+// limited forward-Euler evaluation and Shu-Osher combination as stage_tile (Sections 4
+// and 5.2 of arXiv 2510.11527, d = 2), organised so that every derived quantity is
+// formed once per location and kept in registers.
+//
+// Each warp owns a band of 28 output columns and a strip of S output rows. Lane L holds
+// column 28 * band - 2 + L (periodic image): lanes 2..29 produce outputs, lanes 0, 1,
+// 30, 31 only supply the +-2 halo of the x-stencils, which reach neighbouring columns
+// through warp shuffles. The warp marches up its strip one input row per step, so the
+// y-stencils read the rows before it from registers: at step r it loads row r, forms
+// the row's centres, pointwise f, a, its x-face and cell quantities, the y-face between
+// rows r-1 and r, the point residuals of row r-1, the x-limiter of row r and the
+// y-limiter of row r-1, and finalises the cells of row r-2. Three row slots hold what
+// later steps read (the loop is unrolled by three so the slots rotate without copies).
+//
+// Conservation: every face term of the FP32 update (mu F and nu (A_+ - A)) reaches both
+// adjacent cells unchanged (a shuffle or a register); a face on a band or strip edge is
+// formed by both warps that meet there, from the same values with the same rounding
+// (the kernel's translation unit is compiled without contraction), so the terms cancel
+// exactly across faces. Each cell sums its eight terms without rounding error (TwoSum)
+// and adds them once to the FP64 average, as stage_tile does.
+#pragma once
+#include "stage2d.cuh"
+
+namespace af {
+
+constexpr int STREAM_BAND = 28;   // output columns per warp
+constexpr int STREAM_WPB = 4;     // warps per block
+// Resident blocks per SM the kernel is compiled for: 4 (128 registers per thread, 16
+// warps per SM) measured fastest; Buckley-Leverett's longer live ranges spill there
+// and take 3.
+template <int FLUX>
+constexpr int stream_min_blocks() { return FLUX == FLUX_BL ? 3 : 4; }
+
+// per-lane constants of one launch
+template <class T>
+struct StreamScal {
+  T umin, umax, i6h1, i6h2, i3h21, i3h22, m4_1, n4_1, m4_2, n4_2, k1, k2, q1, q2, taut, cAt, cFt, half, sixth, r36;
+  float m1f, m2f, n1f, n2f;
+  double cA, cF;
+};
+
+// values of one input row that later steps read (a row slot)
+template <class T>
+struct RowSlot {
+  T V, X, Y, C, U;                 // points, recovered centre, cell average (stencil type)
+  T fV, fX, fY, fC, fU;            // f_2 at V, X, Y, centre, average (y-direction flux)
+  T fV1;                           // f_1 at V (x-face Simpson flux of the next row)
+  T dV, dX, dY, dC, dU;            // |f_2'| (Buckley-Leverett)
+  T aV, aX, aY, aC, aU;            // a
+  T Vm, aVm;                       // V and a(V) of the left neighbour column
+  T FH2, AH2;                      // high-order flux of the y-face above, cell potential (y)
+  T rV, rX, rY;                    // point residuals (x-lines, then x + y)
+  T ULp2, ULm2, Alim2;             // y low-order states, limited potential (y)
+  T tF2lo, tD2lo;                  // update terms of the y-face below the row's cell
+  T tF1, tD1;                      // update terms of the x-face right of the cell
+};
+
+// Diffusion kinds compiled into the column-marching kernel (DK_GENERIC takes the
+// model's runtime kind).
+enum : int { DK_GENERIC = -1, DK_NONE = 0, DK_CONST = 1, DK_PWL = 2, DK_PME2 = 3, DK_CUBIC = 4 };
+
+template <int DIFF, class T>
+__device__ __forceinline__ T apot_k(const DevModel& m, T u) {
+  if constexpr (DIFF == DK_NONE) {
+    return T(0);
+  } else if constexpr (DIFF == DK_CONST) {
+    return par<T>(m.dp, m.dpf, 0) * u;
+  } else if constexpr (DIFF == DK_PWL) {
+    // both branches always: a zero coefficient contributes a signed zero, which does not
+    // change the sum
+    return par<T>(m.dp, m.dpf, 0) * tmin(u - par<T>(m.dp, m.dpf, 1), T(0)) +
+           par<T>(m.dp, m.dpf, 2) * tmax(u - par<T>(m.dp, m.dpf, 3), T(0));
+  } else if constexpr (DIFF == DK_PME2) {
+    return u * u;
+  } else if constexpr (DIFF == DK_CUBIC) {
+    return ((par<T>(m.dp, m.dpf, 2) * u + par<T>(m.dp, m.dpf, 1)) * u + par<T>(m.dp, m.dpf, 0)) * u;
+  } else {
+    return apot<T>(m, u);
+  }
+}
+
+// a * b + c with one rounding, written out (the translation unit of this kernel is
+// compiled without contraction)
+__device__ __forceinline__ float sfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double sfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// line residual of stage_tile's line_res with its multiply-adds fused explicitly
+template <class T>
+__device__ __forceinline__ T line_res_s(T z0, T z1, T z2, T z3, T z4, T f0, T f1, T f3, T f4, T alpha, T a0, T a1,
+                                        T a2, T a3, T a4, T i6h, T i3h2) {
+  const T cf = sfma(T(8), f3 - f1, f0 - f4);
+  const T dz = sfma(T(6), z2, sfma(T(-4), z1 + z3, z0 + z4));
+  const T da = sfma(T(-30), a2, sfma(T(16), a1 + a3, -(a0 + a4)));
+  return sfma(da, i3h2, -(sfma(alpha, dz, cf) * i6h));
+}
+
+template <class T>
+__device__ __forceinline__ T shup(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <class T>
+__device__ __forceinline__ T shdn(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+
+// f_l, |f_l'| and a at one value: returns f_1 in f1, f_2 in f2, |f_1'| in d1, |f_2'| in d2
+template <int FLUX, int DIFF, class T>
+__device__ __forceinline__ void point_eval(const DevModel& m, T z, T& f1, T& f2, T& d1, T& d2, T& a) {
+  if constexpr (FLUX == FLUX_BURGERS) {
+    f1 = flux<FLUX, T>(m, 0, z);
+    f2 = f1;
+    d1 = d2 = T(0);
+  } else if constexpr (FLUX == FLUX_BL) {
+    const BLVals<T> r = bl_eval<T>(m, z);
+    f1 = r.f[0];
+    f2 = r.f[1];
+    d1 = r.d[0];
+    d2 = r.d[1];
+  } else {
+    f1 = flux<FLUX, T>(m, 0, z);
+    f2 = flux<FLUX, T>(m, 1, z);
+    d1 = d2 = T(0);
+  }
+  a = apot_k<DIFF, T>(m, z);
+}
+
+// alpha of a 5-point line along dir from the values (Burgers: |z|) or |f'| (Buckley-Leverett)
+template <int FLUX, class T>
+__device__ __forceinline__ T line_alpha(const DevModel& m, int dir, T z0, T z1, T z2, T z3, T z4, T d0, T d1, T d2,
+                                        T d3, T d4) {
+  if constexpr (FLUX == FLUX_BURGERS) {
+    return tabs(T(2) * par<T>(m.fp, m.fpf, 0)) * tmax(tmax(tmax(tabs(z0), tabs(z1)), tmax(tabs(z3), tabs(z4))), tabs(z2));
+  } else if constexpr (FLUX == FLUX_BL) {
+    return tmax(tmax(tmax(d0, d1), tmax(d3, d4)), d2);
+  } else if constexpr (FLUX == FLUX_LINEAR) {
+    return tabs(T(dir == 0 ? m.fp[0] : m.fp[1]));
+  } else {
+    return T(0);
+  }
+}
+
+template <int FLUX, class T>
+__device__ __forceinline__ T llf(const DevModel& m, int dir, T ul, T ur, T fl, T fr, T dl, T dr, T half) {
+  const T al = alpha_interval_pre<FLUX, T>(m, dir, ul, ur, dl, dr);
+  return sfma(-(half * al), ur - ul, half * (fl + fr));
+}
+
+// cell potential (tensor Simpson average of the DC potential along dir): for x,
+// (8 sy - 4 sx + 32 ac - sv) / 36
+template <class T>
+__device__ __forceinline__ T cell_pot(T sv, T sx, T sy, T ac, bool ydir, T r36) {
+  const T a = ydir ? sx : sy, b = ydir ? sy : sx;
+  return sfma(T(32), ac, sfma(T(8), a, sfma(T(-4), b, -sv))) * r36;
+}
+
+template <int FLUX, int DIFF, class T>
+struct StreamCtx {
+  const DevModel& m;
+  const StageArgs2D<T>& A;
+  const StreamScal<T>& k;
+  int nx, ny, gi, lane, rs, re;
+  bool col_out;          // this lane's column produces outputs
+  bool comb;             // the output combines an earlier state (cA != 0)
+};
+
+// per-row input registers (the next row is prefetched one step ahead)
+template <class T>
+struct RowIn {
+  double ub;
+  T V, X, Y;
+};
+template <class T>
+struct OutIn {
+  double ub, Aub;   // FE input and RK combination input of the output cell
+  T V, X, Y;        // RK combination inputs of the point values
+};
+
+template <class T>
+__device__ __forceinline__ RowIn<T> load_row(const StageArgs2D<T>& A, size_t g) {
+  RowIn<T> in;
+  in.ub = __ldg(A.ub + g);
+  in.V = __ldg(A.V + g);
+  in.X = __ldg(A.X + g);
+  in.Y = __ldg(A.Y + g);
+  return in;
+}
+
+// One step: input row r arrives (in), slots p2 (row r-2), p1 (row r-1), cur (row r;
+// held row r-3 before). Finalises the cells of row r-2 if they belong to the strip.
+template <int FLUX, int DIFF, class T>
+__device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, int r, const RowIn<T>& in,
+                                            const OutIn<T>& oin, RowSlot<T>& p2, RowSlot<T>& p1, RowSlot<T>& cur) {
+  const DevModel& m = c.m;
+  const StageArgs2D<T>& A = c.A;
+  const StreamScal<T>& k = c.k;
+  const T half = k.half, sixth = k.sixth;
+  const bool lim = A.limiter != 0;
+  constexpr bool BL = FLUX == FLUX_BL;
+
+  // ---- row r: points, centre, pointwise functions
+  cur.U = to_stencil<T>(in.ub);
+  cur.V = in.V;
+  cur.X = in.X;
+  cur.Y = in.Y;
+  const T Xm = shup(cur.X);
+  cur.Vm = shup(cur.V);
+  // z_ij = [36 zbar - 4 (X_{i-1,j} + X_ij + Y_{i,j-1} + Y_ij) - (four corners)] / 16
+  cur.C = sfma(T(36), cur.U, sfma(T(-4), (Xm + cur.X) + (p1.Y + cur.Y), -((p1.Vm + p1.V) + (cur.Vm + cur.V)))) *
+          T(0.0625);
+  T f1V, f1X, f1Y, f1C, f1U, d1V, d1X, d1Y, d1C, d1U;
+  point_eval<FLUX, DIFF, T>(m, cur.V, f1V, cur.fV, d1V, cur.dV, cur.aV);
+  point_eval<FLUX, DIFF, T>(m, cur.X, f1X, cur.fX, d1X, cur.dX, cur.aX);
+  point_eval<FLUX, DIFF, T>(m, cur.Y, f1Y, cur.fY, d1Y, cur.dY, cur.aY);
+  point_eval<FLUX, DIFF, T>(m, cur.C, f1C, cur.fC, d1C, cur.dC, cur.aC);
+  point_eval<FLUX, DIFF, T>(m, cur.U, f1U, cur.fU, d1U, cur.dU, cur.aU);
+  cur.fV1 = f1V;
+
+  // ---- neighbour values (|f'| only where the flux needs it)
+  auto dup = [](T v) { if constexpr (BL) return shup(v); else return T(0); };
+  auto ddn = [](T v) { if constexpr (BL) return shdn(v); else return T(0); };
+  cur.aVm = shup(cur.aV);
+  const T aXm = shup(cur.aX);
+  const T f1Vm = shup(f1V), d1Vm = dup(d1V);
+  T fVm2;   // f_2(V_{i-1,r})
+  if constexpr (FLUX == FLUX_BURGERS) fVm2 = f1Vm; else fVm2 = shup(cur.fV);
+  const T f1Xm = shup(f1X), d1Xm = dup(d1X);
+  const T Ym = shup(cur.Y), f1Ym = shup(f1Y), aYm = shup(cur.aY), d1Ym = dup(d1Y);
+  const T Up = shdn(cur.U), f1Up = shdn(f1U), aUp = shdn(cur.aU), d1Up = ddn(d1U);
+  const T Vp = shdn(cur.V), f1Vp = shdn(f1V), aVp = shdn(cur.aV), d1Vp = ddn(d1V);
+  const T Yp = shdn(cur.Y), f1Yp = shdn(f1Y), aYp = shdn(cur.aY), d1Yp = ddn(d1Y);
+  const T Xp = shdn(cur.X), f1Xp = shdn(f1X), aXp = shdn(cur.aX), d1Xp = ddn(d1X);
+  const T Cp = shdn(cur.C), f1Cp = shdn(f1C), aCp = shdn(cur.aC), d1Cp = ddn(d1C);
+
+  // ---- faces and cell potentials of row r
+  // x-face right of cell (i, r): Simpson over V_{i,r-1}, X_{i,r}, V_{i,r}
+  const T FH1 = sfma(T(4), f1X, p1.fV1 + f1V) * sixth;
+  // y-face above cell (i, r): Simpson over V_{i-1,r}, Y_{i,r}, V_{i,r}
+  cur.FH2 = sfma(T(4), cur.fY, fVm2 + cur.fV) * sixth;
+  T AH1;   // lives only in this step (x-limiter of row r)
+  {
+    const T sv = (p1.aVm + p1.aV) + (cur.aVm + cur.aV);
+    const T sx = aXm + cur.aX;
+    const T sy = p1.aY + cur.aY;
+    cur.AH2 = cell_pot<T>(sv, sx, sy, cur.aC, true, k.r36);
+    AH1 = cell_pot<T>(sv, sx, sy, cur.aC, false, k.r36);
+  }
+  const T FL1 = llf<FLUX, T>(m, 0, cur.U, Up, f1U, f1Up, d1U, d1Up, half);
+  // y-face between rows r-1 and r
+  const T FL2 = llf<FLUX, T>(m, 1, p1.U, cur.U, p1.fU, cur.fU, p1.dU, cur.dU, half);
+
+  // ---- point residuals: x-lines of row r
+  cur.rV = line_res_s<T>(cur.Vm, cur.Y, cur.V, Yp, Vp, f1Vm, f1Y, f1Yp, f1Vp,
+                       line_alpha<FLUX, T>(m, 0, cur.Vm, cur.Y, cur.V, Yp, Vp, d1Vm, d1Y, d1V, d1Yp, d1Vp), cur.aVm,
+                       cur.aY, cur.aV, aYp, aVp, k.i6h1, k.i3h21);
+  cur.rX = line_res_s<T>(Xm, cur.C, cur.X, Cp, Xp, f1Xm, f1C, f1Cp, f1Xp,
+                       line_alpha<FLUX, T>(m, 0, Xm, cur.C, cur.X, Cp, Xp, d1Xm, d1C, d1X, d1Cp, d1Xp), aXm, cur.aC,
+                       cur.aX, aCp, aXp, k.i6h1, k.i3h21);
+  cur.rY = line_res_s<T>(Ym, cur.Vm, cur.Y, cur.V, Yp, f1Ym, f1Vm, f1V, f1Yp,
+                       line_alpha<FLUX, T>(m, 0, Ym, cur.Vm, cur.Y, cur.V, Yp, d1Ym, d1Vm, d1Y, d1V, d1Yp), aYm,
+                       cur.aVm, cur.aY, cur.aV, aYp, k.i6h1, k.i3h21);
+  // y-lines of row r-1, added to its x-lines (same order as stage_tile: x + y)
+  {
+    const T rV2 = line_res_s<T>(p2.V, p1.X, p1.V, cur.X, cur.V, p2.fV, p1.fX, cur.fX, cur.fV,
+                              line_alpha<FLUX, T>(m, 1, p2.V, p1.X, p1.V, cur.X, cur.V, p2.dV, p1.dX, p1.dV, cur.dX, cur.dV),
+                              p2.aV, p1.aX, p1.aV, cur.aX, cur.aV, k.i6h2, k.i3h22);
+    const T rX2 = line_res_s<T>(p2.X, p2.V, p1.X, p1.V, cur.X, p2.fX, p2.fV, p1.fV, cur.fX,
+                              line_alpha<FLUX, T>(m, 1, p2.X, p2.V, p1.X, p1.V, cur.X, p2.dX, p2.dV, p1.dX, p1.dV, cur.dX),
+                              p2.aX, p2.aV, p1.aX, p1.aV, cur.aX, k.i6h2, k.i3h22);
+    const T rY2 = line_res_s<T>(p2.Y, p1.C, p1.Y, cur.C, cur.Y, p2.fY, p1.fC, cur.fC, cur.fY,
+                              line_alpha<FLUX, T>(m, 1, p2.Y, p1.C, p1.Y, cur.C, cur.Y, p2.dY, p1.dC, p1.dY, cur.dC, cur.dY),
+                              p2.aY, p1.aC, p1.aY, cur.aC, cur.aY, k.i6h2, k.i3h22);
+    p1.rV = p1.rV + rV2;
+    p1.rX = p1.rX + rX2;
+    p1.rY = p1.rY + rY2;
+  }
+
+  // ---- limiter: x-direction of row r, y-direction of row r-1
+  T Flim1 = FH1, Alim1 = AH1, Flim2 = p1.FH2;
+  p1.Alim2 = p1.AH2;
+  if (lim) {
+    const T FL1m = shup(FL1), aUm = shup(cur.aU);
+    const T ULp1 = sfma(k.n4_1, aUp - cur.aU, sfma(-k.m4_1, FL1 - f1U, cur.U));
+    const T ULm1 = sfma(-k.n4_1, cur.aU - aUm, sfma(-k.m4_1, f1U - FL1m, cur.U));
+    const T ULm1p = shdn(ULm1), ULp1m = shup(ULp1);
+    // y: low-order states u^{L,+}_{r-1} and u^{L,-}_r around the face between them
+    p1.ULp2 = sfma(k.n4_2, cur.aU - p1.aU, sfma(-k.m4_2, FL2 - p1.fU, p1.U));
+    cur.ULm2 = sfma(-k.n4_2, cur.aU - p1.aU, sfma(-k.m4_2, cur.fU - FL2, cur.U));
+    // the twelve (low, high) pairs of the two face limiters and the two potential
+    // limiters; Theta = 1 for all of them unless a high-order part leaves the bounds
+    const T dF1 = FH1 - FL1, dA1 = AH1 - cur.aU, e1 = k.q1 * dA1;
+    const T dF2 = p1.FH2 - FL2, dA2 = p1.AH2 - p1.aU, e2 = k.q2 * dA2;
+    T zl[12] = {ULp1, ULm1p, ULp1m, ULp1, ULm1, ULm1p, p1.ULp2, cur.ULm2, p2.ULp2, p1.ULp2, p1.ULm2, cur.ULm2};
+    T zh[12] = {sfma(-k.k1, dF1, ULp1), sfma(k.k1, dF1, ULm1p), ULp1m + e1, ULp1 - e1, ULm1 - e1, ULm1p + e1,
+                sfma(-k.k2, dF2, p1.ULp2), sfma(k.k2, dF2, cur.ULm2), p2.ULp2 + e2, p1.ULp2 - e2, p1.ULm2 - e2,
+                cur.ULm2 + e2};
+    T lo = zh[0], hi = zh[0];
+#pragma unroll
+    for (int q = 1; q < 12; ++q) {
+      lo = tmin(lo, zh[q]);
+      hi = tmax(hi, zh[q]);
+    }
+    if (tlt(lo, k.umin) | tlt(k.umax, hi)) {
+      T t[12];
+#pragma unroll
+      for (int q = 0; q < 12; ++q) t[q] = theta_fn<T>(zl[q], zh[q], k.umin, k.umax);
+      const T tc1 = tmin(t[0], t[1]), td1 = tmin(tmin(t[2], t[3]), tmin(t[4], t[5]));
+      const T tc2 = tmin(t[6], t[7]), td2 = tmin(tmin(t[8], t[9]), tmin(t[10], t[11]));
+      Flim1 = is_one(tc1) ? FH1 : sfma(tc1, dF1, FL1);
+      Alim1 = is_one(td1) ? AH1 : sfma(td1, dA1, cur.aU);
+      Flim2 = is_one(tc2) ? p1.FH2 : sfma(tc2, dF2, FL2);
+      p1.Alim2 = is_one(td2) ? p1.AH2 : sfma(td2, dA2, p1.aU);
+    }
+  }
+  // update terms: x-face right of (i, r); y-face between rows r-1 and r (stored with
+  // the upper row); the diffusion term of that face needs A_{r}, so it is formed one
+  // step later: here the y-face between rows r-2 and r-1
+  const T Alim1p = shdn(Alim1);
+  cur.tF1 = __fmul_rn(k.m1f, Flim1);
+  cur.tD1 = __fmul_rn(k.n1f, __fsub_rn(Alim1p, Alim1));
+  cur.tF2lo = __fmul_rn(k.m2f, Flim2);
+  p1.tD2lo = __fmul_rn(k.n2f, __fsub_rn(p1.Alim2, p2.Alim2));
+
+  // ---- finalise the cells of row j = r - 2
+  const int j = r - 2;
+  const T tF1m = shup(p2.tF1), tD1m = shup(p2.tD1);
+  if (j >= c.rs && j < c.re && c.col_out) {
+    const size_t g = (size_t)j * c.nx + c.gi;
+    // eight face terms in stage_tile's order, summed without rounding error
+    const float t[8] = {tF1m, -p2.tF1, p2.tF2lo, -p1.tF2lo, p2.tD1, -tD1m, p1.tD2lo, -p2.tD2lo};
+    float hs = t[0], ls = 0.0f;
+#pragma unroll
+    for (int q = 1; q < 8; ++q) {
+      float e;
+      two_sum(hs, t[q], hs, e);
+      ls = __fadd_rn(ls, e);
+    }
+    const double ubfe = oin.ub + (f2d_exact(hs) + f2d_exact(ls));
+    T v = rk_fma(k.taut, p2.rV, p2.V), x = rk_fma(k.taut, p2.rX, p2.X), y = rk_fma(k.taut, p2.rY, p2.Y);
+    if (lim) {
+      v = tmin(tmax(v, k.umin), k.umax);
+      x = tmin(tmax(x, k.umin), k.umax);
+      y = tmin(tmax(y, k.umin), k.umax);
+    }
+    double ubo;
+    T vo, xo, yo;
+    if (c.comb) {
+      ubo = rk_comb(k.cA, oin.Aub, k.cF, ubfe);
+      vo = rk_comb(k.cAt, oin.V, k.cFt, v);
+      xo = rk_comb(k.cAt, oin.X, k.cFt, x);
+      yo = rk_comb(k.cAt, oin.Y, k.cFt, y);
+    } else {
+      ubo = rk_scale(k.cF, ubfe);
+      vo = rk_scale(k.cFt, v);
+      xo = rk_scale(k.cFt, x);
+      yo = rk_scale(k.cFt, y);
+    }
+    if (lim && A.sg[0]) {
+      ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
+      vo = safeguard<T>(vo, k.umin, k.umax, A.tol, A.stats);
+      xo = safeguard<T>(xo, k.umin, k.umax, A.tol, A.stats);
+      yo = safeguard<T>(yo, k.umin, k.umax, A.tol, A.stats);
+    }
+    A.Oub[0][g] = ubo;
+    A.OV[0][g] = vo;
+    A.OX[0][g] = xo;
+    A.OY[0][g] = yo;
+  }
+}
+
+// One launch: one output of the stage (the launcher calls it once per output).
+template <int FLUX, int DIFF>
+__global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>()) stream2d_kernel(const DevModel m, const StageArgs2D<float> A, int S,
+                                                                   int bands) {
+  using T = float;
+  const double dtv = *A.dt;
+  if (is_zero_bits(dtv)) return;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * STREAM_WPB + (threadIdx.x >> 5);
+  const int band = w % bands, strip = w / bands;
+  const int nx = A.nx, ny = A.ny;
+  const int rs = strip * S;
+  if (rs >= ny) return;   // whole warp
+  const int re = min(rs + S, ny);
+  const int giu = band * STREAM_BAND - 2 + lane;
+
+  StreamScal<T> k;
+  {
+    const double tau = A.tcoef[0] * dtv;
+    const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
+    const double nu1 = mu1 * A.inv_h1, nu2 = mu2 * A.inv_h2;
+    k.umin = T(m.umin);
+    k.umax = T(m.umax);
+    k.i6h1 = T(A.inv_h1 / 6.0);
+    k.i6h2 = T(A.inv_h2 / 6.0);
+    k.i3h21 = T(A.inv_h1 * A.inv_h1 / 3.0);
+    k.i3h22 = T(A.inv_h2 * A.inv_h2 / 3.0);
+    k.m4_1 = T(4.0 * mu1);
+    k.n4_1 = T(4.0 * nu1);
+    k.m4_2 = T(4.0 * mu2);
+    k.n4_2 = T(4.0 * nu2);
+    k.k1 = T(double(4 * m.lim_parts) * mu1);
+    k.k2 = T(double(4 * m.lim_parts) * mu2);
+    k.q1 = T(12.0 * nu1);
+    k.q2 = T(12.0 * nu2);
+    k.taut = T(tau);
+    k.cA = A.cA[0];
+    k.cF = A.cF[0];
+    k.cAt = T(A.cA[0]);
+    k.cFt = T(A.cF[0]);
+    k.m1f = (float)mu1;
+    k.m2f = (float)mu2;
+    k.n1f = (float)nu1;
+    k.n2f = (float)nu2;
+    k.half = T(0.5);
+    k.sixth = T(1.0 / 6.0);
+    k.r36 = T(1.0 / 36.0);
+  }
+  const bool comb = !is_zero_bits(A.cA[0]);
+  StreamCtx<FLUX, DIFF, T> c{m, A, k, nx, ny, wrapi(giu, nx), lane, rs, re,
+                             lane >= 2 && lane < 2 + STREAM_BAND && giu < nx, comb};
+
+  RowSlot<T> s0, s1, s2;
+  // rows rs-3 .. rs-1 feed the first steps; their slots start as the wrapped row rs-3
+  // so that the warm-up steps read finite values (their results are never stored)
+  int gj = wrapi(rs - 3, ny);
+  {
+    const RowIn<T> a = load_row<T>(A, (size_t)gj * nx + c.gi);
+    s0 = RowSlot<T>{};
+    s1 = RowSlot<T>{};
+    s2 = RowSlot<T>{};
+    s0.U = s1.U = s2.U = to_stencil<T>(a.ub);
+    s0.V = s1.V = s2.V = a.V;
+    s0.X = s1.X = s2.X = a.X;
+    s0.Y = s1.Y = s2.Y = a.Y;
+  }
+  const int r0 = rs - 2, r1 = re + 1;   // steps r0 .. r1
+  gj = gj + 1 == ny ? 0 : gj + 1;       // row r0
+  RowIn<T> in = load_row<T>(A, (size_t)gj * nx + c.gi);
+  auto next_row = [&]() {
+    gj = gj + 1 == ny ? 0 : gj + 1;
+    return load_row<T>(A, (size_t)gj * nx + c.gi);
+  };
+  // RK combination inputs of the cells finalised at step r (row r - 2)
+  auto out_in = [&](int r) {
+    OutIn<T> o{0.0, 0.0, T(0), T(0), T(0)};
+    const int j = r - 2;
+    if (j >= rs && j < re) {
+      const size_t g = (size_t)j * nx + c.gi;
+      o.ub = __ldg(A.ub + g);
+      if (comb) {
+        o.Aub = A.Aub[0][g];
+        o.V = __ldg(A.AV[0] + g);
+        o.X = __ldg(A.AX[0] + g);
+        o.Y = __ldg(A.AY[0] + g);
+      }
+    }
+    return o;
+  };
+  OutIn<T> oin = out_in(r0);
+  for (int r = r0; r <= r1; r += 3) {
+    {
+      const RowIn<T> nin = next_row();
+      const OutIn<T> noin = out_in(r + 1);
+      stream_step<FLUX, DIFF, T>(c, r, in, oin, s1, s2, s0);
+      in = nin;
+      oin = noin;
+    }
+    if (r + 1 > r1) break;
+    {
+      const RowIn<T> nin = next_row();
+      const OutIn<T> noin = out_in(r + 2);
+      stream_step<FLUX, DIFF, T>(c, r + 1, in, oin, s2, s0, s1);
+      in = nin;
+      oin = noin;
+    }
+    if (r + 2 > r1) break;
+    {
+      const RowIn<T> nin = next_row();
+      const OutIn<T> noin = out_in(r + 3);
+      stream_step<FLUX, DIFF, T>(c, r + 2, in, oin, s0, s1, s2);
+      in = nin;
+      oin = noin;
+    }
+  }
+}
+
+}  // namespace af

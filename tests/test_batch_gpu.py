@@ -63,10 +63,17 @@ def test_batch_bitwise_equals_single_mesh(prec, tile, rk):
                 want = one.get_state()
                 tb, ts = capi.af_batch_time(b, i), one.time()
             scale = max(abs(s.umin), abs(s.umax))
-            if rk == 3:
+            if rk == 3 and prec == "fp64":
                 assert tb == ts
                 for x, y in zip(got, want):
                     assert np.array_equal(x.reshape(y.shape), y)
+            elif prec == "fp32_mixed":
+                # the single-mesh FP32-mixed stage is the column-marching kernel, the
+                # batch runs the tile kernel: the same arithmetic in another order,
+                # agreement within the FP32 stencils' rounding
+                assert tb == pytest.approx(ts, rel=2e-6)
+                for x, y in zip(got, want):
+                    assert np.max(np.abs(x.reshape(y.shape) - y)) <= 2e-6 * scale
             else:
                 # separate compilations of the same tile code may contract a few
                 # multiply-adds differently: agreement to a few ulp of the arithmetic
@@ -172,8 +179,8 @@ def test_batch_cfl_interior_extrema_bl():
 def test_batch_tiny_and_ragged_meshes_equal_single_mesh(prec):
     """Meshes smaller than the halo (1x1, 3x2), ragged tile edges (5x7, 33x9) and a
     non-square mesh in one batch, with and without a diffusion term: SSP-RK3 steps agree
-    bit for bit with single-mesh contexts (the periodic wrap takes its modulo path for
-    the smallest ones)."""
+    with single-mesh contexts, bit for bit in FP64 (the periodic wrap takes its modulo
+    path for the smallest ones)."""
     from paper_2510_11527_gb300 import Solver, capi
     sizes = [(1, 1), (3, 2), (5, 7), (33, 9), (40, 17)]
     specs, states = [], []
@@ -196,9 +203,15 @@ def test_batch_tiny_and_ragged_meshes_equal_single_mesh(prec):
                 for _ in range(2):
                     one.step(0.0)
                 want = one.get_state()
-                assert capi.af_batch_time(b, i) == one.time()
+                if prec == "fp64":
+                    assert capi.af_batch_time(b, i) == one.time()
+                else:
+                    assert capi.af_batch_time(b, i) == pytest.approx(one.time(), rel=2e-6)
             for x, y in zip(got, want):
-                assert np.array_equal(x.reshape(y.shape), y)
+                if prec == "fp64":
+                    assert np.array_equal(x.reshape(y.shape), y)
+                else:   # column-marching single-mesh kernel vs the batch's tile kernel
+                    assert np.max(np.abs(x.reshape(y.shape) - y)) <= 2e-6 * max(abs(s.umin), abs(s.umax))
         assert capi.af_batch_stats(b)["errors"] == 0
     finally:
         capi.af_batch_destroy(b)
