@@ -223,6 +223,7 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
   const T f1Xm = shup(f1X), d1Xm = dup(d1X);
   const T Ym = shup(cur.Y), f1Ym = shup(f1Y), aYm = shup(cur.aY), d1Ym = dup(d1Y);
   const T Up = shdn(cur.U), f1Up = shdn(f1U), aUp = shdn(cur.aU), d1Up = ddn(d1U);
+  const T Um = shup(cur.U), f1Um = shup(f1U), aUm = shup(cur.aU), d1Um = dup(d1U);
   const T Vp = shdn(cur.V), f1Vp = shdn(f1V), aVp = shdn(cur.aV), d1Vp = ddn(d1V);
   const T Yp = shdn(cur.Y), f1Yp = shdn(f1Y), aYp = shdn(cur.aY), d1Yp = ddn(d1Y);
   const T Xp = shdn(cur.X), f1Xp = shdn(f1X), aXp = shdn(cur.aX), d1Xp = ddn(d1X);
@@ -242,6 +243,8 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
     AH1 = cell_pot<T>(sv, sx, sy, cur.aC, false, k.r36);
   }
   const T FL1 = llf<FLUX, T>(m, 0, cur.U, Up, f1U, f1Up, d1U, d1Up, half);
+  // the face on the left, formed here as its owner forms it (same inputs, same code)
+  const T FL1m = llf<FLUX, T>(m, 0, Um, cur.U, f1Um, f1U, d1Um, d1U, half);
   // y-face between rows r-1 and r
   const T FL2 = llf<FLUX, T>(m, 1, p1.U, cur.U, p1.fU, cur.fU, p1.dU, cur.dU, half);
 
@@ -275,10 +278,14 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
   T Flim1 = FH1, Alim1 = AH1, Flim2 = p1.FH2;
   p1.Alim2 = p1.AH2;
   if (lim) {
-    const T FL1m = shup(FL1), aUm = shup(cur.aU);
-    const T ULp1 = sfma(k.n4_1, aUp - cur.aU, sfma(-k.m4_1, FL1 - f1U, cur.U));
-    const T ULm1 = sfma(-k.n4_1, cur.aU - aUm, sfma(-k.m4_1, f1U - FL1m, cur.U));
-    const T ULm1p = shdn(ULm1), ULp1m = shup(ULp1);
+    // x low-order states of this cell and of both neighbours (the neighbours' formed
+    // here from the shuffled values, no further shuffle round)
+    auto ulp = [&](T u, T f, T a, T FLr, T ar) { return sfma(k.n4_1, ar - a, sfma(-k.m4_1, FLr - f, u)); };
+    auto ulm = [&](T u, T f, T a, T FLl, T al) { return sfma(-k.n4_1, a - al, sfma(-k.m4_1, f - FLl, u)); };
+    const T ULp1 = ulp(cur.U, f1U, cur.aU, FL1, aUp);
+    const T ULm1 = ulm(cur.U, f1U, cur.aU, FL1m, aUm);
+    const T ULm1p = ulm(Up, f1Up, aUp, FL1, cur.aU);
+    const T ULp1m = ulp(Um, f1Um, aUm, FL1m, cur.aU);
     // y: low-order states u^{L,+}_{r-1} and u^{L,-}_r around the face between them
     p1.ULp2 = sfma(k.n4_2, cur.aU - p1.aU, sfma(-k.m4_2, FL2 - p1.fU, p1.U));
     cur.ULm2 = sfma(-k.n4_2, cur.aU - p1.aU, sfma(-k.m4_2, cur.fU - FL2, cur.U));
@@ -366,22 +373,17 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
 
 // One launch: one output of the stage (the launcher calls it once per output).
 template <int FLUX, int DIFF>
-__global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>()) stream2d_kernel(const DevModel m, const StageArgs2D<float> A, int S,
-                                                                   int bands) {
+__global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
+    stream2d_kernel(const DevModel m, const StageArgs2D<float> A, int S, int bands) {
   using T = float;
   const double dtv = *A.dt;
-  if (is_zero_bits(dtv)) return;
-  const int lane = threadIdx.x & 31;
-  const int w = blockIdx.x * STREAM_WPB + (threadIdx.x >> 5);
-  const int band = w % bands, strip = w / bands;
-  const int nx = A.nx, ny = A.ny;
-  const int rs = strip * S;
-  if (rs >= ny) return;   // whole warp
-  const int re = min(rs + S, ny);
-  const int giu = band * STREAM_BAND - 2 + lane;
-
-  StreamScal<T> k;
-  {
+  if (is_zero_bits(dtv)) return;   // uniform over the grid
+  // the launch's scalars, formed once per block in FP64 and rounded: kept in shared
+  // memory, so that a value the compiler does not keep in a register is reloaded
+  // (one shared load) rather than formed again on GB300's slow FP64 unit
+  __shared__ StreamScal<T> sk;
+  if (threadIdx.x == 0) {
+    StreamScal<T> k;
     const double tau = A.tcoef[0] * dtv;
     const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
     const double nu1 = mu1 * A.inv_h1, nu2 = mu2 * A.inv_h2;
@@ -411,7 +413,18 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>()) st
     k.half = T(0.5);
     k.sixth = T(1.0 / 6.0);
     k.r36 = T(1.0 / 36.0);
+    sk = k;
   }
+  __syncthreads();
+  const StreamScal<T>& k = sk;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * STREAM_WPB + (threadIdx.x >> 5);
+  const int band = w % bands, strip = w / bands;
+  const int nx = A.nx, ny = A.ny;
+  const int rs = strip * S;
+  if (rs >= ny) return;   // whole warp
+  const int re = min(rs + S, ny);
+  const int giu = band * STREAM_BAND - 2 + lane;
   const bool comb = !is_zero_bits(A.cA[0]);
   StreamCtx<FLUX, DIFF, T> c{m, A, k, nx, ny, wrapi(giu, nx), lane, rs, re,
                              lane >= 2 && lane < 2 + STREAM_BAND && giu < nx, comb};
