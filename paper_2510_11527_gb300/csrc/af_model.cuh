@@ -285,6 +285,30 @@ template <> __device__ __forceinline__ float to_stencil<float>(double d) {
   return __int_as_float((int)(sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFull)));
 }
 
+// double -> stencil precision, rounded toward the nearer bound of [umin, umax]: upward
+// above the midpoint mid of the bounds, downward below it (integer operations only).
+// The stencils then see an average that lies between the FP64 average and the nearer
+// bound, so the FP64 update built from their low-order fluxes is not shifted past that
+// bound by the conversion (truncation toward zero would shift it by up to one FP32 ulp).
+template <class T> __device__ __forceinline__ T to_stencil_nb(double d, double mid);
+template <> __device__ __forceinline__ double to_stencil_nb<double>(double d, double) { return d; }
+template <> __device__ __forceinline__ float to_stencil_nb<float>(double d, double mid) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned int hi = (unsigned int)(b >> 32);
+  const unsigned int sign = hi & 0x80000000u;
+  const bool up = dkey(mid) < dkey(d);
+  const bool away = up != (sign != 0u);   // the magnitude grows
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1023 + 127;
+  if (e <= 0) {   // below the normal FP32 range: 0, or the smallest normal away from zero
+    if (!away || (b << 1) == 0) return __int_as_float((int)sign);
+    return __int_as_float((int)(sign | 0x00800000u));
+  }
+  if (e >= 255) return __int_as_float((int)(sign | 0x7F800000u));
+  unsigned int r = sign | ((unsigned int)e << 23) | (unsigned int)((b >> 29) & 0x7FFFFFull);
+  if (away && (b & 0x1FFFFFFFull) != 0) r += 1u;   // next float away from zero
+  return __int_as_float((int)r);
+}
+
 // error-free sum: s + err = a + b exactly (Knuth's TwoSum)
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& err) {
   s = __fadd_rn(a, b);

@@ -111,6 +111,7 @@ struct TileScal {
   float mu1f[2], mu2f[2], nu1f[2], nu2f[2];
   T taut[2], m4_1[2], n4_1[2], m4_2[2], n4_2[2], k1[2], k2[2], q1[2], q2[2], cAt[2], cFt[2];
   T umin, umax, i6h1, i6h2, i3h21, i3h22, i2h1, i2h2, i4h21, i4h22, g;
+  double umid;   // midpoint of the bounds (direction of the averages' conversion)
 };
 
 template <int NT, class F>
@@ -215,6 +216,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   if (tid == 0) {
     sc.umin = T(m.umin);
     sc.umax = T(m.umax);
+    sc.umid = 0.5 * (m.umin + m.umax);
     sc.i6h1 = T(A.inv_h1 / 6.0);
     sc.i6h2 = T(A.inv_h2 / 6.0);
     sc.i3h21 = T(A.inv_h1 * A.inv_h1 / 3.0);
@@ -283,8 +285,8 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
       const int k = tid + it * NT;
       if (k < NV) {
         const int b = (k / PW) * BX + 2 * (k % PW);
-        sU[b] = to_stencil<T>(ldU[it].x);
-        sU[b + 1] = to_stencil<T>(ldU[it].y);
+        sU[b] = to_stencil_nb<T>(ldU[it].x, sc.umid);
+        sU[b + 1] = to_stencil_nb<T>(ldU[it].y, sc.umid);
         sZ[0][b] = T(ldV[it].x);
         sZ[0][b + 1] = T(ldV[it].y);
         sZ[1][b] = T(ldX[it].x);
@@ -324,7 +326,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     for (int it = 0; it < NP0; ++it) {
       const int k = tid + it * NT;
       if (k < BN) {
-        sU[k] = to_stencil<T>(ldU[it]);
+        sU[k] = to_stencil_nb<T>(ldU[it], sc.umid);
         sZ[0][k] = T(ldV[it]);
         sZ[1][k] = T(ldX[it]);
         sZ[2][k] = T(ldY[it]);

@@ -37,7 +37,7 @@ template <class T>
 struct StreamScal {
   T umin, umax, i6h1, i6h2, i3h21, i3h22, m4_1, n4_1, m4_2, n4_2, k1, k2, q1, q2, taut, cAt, cFt, half, sixth, r36;
   float m1f, m2f, n1f, n2f;
-  double cA, cF;
+  double cA, cF, umid;
 };
 
 // values of one input row that later steps read (a row slot)
@@ -195,7 +195,7 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
   constexpr bool BL = FLUX == FLUX_BL;
 
   // ---- row r: points, centre, pointwise functions
-  cur.U = to_stencil<T>(in.ub);
+  cur.U = to_stencil_nb<T>(in.ub, k.umid);
   cur.V = in.V;
   cur.X = in.X;
   cur.Y = in.Y;
@@ -413,6 +413,7 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
     k.half = T(0.5);
     k.sixth = T(1.0 / 6.0);
     k.r36 = T(1.0 / 36.0);
+    k.umid = 0.5 * (m.umin + m.umax);
     sk = k;
   }
   __syncthreads();
@@ -438,7 +439,7 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
     s0 = RowSlot<T>{};
     s1 = RowSlot<T>{};
     s2 = RowSlot<T>{};
-    s0.U = s1.U = s2.U = to_stencil<T>(a.ub);
+    s0.U = s1.U = s2.U = to_stencil_nb<T>(a.ub, k.umid);
     s0.V = s1.V = s2.V = a.V;
     s0.X = s1.X = s2.X = a.X;
     s0.Y = s1.Y = s2.Y = a.Y;
