@@ -382,7 +382,8 @@ def forms(args, headline_value, peaks):
 
 
 def _form_fp32(args, stream, flush, peaks):
-    """Degenerate Burgers 1024^2 (the headline workload) in FP32-mixed."""
+    """Degenerate Burgers 1024^2 (the headline workload) in FP32-mixed, and the FP32-mixed
+    stage on the same problem at 2048^2 and 4096^2."""
     import af_inputs as ai
     res = {}
     spec = ai.config2(1024)
@@ -398,6 +399,16 @@ def _form_fp32(args, stream, flush, peaks):
     s64.close()
     s32.close()
     del st, a64, a32
+    # the same workload on finer meshes: FP32-mixed stage throughput and HBM roofline
+    for n in (2048, 4096):
+        spec = ai.config2(n)
+        st = ai.initial_state(spec, device="cuda", sub=2, order=3)
+        s32, r32 = _single_form(spec, "fp32_mixed", args.form_steps, 3, st, stream, flush)
+        res[f"fp32_mixed_degenerate_burgers_{n}"] = {
+            "value": round(r32["value"], 1), "stage_ms_avg": round(r32["stage_ms_avg"], 5),
+            "roofline": _hbm_roof("fp32_mixed", spec.cells, r32["stage_ms_avg"], peaks)}
+        s32.close()
+        del st
     return res
 
 

@@ -56,6 +56,13 @@ struct RowSlot {
   T tF1, tD1;                      // update terms of the x-face right of the cell
 };
 
+// max / min for values that are never NaN in a valid state: one FMNMX in FP32 (tmax /
+// tmin keep the select semantics of the tile kernel); FP64 keeps the integer compare
+__device__ __forceinline__ float fmx(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float fmn(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double fmx(double a, double b) { return tmax(a, b); }
+__device__ __forceinline__ double fmn(double a, double b) { return tmin(a, b); }
+
 // Diffusion kinds compiled into the column-marching kernel (DK_GENERIC takes the
 // model's runtime kind).
 enum : int { DK_GENERIC = -1, DK_NONE = 0, DK_CONST = 1, DK_PWL = 2, DK_PME2 = 3, DK_CUBIC = 4 };
@@ -69,8 +76,8 @@ __device__ __forceinline__ T apot_k(const DevModel& m, T u) {
   } else if constexpr (DIFF == DK_PWL) {
     // both branches always: a zero coefficient contributes a signed zero, which does not
     // change the sum
-    return par<T>(m.dp, m.dpf, 0) * tmin(u - par<T>(m.dp, m.dpf, 1), T(0)) +
-           par<T>(m.dp, m.dpf, 2) * tmax(u - par<T>(m.dp, m.dpf, 3), T(0));
+    return par<T>(m.dp, m.dpf, 0) * fmn(u - par<T>(m.dp, m.dpf, 1), T(0)) +
+           par<T>(m.dp, m.dpf, 2) * fmx(u - par<T>(m.dp, m.dpf, 3), T(0));
   } else if constexpr (DIFF == DK_PME2) {
     return u * u;
   } else if constexpr (DIFF == DK_CUBIC) {
@@ -126,9 +133,9 @@ template <int FLUX, class T>
 __device__ __forceinline__ T line_alpha(const DevModel& m, int dir, T z0, T z1, T z2, T z3, T z4, T d0, T d1, T d2,
                                         T d3, T d4) {
   if constexpr (FLUX == FLUX_BURGERS) {
-    return tabs(T(2) * par<T>(m.fp, m.fpf, 0)) * tmax(tmax(tmax(tabs(z0), tabs(z1)), tmax(tabs(z3), tabs(z4))), tabs(z2));
+    return tabs(T(2) * par<T>(m.fp, m.fpf, 0)) * fmx(fmx(fmx(tabs(z0), tabs(z1)), fmx(tabs(z3), tabs(z4))), tabs(z2));
   } else if constexpr (FLUX == FLUX_BL) {
-    return tmax(tmax(tmax(d0, d1), tmax(d3, d4)), d2);
+    return fmx(fmx(fmx(d0, d1), fmx(d3, d4)), d2);
   } else if constexpr (FLUX == FLUX_LINEAR) {
     return tabs(T(dir == 0 ? m.fp[0] : m.fp[1]));
   } else {
@@ -300,8 +307,8 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
     T lo = zh[0], hi = zh[0];
 #pragma unroll
     for (int q = 1; q < 12; ++q) {
-      lo = tmin(lo, zh[q]);
-      hi = tmax(hi, zh[q]);
+      lo = fmn(lo, zh[q]);
+      hi = fmx(hi, zh[q]);
     }
     if (tlt(lo, k.umin) | tlt(k.umax, hi)) {
       T t[12];
@@ -341,9 +348,9 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
     const double ubfe = oin.ub + (f2d_exact(hs) + f2d_exact(ls));
     T v = rk_fma(k.taut, p2.rV, p2.V), x = rk_fma(k.taut, p2.rX, p2.X), y = rk_fma(k.taut, p2.rY, p2.Y);
     if (lim) {
-      v = tmin(tmax(v, k.umin), k.umax);
-      x = tmin(tmax(x, k.umin), k.umax);
-      y = tmin(tmax(y, k.umin), k.umax);
+      v = fmn(fmx(v, k.umin), k.umax);
+      x = fmn(fmx(x, k.umin), k.umax);
+      y = fmn(fmx(y, k.umin), k.umax);
     }
     double ubo;
     T vo, xo, yo;
@@ -358,7 +365,9 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
       xo = rk_scale(k.cFt, x);
       yo = rk_scale(k.cFt, y);
     }
-    if (lim && A.sg[0]) {
+    // post-stage safeguard: one test for the four values, the clamp path only if needed
+    if (lim && A.sg[0] &&
+        (tlt(ubo, m.umin) | tlt(m.umax, ubo) | (fmn(fmn(vo, xo), yo) < k.umin) | (fmx(fmx(vo, xo), yo) > k.umax))) {
       ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
       vo = safeguard<T>(vo, k.umin, k.umax, A.tol, A.stats);
       xo = safeguard<T>(xo, k.umin, k.umax, A.tol, A.stats);
@@ -378,11 +387,20 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
   using T = float;
   const double dtv = *A.dt;
   if (is_zero_bits(dtv)) return;   // uniform over the grid
-  // the launch's scalars, formed once per block in FP64 and rounded: kept in shared
-  // memory, so that a value the compiler does not keep in a register is reloaded
-  // (one shared load) rather than formed again on GB300's slow FP64 unit
-  __shared__ StreamScal<T> sk;
-  if (threadIdx.x == 0) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int w = blockIdx.x * STREAM_WPB + wib;
+  const int band = w % bands, strip = w / bands;
+  const int nx = A.nx, ny = A.ny;
+  const int rs = strip * S;
+  if (rs >= ny) return;   // whole warp
+  const int re = min(rs + S, ny);
+  const int giu = band * STREAM_BAND - 2 + lane;
+  // the launch's scalars, formed once per warp in FP64 and rounded: kept in shared
+  // memory, so that a value the compiler does not keep in a register is reloaded (one
+  // shared load) rather than formed again on GB300's slow FP64 unit; one slot per warp,
+  // so no warp waits for another
+  __shared__ StreamScal<T> skw[STREAM_WPB];
+  if (lane == 0) {
     StreamScal<T> k;
     const double tau = A.tcoef[0] * dtv;
     const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
@@ -414,18 +432,10 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
     k.sixth = T(1.0 / 6.0);
     k.r36 = T(1.0 / 36.0);
     k.umid = 0.5 * (m.umin + m.umax);
-    sk = k;
+    skw[wib] = k;
   }
-  __syncthreads();
-  const StreamScal<T>& k = sk;
-  const int lane = threadIdx.x & 31;
-  const int w = blockIdx.x * STREAM_WPB + (threadIdx.x >> 5);
-  const int band = w % bands, strip = w / bands;
-  const int nx = A.nx, ny = A.ny;
-  const int rs = strip * S;
-  if (rs >= ny) return;   // whole warp
-  const int re = min(rs + S, ny);
-  const int giu = band * STREAM_BAND - 2 + lane;
+  __syncwarp();
+  const StreamScal<T>& k = skw[wib];
   const bool comb = !is_zero_bits(A.cA[0]);
   StreamCtx<FLUX, DIFF, T> c{m, A, k, nx, ny, wrapi(giu, nx), lane, rs, re,
                              lane >= 2 && lane < 2 + STREAM_BAND && giu < nx, comb};
