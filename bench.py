@@ -54,12 +54,12 @@ BYTES_PER_CELL_STAGE_3D = 170.67
 FLOPS_PER_CELL_STAGE_3D = 1895.56
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch (SSP-RK3 stage 2) from
 # the ncu captures summarised in profiles/stage2d_fp64_degenerate_burgers_1024.md and
-# profiles/stage2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
+# profiles/stream2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
 # for any other size.
-NCU_TRAFFIC_PER_LAUNCH = {("fp64", 1024): 75.29e6, ("fp32_mixed", 2048): 227.18e6}
-# thread instructions per cell-stage of the FP32-mixed stage from the same capture
-# (smsp__inst_executed.sum x 32 / cells)
-NCU_INSTR_PER_CELL_STAGE = {("fp32_mixed", 2048): 1664.0}
+NCU_TRAFFIC_PER_LAUNCH = {("fp64", 1024): 75.29e6, ("fp32_mixed", 2048): 224.84e6}
+# thread instructions per cell-stage of the FP32-mixed (column-marching) stage from the
+# same capture (smsp__inst_executed.sum x 32 / cells)
+NCU_INSTR_PER_CELL_STAGE = {("fp32_mixed", 2048): 838.0}
 
 
 def load_peaks():
@@ -378,7 +378,54 @@ def forms(args, headline_value, peaks):
         res.update(_form_rect2d(args, stream, flush, peaks))
     if "pme3d" in sel:
         res.update(_form_pme3d(args, stream, peaks))
+    if "pme_full" in sel:
+        res.update(_form_pme_full(args))
     return res
+
+
+def _form_pme_full(args):
+    """The porous-medium workload run to its final time: Barenblatt profile (m = 2) at
+    t = 1 on [-10, 10]^2, to t = 2, SSP-RK(5,4) at the default (capped) step.
+    FP32-mixed at --pme-n cells per direction and both forms at 1024^2: time to
+    solution, steps, L1 / Linf of the cell averages against the closed form's averages,
+    FP32-mixed against FP64 on the same mesh, bounds, mass change and safeguard clamps."""
+    import math
+    import time
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import Solver
+    out = {}
+    finals = {}
+    for n, prec in ((1024, "fp64"), (1024, "fp32_mixed"), (args.pme_n, "fp32_mixed")):
+        key = (n, prec)
+        if key in finals:
+            continue
+        spec = ai.config3(n)
+        st = [a.cpu().numpy() for a in ai.state_2d(lambda x, y: ai.barenblatt(x, y, 1.0), spec, device="cuda", sub=2,
+                                                    order=3)]
+        exact = ai.state_2d(lambda x, y: ai.barenblatt(x, y, 2.0), spec, device="cuda", sub=2, order=3)[0]
+        with Solver(spec, precision=prec, rk=54) as s:
+            s.set_state(st)
+            m0 = s.mass()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = s.run(1.0)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            ub = torch.from_numpy(s.get_state()[0]).cuda().reshape(exact.shape)
+            lo, hi = s.bounds()
+            stats = s.stats()
+            m1 = s.mass()
+        d = (ub - exact).abs()
+        finals[key] = ub
+        out[f"pme_t2_{prec}_{n}"] = {
+            "steps": steps, "seconds": round(secs, 2), "cell_stage_per_s": round(spec.cells * 5 * steps / secs, 1),
+            "l1_vs_closed_form": float(d.mean()), "linf_vs_closed_form": float(d.max()), "min": lo, "max": hi,
+            "mass_rel_change": (m1 - m0) / m0, "clamps": stats["clamps"], "errors": stats["errors"]}
+        del exact, ub
+    a, b = finals[(1024, "fp32_mixed")], finals[(1024, "fp64")]
+    out["pme_t2_fp32_vs_fp64_1024"] = {"l1": float((a - b).abs().mean()), "linf": float((a - b).abs().max())}
+    return out
 
 
 def _form_fp32(args, stream, flush, peaks):
@@ -816,6 +863,7 @@ def main():
     ap.add_argument("--form-steps", type=int, default=5)
     ap.add_argument("--n1d", type=int, default=1 << 24, help="cells of the bounded1d form")
     ap.add_argument("--n3d", type=int, default=128, help="cells per direction of the pme3d form")
+    ap.add_argument("--pme-n", type=int, default=2048, help="FP32-mixed mesh of the pme_full form (run to t = 2)")
     ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl,bounded1d,ex65,ex64_66,rect2d,pme3d",
                     help="comma list of forms to run: fp32 (Burgers 1024^2), rk54 (Burgers 1024^2 with "
                          "SSP-RK(5,4)), pme (4096^2), batch (256), bl (4096^2), bounded1d (Example 6.5's "

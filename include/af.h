@@ -120,8 +120,7 @@ typedef struct {
   int rk;                 /* AF_RK_SSP3 or AF_RK_SSP54                                      */
   double cfl;             /* C in dt = C / max(alpha/h + kappa_max/h^2); <= 0 -> 0.33/dim    */
   double cfl_diff;        /* diffusive cap dt <= Cd h^2/kappa_max; < 0 -> off; 0 -> default:
-                             none for AF_RK_SSP54 with the limiter (the paper's setting, Section
-                             6), else 0.9 x the unlimited scheme's linear diffusive limit      */
+                             0.9 x the unlimited scheme's linear diffusive limit               */
   int limiter;            /* 1: monolithic convex limiter + point projection (Section 5)    */
   int blend;              /* AF_BLEND_*: smoothness-indicator blend (Section 5.1.3)         */
   double gamma;           /* blend strength gamma (1 in the paper's examples)               */

@@ -17,102 +17,9 @@
 #include "af.h"
 #include "model_host.h"
 #include "reduce.cuh"
-#include "stage2d.cuh"
+#include "batch2d.cuh"
 
 namespace af {
-
-struct BatchInst {
-  DevModel m;
-  int nx, ny;
-  double inv_h1, inv_h2, inv_hmin2, kmax, tol;
-  int tile_begin, tiles_x;       // first work item of this instance, tiles along x
-  double* ub[4];
-  void* pv[4];
-  void* px[4];
-  void* py[4];
-  double* dt;                    // this instance's step
-  double* t;                     // this instance's time
-};
-
-struct BatchStage {              // uniform over the batch for one launch
-  int in, nout;
-  int out[2], aidx[2], sg[2];
-  double cA[2], cF[2], tcoef[2];
-  int limiter;
-};
-
-template <int FLUX, class T, class PT, int TX, int TY>
-__device__ __forceinline__ void batch_stage_body(const BatchInst* __restrict__ inst,
-                                                 const int* __restrict__ work_inst, int total, const BatchStage& S,
-                                                 DevStats* stats) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  // the tile's arguments live in shared memory, written by one thread: a per-thread
-  // copy would sit in local memory (its arrays are indexed at run time)
-  __shared__ StageArgs2D<PT> A;
-  for (int w = blockIdx.x; w < total; w += gridDim.x) {
-    const BatchInst& I = inst[work_inst[w]];
-    const int t = w - I.tile_begin;
-    const int i0 = (t % I.tiles_x) * TX, j0 = (t / I.tiles_x) * TY;
-    if (threadIdx.x == 0) {
-    A.nx = I.nx;
-    A.ny = I.ny;
-    A.inv_h1 = I.inv_h1;
-    A.inv_h2 = I.inv_h2;
-    A.ub = I.ub[S.in];
-    A.V = (const PT*)I.pv[S.in];
-    A.X = (const PT*)I.px[S.in];
-    A.Y = (const PT*)I.py[S.in];
-    A.nout = S.nout;
-    for (int o = 0; o < 2; ++o) {
-      const int a = S.aidx[o], d = S.out[o];
-      A.tcoef[o] = S.tcoef[o];
-      A.cA[o] = S.cA[o];
-      A.cF[o] = S.cF[o];
-      A.Aub[o] = a >= 0 ? I.ub[a] : nullptr;
-      A.AV[o] = a >= 0 ? (const PT*)I.pv[a] : nullptr;
-      A.AX[o] = a >= 0 ? (const PT*)I.px[a] : nullptr;
-      A.AY[o] = a >= 0 ? (const PT*)I.py[a] : nullptr;
-      A.Oub[o] = d >= 0 ? I.ub[d] : nullptr;
-      A.OV[o] = d >= 0 ? (PT*)I.pv[d] : nullptr;
-      A.OX[o] = d >= 0 ? (PT*)I.px[d] : nullptr;
-      A.OY[o] = d >= 0 ? (PT*)I.py[d] : nullptr;
-      A.sg[o] = S.sg[o];
-    }
-    A.dt = I.dt;
-    A.s_ext = nullptr;
-    A.limiter = S.limiter;
-    A.blend = 0;
-    A.blend_external = 0;
-    A.gamma = 0.0;
-    A.tol = I.tol;
-    A.stats = stats;
-    A.bc = AF_BC_PERIODIC;
-    A.nodc = 0;
-    }
-    __syncthreads();
-    // element-wise halo loads: the paired path's extra registers spill in this kernel
-    stage_tile<FLUX, T, PT, false, TX, TY, false>(I.m, A, i0, j0, smem_raw);
-    __syncthreads();
-  }
-}
-
-// FP64 stencils: 72.6 KB of shared memory per CTA leave room for 3 CTAs per SM, which
-// the registers must not undercut (<= 80 per thread)
-template <int FLUX, class T, class PT, int TX, int TY>
-__global__ void __launch_bounds__(256, 3) batch_stage_kernel(const BatchInst* __restrict__ inst,
-                                                          const int* __restrict__ work_inst, int total,
-                                                          const BatchStage S, DevStats* stats) {
-  batch_stage_body<FLUX, T, PT, TX, TY>(inst, work_inst, total, S, stats);
-}
-
-// FP32 stencils: compiled for 6 resident CTAs per SM (measured 8% faster than the
-// compiler's 64-register choice at 4 CTAs per SM, despite a few spilled words)
-template <int FLUX, int TX, int TY>
-__global__ void __launch_bounds__(256, 6) batch_stage_kernel_f32occ6(const BatchInst* __restrict__ inst,
-                                                                     const int* __restrict__ work_inst, int total,
-                                                                     const BatchStage S, DevStats* stats) {
-  batch_stage_body<FLUX, float, float, TX, TY>(inst, work_inst, total, S, stats);
-}
 
 // per-tile part of the CFL rate (see dt_rate_kernel) into rate_bits[2 instance] and the
 // interior-extremum flags into rate_bits[2 instance + 1]
@@ -201,8 +108,8 @@ const Shape kShapes[] = {{32, 8}, {64, 4}, {16, 16}};
 }  // namespace
 
 struct af_batch {
-  int n = 0, flux = 0, prec = AF_PREC_FP64, rk = AF_RK_SSP3, nbuf = 3, limiter = 1;
-  double cfl = 0.165, cfl_diff = 0.0;
+  int n = 0, flux = 0, prec = AF_PREC_FP64, rk = AF_RK_SSP3, nbuf = 3, limiter = 1, blend = 0;
+  double cfl = 0.165, cfl_diff = 0.0, gamma = 1.0;
   int tx = 32, ty = 8, total_tiles = 0;
   long long cells = 0;
   std::vector<BatchInst> h_inst;
@@ -237,12 +144,12 @@ struct af_batch {
 
 namespace {
 
-template <int FLUX, class T, class PT, int TX, int TY>
+template <int FLUX, class T, class PT, int TX, int TY, bool BLEND>
 cudaError_t launch_stage_t(af_batch* b, const BatchStage& S) {
-  using L = af::Tile2D<FLUX, T, false, TX, TY>;
+  using L = af::Tile2D<FLUX, T, BLEND, TX, TY>;
   auto k = [] {
-    if constexpr (sizeof(T) == 4) return af::batch_stage_kernel_f32occ6<FLUX, TX, TY>;
-    else return af::batch_stage_kernel<FLUX, T, PT, TX, TY>;
+    if constexpr (sizeof(T) == 4 && !BLEND) return af::batch_stage_kernel_f32occ6<FLUX, TX, TY>;
+    else return af::batch_stage_kernel<FLUX, T, PT, TX, TY, BLEND>;
   }();
   static int blocks = 0;
   if (!blocks) {
@@ -260,12 +167,19 @@ cudaError_t launch_stage_t(af_batch* b, const BatchStage& S) {
   return cudaGetLastError();
 }
 
+template <int FLUX, class T, class PT, bool BLEND>
+cudaError_t launch_stage_bshape(af_batch* b, const BatchStage& S) {
+  if (b->tx == 32 && b->ty == 8) return launch_stage_t<FLUX, T, PT, 32, 8, BLEND>(b, S);
+  if (b->tx == 64 && b->ty == 4) return launch_stage_t<FLUX, T, PT, 64, 4, BLEND>(b, S);
+  if (b->tx == 16 && b->ty == 16) return launch_stage_t<FLUX, T, PT, 16, 16, BLEND>(b, S);
+  return cudaErrorInvalidValue;
+}
 template <int FLUX, class T, class PT>
 cudaError_t launch_stage_shape(af_batch* b, const BatchStage& S) {
-  if (b->tx == 32 && b->ty == 8) return launch_stage_t<FLUX, T, PT, 32, 8>(b, S);
-  if (b->tx == 64 && b->ty == 4) return launch_stage_t<FLUX, T, PT, 64, 4>(b, S);
-  if (b->tx == 16 && b->ty == 16) return launch_stage_t<FLUX, T, PT, 16, 16>(b, S);
-  return cudaErrorInvalidValue;
+  if (b->blend)
+    return af::batch_launch_blend(b->prec, b->flux, b->tx, b->ty, b->d_inst, b->d_work, b->total_tiles, S,
+                                  b->d_stats, b->stream);
+  return launch_stage_bshape<FLUX, T, PT, false>(b, S);
 }
 
 template <class T, class PT>
@@ -347,7 +261,11 @@ std::vector<BatchStage> stages_of(const af_batch* b) {
     v.push_back(s3);
     BatchStage s4 = make_stage(1, 1); set_o(s4, 0, 0, 1.0, 2, A[4][4], B[4][4] / A[4][4], 1); v.push_back(s4);
   }
-  for (auto& s : v) s.limiter = b->limiter;
+  for (auto& s : v) {
+    s.limiter = b->limiter;
+    s.blend = b->blend;
+    s.gamma = b->gamma;
+  }
   return v;
 }
 
@@ -409,7 +327,9 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return AF_E_UNSUPPORTED;
   if (opts->precision != AF_PREC_FP64 && opts->precision != AF_PREC_FP32_MIXED) return AF_E_ARG;
   if (opts->rk != AF_RK_SSP3 && opts->rk != AF_RK_SSP54) return AF_E_ARG;
-  if (opts->blend != AF_BLEND_OFF || opts->diffusion_form != AF_FORM_DC) return AF_E_UNSUPPORTED;
+  // the plain smoothness blend is supported; the external (learned) indicator is not
+  if (opts->blend == AF_BLEND_EXTERNAL || opts->diffusion_form != AF_FORM_DC) return AF_E_UNSUPPORTED;
+  if (opts->blend != AF_BLEND_OFF && opts->blend != AF_BLEND_PLAIN) return AF_E_ARG;
   for (int k = 0; k < n; ++k) {
     if (grids[k].dim != 2 || grids[k].nx < 1 || grids[k].ny < 1) return AF_E_ARG;
     if (grids[k].bc != AF_BC_PERIODIC) return AF_E_UNSUPPORTED;
@@ -427,12 +347,11 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
   b->rk = opts->rk;
   b->nbuf = opts->rk == AF_RK_SSP54 ? 4 : 3;
   b->limiter = opts->limiter;
+  b->blend = opts->blend == AF_BLEND_PLAIN;
+  b->gamma = opts->gamma;
   b->cfl = opts->cfl > 0.0 ? opts->cfl : 0.33 / 2;
-  // default diffusive cap as for a single mesh: none for SSP-RK(5,4) with the limiter
   b->cfl_diff = opts->cfl_diff > 0.0 ? opts->cfl_diff
-                : (opts->cfl_diff < 0.0 || (opts->rk == AF_RK_SSP54 && opts->limiter)
-                       ? 0.0
-                       : 0.9 * (opts->rk == AF_RK_SSP54 ? 0.1307 : 0.0616));
+                                     : (opts->cfl_diff < 0.0 ? 0.0 : 0.9 * (opts->rk == AF_RK_SSP54 ? 0.1307 : 0.0616));
   b->grids.assign(grids, grids + n);
   const size_t ps = b->prec == AF_PREC_FP64 ? 8 : 4;
   auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };

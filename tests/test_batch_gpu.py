@@ -131,9 +131,11 @@ def test_autotune_restores_state_and_picks_a_built_shape():
             outs.append([capi.af_batch_get_state(b, i, s.cells) for i, s in enumerate(specs)])
         finally:
             capi.af_batch_destroy(b)
+    # the tile shapes are separate compilations of the same FP32 tile code, which may
+    # contract a few multiply-adds differently: agreement to the FP32 stencils' rounding
     for a, c in zip(outs[0], outs[1]):
         for x, y in zip(a, c):
-            assert np.array_equal(x, y)
+            assert np.max(np.abs(x - y)) <= 2e-6
 
 
 def test_batch_rejects_mixed_flux_kinds_and_blend():
@@ -144,10 +146,50 @@ def test_batch_rejects_mixed_flux_kinds_and_blend():
         capi.af_batch_create(*_structs([s1, s2], "fp64", 3))
     assert ei.value.status == capi.AF_E_ARG
     g, f, d, b, o = _structs([s1], "fp64", 3)
-    o.blend = 1
+    o.blend = 2   # the external (learned) indicator is a single-mesh option
     with pytest.raises(capi.AfError) as ei:
         capi.af_batch_create(g, f, d, b, o)
     assert ei.value.status == capi.AF_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_batch_plain_blend_matches_single_mesh_and_oracle(prec):
+    """The smoothness-indicator blend (Section 5.1.3) in the batch path: instances of
+    uneven size with gamma = 1 agree with single-mesh contexts (FP64 within 1e-12, FP32
+    within its stencils' rounding) and, in FP64, with the oracle."""
+    from paper_2510_11527_gb300 import Solver, capi
+    inst = _instances(count=5, seed=11, nmax=90)
+    specs = []
+    for s, _ in inst:
+        s.blend = "plain"
+        specs.append(s)
+    states = [[a.numpy() for a in ai.batch_state(s, m)] for s, (_, m) in zip(specs, inst)]
+    g, f, d, bd, o = _structs(specs, prec, 3)
+    o.blend = 1
+    b = capi.af_batch_create(g, f, d, bd, o)
+    try:
+        for i, (s, st) in enumerate(zip(specs, states)):
+            capi.af_batch_set_state(b, i, s.cells, *st)
+        capi.af_batch_step(b, 2)
+        capi.af_batch_sync(b)
+        assert capi.af_batch_stats(b)["errors"] == 0
+        for i, (s, st) in enumerate(zip(specs, states)):
+            got = capi.af_batch_get_state(b, i, s.cells)
+            with Solver(s, precision=prec, rk=3) as one:
+                one.set_state(st)
+                for _ in range(2):
+                    one.step(0.0)
+                want = one.get_state()
+            tol = 1e-12 if prec == "fp64" else 2e-6
+            for x, y in zip(got, want):
+                assert np.max(np.abs(x.reshape(y.shape) - y)) <= tol
+            if prec == "fp64":
+                ref = [a.copy() for a in st]
+                for _ in range(2):
+                    ref, _ = oracle.step(s, 3, ref, oracle.dt_cfl(s, ref[0]))
+                assert max(np.max(np.abs(x.reshape(r.shape) - r)) for x, r in zip(got, ref)) <= 1e-12
+    finally:
+        capi.af_batch_destroy(b)
 
 
 def test_batch_cfl_interior_extrema_bl():

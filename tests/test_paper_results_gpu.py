@@ -256,3 +256,27 @@ def test_barenblatt_1d_gpu(m):
         assert n == nref
         assert max(np.max(np.abs(g - r)) for g, r in zip(got, ref)) <= 1e-12
         assert (lo == 0.0) if lim else (lo < 0.0)
+
+
+def test_config3_to_t2_vs_oracle_96():
+    """The porous-medium workload (Barenblatt m = 2 at t = 1 on [-10, 10]^2, to t = 2,
+    SSP-RK(5,4) at the default step) on 96^2: the FP64 CUDA path takes the oracle's
+    step count and matches its final state within 1e-12; the FP32-mixed path stays
+    within 1e-5 (max) and 1e-6 (mean) of the oracle's FP64 state, with exact bounds."""
+    import oracle
+    spec = ai.config3(96)
+    st = [a.numpy() for a in ai.state_2d(lambda x, y: ai.barenblatt(x, y, 1.0), spec)]
+    ref, nref, stats = oracle.run_native(spec, 54, st, 1.0)
+    assert stats["error"] == 0
+    for prec, tmax, tmean in (("fp64", 1e-12, 1e-12), ("fp32_mixed", 1e-5, 1e-6)):
+        with solver(spec, precision=prec, rk=54) as s:
+            s.set_state(st)
+            n = s.run(1.0)
+            got = s.get_state()
+            lo, hi = s.bounds()
+            assert s.stats()["errors"] == 0
+        assert n == nref
+        assert lo >= 0.0 and hi <= 1.0
+        d = [np.abs(np.asarray(g, dtype=np.float64) - r) for g, r in zip(got, ref)]
+        assert max(float(x.max()) for x in d) <= tmax
+        assert max(float(x.mean()) for x in d) <= tmean
