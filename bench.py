@@ -380,6 +380,8 @@ def forms(args, headline_value, peaks):
         res.update(_form_pme3d(args, stream, peaks))
     if "pme_full" in sel:
         res.update(_form_pme_full(args))
+    if "c2_full" in sel:
+        res.update(_form_c2_full(args))
     return res
 
 
@@ -425,6 +427,43 @@ def _form_pme_full(args):
         del exact, ub
     a, b = finals[(1024, "fp32_mixed")], finals[(1024, "fp64")]
     out["pme_t2_fp32_vs_fp64_1024"] = {"l1": float((a - b).abs().mean()), "linf": float((a - b).abs().max())}
+    return out
+
+
+def _form_c2_full(args):
+    """The degenerate Burgers workload (1024^2) run to its final time T = 0.5 with
+    SSP-RK3 at the default step, FP32-mixed (and FP64 with --c2-fp64): steps, time to
+    solution, bounds, the safeguard's counts (values clamped, of which cell averages;
+    the largest excess) and the relative mass change; with FP64, the L1
+    / Linf distance of the FP32-mixed cell averages to FP64's."""
+    import time
+    import numpy as np
+    import torch
+    import af_inputs as ai
+    from paper_2510_11527_gb300 import Solver
+    spec = ai.config2(1024)
+    st = [a.cpu().numpy() for a in ai.initial_state(spec, device="cuda")]
+    scale = float(np.sum(np.abs(st[0]))) * spec.dx * spec.dy
+    out, finals = {}, {}
+    for prec in (("fp32_mixed", "fp64") if args.c2_fp64 else ("fp32_mixed",)):
+        with Solver(spec, precision=prec) as s:
+            s.set_state(st)
+            m0 = s.mass()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            steps = s.run(0.5)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            finals[prec] = s.get_state()[0]
+            lo, hi = s.bounds()
+            stats = s.stats()
+            m1 = s.mass()
+        out[f"config2_T05_{prec}_1024"] = {
+            "steps": steps, "seconds": round(secs, 2), "cell_stage_per_s": round(spec.cells * 3 * steps / secs, 1),
+            "min": lo, "max": hi, "mass_change_rel_to_sum_abs": (m1 - m0) / scale, "stats": stats}
+    if args.c2_fp64:
+        d = np.abs(finals["fp32_mixed"] - finals["fp64"])
+        out["config2_T05_fp32_vs_fp64_1024"] = {"l1": float(d.mean()), "linf": float(d.max())}
     return out
 
 
@@ -864,6 +903,7 @@ def main():
     ap.add_argument("--n1d", type=int, default=1 << 24, help="cells of the bounded1d form")
     ap.add_argument("--n3d", type=int, default=128, help="cells per direction of the pme3d form")
     ap.add_argument("--pme-n", type=int, default=2048, help="FP32-mixed mesh of the pme_full form (run to t = 2)")
+    ap.add_argument("--c2-fp64", action="store_true", help="c2_full form: also run FP64 to T = 0.5 (about 4 min)")
     ap.add_argument("--forms", default="fp32,rk54,pme,batch,bl,bounded1d,ex65,ex64_66,rect2d,pme3d",
                     help="comma list of forms to run: fp32 (Burgers 1024^2), rk54 (Burgers 1024^2 with "
                          "SSP-RK(5,4)), pme (4096^2), batch (256), bl (4096^2), bounded1d (Example 6.5's "

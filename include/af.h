@@ -216,6 +216,12 @@ af_status af_dt_cfl(af_ctx* ctx, double* dt);                 /* CFL step of cur
  * averages moved (sum of |clamped - raw| times dx dy: a bound on their effect on the
  * total mass). Any pointer may be NULL. */
 af_status af_stats(af_ctx* ctx, long long* clamps, long long* errors, double* max_excess, double* mass_adjust);
+/* The cell averages among those clamps (the rest are point values, which the
+ * projection bounds anyway). Each changes the total mass; their mass is af_stats'
+ * mass_adjust. In the FP32-mixed form such an excess comes from the FP32 rounding of
+ * the limited terms, which the FP64 average update adds exactly (less than an FP32 ulp
+ * of the bound); the FP64 form has none on the paper's workloads. NULL allowed. */
+af_status af_stats_detail(af_ctx* ctx, long long* avg_clamps);
 
 /* ---- batches of independent meshes -------------------------------------------------
  * A batch holds n independent periodic 2D meshes (uneven sizes; per-instance flux and

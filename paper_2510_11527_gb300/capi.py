@@ -89,6 +89,7 @@ def lib():
         "af_bounds": [_V, _D, _D],
         "af_dt_cfl": [_V, _D],
         "af_stats": [_V, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), _D, _D],
+        "af_stats_detail": [_V, ctypes.POINTER(ctypes.c_longlong)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -151,7 +152,7 @@ def exported_symbols():
     """Names of the entry points declared in include/af.h (for the export test)."""
     return ["af_create", "af_destroy", "af_last_error", "af_set_stream", "af_set_state", "af_get_state",
             "af_device_ptrs", "af_set_state_arrays", "af_get_state_arrays", "af_device_ptrs_arrays", "af_set_indicator", "af_set_indicator_device", "af_forward_euler", "af_stage", "af_dt_device",
-            "af_num_stages", "af_step", "af_run", "af_time", "af_mass", "af_bounds", "af_dt_cfl", "af_stats",
+            "af_num_stages", "af_step", "af_run", "af_time", "af_mass", "af_bounds", "af_dt_cfl", "af_stats", "af_stats_detail",
             "af_mass_noalloc", "af_batch_create", "af_batch_destroy", "af_batch_last_error", "af_batch_set_stream",
             "af_batch_info", "af_batch_set_tile", "af_batch_autotune", "af_batch_set_state", "af_batch_get_state",
             "af_batch_device_ptrs", "af_batch_step", "af_batch_sync", "af_batch_time", "af_batch_mass",
@@ -484,4 +485,7 @@ def af_mass_noalloc(ub_dev_ptr, ncells, cell_area, stream_handle=None):
 def af_stats(ctx):
     c, e, m, a = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double()
     _check(ctx, lib().af_stats(ctx, ctypes.byref(c), ctypes.byref(e), ctypes.byref(m), ctypes.byref(a)))
-    return {"clamps": c.value, "errors": e.value, "max_excess": m.value, "mass_adjust": a.value}
+    ac = ctypes.c_longlong()
+    _check(ctx, lib().af_stats_detail(ctx, ctypes.byref(ac)))
+    return {"clamps": c.value, "errors": e.value, "max_excess": m.value, "mass_adjust": a.value,
+            "avg_clamps": ac.value}

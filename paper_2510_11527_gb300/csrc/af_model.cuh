@@ -357,6 +357,7 @@ struct DevStats {
   unsigned long long errors;
   unsigned long long max_excess_bits;   // bit pattern of a non-negative double
   double ub_adjust;                     // sum of |clamped - raw| over cell averages
+  unsigned long long avg_clamps;        // cell averages among the clamps
 };
 
 __device__ __forceinline__ void record_excess(DevStats* st, double e, double tol, bool* clamp_ok) {
@@ -378,7 +379,10 @@ __device__ __noinline__ S safeguard_violation(S v, S umin, S umax, double tol, D
   const double e = below ? (double)umin - (double)v : (double)v - (double)umax;
   bool ok;
   record_excess(st, e, tol, &ok);
-  if (ok && is_avg) atomicAdd(&st->ub_adjust, e);
+  if (ok && is_avg) {
+    atomicAdd(&st->ub_adjust, e);
+    atomicAdd(&st->avg_clamps, 1ull);
+  }
   return ok ? (below ? umin : umax) : v;
 }
 

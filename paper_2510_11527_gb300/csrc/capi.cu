@@ -88,6 +88,10 @@ StageArgs2D<PT> base_args(af_ctx* c, int in) {
   a.Y = (const PT*)c->py[in];
   a.dt = c->dt_dev;
   a.s_ext = (c->s_ext_user && !c->mlp) ? c->s_ext_user : c->s_ext;
+  // the plain indicator of the column-marching FP32 stage: s_1, s_2 as FP32 in the
+  // indicator scratch (n doubles), which the plain blend does not use otherwise
+  a.sb[0] = (const float*)c->s_ext;
+  a.sb[1] = (const float*)c->s_ext + c->n;
   a.limiter = c->opts.limiter;
   a.blend = c->opts.blend;
   a.blend_external = c->opts.blend == AF_BLEND_EXTERNAL;
@@ -278,9 +282,14 @@ af_status stage_any(af_ctx* c, int k) {
 template <int FLUX>
 cudaError_t launch_rate(af_ctx* c) {
   const int blocks = 152 * 4;
-  af::dt_rate_kernel<FLUX><<<blocks, af::RED_THREADS, 0, c->stream>>>(c->m, c->dim, c->pnx, c->pny, c->inv_h1,
-                                                                       c->inv_h2, c->kmax, c->ub[0], c->rate_bits,
-                                                                       c->grid.bc, c->grid.bc_left, c->grid.bc_right);
+  if constexpr (FLUX == af::FLUX_BL)
+    af::dt_rate_kernel<FLUX><<<blocks, af::RED_THREADS, 0, c->stream>>>(c->m, c->dim, c->pnx, c->pny, c->inv_h1,
+                                                                         c->inv_h2, c->kmax, c->ub[0], c->rate_bits,
+                                                                         c->grid.bc, c->grid.bc_left, c->grid.bc_right);
+  else
+    af::dt_rate_maxu_kernel<FLUX><<<blocks, af::RED_THREADS, 0, c->stream>>>(
+        c->m, c->dim, c->pnx, c->pny, c->inv_h1, c->inv_h2, c->kmax, c->ub[0], c->rate_bits, c->grid.bc,
+        c->grid.bc_left, c->grid.bc_right);
   return cudaGetLastError();
 }
 
@@ -864,6 +873,15 @@ af_status af_stats(af_ctx* c, long long* clamps, long long* errors, double* max_
     *max_excess = v;
   }
   if (mass_adjust) *mass_adjust = st.ub_adjust * c->dx * c->dy * c->dz;
+  return AF_OK;
+}
+
+af_status af_stats_detail(af_ctx* c, long long* avg_clamps) {
+  if (!c) return AF_E_ARG;
+  DevStats st;
+  CK(c, cudaMemcpyAsync(&st, c->stats, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
+  CK(c, cudaStreamSynchronize(c->stream));
+  if (avg_clamps) *avg_clamps = (long long)st.avg_clamps;
   return AF_OK;
 }
 

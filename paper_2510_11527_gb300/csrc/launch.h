@@ -12,7 +12,10 @@ cudaError_t launch_stage2d_f64(int flux, bool blend, const DevModel& m, const St
                                cudaStream_t s);
 cudaError_t launch_stage2d_f32(int flux, bool blend, const DevModel& m, const StageArgs2D<float>& a,
                                cudaStream_t s);
-cudaError_t launch_stream2d_f32(int flux, const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s);
+// bk: 0 no blend, 1 smoothness blend with the plain indicator, 2 with the external one
+cudaError_t launch_stream2d_f32(int flux, int bk, const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s);
+cudaError_t launch_stream2d_blend_f32(int flux, int bk, const DevModel& m, const StageArgs2D<float>& a,
+                                      cudaStream_t s);
 cudaError_t launch_stage2d_rect_f64(int flux, bool blend, const DevModel& m, const StageArgs2D<double>& a,
                                     cudaStream_t s);
 cudaError_t launch_stage2d_rect_f32(int flux, bool blend, const DevModel& m, const StageArgs2D<float>& a,

@@ -198,8 +198,14 @@ __device__ __forceinline__ void net_rows(const NetFrags& F, const __nv_bfloat16 
 // are staged in shared memory (coalesced row loads, converted to FP32 once), every lane
 // builds the patch of one cell from there, and each warp runs the network on its 32
 // patches as two 16-row blocks.
+// Resident CTAs per SM the indicator kernel is compiled for (3: 85 registers, the
+// weight fragments partly spilled; 2: 122 registers, no spill).
+#ifndef AF_INDICATOR_MIN_CTAS
+#define AF_INDICATOR_MIN_CTAS 3
+#endif
+
 template <class PT>
-__global__ void __launch_bounds__(256, 3) indicator_kernel(const double* __restrict__ ub, const PT* __restrict__ V,
+__global__ void __launch_bounds__(256, AF_INDICATOR_MIN_CTAS) indicator_kernel(const double* __restrict__ ub, const PT* __restrict__ V,
                                                            const PT* __restrict__ X, const PT* __restrict__ Y, int nx,
                                                            int ny, const __nv_bfloat16* __restrict__ w1q,
                                                            const __nv_bfloat16* __restrict__ w2q,
@@ -452,7 +458,7 @@ namespace af {
 cudaError_t mlp_indicator_launch(const af_ctx* c, const af_mlp* net, int buf, double* out) {
   if (c->dim != 2) return cudaErrorInvalidValue;
   const long long tiles = (long long)((c->nx + 31) / 32) * ((c->ny + 7) / 8);
-  const int grid = (int)std::min<long long>(tiles, 152 * 3);
+  const int grid = (int)std::min<long long>(tiles, 152LL * AF_INDICATOR_MIN_CTAS);
   if (c->prec == AF_PREC_FP64)
     indicator_kernel<double><<<grid, 256, 0, c->stream>>>(c->ub[buf], (const double*)c->pv[buf],
                                                           (const double*)c->px[buf], (const double*)c->py[buf],

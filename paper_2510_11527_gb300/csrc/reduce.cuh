@@ -35,6 +35,53 @@ __device__ __forceinline__ unsigned crit_flags(const DevModel& m, int dir, doubl
   return f;
 }
 
+// The same rate for a flux whose |f_l'| is a nondecreasing function of |u| (Burgers) or a
+// constant (linear, zero): rounding is monotone, so the largest rate is the rate at the
+// largest |u|. A maximum of the magnitude bits (integer units only) per block, the rate
+// formed once per block.
+template <int FLUX>
+__global__ void __launch_bounds__(RED_THREADS) dt_rate_maxu_kernel(const DevModel m, int dim, int nx, int ny,
+                                                                    double inv_h1, double inv_h2, double kmax,
+                                                                    const double* __restrict__ ub,
+                                                                    unsigned long long* rate_bits, int bc, double gl,
+                                                                    double gr) {
+  const size_t n = (size_t)nx * ny;
+  const double kd1 = kmax * inv_h1 * inv_h1, kd2 = kmax * inv_h2 * inv_h2;
+  const bool rect = dim == 2 && bc != AF_BC_PERIODIC;
+  unsigned long long mb = 0ull;
+  if constexpr (FLUX == FLUX_BURGERS) {
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+      if (rect) {
+        const int i = (int)(k % nx), j = (int)(k / nx);
+        if (i == 0 || j == 0) continue;
+      }
+      const unsigned long long b = (unsigned long long)__double_as_longlong(ub[k]) & 0x7FFFFFFFFFFFFFFFull;
+      mb = b > mb ? b : mb;
+    }
+    if (dim == 1 && bc == AF_BC_DIRICHLET && blockIdx.x == 0 && threadIdx.x == 0) {
+      const unsigned long long bl = (unsigned long long)__double_as_longlong(gl) & 0x7FFFFFFFFFFFFFFFull;
+      const unsigned long long br = (unsigned long long)__double_as_longlong(gr) & 0x7FFFFFFFFFFFFFFFull;
+      mb = bl > mb ? bl : mb;
+      mb = br > mb ? br : mb;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, mb, o);
+    mb = v > mb ? v : mb;
+  }
+  __shared__ unsigned long long smb[RED_THREADS / 32];
+  if ((threadIdx.x & 31) == 0) smb[threadIdx.x >> 5] = mb;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < RED_THREADS / 32; ++w) mb = smb[w] > mb ? smb[w] : mb;
+    const double u = __longlong_as_double((long long)mb);
+    const double a1 = alpha_interval<FLUX, double>(m, 0, u, u), a2 = alpha_interval<FLUX, double>(m, 1, u, u);
+    double b = a1 * inv_h1 + kd1;
+    if (dim == 2) b = tmax(b, a2 * inv_h2 + kd2);
+    atomicMax(rate_bits, (unsigned long long)__double_as_longlong(b));
+  }
+}
+
 template <int FLUX>
 __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, int dim, int nx, int ny,
                                                                double inv_h1, double inv_h2, double kmax,

@@ -53,6 +53,7 @@ struct StageArgs2D {
   PT* OY[2];
   const double* dt;                  // device scalar
   const double* s_ext;               // external per-cell indicator (blend external)
+  const float* sb[2];                // s_1, s_2 per cell (column-marching FP32 blend)
   int limiter;
   int blend;                         // 0 off, 1 smoothness indicator, 2 external indicator
   int blend_external;

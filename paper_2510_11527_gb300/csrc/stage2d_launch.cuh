@@ -1,8 +1,8 @@
 // Launchers of the fused 2D stage kernels (internal). The FP32-mixed form of a periodic
-// mesh without the blend runs the column-marching kernel (stream2d.cuh). The others run
-// one CTA per 32 x 8 tile of the mesh, or of the padded layout of a rectangle with ends
-// (RECT): the FP64 form and the blended FP32 form stage2d_kernel, the FP32 rectangle
-// without the blend the 6-CTAs-per-SM compilation. The translation units instantiate
+// mesh runs the column-marching kernel (stream2d.cuh), with or without the blend. The
+// others run one CTA per 32 x 8 tile of the mesh, or of the padded layout of a
+// rectangle with ends (RECT): the FP64 form and the blended FP32 rectangle
+// stage2d_kernel, the FP32 rectangle without the blend the 6-CTAs-per-SM compilation. The translation units instantiate
 // the periodic (RECT = false) and the rectangle (RECT = true) launchers separately, so
 // they compile in parallel and the periodic kernels are unaffected by the rectangle's
 // code.
@@ -21,7 +21,8 @@ static auto stage2d_kernel_for() {
 
 template <int FLUX, class T, bool BLEND, bool RECT>
 static cudaError_t stage2d_go(const DevModel& m, const StageArgs2D<T>& a, cudaStream_t s) {
-  if constexpr (std::is_same_v<T, float> && !BLEND && !RECT) return launch_stream2d_f32(FLUX, m, a, s);
+  if constexpr (std::is_same_v<T, float> && !RECT)
+    return launch_stream2d_f32(FLUX, BLEND ? (a.blend_external ? 2 : 1) : 0, m, a, s);
   using L = Tile2D<FLUX, T, BLEND>;
   static bool attr = false;
   auto k = stage2d_kernel_for<FLUX, T, BLEND, RECT>();

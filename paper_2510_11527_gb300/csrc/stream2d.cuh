@@ -1,7 +1,7 @@
-// Column-marching 2D stage kernel (periodic meshes, no smoothness blend): the same
-// limited forward-Euler evaluation and Shu-Osher combination as stage_tile (Sections 4
-// and 5.2 of arXiv 2510.11527, d = 2), organised so that every derived quantity is
-// formed once per location and kept in registers.
+// Column-marching 2D stage kernel (periodic meshes, with or without the smoothness
+// blend): the same limited forward-Euler evaluation and Shu-Osher combination as
+// stage_tile (Sections 4 and 5.2 of arXiv 2510.11527, d = 2), organised so that every
+// derived quantity is formed once per location and kept in registers.
 //
 // Each warp owns a band of 28 output columns and a strip of S output rows. Lane L holds
 // column 28 * band - 2 + L (periodic image): lanes 2..29 produce outputs, lanes 0, 1,
@@ -27,15 +27,16 @@ namespace af {
 constexpr int STREAM_BAND = 28;   // output columns per warp
 constexpr int STREAM_WPB = 4;     // warps per block
 // Resident blocks per SM the kernel is compiled for: 4 (128 registers per thread, 16
-// warps per SM) measured fastest; Buckley-Leverett's longer live ranges spill there
-// and take 3.
-template <int FLUX>
-constexpr int stream_min_blocks() { return FLUX == FLUX_BL ? 3 : 4; }
+// warps per SM) measured fastest; Buckley-Leverett's and the blend's longer live
+// ranges spill there and take 3.
+template <int FLUX, int BK = 0>
+constexpr int stream_min_blocks() { return FLUX == FLUX_BL || BK != 0 ? 3 : 4; }
 
 // per-lane constants of one launch
 template <class T>
 struct StreamScal {
   T umin, umax, i6h1, i6h2, i3h21, i3h22, m4_1, n4_1, m4_2, n4_2, k1, k2, q1, q2, taut, cAt, cFt, half, sixth, r36;
+  T g, i2h1, i2h2, i4h21, i4h22;   // smoothness blend: gamma; 2/h, 4/h^2 of the low-order residual
   float m1f, m2f, n1f, n2f;
   double cA, cF, umid;
 };
@@ -54,6 +55,9 @@ struct RowSlot {
   T ULp2, ULm2, Alim2;             // y low-order states, limited potential (y)
   T tF2lo, tD2lo;                  // update terms of the y-face below the row's cell
   T tF1, tD1;                      // update terms of the x-face right of the cell
+  // smoothness blend: s_2 of the cell, theta^{c,s} of the x-face right of the cell,
+  // theta^{d,s}_1 of the cell, low-order residuals of the row's x-lines (V, X, Y)
+  T s2, tc1, td1, LV1, LX1, LY1;
 };
 
 // max / min for values that are never NaN in a valid state: one FMNMX in FP32 (tmax /
@@ -149,6 +153,21 @@ __device__ __forceinline__ T llf(const DevModel& m, int dir, T ul, T ur, T fl, T
   return sfma(-(half * al), ur - ul, half * (fl + fr));
 }
 
+// first-order point residual of the smoothness blend on the +-h/2 neighbours (m, 0, p)
+// of a point along dir: -(2/h) [F(z0, zp) - F(zm, z0)] + (4/h^2) (a_p - 2 a_0 + a_m),
+// F the LLF flux (a recovered centre enters as its cell's average)
+template <int FLUX, class T>
+__device__ __forceinline__ T lowres_s(const DevModel& m, int dir, T zm, T fm, T am, T dm, T z0, T f0, T a0, T d0, T zp,
+                                      T fp, T ap, T dp, T half, T i2h, T i4h2) {
+  const T Fr = llf<FLUX, T>(m, dir, z0, zp, f0, fp, d0, dp, half);
+  const T Fl = llf<FLUX, T>(m, dir, zm, z0, fm, f0, dm, d0, half);
+  return sfma(sfma(T(-2), a0, ap + am), i4h2, -((Fr - Fl) * i2h));
+}
+
+// w h + (1 - w) l: a blend weight applied to a high-order and a low-order value
+template <class T>
+__device__ __forceinline__ T blendw(T w, T h, T l) { return sfma(w, h - l, l); }
+
 // cell potential (tensor Simpson average of the DC potential along dir): for x,
 // (8 sy - 4 sx + 32 ac - sv) / 36
 template <class T>
@@ -172,6 +191,7 @@ template <class T>
 struct RowIn {
   double ub;
   T V, X, Y;
+  T s1, s2;   // smoothness indicators (blend)
 };
 template <class T>
 struct OutIn {
@@ -179,19 +199,30 @@ struct OutIn {
   T V, X, Y;        // RK combination inputs of the point values
 };
 
-template <class T>
+// BK: the smoothness blend's indicator. 0: no blend; 1: s_1 and s_2 per cell (FP32
+// arrays A.sb[0], A.sb[1]); 2: one external indicator per cell for both directions
+// (FP64 array A.s_ext).
+template <class T, int BK = 0>
 __device__ __forceinline__ RowIn<T> load_row(const StageArgs2D<T>& A, size_t g) {
   RowIn<T> in;
   in.ub = __ldg(A.ub + g);
   in.V = __ldg(A.V + g);
   in.X = __ldg(A.X + g);
   in.Y = __ldg(A.Y + g);
+  if constexpr (BK == 1) {
+    in.s1 = __ldg(A.sb[0] + g);
+    in.s2 = __ldg(A.sb[1] + g);
+  } else if constexpr (BK == 2) {
+    in.s1 = in.s2 = T(__ldg(A.s_ext + g));
+  } else {
+    in.s1 = in.s2 = T(0);
+  }
   return in;
 }
 
 // One step: input row r arrives (in), slots p2 (row r-2), p1 (row r-1), cur (row r;
 // held row r-3 before). Finalises the cells of row r-2 if they belong to the strip.
-template <int FLUX, int DIFF, class T>
+template <int FLUX, int DIFF, class T, int BK>
 __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, int r, const RowIn<T>& in,
                                             const OutIn<T>& oin, RowSlot<T>& p2, RowSlot<T>& p1, RowSlot<T>& cur) {
   const DevModel& m = c.m;
@@ -218,6 +249,16 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
   point_eval<FLUX, DIFF, T>(m, cur.C, f1C, cur.fC, d1C, cur.dC, cur.aC);
   point_eval<FLUX, DIFF, T>(m, cur.U, f1U, cur.fU, d1U, cur.dU, cur.aU);
   cur.fV1 = f1V;
+  // smoothness blend (Section 5.1.3, direction by direction as in Section 5.2):
+  // theta^{d,s}_1 of cell (i, r) and theta^{c,s}_1 of the x-face right of it
+  T td1 = T(1), tc1 = T(1);
+  if constexpr (BK != 0) {
+    cur.s2 = in.s2;
+    td1 = expf(-k.g * in.s1);
+    tc1 = expf(-k.g * (half * (in.s1 + shdn(in.s1))));
+    cur.td1 = td1;
+    cur.tc1 = tc1;
+  }
 
   // ---- neighbour values (|f'| only where the flux needs it)
   auto dup = [](T v) { if constexpr (BL) return shup(v); else return T(0); };
@@ -238,7 +279,7 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
 
   // ---- faces and cell potentials of row r
   // x-face right of cell (i, r): Simpson over V_{i,r-1}, X_{i,r}, V_{i,r}
-  const T FH1 = sfma(T(4), f1X, p1.fV1 + f1V) * sixth;
+  T FH1 = sfma(T(4), f1X, p1.fV1 + f1V) * sixth;
   // y-face above cell (i, r): Simpson over V_{i-1,r}, Y_{i,r}, V_{i,r}
   cur.FH2 = sfma(T(4), cur.fY, fVm2 + cur.fV) * sixth;
   T AH1;   // lives only in this step (x-limiter of row r)
@@ -248,12 +289,31 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
     const T sy = p1.aY + cur.aY;
     cur.AH2 = cell_pot<T>(sv, sx, sy, cur.aC, true, k.r36);
     AH1 = cell_pot<T>(sv, sx, sy, cur.aC, false, k.r36);
+    if constexpr (BK != 0) AH1 = blendw(td1, AH1, cur.aU);
   }
   const T FL1 = llf<FLUX, T>(m, 0, cur.U, Up, f1U, f1Up, d1U, d1Up, half);
   // the face on the left, formed here as its owner forms it (same inputs, same code)
   const T FL1m = llf<FLUX, T>(m, 0, Um, cur.U, f1Um, f1U, d1Um, d1U, half);
   // y-face between rows r-1 and r
   const T FL2 = llf<FLUX, T>(m, 1, p1.U, cur.U, p1.fU, cur.fU, p1.dU, cur.dU, half);
+  // blend: the x-face of row r; theta^{c,s}_2 of the y-face between rows r-1 and r and
+  // theta^{d,s}_2 of cell (i, r-1), with the y-face flux and the y cell potential of
+  // row r-1 (both first used by this step's y-limiter); the low-order residuals of the
+  // x-lines of row r
+  T tc2 = T(1), td2 = T(1);
+  if constexpr (BK != 0) {
+    FH1 = blendw(tc1, FH1, FL1);
+    tc2 = expf(-k.g * (half * (p1.s2 + cur.s2)));
+    td2 = expf(-k.g * p1.s2);
+    p1.FH2 = blendw(tc2, p1.FH2, FL2);
+    p1.AH2 = blendw(td2, p1.AH2, p1.aU);
+    cur.LV1 = lowres_s<FLUX, T>(m, 0, cur.Y, f1Y, cur.aY, d1Y, cur.V, f1V, cur.aV, d1V, Yp, f1Yp, aYp, d1Yp, half,
+                                k.i2h1, k.i4h21);
+    cur.LX1 = lowres_s<FLUX, T>(m, 0, cur.U, f1U, cur.aU, d1U, cur.X, f1X, cur.aX, d1X, Up, f1Up, aUp, d1Up, half,
+                                k.i2h1, k.i4h21);
+    cur.LY1 = lowres_s<FLUX, T>(m, 0, cur.Vm, f1Vm, cur.aVm, d1Vm, cur.Y, f1Y, cur.aY, d1Y, cur.V, f1V, cur.aV, d1V,
+                                half, k.i2h1, k.i4h21);
+  }
 
   // ---- point residuals: x-lines of row r
   cur.rV = line_res_s<T>(cur.Vm, cur.Y, cur.V, Yp, Vp, f1Vm, f1Y, f1Yp, f1Vp,
@@ -276,9 +336,24 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
     const T rY2 = line_res_s<T>(p2.Y, p1.C, p1.Y, cur.C, cur.Y, p2.fY, p1.fC, cur.fC, cur.fY,
                               line_alpha<FLUX, T>(m, 1, p2.Y, p1.C, p1.Y, cur.C, cur.Y, p2.dY, p1.dC, p1.dY, cur.dC, cur.dY),
                               p2.aY, p1.aC, p1.aY, cur.aC, cur.aY, k.i6h2, k.i3h22);
-    p1.rV = p1.rV + rV2;
-    p1.rX = p1.rX + rX2;
-    p1.rY = p1.rY + rY2;
+    if constexpr (BK != 0) {
+      // blended residuals: each direction's high-order residual against its low-order one
+      // with the weight of the faces / cells the point lies on
+      const T tc2p = shdn(tc2), td2p = shdn(td2);
+      const T LV2 = lowres_s<FLUX, T>(m, 1, p1.X, p1.fX, p1.aX, p1.dX, p1.V, p1.fV, p1.aV, p1.dV, cur.X, cur.fX, cur.aX,
+                                      cur.dX, half, k.i2h2, k.i4h22);
+      const T LX2 = lowres_s<FLUX, T>(m, 1, p2.V, p2.fV, p2.aV, p2.dV, p1.X, p1.fX, p1.aX, p1.dX, p1.V, p1.fV, p1.aV,
+                                      p1.dV, half, k.i2h2, k.i4h22);
+      const T LY2 = lowres_s<FLUX, T>(m, 1, p1.U, p1.fU, p1.aU, p1.dU, p1.Y, p1.fY, p1.aY, p1.dY, cur.U, cur.fU, cur.aU,
+                                      cur.dU, half, k.i2h2, k.i4h22);
+      p1.rV = blendw(tmin(p1.tc1, tc1), p1.rV, p1.LV1) + blendw(tmin(tc2, tc2p), rV2, LV2);
+      p1.rX = blendw(p1.tc1, p1.rX, p1.LX1) + blendw(tmin(td2, td2p), rX2, LX2);
+      p1.rY = blendw(tmin(p1.td1, td1), p1.rY, p1.LY1) + blendw(tc2, rY2, LY2);
+    } else {
+      p1.rV = p1.rV + rV2;
+      p1.rX = p1.rX + rX2;
+      p1.rY = p1.rY + rY2;
+    }
   }
 
   // ---- limiter: x-direction of row r, y-direction of row r-1
@@ -381,8 +456,8 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
 }
 
 // One launch: one output of the stage (the launcher calls it once per output).
-template <int FLUX, int DIFF>
-__global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
+template <int FLUX, int DIFF, int BK = 0>
+__global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, BK>())
     stream2d_kernel(const DevModel m, const StageArgs2D<float> A, int S, int bands) {
   using T = float;
   const double dtv = *A.dt;
@@ -432,6 +507,11 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
     k.sixth = T(1.0 / 6.0);
     k.r36 = T(1.0 / 36.0);
     k.umid = 0.5 * (m.umin + m.umax);
+    k.g = T(A.gamma);
+    k.i2h1 = T(2.0 * A.inv_h1);
+    k.i2h2 = T(2.0 * A.inv_h2);
+    k.i4h21 = T(4.0 * A.inv_h1 * A.inv_h1);
+    k.i4h22 = T(4.0 * A.inv_h2 * A.inv_h2);
     skw[wib] = k;
   }
   __syncwarp();
@@ -445,7 +525,7 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
   // so that the warm-up steps read finite values (their results are never stored)
   int gj = wrapi(rs - 3, ny);
   {
-    const RowIn<T> a = load_row<T>(A, (size_t)gj * nx + c.gi);
+    const RowIn<T> a = load_row<T, BK>(A, (size_t)gj * nx + c.gi);
     s0 = RowSlot<T>{};
     s1 = RowSlot<T>{};
     s2 = RowSlot<T>{};
@@ -456,10 +536,10 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
   }
   const int r0 = rs - 2, r1 = re + 1;   // steps r0 .. r1
   gj = gj + 1 == ny ? 0 : gj + 1;       // row r0
-  RowIn<T> in = load_row<T>(A, (size_t)gj * nx + c.gi);
+  RowIn<T> in = load_row<T, BK>(A, (size_t)gj * nx + c.gi);
   auto next_row = [&]() {
     gj = gj + 1 == ny ? 0 : gj + 1;
-    return load_row<T>(A, (size_t)gj * nx + c.gi);
+    return load_row<T, BK>(A, (size_t)gj * nx + c.gi);
   };
   // RK combination inputs of the cells finalised at step r (row r - 2)
   auto out_in = [&](int r) {
@@ -478,31 +558,92 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX>())
     return o;
   };
   OutIn<T> oin = out_in(r0);
-  for (int r = r0; r <= r1; r += 3) {
-    {
+  if constexpr (BK != 0) {
+    // the blended step is too large to unroll three times (the unrolled loop misses the
+    // instruction cache): one step per iteration, the slots rotated by copies
+#pragma unroll 1
+    for (int r = r0; r <= r1; ++r) {
       const RowIn<T> nin = next_row();
       const OutIn<T> noin = out_in(r + 1);
-      stream_step<FLUX, DIFF, T>(c, r, in, oin, s1, s2, s0);
+      stream_step<FLUX, DIFF, T, BK>(c, r, in, oin, s1, s2, s0);
+      const RowSlot<T> t = s1;
+      s1 = s2;
+      s2 = s0;
+      s0 = t;
       in = nin;
       oin = noin;
     }
-    if (r + 1 > r1) break;
-    {
-      const RowIn<T> nin = next_row();
-      const OutIn<T> noin = out_in(r + 2);
-      stream_step<FLUX, DIFF, T>(c, r + 1, in, oin, s2, s0, s1);
-      in = nin;
-      oin = noin;
-    }
-    if (r + 2 > r1) break;
-    {
-      const RowIn<T> nin = next_row();
-      const OutIn<T> noin = out_in(r + 3);
-      stream_step<FLUX, DIFF, T>(c, r + 2, in, oin, s0, s1, s2);
-      in = nin;
-      oin = noin;
+  } else {
+    for (int r = r0; r <= r1; r += 3) {
+      {
+        const RowIn<T> nin = next_row();
+        const OutIn<T> noin = out_in(r + 1);
+        stream_step<FLUX, DIFF, T, BK>(c, r, in, oin, s1, s2, s0);
+        in = nin;
+        oin = noin;
+      }
+      if (r + 1 > r1) break;
+      {
+        const RowIn<T> nin = next_row();
+        const OutIn<T> noin = out_in(r + 2);
+        stream_step<FLUX, DIFF, T, BK>(c, r + 1, in, oin, s2, s0, s1);
+        in = nin;
+        oin = noin;
+      }
+      if (r + 2 > r1) break;
+      {
+        const RowIn<T> nin = next_row();
+        const OutIn<T> noin = out_in(r + 3);
+        stream_step<FLUX, DIFF, T, BK>(c, r + 2, in, oin, s0, s1, s2);
+        in = nin;
+        oin = noin;
+      }
     }
   }
+}
+
+// ---- launch (host)
+
+// Strip height of the column-marching kernel: about four waves of 16 resident warps
+// per SM, at least 16 rows (the warm-up of a strip is 4 rows) and at most 64 (measured
+// on 1024^2 to 4096^2 meshes).
+static int stream_strip(int nx, int ny) {
+  const long long bands = (nx + STREAM_BAND - 1) / STREAM_BAND;
+  const long long target = 152LL * 16 * 4;
+  long long S = (bands * ny + target - 1) / target;
+  if (S < 16) S = 16;
+  if (S > 64) S = 64;
+  return (int)S;
+}
+
+// one launch per output of the stage
+template <int FLUX, int DIFF, int BK = 0>
+static cudaError_t stream2d_go(const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s) {
+  const int S = stream_strip(a.nx, a.ny);
+  const int bands = (a.nx + STREAM_BAND - 1) / STREAM_BAND;
+  const long long warps = (long long)bands * ((a.ny + S - 1) / S);
+  const long long blocks = (warps + STREAM_WPB - 1) / STREAM_WPB;
+  if (blocks > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
+  for (int o = 0; o < a.nout; ++o) {
+    StageArgs2D<float> b = a;
+    b.nout = 1;
+    b.tcoef[0] = a.tcoef[o];
+    b.cA[0] = a.cA[o];
+    b.cF[0] = a.cF[o];
+    b.Aub[0] = a.Aub[o];
+    b.AV[0] = a.AV[o];
+    b.AX[0] = a.AX[o];
+    b.AY[0] = a.AY[o];
+    b.Oub[0] = a.Oub[o];
+    b.OV[0] = a.OV[o];
+    b.OX[0] = a.OX[o];
+    b.OY[0] = a.OY[o];
+    b.sg[0] = a.sg[o];
+    stream2d_kernel<FLUX, DIFF, BK><<<(unsigned)blocks, 32 * STREAM_WPB, 0, s>>>(m, b, S, bands);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace af

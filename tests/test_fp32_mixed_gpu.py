@@ -69,7 +69,7 @@ def test_fp32_config2_1024_l1_vs_fp64_and_bounds():
             assert stats["errors"] == 0
             scale = np.sum(np.abs(st[0])) * spec.dx * spec.dy
             # conservation holds to FP64 round-off plus the (counted) mass the safeguard
-            # clamps moved
+            # clamps of cell averages moved
             assert abs(s.mass() - m0) <= 1e-13 * scale + stats["mass_adjust"]
     e1 = l1(res["fp32_mixed"], res["fp64"])
     assert e1 <= 1e-5, e1
