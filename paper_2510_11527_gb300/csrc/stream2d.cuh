@@ -58,6 +58,7 @@ struct RowSlot {
   // smoothness blend: s_2 of the cell, theta^{c,s} of the x-face right of the cell,
   // theta^{d,s}_1 of the cell, low-order residuals of the row's x-lines (V, X, Y)
   T s2, tc1, td1, LV1, LX1, LY1;
+  T FVX;   // LLF flux (y) between V of the row below and X of this row
 };
 
 // max / min for values that are never NaN in a valid state: one FMNMX in FP32 (tmax /
@@ -156,11 +157,10 @@ __device__ __forceinline__ T llf(const DevModel& m, int dir, T ul, T ur, T fl, T
 // first-order point residual of the smoothness blend on the +-h/2 neighbours (m, 0, p)
 // of a point along dir: -(2/h) [F(z0, zp) - F(zm, z0)] + (4/h^2) (a_p - 2 a_0 + a_m),
 // F the LLF flux (a recovered centre enters as its cell's average)
-template <int FLUX, class T>
-__device__ __forceinline__ T lowres_s(const DevModel& m, int dir, T zm, T fm, T am, T dm, T z0, T f0, T a0, T d0, T zp,
-                                      T fp, T ap, T dp, T half, T i2h, T i4h2) {
-  const T Fr = llf<FLUX, T>(m, dir, z0, zp, f0, fp, d0, dp, half);
-  const T Fl = llf<FLUX, T>(m, dir, zm, z0, fm, f0, dm, d0, half);
+// from the two LLF fluxes (left Fl = F(zm, z0), right Fr = F(z0, zp)), which the
+// neighbouring points' residuals share
+template <class T>
+__device__ __forceinline__ T lowres_s(T Fl, T Fr, T am, T a0, T ap, T i2h, T i4h2) {
   return sfma(sfma(T(-2), a0, ap + am), i4h2, -((Fr - Fl) * i2h));
 }
 
@@ -213,7 +213,8 @@ __device__ __forceinline__ RowIn<T> load_row(const StageArgs2D<T>& A, size_t g) 
     in.s1 = __ldg(A.sb[0] + g);
     in.s2 = __ldg(A.sb[1] + g);
   } else if constexpr (BK == 2) {
-    in.s1 = in.s2 = T(__ldg(A.s_ext + g));
+    // integer conversion (toward zero): GB300 runs double -> float on its FP64 unit
+    in.s1 = in.s2 = to_stencil<T>(__ldg(A.s_ext + g));
   } else {
     in.s1 = in.s2 = T(0);
   }
@@ -307,12 +308,17 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
     td2 = expf(-k.g * p1.s2);
     p1.FH2 = blendw(tc2, p1.FH2, FL2);
     p1.AH2 = blendw(td2, p1.AH2, p1.aU);
-    cur.LV1 = lowres_s<FLUX, T>(m, 0, cur.Y, f1Y, cur.aY, d1Y, cur.V, f1V, cur.aV, d1V, Yp, f1Yp, aYp, d1Yp, half,
-                                k.i2h1, k.i4h21);
-    cur.LX1 = lowres_s<FLUX, T>(m, 0, cur.U, f1U, cur.aU, d1U, cur.X, f1X, cur.aX, d1X, Up, f1Up, aUp, d1Up, half,
-                                k.i2h1, k.i4h21);
-    cur.LY1 = lowres_s<FLUX, T>(m, 0, cur.Vm, f1Vm, cur.aVm, d1Vm, cur.Y, f1Y, cur.aY, d1Y, cur.V, f1V, cur.aV, d1V,
-                                half, k.i2h1, k.i4h21);
+    // x-lines: V between Y_i and Y_{i+1}, X between the averages of cells i and i+1,
+    // Y between V_{i-1} and V_i; F(V_{i-1}, Y_i) is the left lane's F(V, Y_{+1})
+    const T FYV = llf<FLUX, T>(m, 0, cur.Y, cur.V, f1Y, f1V, d1Y, d1V, half);
+    const T FVY = llf<FLUX, T>(m, 0, cur.V, Yp, f1V, f1Yp, d1V, d1Yp, half);
+    const T FUX = llf<FLUX, T>(m, 0, cur.U, cur.X, f1U, f1X, d1U, d1X, half);
+    const T FXU = llf<FLUX, T>(m, 0, cur.X, Up, f1X, f1Up, d1X, d1Up, half);
+    cur.LV1 = lowres_s<T>(FYV, FVY, cur.aY, cur.aV, aYp, k.i2h1, k.i4h21);
+    cur.LX1 = lowres_s<T>(FUX, FXU, cur.aU, cur.aX, aUp, k.i2h1, k.i4h21);
+    cur.LY1 = lowres_s<T>(shup(FVY), FYV, cur.aVm, cur.aY, cur.aV, k.i2h1, k.i4h21);
+    // y-direction flux between V of row r-1 and X of row r (the next step's X-line)
+    cur.FVX = llf<FLUX, T>(m, 1, p1.V, cur.X, p1.fV, cur.fX, p1.dV, cur.dX, half);
   }
 
   // ---- point residuals: x-lines of row r
@@ -340,12 +346,15 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
       // blended residuals: each direction's high-order residual against its low-order one
       // with the weight of the faces / cells the point lies on
       const T tc2p = shdn(tc2), td2p = shdn(td2);
-      const T LV2 = lowres_s<FLUX, T>(m, 1, p1.X, p1.fX, p1.aX, p1.dX, p1.V, p1.fV, p1.aV, p1.dV, cur.X, cur.fX, cur.aX,
-                                      cur.dX, half, k.i2h2, k.i4h22);
-      const T LX2 = lowres_s<FLUX, T>(m, 1, p2.V, p2.fV, p2.aV, p2.dV, p1.X, p1.fX, p1.aX, p1.dX, p1.V, p1.fV, p1.aV,
-                                      p1.dV, half, k.i2h2, k.i4h22);
-      const T LY2 = lowres_s<FLUX, T>(m, 1, p1.U, p1.fU, p1.aU, p1.dU, p1.Y, p1.fY, p1.aY, p1.dY, cur.U, cur.fU, cur.aU,
-                                      cur.dU, half, k.i2h2, k.i4h22);
+      // y-lines of row r-1: V between X_{r-1} and X_r, X between V_{r-2} and V_{r-1}
+      // (F(V_{r-2}, X_{r-1}) formed one step earlier), Y between the averages of rows
+      // r-1 and r
+      const T FXV = llf<FLUX, T>(m, 1, p1.X, p1.V, p1.fX, p1.fV, p1.dX, p1.dV, half);
+      const T FUY = llf<FLUX, T>(m, 1, p1.U, p1.Y, p1.fU, p1.fY, p1.dU, p1.dY, half);
+      const T FYU = llf<FLUX, T>(m, 1, p1.Y, cur.U, p1.fY, cur.fU, p1.dY, cur.dU, half);
+      const T LV2 = lowres_s<T>(FXV, cur.FVX, p1.aX, p1.aV, cur.aX, k.i2h2, k.i4h22);
+      const T LX2 = lowres_s<T>(p1.FVX, FXV, p2.aV, p1.aX, p1.aV, k.i2h2, k.i4h22);
+      const T LY2 = lowres_s<T>(FUY, FYU, p1.aU, p1.aY, cur.aU, k.i2h2, k.i4h22);
       p1.rV = blendw(tmin(p1.tc1, tc1), p1.rV, p1.LV1) + blendw(tmin(tc2, tc2p), rV2, LV2);
       p1.rX = blendw(p1.tc1, p1.rX, p1.LX1) + blendw(tmin(td2, td2p), rX2, LX2);
       p1.rY = blendw(tmin(p1.td1, td1), p1.rY, p1.LY1) + blendw(tc2, rY2, LY2);
