@@ -151,8 +151,14 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     prec = args.precision
-    spec = ai.config2(args.n)
+    bl = args.workload == "buckley_leverett_plain_blend"
+    if bl and prec != "fp32_mixed":
+        raise SystemExit("the Buckley-Leverett blend workload is timed in fp32_mixed only")
+    spec = ai.config5(args.n) if bl else ai.config2(args.n)
     st = [a.cpu().numpy() for a in ai.initial_state(spec, device="cuda")]
+    wname = (f"buckley_leverett2d_{args.n}x{args.n}_{prec}_ssprk3_mpp_plain_blend" if bl else
+             f"degenerate_burgers2d_{args.n}x{args.n}_{prec}_ssprk3_mpp")
+    tkey = ("bl_blend" if bl else "") + prec
     stream = torch.cuda.Stream()
     solver = Solver(spec, precision=prec, rk=3)
     solver.set_stream(stream)
@@ -226,7 +232,7 @@ def run_gpu(args):
         if prec == "fp64":
             ach = fpc * cells / avg_stage_s / 1e12
             roof = {"bound": "alu", "achieved": round(ach, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get((prec, args.n)),
+                    "frac": round(ach / FP64_PEAK_TFLOPS, 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get((tkey, args.n)),
                     "peak_source": "derived (GB300 FP64 non-tensor nominal)",
                     "flops_per_cell_stage": round(fpc, 1),
                     "hbm_view": {"achieved_gbs": round(BYTES_PER_CELL_STAGE[prec] * cells / avg_stage_s / 1e9, 1),
@@ -235,9 +241,9 @@ def run_gpu(args):
         else:
             ach = BYTES_PER_CELL_STAGE[prec] * cells / avg_stage_s / 1e9
             roof = {"bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get((prec, args.n)),
+                    "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": NCU_TRAFFIC_PER_LAUNCH.get((tkey, args.n)),
                     "peak_source": peak_src}
-            ipc = NCU_INSTR_PER_CELL_STAGE.get((prec, args.n))
+            ipc = NCU_INSTR_PER_CELL_STAGE.get((tkey, args.n))
             if ipc:
                 # what actually bounds this form: instruction issue (one warp instruction
                 # per clock per SM sub-partition at the sampled maximum SM clock)
@@ -253,14 +259,16 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == "fp64" else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": f"degenerate_burgers2d_{args.n}x{args.n}_{prec}_ssprk3_mpp",
+            "config": {"workload": wname,
                        "cells": cells, "stages_per_step": nst, "precision": prec,
                        "l2": "flushed between timed steps (256 MiB write)", "parallelism": f"replicas{world}"},
             "roofline": roof,
             "kernels": {"stage_ms_avg": round(statistics.mean(stage_ms), 5), "dt_reduce_ms_avg": round(statistics.mean(dt_ms), 5)},
             "e2e": {"value": round(e2e_value, 1), "unit": UNIT, "h2d_bytes_per_step": bytes_in,
                     "d2h_bytes_per_step": bytes_in},
-            "gpu_launches": (nst + 2) * args.steps,
+            # per step: the CFL rate and its finalisation, one stage launch per stage (and
+            # the plain indicator's pass before each blended stage)
+            "gpu_launches": (nst * (2 if bl else 1) + 2) * args.steps,
             "checks": {"bounds": [lo, hi], "safeguard": stats},
             "clocks": clk.summary(),
             "wall_s": round(wall, 3),
@@ -897,6 +905,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_mixed"])
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--workload", default="degenerate_burgers",
+                    choices=["degenerate_burgers", "buckley_leverett_plain_blend"],
+                    help="the timed workload: config 2 (default) or Buckley-Leverett with the plain blend")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP32/batched/learned forms")
     ap.add_argument("--form-steps", type=int, default=5)

@@ -36,10 +36,17 @@ constexpr int stream_min_blocks() { return FLUX == FLUX_BL || BK != 0 ? 3 : 4; }
 template <class T>
 struct StreamScal {
   T umin, umax, i6h1, i6h2, i3h21, i3h22, m4_1, n4_1, m4_2, n4_2, k1, k2, q1, q2, taut, cAt, cFt, half, sixth, r36;
-  T g, i2h1, i2h2, i4h21, i4h22;   // smoothness blend: gamma; 2/h, 4/h^2 of the low-order residual
   float m1f, m2f, n1f, n2f;
   double cA, cF, umid;
 };
+
+// per-warp constants of the smoothness blend (kept apart from StreamScal: a larger
+// StreamScal cost the kernels without the blend registers); static shared memory of
+// the kernel's translation unit, one slot per warp of a block
+struct BlendScal {
+  float g, i2h1, i2h2, i4h21, i4h22;   // gamma; 2/h and 4/h^2 of the low-order residual
+};
+static __shared__ BlendScal stream_kb[STREAM_WPB];
 
 // values of one input row that later steps read (a row slot)
 template <class T>
@@ -253,10 +260,11 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
   // smoothness blend (Section 5.1.3, direction by direction as in Section 5.2):
   // theta^{d,s}_1 of cell (i, r) and theta^{c,s}_1 of the x-face right of it
   T td1 = T(1), tc1 = T(1);
+  const BlendScal& kb = stream_kb[threadIdx.x >> 5];
   if constexpr (BK != 0) {
     cur.s2 = in.s2;
-    td1 = expf(-k.g * in.s1);
-    tc1 = expf(-k.g * (half * (in.s1 + shdn(in.s1))));
+    td1 = expf(-kb.g * in.s1);
+    tc1 = expf(-kb.g * (half * (in.s1 + shdn(in.s1))));
     cur.td1 = td1;
     cur.tc1 = tc1;
   }
@@ -304,8 +312,8 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
   T tc2 = T(1), td2 = T(1);
   if constexpr (BK != 0) {
     FH1 = blendw(tc1, FH1, FL1);
-    tc2 = expf(-k.g * (half * (p1.s2 + cur.s2)));
-    td2 = expf(-k.g * p1.s2);
+    tc2 = expf(-kb.g * (half * (p1.s2 + cur.s2)));
+    td2 = expf(-kb.g * p1.s2);
     p1.FH2 = blendw(tc2, p1.FH2, FL2);
     p1.AH2 = blendw(td2, p1.AH2, p1.aU);
     // x-lines: V between Y_i and Y_{i+1}, X between the averages of cells i and i+1,
@@ -314,9 +322,9 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
     const T FVY = llf<FLUX, T>(m, 0, cur.V, Yp, f1V, f1Yp, d1V, d1Yp, half);
     const T FUX = llf<FLUX, T>(m, 0, cur.U, cur.X, f1U, f1X, d1U, d1X, half);
     const T FXU = llf<FLUX, T>(m, 0, cur.X, Up, f1X, f1Up, d1X, d1Up, half);
-    cur.LV1 = lowres_s<T>(FYV, FVY, cur.aY, cur.aV, aYp, k.i2h1, k.i4h21);
-    cur.LX1 = lowres_s<T>(FUX, FXU, cur.aU, cur.aX, aUp, k.i2h1, k.i4h21);
-    cur.LY1 = lowres_s<T>(shup(FVY), FYV, cur.aVm, cur.aY, cur.aV, k.i2h1, k.i4h21);
+    cur.LV1 = lowres_s<T>(FYV, FVY, cur.aY, cur.aV, aYp, kb.i2h1, kb.i4h21);
+    cur.LX1 = lowres_s<T>(FUX, FXU, cur.aU, cur.aX, aUp, kb.i2h1, kb.i4h21);
+    cur.LY1 = lowres_s<T>(shup(FVY), FYV, cur.aVm, cur.aY, cur.aV, kb.i2h1, kb.i4h21);
     // y-direction flux between V of row r-1 and X of row r (the next step's X-line)
     cur.FVX = llf<FLUX, T>(m, 1, p1.V, cur.X, p1.fV, cur.fX, p1.dV, cur.dX, half);
   }
@@ -352,9 +360,9 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
       const T FXV = llf<FLUX, T>(m, 1, p1.X, p1.V, p1.fX, p1.fV, p1.dX, p1.dV, half);
       const T FUY = llf<FLUX, T>(m, 1, p1.U, p1.Y, p1.fU, p1.fY, p1.dU, p1.dY, half);
       const T FYU = llf<FLUX, T>(m, 1, p1.Y, cur.U, p1.fY, cur.fU, p1.dY, cur.dU, half);
-      const T LV2 = lowres_s<T>(FXV, cur.FVX, p1.aX, p1.aV, cur.aX, k.i2h2, k.i4h22);
-      const T LX2 = lowres_s<T>(p1.FVX, FXV, p2.aV, p1.aX, p1.aV, k.i2h2, k.i4h22);
-      const T LY2 = lowres_s<T>(FUY, FYU, p1.aU, p1.aY, cur.aU, k.i2h2, k.i4h22);
+      const T LV2 = lowres_s<T>(FXV, cur.FVX, p1.aX, p1.aV, cur.aX, kb.i2h2, kb.i4h22);
+      const T LX2 = lowres_s<T>(p1.FVX, FXV, p2.aV, p1.aX, p1.aV, kb.i2h2, kb.i4h22);
+      const T LY2 = lowres_s<T>(FUY, FYU, p1.aU, p1.aY, cur.aU, kb.i2h2, kb.i4h22);
       p1.rV = blendw(tmin(p1.tc1, tc1), p1.rV, p1.LV1) + blendw(tmin(tc2, tc2p), rV2, LV2);
       p1.rX = blendw(p1.tc1, p1.rX, p1.LX1) + blendw(tmin(td2, td2p), rX2, LX2);
       p1.rY = blendw(tmin(p1.td1, td1), p1.rY, p1.LY1) + blendw(tc2, rY2, LY2);
@@ -516,11 +524,15 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, BK>()
     k.sixth = T(1.0 / 6.0);
     k.r36 = T(1.0 / 36.0);
     k.umid = 0.5 * (m.umin + m.umax);
-    k.g = T(A.gamma);
-    k.i2h1 = T(2.0 * A.inv_h1);
-    k.i2h2 = T(2.0 * A.inv_h2);
-    k.i4h21 = T(4.0 * A.inv_h1 * A.inv_h1);
-    k.i4h22 = T(4.0 * A.inv_h2 * A.inv_h2);
+    if constexpr (BK != 0) {
+      BlendScal b;
+      b.g = float(A.gamma);
+      b.i2h1 = float(2.0 * A.inv_h1);
+      b.i2h2 = float(2.0 * A.inv_h2);
+      b.i4h21 = float(4.0 * A.inv_h1 * A.inv_h1);
+      b.i4h22 = float(4.0 * A.inv_h2 * A.inv_h2);
+      stream_kb[wib] = b;
+    }
     skw[wib] = k;
   }
   __syncwarp();

@@ -26,8 +26,10 @@ __global__ void __launch_bounds__(256) blend_s_kernel(const double* __restrict__
     su[by][bx] = to_stencil_nb<float>(ub[(size_t)gj * nx + gi], umid);
   }
   __syncthreads();
+  // the quotient with the fast approximate division (2 ulp): the indicator only sets
+  // the blend weights, and the IEEE division cost this pass most of its time
   auto stl = [](float a, float b, float c) {
-    return fabsf(a - 2.0f * b + c) / (fabsf(a) + 2.0f * fabsf(b) + fabsf(c) + 1e-13f);
+    return __fdividef(fabsf(a - 2.0f * b + c), fabsf(a) + 2.0f * fabsf(b) + fabsf(c) + 1e-13f);
   };
   for (int q = threadIdx.x; q < BS_TY * (BS_TX + 2); q += blockDim.x) {
     const int x = q % (BS_TX + 2), y = q / (BS_TX + 2);
