@@ -537,3 +537,92 @@ def test_barenblatt_error_decreases():
         errs.append(np.sum(np.abs(out[0] - ex)) * spec.dx * spec.dy)
         assert oracle.bounds(out)[0] >= 0.0
     assert errs[1] < 0.5 * errs[0]
+
+
+# ----------------------------------------------------------------------------------
+# 10. the blend's low-order residual and its weights (readings 6 and 7), pinned by the
+# cases where they reduce to textbook schemes: with theta = 0 (an external indicator so
+# large that exp(-gamma s) underflows) every face flux, cell potential and point
+# residual is the low-order one, which for a linear flux c > 0 and a = k0 u is first-
+# order upwinding plus the central second difference -- on the mesh for the cell
+# averages and on the half-spaced points for the point values; with one indicator
+# value everywhere every weight equals exp(-gamma s), so the evaluation is the convex
+# combination of the unblended (s = 0) and the low-order (s huge) evaluations.
+
+def _rng_state_1d(n, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(0.2, 0.8, n), rng.uniform(0.2, 0.8, n)]
+
+
+@pytest.mark.parametrize("c,k0", [(1.0, 0.0), (0.7, 0.05), (-0.9, 0.02)])
+def test_low_order_blend_is_upwind_1d(c, k0):
+    n, L = 24, 1.3
+    spec = ai.Spec(dim=1, nx=n, x0=0.0, x1=L, flux=("linear", (c, 0.0)), diff=("const", (k0,)), umin=-10.0,
+                   umax=10.0, limiter=False, blend="external", gamma=1.0)
+    ub, P = _rng_state_1d(n, 5)
+    h, tau = L / n, 1e-3
+    got = oracle.fe(spec, [ub, P], tau, s_ext=np.full(n, 1e3))
+    # textbook first-order upwind flux c u_upwind; P_j sits between ub_j and ub_{j+1}
+    ubm, ubp = np.roll(ub, 1), np.roll(ub, -1)
+    up = lambda left, right: c * (left if c > 0 else right)
+    want_ub = ub - tau / h * (up(ub, ubp) - up(ubm, ub)) + tau * k0 / h ** 2 * (ubp - 2 * ub + ubm)
+    hh = h / 2   # spacing of the point's low-order stencil (its neighbouring averages)
+    want_P = P - tau / hh * (up(P, ubp) - up(ub, P)) + tau * k0 / hh ** 2 * (ubp - 2 * P + ub)
+    np.testing.assert_allclose(got[0], want_ub, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(got[1], want_P, rtol=0, atol=1e-13)
+
+
+def test_low_order_blend_is_upwind_2d():
+    nx, ny, Lx, Ly = 12, 10, 1.2, 0.8
+    c1, c2, k0 = 0.8, -0.6, 0.03
+    spec = ai.Spec(dim=2, nx=nx, ny=ny, x0=0, x1=Lx, y0=0, y1=Ly, flux=("linear", (c1, c2)), diff=("const", (k0,)),
+                   umin=-10.0, umax=10.0, limiter=False, blend="external", gamma=1.0)
+    rng = np.random.default_rng(9)
+    ub, V, X, Y = (rng.uniform(0.2, 0.8, (ny, nx)) for _ in range(4))
+    hx, hy, tau = Lx / nx, Ly / ny, 1e-3
+    got = oracle.fe(spec, [ub, V, X, Y], tau, s_ext=np.full((ny, nx), 1e3))
+    sh = lambda a, di, dj: np.roll(np.roll(a, -dj, axis=0), -di, axis=1)   # a[j + dj, i + di]
+
+    def upd(left, mid, right, c, h):
+        # -(F(mid, right) - F(left, mid)) / h with the upwind flux, + k0 (right - 2 mid + left) / h^2
+        f = lambda a, b: c * (a if c > 0 else b)
+        return -(f(mid, right) - f(left, mid)) / h + k0 * (right - 2 * mid + left) / h ** 2
+
+    want_ub = ub + tau * (upd(sh(ub, -1, 0), ub, sh(ub, 1, 0), c1, hx) + upd(sh(ub, 0, -1), ub, sh(ub, 0, 1), c2, hy))
+    # V_ij (corner x_{i+1/2}, y_{j+1/2}): along x between Y_ij and Y_{i+1,j}, along y between
+    # X_ij and X_{i,j+1}; X_ij (x_{i+1/2}, y_j): along x between the averages of cells i
+    # and i+1, along y between V_{i,j-1} and V_ij; Y_ij (x_i, y_{j+1/2}): along x between
+    # V_{i-1,j} and V_ij, along y between the averages of rows j and j+1
+    want_V = V + tau * (upd(Y, V, sh(Y, 1, 0), c1, hx / 2) + upd(X, V, sh(X, 0, 1), c2, hy / 2))
+    want_X = X + tau * (upd(ub, X, sh(ub, 1, 0), c1, hx / 2) + upd(sh(V, 0, -1), X, V, c2, hy / 2))
+    want_Y = Y + tau * (upd(sh(V, -1, 0), Y, V, c1, hx / 2) + upd(ub, Y, sh(ub, 0, 1), c2, hy / 2))
+    for g, w in zip(got, [want_ub, want_V, want_X, want_Y]):
+        np.testing.assert_allclose(g, w, rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_constant_indicator_blend_is_convex_combination(dim):
+    if dim == 1:
+        spec = ai.Spec(dim=1, nx=20, x0=0, x1=1.0, flux=("burgers", (0.5,)), diff=("cubic", (0.01, 0.02, 0.0)),
+                       umin=-10.0, umax=10.0, limiter=False, blend="external", gamma=2.0)
+        st = _rng_state_1d(20, 3)
+        shape = (20,)
+    else:
+        spec = ai.Spec(dim=2, nx=11, ny=9, x0=0, x1=1.1, y0=0, y1=0.9, flux=("bl", (5.0,)),
+                       diff=("cubic", (0.01, 0.02, 0.0)), umin=-10.0, umax=10.0, limiter=False, blend="external",
+                       gamma=2.0)
+        rng = np.random.default_rng(4)
+        st = [rng.uniform(0.2, 0.8, (9, 11)) for _ in range(4)]
+        shape = (9, 11)
+    tau, s = 1e-3, 0.37
+    hi = oracle.fe(spec, st, tau, s_ext=np.zeros(shape))
+    lo = oracle.fe(spec, st, tau, s_ext=np.full(shape, 1e3))
+    mid = oracle.fe(spec, st, tau, s_ext=np.full(shape, s))
+    w = math.exp(-spec.gamma * s)
+    for m_, h_, l_ in zip(mid, hi, lo):
+        np.testing.assert_allclose(m_, w * h_ + (1 - w) * l_, rtol=0, atol=1e-13)
+    # and s = 0 is the method without the blend, bit for bit
+    spec_off = ai.Spec(**{**spec.__dict__, "blend": "off"})
+    off = oracle.fe(spec_off, st, tau)
+    for a, b in zip(hi, off):
+        np.testing.assert_array_equal(a, b)
