@@ -111,6 +111,9 @@ struct af_batch {
   int n = 0, flux = 0, prec = AF_PREC_FP64, rk = AF_RK_SSP3, nbuf = 3, limiter = 1, blend = 0;
   double cfl = 0.165, cfl_diff = 0.0, gamma = 1.0;
   int tx = 32, ty = 8, total_tiles = 0;
+  // FP32-mixed without the blend: column-marching items (strips of stream_S rows)
+  int stream_S = 32, total_items = 0, diff_uniform = -1, pme_e = 0;
+  int* d_items = nullptr;
   long long cells = 0;
   std::vector<BatchInst> h_inst;
   std::vector<af_grid> grids;
@@ -176,6 +179,9 @@ cudaError_t launch_stage_bshape(af_batch* b, const BatchStage& S) {
 }
 template <int FLUX, class T, class PT>
 cudaError_t launch_stage_shape(af_batch* b, const BatchStage& S) {
+  if (sizeof(T) == 4 && !b->blend)
+    return af::batch_launch_stream(b->flux, b->diff_uniform, b->pme_e, b->d_inst, b->d_items, b->total_items, S,
+                                   b->d_stats, b->stream_S, b->stream);
   if (b->blend)
     return af::batch_launch_blend(b->prec, b->flux, b->tx, b->ty, b->d_inst, b->d_work, b->total_tiles, S,
                                   b->d_stats, b->stream);
@@ -280,6 +286,20 @@ af_status build_work(af_batch* b) {
     for (int t = 0; t < I.tiles_x * tiles_y; ++t) work.push_back(k);
   }
   b->total_tiles = (int)work.size();
+  // column-marching items of every instance (FP32-mixed without the blend)
+  std::vector<int> items;
+  for (int k = 0; k < b->n; ++k) {
+    BatchInst& I = b->h_inst[k];
+    I.bands = (I.nx + af::BATCH_STREAM_BAND - 1) / af::BATCH_STREAM_BAND;
+    const int strips = (I.ny + b->stream_S - 1) / b->stream_S;
+    I.item_begin = (int)items.size();
+    for (int t = 0; t < I.bands * strips; ++t) items.push_back(k);
+  }
+  b->total_items = (int)items.size();
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  BCK(b, cudaMalloc(&b->d_items, items.size() * sizeof(int)));
+  BCK(b, cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int), cudaMemcpyHostToDevice));
   if (b->d_work) cudaFree(b->d_work);
   b->d_work = nullptr;
   BCK(b, cudaMalloc(&b->d_work, work.size() * sizeof(int)));
@@ -396,6 +416,11 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
       I.py[s] = p; p += al(c * ps);
     }
   }
+  // the diffusion kind every instance shares (compiled into the column-marching stage)
+  b->diff_uniform = b->h_inst[0].m.diff_kind;
+  b->pme_e = b->h_inst[0].m.pme_e;
+  for (int k = 1; k < n; ++k)
+    if (b->h_inst[k].m.diff_kind != b->diff_uniform || b->h_inst[k].m.pme_e != b->pme_e) b->diff_uniform = -1;
   bool ok = cudaMalloc(&b->d_inst, n * sizeof(BatchInst)) == cudaSuccess &&
             cudaMalloc(&b->d_rate, 2 * n * sizeof(unsigned long long)) == cudaSuccess &&
             cudaMalloc(&b->d_dt, n * sizeof(double)) == cudaSuccess &&
@@ -437,6 +462,7 @@ af_status af_batch_destroy(af_batch* b) {
   cudaFree(b->block);
   cudaFree(b->d_inst);
   cudaFree(b->d_work);
+  cudaFree(b->d_items);
   cudaFree(b->d_rate);
   cudaFree(b->d_dt);
   cudaFree(b->d_t);

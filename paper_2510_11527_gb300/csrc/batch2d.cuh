@@ -9,11 +9,14 @@
 
 namespace af {
 
+constexpr int BATCH_STREAM_BAND = 28;   // output columns per warp of the column-marching kernel
+
 struct BatchInst {
   DevModel m;
   int nx, ny;
   double inv_h1, inv_h2, inv_hmin2, kmax, tol;
   int tile_begin, tiles_x;       // first work item of this instance, tiles along x
+  int item_begin, bands;         // column-marching items: first item, bands of 28 columns
   double* ub[4];
   void* pv[4];
   void* px[4];
@@ -108,5 +111,11 @@ __global__ void __launch_bounds__(256, 6) batch_stage_kernel_f32occ6(const Batch
 // of `blocks` CTAs (0: the occupancy limit times the SM count) for tile shape tx x ty.
 cudaError_t batch_launch_blend(int prec, int flux, int tx, int ty, const BatchInst* inst, const int* work, int total,
                                const BatchStage& S, DevStats* stats, cudaStream_t stream);
+
+// The FP32-mixed stage without the blend on the column-marching kernel
+// (batch2d_stream.cu): `total` (instance, band, strip) items of strips of S rows; diff
+// the diffusion kind all instances share (pme_e its PME exponent), -1 if they differ.
+cudaError_t batch_launch_stream(int flux, int diff, int pme_e, const BatchInst* inst, const int* items, int total,
+                                const BatchStage& St, DevStats* stats, int S, cudaStream_t s);
 
 }  // namespace af

@@ -472,16 +472,15 @@ __device__ __forceinline__ void stream_step(const StreamCtx<FLUX, DIFF, T>& c, i
   }
 }
 
-// One launch: one output of the stage (the launcher calls it once per output).
-template <int FLUX, int DIFF, int BK = 0>
-__global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, BK>())
-    stream2d_kernel(const DevModel m, const StageArgs2D<float> A, int S, int bands) {
+// One warp's march over its band and strip of rows (all 32 lanes; the single-mesh
+// kernel and the batch kernel call it).
+template <int FLUX, int DIFF, int BK>
+__device__ __forceinline__ void stream_run(const DevModel& m, const StageArgs2D<float>& A, int S, int band,
+                                           int strip) {
   using T = float;
   const double dtv = *A.dt;
-  if (is_zero_bits(dtv)) return;   // uniform over the grid
+  if (is_zero_bits(dtv)) return;   // uniform over the mesh
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int w = blockIdx.x * STREAM_WPB + wib;
-  const int band = w % bands, strip = w / bands;
   const int nx = A.nx, ny = A.ny;
   const int rs = strip * S;
   if (rs >= ny) return;   // whole warp
@@ -621,6 +620,15 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, BK>()
       }
     }
   }
+}
+
+// One launch: one output of the stage (the launcher calls it once per output); warp w
+// takes band w % bands and strip w / bands.
+template <int FLUX, int DIFF, int BK = 0>
+__global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, BK>())
+    stream2d_kernel(const DevModel m, const StageArgs2D<float> A, int S, int bands) {
+  const int w = blockIdx.x * STREAM_WPB + (threadIdx.x >> 5);
+  stream_run<FLUX, DIFF, BK>(m, A, S, w % bands, w / bands);
 }
 
 // ---- launch (host)
