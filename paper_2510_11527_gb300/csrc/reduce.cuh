@@ -93,15 +93,31 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
   unsigned flags = 0u;
   const double kd1 = kmax * inv_h1 * inv_h1, kd2 = kmax * inv_h2 * inv_h2;
   const bool rect = dim == 2 && bc != AF_BC_PERIODIC;
+  // The cell's rate max_l |f_l'(u)| / h_l + kappa_max / h_l^2 (1D: the gravity form,
+  // whose extrema tables sit in slot 0), in FP64 and as an FP32 estimate (within a few
+  // ulps). The FP64 one costs a division on GB300's slow FP64 unit, so it is formed only
+  // for the cells whose estimate is within 2^-12 of the block's largest estimate: the
+  // cell with the largest FP64 rate is always among them, so the maximum is the same.
+  auto rate64 = [&](double u) {
+    const BLVals<double> r = bl_eval<double>(m, u);
+    double b = r.d[dim == 1 ? 1 : 0] * inv_h1 + kd1;
+    if (dim == 2) b = tmax(b, r.d[1] * inv_h2 + kd2);
+    return b;
+  };
+  const float ih1f = (float)inv_h1, ih2f = (float)inv_h2, kd1f = (float)kd1, kd2f = (float)kd2;
+  auto rate32 = [&](double u) {
+    const BLVals<float> r = bl_eval<float>(m, to_stencil<float>(u));
+    float b = r.d[dim == 1 ? 1 : 0] * ih1f + kd1f;
+    if (dim == 2) b = fmaxf(b, r.d[1] * ih2f + kd2f);
+    return b;
+  };
+  float m32 = 0.0f;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     const int i = (int)(k % nx), j = (int)(k / nx);
     if (rect && (i == 0 || j == 0)) continue;
     const double u = ub[k];
-    double a1, a2;
     if constexpr (FLUX == FLUX_BL) {
-      const BLVals<double> r = bl_eval<double>(m, u);
-      a1 = r.d[dim == 1 ? 1 : 0];   // 1D: the gravity form (its extrema tables sit in slot 0)
-      a2 = r.d[1];
+      m32 = fmaxf(m32, rate32(u));
       double un = ub[(size_t)j * nx + (i + 1 == nx ? 0 : i + 1)];
       if (dim == 1 && bc != AF_BC_PERIODIC && i + 1 == nx) un = bc == AF_BC_DIRICHLET ? gr : u;
       if (rect && i + 1 == nx) un = u;
@@ -112,11 +128,33 @@ __global__ void __launch_bounds__(RED_THREADS) dt_rate_kernel(const DevModel m, 
         flags |= crit_flags<FLUX>(m, 1, u, ut) << 8;
       }
     } else {
-      a1 = alpha_interval<FLUX, double>(m, 0, u, u);
-      a2 = alpha_interval<FLUX, double>(m, 1, u, u);
+      best = tmax(best, alpha_interval<FLUX, double>(m, 0, u, u) * inv_h1 + kd1);
+      if (dim == 2) best = tmax(best, alpha_interval<FLUX, double>(m, 1, u, u) * inv_h2 + kd2);
     }
-    best = tmax(best, a1 * inv_h1 + kd1);
-    if (dim == 2) best = tmax(best, a2 * inv_h2 + kd2);
+  }
+  if constexpr (FLUX == FLUX_BL) {
+    __shared__ float s32[RED_THREADS / 32];
+    for (int o = 16; o > 0; o >>= 1) m32 = fmaxf(m32, __shfl_xor_sync(0xffffffffu, m32, o));
+    if ((threadIdx.x & 31) == 0) s32[threadIdx.x >> 5] = m32;
+    __syncthreads();
+    for (int w = 0; w < RED_THREADS / 32; ++w) m32 = fmaxf(m32, s32[w]);
+    const float thr = m32 - m32 * (1.0f / 4096.0f);
+    unsigned long long last = ~0ull;   // bits of the last u evaluated in FP64 (NaN: none)
+    double lastr = 0.0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+      if (rect) {
+        const int i = (int)(k % nx), j = (int)(k / nx);
+        if (i == 0 || j == 0) continue;
+      }
+      const double u = ub[k];
+      if (rate32(u) < thr) continue;
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(u);
+      if (bits != last) {
+        lastr = rate64(u);
+        last = bits;
+      }
+      best = tmax(best, lastr);
+    }
   }
   if (dim == 1 && bc == AF_BC_DIRICHLET && blockIdx.x == 0 && threadIdx.x == 0) {
     const double gv[2] = {gl, gr};
