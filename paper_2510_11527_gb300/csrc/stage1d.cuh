@@ -97,13 +97,13 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
     aU[b] = apot<T>(m, u);
     const T p = sP[b];
     fP[b] = flux<FLUX, T>(m, XD, p);
-    dP[b] = dflux_abs<FLUX, T>(m, XD, p);
+    if constexpr (FLUX != FLUX_BURGERS) dP[b] = dflux_abs<FLUX, T>(m, XD, p);
     aP[b] = nodc ? kappa_fn<T>(m, p) : apot<T>(m, p);
     if (b >= 1) {
       const T c = (T(6) * u - sP[b - 1] - p) * T(0.25);
       sC[b] = c;
       fC[b] = flux<FLUX, T>(m, XD, c);
-      dC[b] = dflux_abs<FLUX, T>(m, XD, c);
+      if constexpr (FLUX != FLUX_BURGERS) dC[b] = dflux_abs<FLUX, T>(m, XD, c);
       aC[b] = nodc ? kappa_fn<T>(m, c) : apot<T>(m, c);
     }
     if (blend && !ext && b >= 1 && b < BX - 1) {
@@ -124,7 +124,14 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   T rH[2] = {T(0), T(0)};
   for (int q = 0; q < nq; ++q) {
     const int b = bq[q];
-    const T alpha = tmax(tmax(tmax(dP[b - 1], dC[b]), tmax(dC[b + 1], dP[b + 1])), dP[b]);
+    // max |f'| over the line; for Burgers |2p| max |z| (the same value: rounding is
+    // monotone), which spares two FP64 multiplies per cell
+    T alpha;
+    if constexpr (FLUX == FLUX_BURGERS)
+      alpha = tabs(T(2) * par<T>(m.fp, m.fpf, 0)) *
+              tmax(tmax(tmax(tabs(sP[b - 1]), tabs(sC[b])), tmax(tabs(sC[b + 1]), tabs(sP[b + 1]))), tabs(sP[b]));
+    else
+      alpha = tmax(tmax(tmax(dP[b - 1], dC[b]), tmax(dC[b + 1], dP[b + 1])), dP[b]);
     if (!nodc) {
       rH[q] = line_res<T>(sP[b - 1], sC[b], sP[b], sC[b + 1], sP[b + 1], fP[b - 1], fC[b], fC[b + 1], fP[b + 1],
                           alpha, aP[b - 1], aC[b], aP[b], aC[b + 1], aP[b + 1], i6h, i3h2);
@@ -138,7 +145,8 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   }
   for (int b = H - 2 + tid; b <= H + TX; b += NT) {
     const T ul = sU[b], ur = sU[b + 1];
-    const T fl = T(0.5) * (fU[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, XD, ul, ur) * (ur - ul);
+    // LLF flux (f_l + f_r - alpha (u_r - u_l)) / 2: one multiply-add and one multiply
+    const T fl = T(0.5) * ((fU[b] + fU[b + 1]) - alpha_interval<FLUX, T>(m, XD, ul, ur) * (ur - ul));
     if (!nodc) {
       if (b >= H - 1 && b < H + TX) sFH[b] = fP[b];
       if (b >= H - 1) sAH[b] = (T(8) * aC[b] - aP[b - 1] - aP[b]) * T(1.0 / 6.0);
