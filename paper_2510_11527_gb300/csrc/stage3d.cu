@@ -154,15 +154,20 @@ __global__ void __launch_bounds__(T3) cellq3d_kernel(const DevModel m, const Sta
         const int mm[3] = {o % 3 - 1, (o / 3) % 3 - 1, o / 9 - 1};
         if (mm[l] != 0) continue;
         const T w = wtrans<T>(o, l);
-        fs = fs + w * flux<FLUX, T>(m, l, zb[o + st]);
+        // without a flux (pure diffusion) its terms are exact zeros: not formed
+        if constexpr (FLUX != FLUX_ZERO) fs = fs + w * flux<FLUX, T>(m, l, zb[o + st]);
         const T ahat = (-ab[o - st] + T(8) * ab[o] - ab[o + st]) * T(1.0 / 6.0);
         as = as + w * ahat;
       }
       A.FH[l][q] = fs * T(1.0 / 36.0);
       A.AH[l][q] = as * T(1.0 / 36.0);
-      const T un = to_stencil<T>(A.ub[nbr3(A, c, l, 1)]);
-      const T al = alpha_interval<FLUX, T>(m, l, u, un);
-      A.FL[l][q] = T(0.5) * (flux<FLUX, T>(m, l, u) + flux<FLUX, T>(m, l, un)) - T(0.5) * al * (un - u);
+      if constexpr (FLUX == FLUX_ZERO) {
+        A.FL[l][q] = T(0);
+      } else {
+        const T un = to_stencil<T>(A.ub[nbr3(A, c, l, 1)]);
+        const T al = alpha_interval<FLUX, T>(m, l, u, un);
+        A.FL[l][q] = T(0.5) * (flux<FLUX, T>(m, l, u) + flux<FLUX, T>(m, l, un)) - T(0.5) * al * (un - u);
+      }
       if (A.blend) {
         T v[5];
         for (int t = 0; t < 5; ++t) v[t] = to_stencil<T>(A.ub[nbr3(A, c, l, t - 2)]);
@@ -287,9 +292,15 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
           dz[t] = dflux_abs<FLUX, T>(m, l, z[t]);
           az[t] = apot<T>(m, z[t]);
         }
-        const T alpha = tmax(tmax(tmax(dz[0], dz[1]), tmax(dz[3], dz[4])), dz[2]);
-        const T rh = line_res<T>(z[0], z[1], z[2], z[3], z[4], fz[0], fz[1], fz[3], fz[4], alpha, az[0], az[1], az[2],
-                                 az[3], az[4], A.i6hT[l], A.i3h2T[l]);
+        T rh;
+        if constexpr (FLUX == FLUX_ZERO) {
+          // the diffusion part of line_res alone (its convection part is an exact zero)
+          rh = (T(16) * (az[1] + az[3]) - (az[0] + az[4]) - T(30) * az[2]) * A.i3h2T[l];
+        } else {
+          const T alpha = tmax(tmax(tmax(dz[0], dz[1]), tmax(dz[3], dz[4])), dz[2]);
+          rh = line_res<T>(z[0], z[1], z[2], z[3], z[4], fz[0], fz[1], fz[3], fz[4], alpha, az[0], az[1], az[2], az[3],
+                           az[4], A.i6hT[l], A.i3h2T[l]);
+        }
         T r = rh;
         if (A.blend) {
           // weight: min of theta^{c,s}_l over the l-faces holding the point (s_l = 1),
