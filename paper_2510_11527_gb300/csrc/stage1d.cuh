@@ -61,6 +61,22 @@ __device__ __forceinline__ T nodc_d2(const T z[5], const T k[5]) {
   return T(4) * ((k[0] * r0 + k[1] * r1) + (k[2] * r2 + (k[3] * r3 + k[4] * r4)));
 }
 
+// double -> exact widening of a stencil value (FP32 on the integer pipe)
+__device__ __forceinline__ double d_of(double v) { return v; }
+__device__ __forceinline__ double d_of(float v) { return f2d_exact(v); }
+
+// The launch's scalars, formed once per CTA by one thread: GB300 runs FP64 arithmetic,
+// FP64 compares and double <-> float conversions on its FP64 unit at 1/64 of the FP32
+// rate, so per-thread copies would cost each cell as much as its own FP64 work.
+template <class T>
+struct Scal1D {
+  T umin, umax, ih, i6h, i3h2, g, i4hh, i2h;
+  double umid;
+  T taut[2], m2[2], n2[2], k6[2], q6[2], cAt[2], cFt[2];
+  double mu[2], nu[2];
+  int comb[2];
+};
+
 template <int FLUX, class T, class PT>
 __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const StageArgs2D<PT> A) {
   using L = Tile1D<FLUX, T>;
@@ -75,11 +91,38 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   __shared__ T sS[BX], sTC[BX], sTD[BX];
 
   const double dtv = *A.dt;
-  if (dtv == 0.0) return;
+  if (is_zero_bits(dtv)) return;   // uniform over the grid
   const int nx = A.nx;
   const int i0 = blockIdx.x * TX;
   const int tid = threadIdx.x;
-  const T umin = T(m.umin), umax = T(m.umax);
+  __shared__ Scal1D<T> sc;
+  if (tid == 0) {
+    sc.umin = T(m.umin);
+    sc.umax = T(m.umax);
+    sc.umid = 0.5 * (m.umin + m.umax);
+    sc.ih = T(A.inv_h1);
+    sc.i6h = T(A.inv_h1 / 6.0);
+    sc.i3h2 = T(A.inv_h1 * A.inv_h1 / 3.0);
+    sc.g = T(A.gamma);
+    sc.i4hh = T(4.0 * A.inv_h1 * A.inv_h1);
+    sc.i2h = T(2.0 * A.inv_h1);
+    for (int o = 0; o < A.nout; ++o) {
+      const double tau = A.tcoef[o] * dtv;
+      const double mu = tau * A.inv_h1, nu = mu * A.inv_h1;
+      sc.mu[o] = mu;
+      sc.nu[o] = nu;
+      sc.taut[o] = T(tau);
+      sc.m2[o] = T(2.0 * mu);
+      sc.n2[o] = T(2.0 * nu);
+      sc.k6[o] = T((A.nodc ? 2.0 : double(2 * m.lim_parts)) * mu);
+      sc.q6[o] = T(6.0 * nu);
+      sc.cAt[o] = T(A.cA[o]);
+      sc.cFt[o] = T(A.cF[o]);
+      sc.comb[o] = !is_zero_bits(A.cA[o]);
+    }
+  }
+  __syncthreads();
+  const T umin = sc.umin, umax = sc.umax;
   const bool blend = A.blend != 0;
   const bool ext = A.blend == 2;
   const bool nodc = A.nodc != 0;
@@ -87,7 +130,8 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   const int poff = bounded ? 1 : 0;   // point u_{j+1/2} is stored at index j + poff
 
   for (int k = tid; k < BX; k += NT) {
-    sU[k] = T(cell1d(A, i0 - H + k, H));
+    // rounded toward the nearer bound, as the 2D stages round the averages (integer ops)
+    sU[k] = to_stencil_nb<T>(cell1d(A, i0 - H + k, H), sc.umid);
     sP[k] = T(point1d(A, i0 - H + k, H));
   }
   __syncthreads();
@@ -112,8 +156,7 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
     }
   }
   __syncthreads();
-  const T ih = T(A.inv_h1);
-  const T i6h = T(A.inv_h1 / 6.0), i3h2 = T(A.inv_h1 * A.inv_h1 / 3.0);
+  const T ih = sc.ih, i6h = sc.i6h, i3h2 = sc.i3h2;
   // points updated by this thread: its own u_{i+1/2} and, in CTA 0 of a bounded
   // interval, thread 0 also the left end point u_{-1/2} (held at the boundary value
   // when the end is Dirichlet)
@@ -166,7 +209,7 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   __syncthreads();
   T rP[2] = {rH[0], rH[1]};
   if (blend) {
-    const T g = T(A.gamma);
+    const T g = sc.g;
     for (int b = H - 1 + tid; b <= H + TX; b += NT) {
       sTD[b] = exp(-g * sS[b]);
       if (b < H + TX) sTC[b] = exp(-g * (T(0.5) * (sS[b] + sS[b + 1])));
@@ -181,7 +224,7 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
       const T zm = sU[b], z0 = sP[b], zp = sU[b + 1];
       const T Fr = T(0.5) * (fP[b] + fU[b + 1]) - T(0.5) * alpha_interval<FLUX, T>(m, XD, z0, zp) * (zp - z0);
       const T Fl = T(0.5) * (fU[b] + fP[b]) - T(0.5) * alpha_interval<FLUX, T>(m, XD, zm, z0) * (z0 - zm);
-      const T RL = (aU[b + 1] - T(2) * aP[b] + aU[b]) * (T(4) * ih * ih) - (Fr - Fl) * (T(2) * ih);
+      const T RL = (aU[b + 1] - T(2) * aP[b] + aU[b]) * sc.i4hh - (Fr - Fl) * sc.i2h;
       rP[q] = sTC[b] * rH[q] + (T(1) - sTC[b]) * RL;
     }
     __syncthreads();
@@ -191,10 +234,9 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   T* Flim = A.limiter ? sFlim : sFH;
   T* Alim = A.limiter ? sAlim : sAH;
   for (int o = 0; o < A.nout; ++o) {
-    const double tau = A.tcoef[o] * dtv;
-    const double mu = tau * A.inv_h1, nu = mu * A.inv_h1;
+    const double mu = sc.mu[o], nu = sc.nu[o];
     if (A.limiter) {
-      const T m2 = T(2.0 * mu), n2 = T(2.0 * nu);
+      const T m2 = sc.m2[o], n2 = sc.n2[o];
       for (int b = H - 2 + tid; b <= H + TX + 1; b += NT) {
         const T u = sU[b], f = fU[b], a = aU[b];
         if (!nodc) {
@@ -210,7 +252,7 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
       // face factor 2 * parts (6 with diffusion, 2 without); the total face flux of the
       // form without double conservation takes factor 2 (the average is the mean of
       // u^{L,+} and u^{L,-}, one face correction each)
-      const T k6 = T((nodc ? 2.0 : double(2 * m.lim_parts)) * mu), q6 = T(6.0 * nu);
+      const T k6 = sc.k6[o], q6 = sc.q6[o];
       for (int b = H - 1 + tid; b <= H + TX; b += NT) {
         if (b < H + TX) {
           const T fh = sFH[b], fl = sFL[b], dF = fh - fl;
@@ -232,10 +274,9 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
     if (own) {
       const int b = H + tid;
       const size_t g = (size_t)gi;
-      double ubfe = A.ub[g] - mu * ((double)Flim[b] - (double)Flim[b - 1]);
-      if (!nodc) ubfe += nu * (((double)Alim[b + 1] - 2.0 * (double)Alim[b]) + (double)Alim[b - 1]);
-      const double cA = A.cA[o], cF = A.cF[o];
-      double ubo = cA != 0.0 ? rk_comb(cA, A.Aub[o][g], cF, ubfe) : rk_scale(cF, ubfe);
+      double ubfe = A.ub[g] - mu * (d_of(Flim[b]) - d_of(Flim[b - 1]));
+      if (!nodc) ubfe += nu * ((d_of(Alim[b + 1]) - 2.0 * d_of(Alim[b])) + d_of(Alim[b - 1]));
+      double ubo = sc.comb[o] ? rk_comb(A.cA[o], A.Aub[o][g], A.cF[o], ubfe) : rk_scale(A.cF[o], ubfe);
       if (A.limiter && A.sg[o]) ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
       A.Oub[o][g] = ubo;
     }
@@ -247,11 +288,10 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
       if (A.bc == AF_BC_DIRICHLET && (gj == -1 || gj == nx - 1)) {
         po = PT(gj == -1 ? A.bc_left : A.bc_right);
       } else {
-        T p = sP[bq[q]] + T(tau) * rP[q];
+        T p = sP[bq[q]] + sc.taut[o] * rP[q];
         if (A.limiter) p = tmin(tmax(p, umin), umax);
-        const double cA = A.cA[o], cF = A.cF[o];
-        po = cA != 0.0 ? PT(rk_comb(T(cA), T(A.AV[o][g]), T(cF), p)) : PT(rk_scale(T(cF), p));
-        if (A.limiter && A.sg[o]) po = safeguard<PT>(po, PT(m.umin), PT(m.umax), A.tol, A.stats);
+        po = sc.comb[o] ? PT(rk_comb(sc.cAt[o], T(A.AV[o][g]), sc.cFt[o], p)) : PT(rk_scale(sc.cFt[o], p));
+        if (A.limiter && A.sg[o]) po = safeguard<PT>(po, PT(umin), PT(umax), A.tol, A.stats);
       }
       A.OV[o][g] = po;
     }
