@@ -36,22 +36,39 @@ __global__ void __launch_bounds__(256) batch_rate_kernel(const BatchInst* __rest
     const int i = (t % I.tiles_x) * TX + (int)threadIdx.x % TX, j = (t / I.tiles_x) * TY + (int)threadIdx.x / TX;
     double best = 0.0;
     unsigned flags = 0u;
+    if constexpr (FLUX != FLUX_BL) {
+      // |f_l'| nondecreasing in |u| (Burgers) or constant: the tile's rate is the rate at
+      // its largest |u|, a maximum of magnitude bits (integer units), formed once per
+      // tile below -- per cell it would cost GB300's slow FP64 unit several operations
+      unsigned long long mb = 0ull;
+      if (i < I.nx && j < I.ny)
+        mb = (unsigned long long)__double_as_longlong(I.ub[in][(size_t)j * I.nx + i]) & 0x7FFFFFFFFFFFFFFFull;
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = v > mb ? v : mb;
+      }
+      __shared__ unsigned long long smb[8];
+      if ((threadIdx.x & 31) == 0) smb[threadIdx.x >> 5] = mb;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int q = 1; q < 8; ++q) mb = smb[q] > mb ? smb[q] : mb;
+        const double u = __longlong_as_double((long long)mb);
+        const double kd1 = I.kmax * I.inv_h1 * I.inv_h1, kd2 = I.kmax * I.inv_h2 * I.inv_h2;
+        const double b = tmax(alpha_interval<FLUX, double>(I.m, 0, u, u) * I.inv_h1 + kd1,
+                              alpha_interval<FLUX, double>(I.m, 1, u, u) * I.inv_h2 + kd2);
+        atomicMax(rate_bits + 2 * k, (unsigned long long)__double_as_longlong(b));
+      }
+      __syncthreads();
+      continue;
+    }
     if (i < I.nx && j < I.ny) {
       const double* ub = I.ub[in];
       const double u = ub[(size_t)j * I.nx + i];
       const double kd1 = I.kmax * I.inv_h1 * I.inv_h1, kd2 = I.kmax * I.inv_h2 * I.inv_h2;
-      double a1, a2;
-      if constexpr (FLUX == FLUX_BL) {
-        const BLVals<double> r = bl_eval<double>(I.m, u);
-        a1 = r.d[0];
-        a2 = r.d[1];
-        flags = crit_flags<FLUX>(I.m, 0, u, ub[(size_t)j * I.nx + (i + 1 == I.nx ? 0 : i + 1)]) |
-                (crit_flags<FLUX>(I.m, 1, u, ub[(size_t)(j + 1 == I.ny ? 0 : j + 1) * I.nx + i]) << 8);
-      } else {
-        a1 = alpha_interval<FLUX, double>(I.m, 0, u, u);
-        a2 = alpha_interval<FLUX, double>(I.m, 1, u, u);
-      }
-      best = tmax(a1 * I.inv_h1 + kd1, a2 * I.inv_h2 + kd2);
+      const BLVals<double> r = bl_eval<double>(I.m, u);
+      flags = crit_flags<FLUX>(I.m, 0, u, ub[(size_t)j * I.nx + (i + 1 == I.nx ? 0 : i + 1)]) |
+              (crit_flags<FLUX>(I.m, 1, u, ub[(size_t)(j + 1 == I.ny ? 0 : j + 1) * I.nx + i]) << 8);
+      best = tmax(r.d[0] * I.inv_h1 + kd1, r.d[1] * I.inv_h2 + kd2);
     }
     for (int o = 16; o > 0; o >>= 1) best = tmax(best, __shfl_xor_sync(0xffffffffu, best, o));
     flags = __reduce_or_sync(0xffffffffu, flags);
