@@ -21,8 +21,9 @@
 
 namespace af {
 
-// per-tile part of the CFL rate (see dt_rate_kernel) into rate_bits[2 instance] and the
-// interior-extremum flags into rate_bits[2 instance + 1]
+// per-tile part of the CFL rate for the Buckley-Leverett flux (see dt_rate_kernel) into
+// rate_bits[2 instance] and the interior-extremum flags of f_l' into
+// rate_bits[2 instance + 1]; the other fluxes take batch_rate_maxu_kernel
 template <int FLUX, int TX, int TY>
 __global__ void __launch_bounds__(256) batch_rate_kernel(const BatchInst* __restrict__ inst,
                                                          const int* __restrict__ work_inst, int total, int in,
@@ -36,31 +37,6 @@ __global__ void __launch_bounds__(256) batch_rate_kernel(const BatchInst* __rest
     const int i = (t % I.tiles_x) * TX + (int)threadIdx.x % TX, j = (t / I.tiles_x) * TY + (int)threadIdx.x / TX;
     double best = 0.0;
     unsigned flags = 0u;
-    if constexpr (FLUX != FLUX_BL) {
-      // |f_l'| nondecreasing in |u| (Burgers) or constant: the tile's rate is the rate at
-      // its largest |u|, a maximum of magnitude bits (integer units), formed once per
-      // tile below -- per cell it would cost GB300's slow FP64 unit several operations
-      unsigned long long mb = 0ull;
-      if (i < I.nx && j < I.ny)
-        mb = (unsigned long long)__double_as_longlong(I.ub[in][(size_t)j * I.nx + i]) & 0x7FFFFFFFFFFFFFFFull;
-      for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mb, o);
-        mb = v > mb ? v : mb;
-      }
-      __shared__ unsigned long long smb[8];
-      if ((threadIdx.x & 31) == 0) smb[threadIdx.x >> 5] = mb;
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        for (int q = 1; q < 8; ++q) mb = smb[q] > mb ? smb[q] : mb;
-        const double u = __longlong_as_double((long long)mb);
-        const double kd1 = I.kmax * I.inv_h1 * I.inv_h1, kd2 = I.kmax * I.inv_h2 * I.inv_h2;
-        const double b = tmax(alpha_interval<FLUX, double>(I.m, 0, u, u) * I.inv_h1 + kd1,
-                              alpha_interval<FLUX, double>(I.m, 1, u, u) * I.inv_h2 + kd2);
-        atomicMax(rate_bits + 2 * k, (unsigned long long)__double_as_longlong(b));
-      }
-      __syncthreads();
-      continue;
-    }
     if (i < I.nx && j < I.ny) {
       const double* ub = I.ub[in];
       const double u = ub[(size_t)j * I.nx + i];
@@ -88,6 +64,44 @@ __global__ void __launch_bounds__(256) batch_rate_kernel(const BatchInst* __rest
       if (f) atomicOr(rate_bits + 2 * k + 1, (unsigned long long)f);
     }
     __syncthreads();
+  }
+}
+
+// The same for a flux whose |f_l'| is nondecreasing in |u| (Burgers) or constant: the
+// tile's rate is the rate at its largest |u|, a maximum of magnitude bits (integer
+// units; per cell the rate would cost GB300's slow FP64 unit several operations). One
+// warp per tile, no block-wide synchronisation.
+template <int FLUX, int TX, int TY>
+__global__ void __launch_bounds__(256) batch_rate_maxu_kernel(const BatchInst* __restrict__ inst,
+                                                              const int* __restrict__ work_inst, int total, int in,
+                                                              unsigned long long* rate_bits) {
+  const int lane = threadIdx.x & 31;
+  for (int w = blockIdx.x * 8 + (threadIdx.x >> 5); w < total; w += gridDim.x * 8) {
+    const int k = work_inst[w];
+    const BatchInst& I = inst[k];
+    const int t = w - I.tile_begin;
+    const int i0 = (t % I.tiles_x) * TX, j0 = (t / I.tiles_x) * TY;
+    const double* ub = I.ub[in];
+    unsigned long long mb = 0ull;
+    for (int c = lane; c < TX * TY; c += 32) {
+      const int i = i0 + c % TX, j = j0 + c / TX;
+      if (i < I.nx && j < I.ny) {
+        const unsigned long long v =
+            (unsigned long long)__double_as_longlong(ub[(size_t)j * I.nx + i]) & 0x7FFFFFFFFFFFFFFFull;
+        mb = v > mb ? v : mb;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, mb, o);
+      mb = v > mb ? v : mb;
+    }
+    if (lane == 0) {
+      const double u = __longlong_as_double((long long)mb);
+      const double kd1 = I.kmax * I.inv_h1 * I.inv_h1, kd2 = I.kmax * I.inv_h2 * I.inv_h2;
+      const double b = tmax(alpha_interval<FLUX, double>(I.m, 0, u, u) * I.inv_h1 + kd1,
+                            alpha_interval<FLUX, double>(I.m, 1, u, u) * I.inv_h2 + kd2);
+      atomicMax(rate_bits + 2 * k, (unsigned long long)__double_as_longlong(b));
+    }
   }
 }
 
@@ -221,9 +235,15 @@ cudaError_t launch_stage(af_batch* b, const BatchStage& S) {
 
 template <int FLUX, int TX, int TY>
 cudaError_t launch_rate_t(af_batch* b) {
-  const int grid = std::min(b->total_tiles, 152 * 8);
-  af::batch_rate_kernel<FLUX, TX, TY><<<grid, 256, 0, b->stream>>>(b->d_inst, b->d_work, b->total_tiles, 0,
-                                                                   b->d_rate);
+  if constexpr (FLUX == af::FLUX_BL) {
+    const int grid = std::min(b->total_tiles, 152 * 8);
+    af::batch_rate_kernel<FLUX, TX, TY><<<grid, 256, 0, b->stream>>>(b->d_inst, b->d_work, b->total_tiles, 0,
+                                                                     b->d_rate);
+  } else {
+    const int grid = std::min((b->total_tiles + 7) / 8, 152 * 8);
+    af::batch_rate_maxu_kernel<FLUX, TX, TY><<<grid, 256, 0, b->stream>>>(b->d_inst, b->d_work, b->total_tiles, 0,
+                                                                          b->d_rate);
+  }
   return cudaGetLastError();
 }
 
