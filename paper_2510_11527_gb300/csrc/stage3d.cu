@@ -347,15 +347,146 @@ __global__ void __launch_bounds__(T3) update3d_kernel(const DevModel m, const St
   }
 }
 
+// K4 with the point values staged: one CTA per tile of U3X x U3Y x U3Z cells loads the
+// centres and the 7 point kinds of the tile and a one-cell halo into shared memory
+// once, with a(z) evaluated once per location; every 5-point line of the tile's points
+// then reads there (a line of a point owned by cell c spans the cells c - 1 .. c + 1
+// along its axis). Values, order of operations and results are those of the gathered
+// form; the blend's extra neighbours (averages, smoothness values) are still read
+// from global memory.
+constexpr int U3X = 8, U3Y = 4, U3Z = 4, U3T = U3X * U3Y * U3Z;
+constexpr int B3X = U3X + 2, B3Y = U3Y + 2, B3Z = U3Z + 2, B3N = B3X * B3Y * B3Z;
+
+template <int FLUX, class T>
+__global__ void __launch_bounds__(U3T) update3d_tile_kernel(const DevModel m, const StageArgs3D<T> A, int o) {
+  const double dtv = *A.dt;
+  if (is_zero_bits(dtv)) return;   // uniform over the grid
+  __shared__ double sMu[3], sNu[3];
+  __shared__ T sZ[8][B3N], sAz[8][B3N];
+  if (threadIdx.x < 3) {
+    const int l = threadIdx.x;
+    const double tau = A.tcoef[o] * dtv;
+    sMu[l] = tau * A.inv_h[l];
+    sNu[l] = sMu[l] * A.inv_h[l];
+  }
+  const int n0 = A.n[0], n1 = A.n[1], n2 = A.n[2];
+  const int tiles_x = (n0 + U3X - 1) / U3X, tiles_y = (n1 + U3Y - 1) / U3Y;
+  const int tb = blockIdx.x;
+  const int c0x = (tb % tiles_x) * U3X, c0y = ((tb / tiles_x) % tiles_y) * U3Y, c0z = (tb / (tiles_x * tiles_y)) * U3Z;
+  for (int k = threadIdx.x; k < 8 * B3N; k += U3T) {
+    const int sk = k / B3N, b = k - sk * B3N;
+    const int bx = b % B3X, by = (b / B3X) % B3Y, bz = b / (B3X * B3Y);
+    const size_t q = ((size_t)wrapi(c0z - 1 + bz, n2) * n1 + wrapi(c0y - 1 + by, n1)) * n0 + wrapi(c0x - 1 + bx, n0);
+    const T z = sk == 0 ? A.C[q] : A.pt[sk][q];
+    sZ[sk][b] = z;
+    sAz[sk][b] = apot<T>(m, z);
+  }
+  __syncthreads();
+  const int lx = threadIdx.x % U3X, ly = (threadIdx.x / U3X) % U3Y, lz = threadIdx.x / (U3X * U3Y);
+  const int c[3] = {c0x + lx, c0y + ly, c0z + lz};
+  if (c[0] >= n0 || c[1] >= n1 || c[2] >= n2) return;   // after the only barrier
+  const size_t q = ((size_t)c[2] * n1 + c[1]) * n0 + c[0];
+  const double cA = A.cA[o], cF = A.cF[o];
+  const T taut = T(A.tcoef[o] * dtv), cAt = T(cA), cFt = T(cF), umin = T(m.umin), umax = T(m.umax),
+          g = T(A.gamma);
+  // an integer test: GB300 runs FP64 compares on its slow FP64 unit
+  const bool comb = !is_zero_bits(cA);
+  // limited cell-average update (eq. multid_limited_average), in FP64
+  double v = A.ub[q];
+  for (int l = 0; l < 3; ++l) {
+    const double mu = sMu[l], nu = sNu[l];
+    const size_t qm = nbr3(A, c, l, -1), qp = nbr3(A, c, l, 1);
+    const double f0 = wide(A.Flim[l][q]), fm = wide(A.Flim[l][qm]);
+    const double a0 = wide(A.Alim[l][q]), am = wide(A.Alim[l][qm]), ap = wide(A.Alim[l][qp]);
+    v = v - mu * (f0 - fm) + nu * (ap - 2.0 * a0 + am);
+  }
+  double ubo = comb ? rk_comb(cA, A.Aub[o][q], cF, v) : rk_scale(cF, v);
+  if (A.limiter && A.sg[o]) ubo = safeguard<double>(ubo, m.umin, m.umax, A.tol, A.stats, true);
+  A.Oub[o][q] = ubo;
+  // point values owned by the cell: kinds 1..7 at fine 2c + s (scalar indices only, so
+  // that nothing indexed by the loop variables lands in local memory)
+  for (int s = 1; s < 8; ++s) {
+    const int px = s & 1, py = (s >> 1) & 1, pz = (s >> 2) & 1;   // offsets from 2c
+    T acc = T(0);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const T ih = A.inv_hT[l];
+      const int pl = l == 0 ? px : (l == 1 ? py : pz);
+      T z[5], fz[5], dz[5], az[5];
+#pragma unroll
+      for (int t = 0; t < 5; ++t) {
+        // fine offset F = p_l + t - 2 along l: cell offset floor(F / 2), kind bit F & 1
+        const int F = pl + t - 2, dc = F >> 1, kbit = F & 1;
+        const int b = (lx + 1 + (l == 0 ? dc : 0)) + B3X * ((ly + 1 + (l == 1 ? dc : 0)) + B3Y * (lz + 1 + (l == 2 ? dc : 0)));
+        const int kind = (l == 0 ? kbit : px) | ((l == 1 ? kbit : py) << 1) | ((l == 2 ? kbit : pz) << 2);
+        z[t] = sZ[kind][b];
+        fz[t] = flux<FLUX, T>(m, l, z[t]);
+        dz[t] = dflux_abs<FLUX, T>(m, l, z[t]);
+        az[t] = sAz[kind][b];
+      }
+      T rh;
+      if constexpr (FLUX == FLUX_ZERO) {
+        // the diffusion part of line_res alone (its convection part is an exact zero)
+        rh = (T(16) * (az[1] + az[3]) - (az[0] + az[4]) - T(30) * az[2]) * A.i3h2T[l];
+      } else {
+        const T alpha = tmax(tmax(tmax(dz[0], dz[1]), tmax(dz[3], dz[4])), dz[2]);
+        rh = line_res<T>(z[0], z[1], z[2], z[3], z[4], fz[0], fz[1], fz[3], fz[4], alpha, az[0], az[1], az[2], az[3],
+                         az[4], A.i6hT[l], A.i3h2T[l]);
+      }
+      T r = rh;
+      if (A.blend) {
+        const FineAxes fa = fine_axes(A, c);
+        // weight: min of theta^{c,s}_l over the l-faces holding the point (s_l = 1),
+        // else of theta^{d,s}_l over the cells holding it
+        const bool onface = (s >> l) & 1;
+        T w = T(2);
+        for (int bits = 0; bits < 8; ++bits) {
+          int cc[3] = {c[0], c[1], c[2]};
+          bool ok = true;
+          for (int t = 0; t < 3; ++t) {
+            if (!((bits >> t) & 1)) continue;
+            if (t == l || !((s >> t) & 1)) { ok = false; break; }
+            cc[t] = cc[t] + 1 == A.n[t] ? 0 : cc[t] + 1;   // periodic, so nbr3 below sees wrapped coordinates
+          }
+          if (!ok) continue;
+          const size_t qq = cell3(A, cc);
+          const T sv = A.S[l][qq];
+          const T wv = onface ? exp(-g * (T(0.5) * (sv + A.S[l][nbr3(A, cc, l, 1)]))) : exp(-g * sv);
+          w = (w == T(2)) ? wv : tmin(w, wv);
+        }
+        // low-order residual on the +-h/2 neighbours (a centre replaced by its average)
+        int fm[3] = {px, py, pz}, fp[3] = {px, py, pz};
+        fm[l] -= 1;
+        fp[l] += 1;
+        const T zm = zoff(A, fa, fm[0], fm[1], fm[2], true), z0 = z[2], zp = zoff(A, fa, fp[0], fp[1], fp[2], true);
+        const T Fr = T(0.5) * (flux<FLUX, T>(m, l, z0) + flux<FLUX, T>(m, l, zp)) -
+                     T(0.5) * alpha_interval<FLUX, T>(m, l, z0, zp) * (zp - z0);
+        const T Fl = T(0.5) * (flux<FLUX, T>(m, l, zm) + flux<FLUX, T>(m, l, z0)) -
+                     T(0.5) * alpha_interval<FLUX, T>(m, l, zm, z0) * (z0 - zm);
+        const T RL = (apot<T>(m, zp) - T(2) * apot<T>(m, z0) + apot<T>(m, zm)) * (T(4) * ih * ih) - (Fr - Fl) * (T(2) * ih);
+        r = w * rh + (T(1) - w) * RL;
+      }
+      acc = (l == 0) ? r : acc + r;
+    }
+    T pv = A.pt[s][q] + taut * acc;
+    if (A.limiter) pv = tmin(tmax(pv, umin), umax);
+    T po = comb ? rk_comb(cAt, A.Apt[o][s][q], cFt, pv) : rk_scale(cFt, pv);
+    if (A.limiter && A.sg[o]) po = safeguard<T>(po, umin, umax, A.tol, A.stats);
+    A.Opt[o][s][q] = po;
+  }
+}
+
 template <int FLUX, class T>
 cudaError_t run3d(const DevModel& m, const StageArgs3D<T>& a, cudaStream_t s) {
   const size_t N = (size_t)a.n[0] * a.n[1] * a.n[2];
   const int grid = (int)std::min<size_t>((N + T3 - 1) / T3, 152 * 16);
+  const long long tiles = (long long)((a.n[0] + U3X - 1) / U3X) * ((a.n[1] + U3Y - 1) / U3Y) * ((a.n[2] + U3Z - 1) / U3Z);
+  if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
   centre3d_kernel<T><<<grid, T3, 0, s>>>(a);
   cellq3d_kernel<FLUX, T><<<grid, T3, 0, s>>>(m, a);
   for (int o = 0; o < a.nout; ++o) {
     limit3d_kernel<FLUX, T><<<grid, T3, 0, s>>>(m, a, o);
-    update3d_kernel<FLUX, T><<<grid, T3, 0, s>>>(m, a, o);
+    update3d_tile_kernel<FLUX, T><<<(unsigned)tiles, U3T, 0, s>>>(m, a, o);
   }
   return cudaGetLastError();
 }
