@@ -15,6 +15,7 @@ struct BatchInst {
   DevModel m;
   int nx, ny;
   double inv_h1, inv_h2, inv_hmin2, kmax, tol;
+  float i6hf[2], i3h2f[2];       // 1/(6 h_l), 1/(3 h_l^2) in FP32 (column-marching stage)
   int tile_begin, tiles_x;       // first work item of this instance, tiles along x
   int item_begin, bands;         // column-marching items: first item, bands of 28 columns
   double* ub[4];

@@ -41,6 +41,10 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, 0>())
         A.ny = I.ny;
         A.inv_h1 = I.inv_h1;
         A.inv_h2 = I.inv_h2;
+        A.i6hf[0] = I.i6hf[0];
+        A.i6hf[1] = I.i6hf[1];
+        A.i3h2f[0] = I.i3h2f[0];
+        A.i3h2f[1] = I.i3h2f[1];
         A.ub = I.ub[St.in];
         A.V = (const float*)I.pv[St.in];
         A.X = (const float*)I.px[St.in];

@@ -82,6 +82,10 @@ StageArgs2D<PT> base_args(af_ctx* c, int in) {
   a.ny = c->pny;
   a.inv_h1 = c->inv_h1;
   a.inv_h2 = c->inv_h2;
+  a.i6hf[0] = (float)(c->inv_h1 / 6.0);
+  a.i6hf[1] = (float)(c->inv_h2 / 6.0);
+  a.i3h2f[0] = (float)(c->inv_h1 * c->inv_h1 / 3.0);
+  a.i3h2f[1] = (float)(c->inv_h2 * c->inv_h2 / 3.0);
   a.ub = c->ub[in];
   a.V = (const PT*)c->pv[in];
   a.X = (const PT*)c->px[in];

@@ -36,6 +36,8 @@ template <class PT>
 struct StageArgs2D {
   int nx, ny;
   double inv_h1, inv_h2;             // 1/dx, 1/dy
+  float i6hf[2], i3h2f[2];           // 1/(6 h_l), 1/(3 h_l^2) in FP32, formed on the host
+                                     // (the column-marching FP32 stage's line scales)
   const double* ub;                  // FE input (read with halo)
   const PT* V;
   const PT* X;

@@ -486,53 +486,74 @@ __device__ __forceinline__ void stream_run(const DevModel& m, const StageArgs2D<
   if (rs >= ny) return;   // whole warp
   const int re = min(rs + S, ny);
   const int giu = band * STREAM_BAND - 2 + lane;
-  // the launch's scalars, formed once per warp in FP64 and rounded: kept in shared
-  // memory, so that a value the compiler does not keep in a register is reloaded (one
-  // shared load) rather than formed again on GB300's slow FP64 unit; one slot per warp,
-  // so no warp waits for another
+  // the launch's scalars, kept in shared memory (one slot per warp, so that no warp
+  // waits for another): a value the compiler does not keep in a register is reloaded
+  // rather than formed again on GB300's slow FP64 unit. The FP64 unit takes as long
+  // for a warp instruction with one active lane as with 32, so the lanes form one
+  // scalar each at once: lane l rounds fl(fl(fl(x y1) y2) y3) to FP32, the products in
+  // the order of tau = tcoef dt, mu_l = tau / h_l, nu_l = mu_l / h_l and their scaled
+  // copies (a factor 1 is exact, so every value is rounded as its own formula is).
+  // The divided line scales come from the host (StageArgs2D::i6hf, i3h2f).
   __shared__ StreamScal<T> skw[STREAM_WPB];
-  if (lane == 0) {
-    StreamScal<T> k;
+  {
     const double tau = A.tcoef[0] * dtv;
-    const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
-    const double nu1 = mu1 * A.inv_h1, nu2 = mu2 * A.inv_h2;
-    k.umin = T(m.umin);
-    k.umax = T(m.umax);
-    k.i6h1 = T(A.inv_h1 / 6.0);
-    k.i6h2 = T(A.inv_h2 / 6.0);
-    k.i3h21 = T(A.inv_h1 * A.inv_h1 / 3.0);
-    k.i3h22 = T(A.inv_h2 * A.inv_h2 / 3.0);
-    k.m4_1 = T(4.0 * mu1);
-    k.n4_1 = T(4.0 * nu1);
-    k.m4_2 = T(4.0 * mu2);
-    k.n4_2 = T(4.0 * nu2);
-    k.k1 = T(double(4 * m.lim_parts) * mu1);
-    k.k2 = T(double(4 * m.lim_parts) * mu2);
-    k.q1 = T(12.0 * nu1);
-    k.q2 = T(12.0 * nu2);
-    k.taut = T(tau);
+    const int q = lane & 1;   // direction of lanes 0 .. 11 and 18 .. 21
+    const double ih = q ? A.inv_h2 : A.inv_h1;
+    double x = tau, y1 = ih, y2 = 1.0, y3 = 1.0;
+    if (lane < 12) {
+      const int kind = lane >> 1;   // 4 mu, 4 nu, 4 P mu, 12 nu, mu, nu
+      y2 = (kind == 1 || kind == 3 || kind == 5) ? ih : (kind == 2 ? double(4 * m.lim_parts) : (kind == 0 ? 4.0 : 1.0));
+      y3 = kind == 1 ? 4.0 : (kind == 3 ? 12.0 : 1.0);
+    } else if (lane < 18) {
+      // tau, u_min, u_max, cA, cF, gamma
+      x = lane == 12 ? tau
+                     : (lane == 13 ? m.umin : (lane == 14 ? m.umax : (lane == 15 ? A.cA[0] : (lane == 16 ? A.cF[0] : A.gamma))));
+      y1 = 1.0;
+    } else {
+      // 2 / h_l and (4 / h_l) / h_l of the blend's low-order residual
+      x = lane < 20 ? 2.0 : 4.0;
+      y2 = lane < 20 ? 1.0 : ih;
+    }
+    const float v = (float)(((x * y1) * y2) * y3);
+    auto at = [&](int l) { return __shfl_sync(0xffffffffu, v, l); };
+    StreamScal<T> k;
+    k.m4_1 = at(0);
+    k.m4_2 = at(1);
+    k.n4_1 = at(2);
+    k.n4_2 = at(3);
+    k.k1 = at(4);
+    k.k2 = at(5);
+    k.q1 = at(6);
+    k.q2 = at(7);
+    k.m1f = at(8);
+    k.m2f = at(9);
+    k.n1f = at(10);
+    k.n2f = at(11);
+    k.taut = at(12);
+    k.umin = at(13);
+    k.umax = at(14);
+    k.cAt = at(15);
+    k.cFt = at(16);
+    k.i6h1 = A.i6hf[0];
+    k.i6h2 = A.i6hf[1];
+    k.i3h21 = A.i3h2f[0];
+    k.i3h22 = A.i3h2f[1];
     k.cA = A.cA[0];
     k.cF = A.cF[0];
-    k.cAt = T(A.cA[0]);
-    k.cFt = T(A.cF[0]);
-    k.m1f = (float)mu1;
-    k.m2f = (float)mu2;
-    k.n1f = (float)nu1;
-    k.n2f = (float)nu2;
     k.half = T(0.5);
     k.sixth = T(1.0 / 6.0);
     k.r36 = T(1.0 / 36.0);
     k.umid = 0.5 * (m.umin + m.umax);
     if constexpr (BK != 0) {
       BlendScal b;
-      b.g = float(A.gamma);
-      b.i2h1 = float(2.0 * A.inv_h1);
-      b.i2h2 = float(2.0 * A.inv_h2);
-      b.i4h21 = float(4.0 * A.inv_h1 * A.inv_h1);
-      b.i4h22 = float(4.0 * A.inv_h2 * A.inv_h2);
-      stream_kb[wib] = b;
+      b.g = at(17);
+      b.i2h1 = at(18);
+      b.i2h2 = at(19);
+      b.i4h21 = at(20);
+      b.i4h22 = at(21);
+      if (lane == 0) stream_kb[wib] = b;
     }
-    skw[wib] = k;
+    if (lane == 0) skw[wib] = k;
   }
   __syncwarp();
   const StreamScal<T>& k = skw[wib];
