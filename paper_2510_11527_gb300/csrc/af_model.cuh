@@ -24,6 +24,7 @@ struct DevModel {
   double crit[2][8];
   double critv[2][8];    // |f_l'| at those extrema
   double umin, umax;
+  double umid;           // (umin + umax) / 2: direction of the averages' FP32 conversion
   // the same parameters rounded to float, read by the FP32 stencils (GB300's FP64
   // unit also performs the double->float conversions, so none happen per use)
   float fpf[4], dpf[4], critf[2][8], critvf[2][8];
@@ -41,6 +42,7 @@ template <> __device__ __forceinline__ double par<double>(const double* d, const
 template <> __device__ __forceinline__ float par<float>(const double*, const float* f, int k) { return f[k]; }
 
 inline void fill_float_params(DevModel& m) {
+  m.umid = 0.5 * (m.umin + m.umax);
   for (int k = 0; k < 4; ++k) {
     m.fpf[k] = (float)m.fp[k];
     m.dpf[k] = (float)m.dp[k];

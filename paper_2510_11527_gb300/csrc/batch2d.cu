@@ -437,10 +437,14 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     I.inv_h1 = 1.0 / dx;
     I.inv_h2 = 1.0 / dy;
     I.inv_hmin2 = 1.0 / (std::min(dx, dy) * std::min(dx, dy));
-    I.i6hf[0] = (float)(I.inv_h1 / 6.0);
-    I.i6hf[1] = (float)(I.inv_h2 / 6.0);
-    I.i3h2f[0] = (float)(I.inv_h1 * I.inv_h1 / 3.0);
-    I.i3h2f[1] = (float)(I.inv_h2 * I.inv_h2 / 3.0);
+    I.i6h[0] = I.inv_h1 / 6.0;
+    I.i6h[1] = I.inv_h2 / 6.0;
+    I.i3h2[0] = I.inv_h1 * I.inv_h1 / 3.0;
+    I.i3h2[1] = I.inv_h2 * I.inv_h2 / 3.0;
+    for (int l = 0; l < 2; ++l) {
+      I.i6hf[l] = (float)I.i6h[l];
+      I.i3h2f[l] = (float)I.i3h2[l];
+    }
     I.m.flux_kind = fluxes[k].kind;
     I.m.diff_kind = diffs[k].kind;
     for (int q = 0; q < 4; ++q) { I.m.fp[q] = fluxes[k].p[q]; I.m.dp[q] = diffs[k].p[q]; }

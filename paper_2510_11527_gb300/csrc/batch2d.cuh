@@ -15,7 +15,8 @@ struct BatchInst {
   DevModel m;
   int nx, ny;
   double inv_h1, inv_h2, inv_hmin2, kmax, tol;
-  float i6hf[2], i3h2f[2];       // 1/(6 h_l), 1/(3 h_l^2) in FP32 (column-marching stage)
+  double i6h[2], i3h2[2];        // 1/(6 h_l), (1/h_l^2)/3 (line scales)
+  float i6hf[2], i3h2f[2];       // the same in FP32
   int tile_begin, tiles_x;       // first work item of this instance, tiles along x
   int item_begin, bands;         // column-marching items: first item, bands of 28 columns
   double* ub[4];
@@ -52,6 +53,12 @@ __device__ __forceinline__ void batch_stage_body(const BatchInst* __restrict__ i
     A.ny = I.ny;
     A.inv_h1 = I.inv_h1;
     A.inv_h2 = I.inv_h2;
+    for (int l = 0; l < 2; ++l) {
+      A.i6h[l] = I.i6h[l];
+      A.i3h2[l] = I.i3h2[l];
+      A.i6hf[l] = I.i6hf[l];
+      A.i3h2f[l] = I.i3h2f[l];
+    }
     A.ub = I.ub[S.in];
     A.V = (const PT*)I.pv[S.in];
     A.X = (const PT*)I.px[S.in];

@@ -82,10 +82,14 @@ StageArgs2D<PT> base_args(af_ctx* c, int in) {
   a.ny = c->pny;
   a.inv_h1 = c->inv_h1;
   a.inv_h2 = c->inv_h2;
-  a.i6hf[0] = (float)(c->inv_h1 / 6.0);
-  a.i6hf[1] = (float)(c->inv_h2 / 6.0);
-  a.i3h2f[0] = (float)(c->inv_h1 * c->inv_h1 / 3.0);
-  a.i3h2f[1] = (float)(c->inv_h2 * c->inv_h2 / 3.0);
+  a.i6h[0] = c->inv_h1 / 6.0;
+  a.i6h[1] = c->inv_h2 / 6.0;
+  a.i3h2[0] = c->inv_h1 * c->inv_h1 / 3.0;
+  a.i3h2[1] = c->inv_h2 * c->inv_h2 / 3.0;
+  for (int l = 0; l < 2; ++l) {
+    a.i6hf[l] = (float)a.i6h[l];
+    a.i3h2f[l] = (float)a.i3h2[l];
+  }
   a.ub = c->ub[in];
   a.V = (const PT*)c->pv[in];
   a.X = (const PT*)c->px[in];
@@ -524,6 +528,7 @@ af_status af_set_state(af_ctx* c, const double* ub, const double* V, const doubl
     if (!(hi > lo)) FAIL(c, AF_E_STATE, "bounds from initial data need max > min");
     c->m.umin = lo;
     c->m.umax = hi;
+    c->m.umid = 0.5 * (lo + hi);
     c->kmax = af::kappa_max_of(c->diff, lo, hi);
     const double scale = std::max(std::fabs(lo), std::fabs(hi));
     c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) * scale;
@@ -622,6 +627,7 @@ af_status af_set_state_arrays(af_ctx* c, int narr, const double* const* arrays) 
     if (!(hi > lo)) FAIL(c, AF_E_STATE, "bounds from initial data need max > min");
     c->m.umin = lo;
     c->m.umax = hi;
+    c->m.umid = 0.5 * (lo + hi);
     c->kmax = af::kappa_max_of(c->diff, lo, hi);
     c->tol = (c->prec == AF_PREC_FP64 ? 8.0 * 2.220446049250313e-16 : 64.0 * 1.1920929e-07) *
              std::max(std::fabs(lo), std::fabs(hi));

@@ -71,14 +71,13 @@ __device__ __forceinline__ double d_of(float v) { return f2d_exact(v); }
 template <class T>
 struct Scal1D {
   T umin, umax, ih, i6h, i3h2, g, i4hh, i2h;
-  double umid;
   T taut[2], m2[2], n2[2], k6[2], q6[2], cAt[2], cFt[2];
   double mu[2], nu[2];
   int comb[2];
 };
 
 template <int FLUX, class T, class PT>
-__global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const StageArgs2D<PT> A) {
+__global__ void __launch_bounds__(256, 4) stage1d_kernel(const DevModel m, const StageArgs2D<PT> A) {
   using L = Tile1D<FLUX, T>;
   constexpr int TX = L::TX, NT = L::NT, H = L::H, BX = L::BX;
   // flux direction of the model functions: the 1D Buckley-Leverett flux is the gravity
@@ -96,29 +95,61 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
   const int i0 = blockIdx.x * TX;
   const int tid = threadIdx.x;
   __shared__ Scal1D<T> sc;
-  if (tid == 0) {
-    sc.umin = T(m.umin);
-    sc.umax = T(m.umax);
-    sc.umid = 0.5 * (m.umin + m.umax);
-    sc.ih = T(A.inv_h1);
-    sc.i6h = T(A.inv_h1 / 6.0);
-    sc.i3h2 = T(A.inv_h1 * A.inv_h1 / 3.0);
-    sc.g = T(A.gamma);
-    sc.i4hh = T(4.0 * A.inv_h1 * A.inv_h1);
-    sc.i2h = T(2.0 * A.inv_h1);
-    for (int o = 0; o < A.nout; ++o) {
-      const double tau = A.tcoef[o] * dtv;
-      const double mu = tau * A.inv_h1, nu = mu * A.inv_h1;
-      sc.mu[o] = mu;
-      sc.nu[o] = nu;
-      sc.taut[o] = T(tau);
-      sc.m2[o] = T(2.0 * mu);
-      sc.n2[o] = T(2.0 * nu);
-      sc.k6[o] = T((A.nodc ? 2.0 : double(2 * m.lim_parts)) * mu);
-      sc.q6[o] = T(6.0 * nu);
-      sc.cAt[o] = T(A.cA[o]);
-      sc.cFt[o] = T(A.cF[o]);
-      sc.comb[o] = !is_zero_bits(A.cA[o]);
+  // formed at once by the lanes of warp o (output o) and the upper lanes of warp 0 (the
+  // mesh's values): GB300's FP64 unit takes as long for a warp instruction with one
+  // active lane as with 32. Lane l evaluates fl(fl(fl(x y1) y2) y3) with the factors of
+  // its value's formula (a factor 1 is exact, so each value is rounded as its formula
+  // is; the divided line scales come from the host); only the stores differ between
+  // lanes.
+  if ((tid >> 5) < A.nout) {
+    const int o = tid >> 5, l = tid & 31;
+    const double ih = A.inv_h1, tau = A.tcoef[o] * dtv;
+    double x = tau, y1 = 1.0, y2 = 1.0, y3 = 1.0;
+    if (l < 16) {
+      // 0: tau; 1: mu; 2: nu; 3: 2 mu; 4: 2 nu; 5: (2 or 2 P) mu; 6: 6 nu; 7, 8: cA, cF
+      if (l >= 1 && l <= 6) y1 = ih;
+      if (l == 2 || l == 4 || l == 6) y2 = ih;
+      if (l == 3) y2 = 2.0;
+      if (l == 5) y2 = A.nodc ? 2.0 : double(2 * m.lim_parts);
+      if (l == 4) y3 = 2.0;
+      if (l == 6) y3 = 6.0;
+      if (l == 7) x = A.cA[o];
+      if (l == 8) x = A.cF[o];
+    } else {
+      // 16, 17: u_min, u_max; 18: 1/h; 19: 1/(6h); 20: (1/h/h)/3; 21: gamma; 22: (4/h)/h;
+      // 23: 2/h
+      x = l == 16   ? m.umin
+          : l == 17 ? m.umax
+          : l == 21 ? A.gamma
+          : l == 22 ? 4.0
+          : l == 23 ? 2.0
+          : l == 19 ? A.i6h[0]
+          : l == 20 ? A.i3h2[0]
+                    : ih;
+      y1 = (l == 22 || l == 23) ? ih : 1.0;
+      y2 = l == 22 ? ih : 1.0;
+    }
+    const double d = ((x * y1) * y2) * y3;
+    const T dt = T(d);
+    switch (o == 0 || l < 16 ? l : 31) {
+      case 0: sc.taut[o] = dt; sc.comb[o] = !is_zero_bits(A.cA[o]); break;
+      case 1: sc.mu[o] = d; break;
+      case 2: sc.nu[o] = d; break;
+      case 3: sc.m2[o] = dt; break;
+      case 4: sc.n2[o] = dt; break;
+      case 5: sc.k6[o] = dt; break;
+      case 6: sc.q6[o] = dt; break;
+      case 7: sc.cAt[o] = dt; break;
+      case 8: sc.cFt[o] = dt; break;
+      case 16: sc.umin = dt; break;
+      case 17: sc.umax = dt; break;
+      case 18: sc.ih = dt; break;
+      case 19: sc.i6h = dt; break;
+      case 20: sc.i3h2 = dt; break;
+      case 21: sc.g = dt; break;
+      case 22: sc.i4hh = dt; break;
+      case 23: sc.i2h = dt; break;
+      default: break;
     }
   }
   __syncthreads();
@@ -131,7 +162,7 @@ __global__ void __launch_bounds__(256) stage1d_kernel(const DevModel m, const St
 
   for (int k = tid; k < BX; k += NT) {
     // rounded toward the nearer bound, as the 2D stages round the averages (integer ops)
-    sU[k] = to_stencil_nb<T>(cell1d(A, i0 - H + k, H), sc.umid);
+    sU[k] = to_stencil_nb<T>(cell1d(A, i0 - H + k, H), m.umid);
     sP[k] = T(point1d(A, i0 - H + k, H));
   }
   __syncthreads();

@@ -36,8 +36,8 @@ template <class PT>
 struct StageArgs2D {
   int nx, ny;
   double inv_h1, inv_h2;             // 1/dx, 1/dy
-  float i6hf[2], i3h2f[2];           // 1/(6 h_l), 1/(3 h_l^2) in FP32, formed on the host
-                                     // (the column-marching FP32 stage's line scales)
+  double i6h[2], i3h2[2];            // 1/(6 h_l), (1/h_l^2)/3: line scales, formed on the host
+  float i6hf[2], i3h2f[2];           // the same rounded to FP32
   const double* ub;                  // FE input (read with halo)
   const PT* V;
   const PT* X;
@@ -114,7 +114,6 @@ struct TileScal {
   float mu1f[2], mu2f[2], nu1f[2], nu2f[2];
   T taut[2], m4_1[2], n4_1[2], m4_2[2], n4_2[2], k1[2], k2[2], q1[2], q2[2], cAt[2], cFt[2];
   T umin, umax, i6h1, i6h2, i3h21, i3h22, i2h1, i2h2, i4h21, i4h22, g;
-  double umid;   // midpoint of the bounds (direction of the averages' conversion)
 };
 
 template <int NT, class F>
@@ -214,45 +213,73 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
 
-  // tile-uniform scalars, formed once (in FP64, then rounded) by one thread
+  // tile-uniform scalars, formed once in FP64 and rounded. GB300's FP64 unit takes as
+  // long for a warp instruction with one active lane as with 32, so the lanes of warp o
+  // form output o's values at once and the upper lanes of warp 0 the mesh's: lane l
+  // evaluates fl(fl(fl(x y1) y2) y3) with the factors of its value's formula (a factor 1
+  // is exact, so each value is rounded as its formula is; the divided line scales come
+  // from the host), then only the stores differ between lanes.
   __shared__ TileScal<T> sc;
-  if (tid == 0) {
-    sc.umin = T(m.umin);
-    sc.umax = T(m.umax);
-    sc.umid = 0.5 * (m.umin + m.umax);
-    sc.i6h1 = T(A.inv_h1 / 6.0);
-    sc.i6h2 = T(A.inv_h2 / 6.0);
-    sc.i3h21 = T(A.inv_h1 * A.inv_h1 / 3.0);
-    sc.i3h22 = T(A.inv_h2 * A.inv_h2 / 3.0);
-    sc.i2h1 = T(2.0 * A.inv_h1);
-    sc.i2h2 = T(2.0 * A.inv_h2);
-    sc.i4h21 = T(4.0 * A.inv_h1 * A.inv_h1);
-    sc.i4h22 = T(4.0 * A.inv_h2 * A.inv_h2);
-    sc.g = T(A.gamma);
-    for (int o = 0; o < A.nout; ++o) {
-      const double tau = A.tcoef[o] * dtv;
-      const double mu1 = tau * A.inv_h1, mu2 = tau * A.inv_h2;
-      const double nu1 = mu1 * A.inv_h1, nu2 = mu2 * A.inv_h2;
-      sc.tau[o] = tau;
-      sc.mu1[o] = mu1;
-      sc.mu2[o] = mu2;
-      sc.nu1[o] = nu1;
-      sc.nu2[o] = nu2;
-      sc.mu1f[o] = (float)mu1;
-      sc.mu2f[o] = (float)mu2;
-      sc.nu1f[o] = (float)nu1;
-      sc.nu2f[o] = (float)nu2;
-      sc.taut[o] = T(tau);
-      sc.m4_1[o] = T(4.0 * mu1);
-      sc.n4_1[o] = T(4.0 * nu1);
-      sc.m4_2[o] = T(4.0 * mu2);
-      sc.n4_2[o] = T(4.0 * nu2);
-      sc.k1[o] = T(double(4 * m.lim_parts) * mu1);
-      sc.k2[o] = T(double(4 * m.lim_parts) * mu2);
-      sc.q1[o] = T(12.0 * nu1);
-      sc.q2[o] = T(12.0 * nu2);
-      sc.cAt[o] = T(A.cA[o]);
-      sc.cFt[o] = T(A.cF[o]);
+  if ((tid >> 5) < A.nout) {
+    const int o = tid >> 5, l = tid & 31;
+    const double tau = A.tcoef[o] * dtv;
+    // direction: the second of each pair of lanes 1 .. 14 (odd, even), 18 .. 25 (even, odd)
+    const bool second = l < 16 ? !(l & 1) : (l & 1);
+    const double ih = second ? A.inv_h2 : A.inv_h1;
+    double x = tau, y1 = 1.0, y2 = 1.0, y3 = 1.0;
+    if (l >= 1 && l < 15) {
+      // 1, 2: mu_l; 3, 4: nu_l; 5, 6: 4 mu_l; 7, 8: 4 nu_l; 9, 10: 4 P mu_l; 11, 12: 12 nu_l
+      const int kind = (l - 1) >> 1;
+      y1 = ih;
+      y2 = (kind & 1) ? ih : (kind == 2 ? 4.0 : (kind == 4 ? double(4 * m.lim_parts) : 1.0));
+      y3 = kind == 3 ? 4.0 : (kind == 5 ? 12.0 : 1.0);
+      if (kind == 6) {   // lanes 13, 14: cA, cF of the output
+        x = l == 13 ? A.cA[o] : A.cF[o];
+        y1 = y2 = 1.0;
+      }
+    } else if (l >= 16) {
+      // 16, 17: u_min, u_max; 18, 19: 2 / h_l; 20, 21: (4 / h_l) / h_l; 22, 23: 1 / (6 h_l);
+      // 24, 25: (1 / h_l / h_l) / 3; 26: gamma
+      x = l == 16 ? m.umin : (l == 17 ? m.umax : (l == 26 ? A.gamma : 1.0));
+      if (l >= 18 && l < 26) {
+        const int kind = (l - 18) >> 1;
+        x = kind == 0 ? 2.0 : (kind == 1 ? 4.0 : (kind == 2 ? (second ? A.i6h[1] : A.i6h[0])
+                                                                : (second ? A.i3h2[1] : A.i3h2[0])));
+        y1 = kind < 2 ? ih : 1.0;
+        y2 = kind == 1 ? ih : 1.0;
+      }
+    }
+    const double d = ((x * y1) * y2) * y3;
+    const T dt = T(d);
+    const float df = (float)d;
+    switch (o == 0 || l < 16 ? l : 31) {
+      case 0: sc.tau[o] = d; sc.taut[o] = dt; break;
+      case 1: sc.mu1[o] = d; sc.mu1f[o] = df; break;
+      case 2: sc.mu2[o] = d; sc.mu2f[o] = df; break;
+      case 3: sc.nu1[o] = d; sc.nu1f[o] = df; break;
+      case 4: sc.nu2[o] = d; sc.nu2f[o] = df; break;
+      case 5: sc.m4_1[o] = dt; break;
+      case 6: sc.m4_2[o] = dt; break;
+      case 7: sc.n4_1[o] = dt; break;
+      case 8: sc.n4_2[o] = dt; break;
+      case 9: sc.k1[o] = dt; break;
+      case 10: sc.k2[o] = dt; break;
+      case 11: sc.q1[o] = dt; break;
+      case 12: sc.q2[o] = dt; break;
+      case 13: sc.cAt[o] = dt; break;
+      case 14: sc.cFt[o] = dt; break;
+      case 16: sc.umin = dt; break;
+      case 17: sc.umax = dt; break;
+      case 18: sc.i2h1 = dt; break;
+      case 19: sc.i2h2 = dt; break;
+      case 20: sc.i4h21 = dt; break;
+      case 21: sc.i4h22 = dt; break;
+      case 22: sc.i6h1 = dt; break;
+      case 23: sc.i6h2 = dt; break;
+      case 24: sc.i3h21 = dt; break;
+      case 25: sc.i3h22 = dt; break;
+      case 26: sc.g = dt; break;
+      default: break;
     }
   }
 
@@ -288,8 +315,8 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
       const int k = tid + it * NT;
       if (k < NV) {
         const int b = (k / PW) * BX + 2 * (k % PW);
-        sU[b] = to_stencil_nb<T>(ldU[it].x, sc.umid);
-        sU[b + 1] = to_stencil_nb<T>(ldU[it].y, sc.umid);
+        sU[b] = to_stencil_nb<T>(ldU[it].x, m.umid);
+        sU[b + 1] = to_stencil_nb<T>(ldU[it].y, m.umid);
         sZ[0][b] = T(ldV[it].x);
         sZ[0][b + 1] = T(ldV[it].y);
         sZ[1][b] = T(ldX[it].x);
@@ -329,7 +356,7 @@ __device__ __forceinline__ void stage_tile(const DevModel& m, const StageArgs2D<
     for (int it = 0; it < NP0; ++it) {
       const int k = tid + it * NT;
       if (k < BN) {
-        sU[k] = to_stencil_nb<T>(ldU[it], sc.umid);
+        sU[k] = to_stencil_nb<T>(ldU[it], m.umid);
         sZ[0][k] = T(ldV[it]);
         sZ[1][k] = T(ldX[it]);
         sZ[2][k] = T(ldY[it]);

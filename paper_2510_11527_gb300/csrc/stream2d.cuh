@@ -543,7 +543,7 @@ __device__ __forceinline__ void stream_run(const DevModel& m, const StageArgs2D<
     k.half = T(0.5);
     k.sixth = T(1.0 / 6.0);
     k.r36 = T(1.0 / 36.0);
-    k.umid = 0.5 * (m.umin + m.umax);
+    k.umid = m.umid;
     if constexpr (BK != 0) {
       BlendScal b;
       b.g = at(17);

@@ -79,7 +79,7 @@ cudaError_t launch_stream2d_blend_f32(int flux, int bk, const DevModel& m, const
     if (!a.sb[0] || !a.sb[1]) return cudaErrorInvalidValue;
     const long long tiles = (long long)((a.nx + BS_TX - 1) / BS_TX) * ((a.ny + BS_TY - 1) / BS_TY);
     if (tiles > 0x7FFFFFFFLL) return cudaErrorInvalidConfiguration;
-    blend_s_kernel<<<(unsigned)tiles, 256, 0, s>>>(a.ub, a.nx, a.ny, 0.5 * (m.umin + m.umax),
+    blend_s_kernel<<<(unsigned)tiles, 256, 0, s>>>(a.ub, a.nx, a.ny, m.umid,
                                                    const_cast<float*>(a.sb[0]), const_cast<float*>(a.sb[1]));
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
