@@ -719,9 +719,11 @@ def _form_bounded1d(args, stream, peaks):
     return res
 
 
-def _batch_run(inst, prec, steps):
-    """Build the batch in precision `prec`, autotune its tile, time `steps` graph-replayed
-    steps; returns (cell-stage/s, cells, tile, ms per step, safeguard errors)."""
+def _batch_run(inst, prec, steps, blend=0):
+    """Build the batch in precision `prec` (blend 0 off, 1 plain, 2 learned: a seeded
+    network of random weights -- the cost does not depend on them), autotune its tile,
+    time `steps` graph-replayed steps; returns (cell-stage/s, cells, tile, ms per step,
+    safeguard errors)."""
     import torch
     import af_inputs as ai
     from paper_2510_11527_gb300 import capi
@@ -738,9 +740,14 @@ def _batch_run(inst, prec, steps):
         fl.append(f)
         df.append(d)
         bd.append(capi.af_bounds_t(s_.umin, s_.umax, 0))
-    opts = capi.af_opts(capi.PREC[prec], 3, 0.0, 0.0, 1, 0, 1.0)
+    opts = capi.af_opts(capi.PREC[prec], 3, 0.0, 0.0, 1, blend, 1.0)
     b = capi.af_batch_create(grids, fl, df, bd, opts)
+    net = None
     try:
+        if blend == 2:
+            net = capi.af_mlp_create()
+            capi.af_mlp_set_params(net, ai.mlp_init_params(6))
+            capi.af_batch_set_mlp(b, net)
         cells = 0
         for i, (s_, modes) in enumerate(inst):
             stt = ai.batch_state(s_, modes, device="cuda")
@@ -765,18 +772,26 @@ def _batch_run(inst, prec, steps):
         return cells * 3 * steps / (ms / 1e3), cells, tile, ms / steps, capi.af_batch_stats(b)["errors"]
     finally:
         capi.af_batch_destroy(b)
+        if net is not None:
+            capi.af_mlp_destroy(net)
 
 
 def _form_batch(args, stream, headline_value, peaks):
-    """256 uneven instances (FP32-mixed and FP64), graph replay, autotuned tile."""
+    """256 uneven instances (FP32-mixed and FP64), graph replay, autotuned tile; the
+    FP32-mixed batch also with the plain and the learned blend."""
     import af_inputs as ai
     inst = ai.batch_instances()
     val, cells, tile, ms_step, errors = _batch_run(inst, "fp32_mixed", args.form_steps)
     v64, _, tile64, _, err64 = _batch_run(inst, "fp64", max(1, args.form_steps // 2))
+    vp, _, tp, _, errp = _batch_run(inst, "fp32_mixed", args.form_steps, blend=1)
+    vl, _, tl, _, errl = _batch_run(inst, "fp32_mixed", args.form_steps, blend=2)
     return {"batch_256_fp32_mixed": {
         "value": round(val, 1), "cells": cells, "tile": list(tile), "ms_per_step": round(ms_step, 4),
         "fp64_value": round(v64, 1), "fp64_tile": list(tile64), "speedup_vs_fp64": round(val / v64, 2),
-        "speedup_vs_fp64_single_mesh": round(val / headline_value, 2), "safeguard_errors": errors + err64,
+        "speedup_vs_fp64_single_mesh": round(val / headline_value, 2),
+        "plain_blend_value": round(vp, 1), "plain_blend_tile": list(tp),
+        "learned_blend_value": round(vl, 1), "learned_blend_tile": list(tl),
+        "safeguard_errors": errors + err64 + errp + errl,
         "roofline": _hbm_roof("fp32_mixed", cells, ms_step / 3, peaks)}}
 
 

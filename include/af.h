@@ -226,8 +226,9 @@ af_status af_stats_detail(af_ctx* ctx, long long* avg_clamps);
 /* ---- batches of independent meshes -------------------------------------------------
  * A batch holds n independent periodic 2D meshes (uneven sizes; per-instance flux and
  * diffusion parameters and bounds) that share the flux kind, precision, RK scheme,
- * limiter and CFL options of *opts (blend off, AF_FORM_DC; grids periodic, else
- * AF_E_UNSUPPORTED). One persistent launch per RK
+ * limiter, blend and CFL options of *opts (AF_FORM_DC and periodic grids, else
+ * AF_E_UNSUPPORTED; blend AF_BLEND_EXTERNAL takes its indicator from a network
+ * attached with af_batch_set_mlp). One persistent launch per RK
  * stage walks the (instance, tile) work list with the same tile computation as the
  * single-mesh kernel, so every instance evolves as a single-mesh context with the same
  * options does (bit for bit with SSP-RK3; to a few ulp with SSP-RK(5,4), where the two
@@ -296,6 +297,14 @@ af_status af_mlp_train(af_mlp* net, const float* feat_dev, const float* label_de
 /* attach (or detach with NULL) a network to a 2D context created with
  * blend = AF_BLEND_EXTERNAL: every stage then computes s from its input state first */
 af_status af_set_mlp(af_ctx* ctx, const af_mlp* net);
+/* the same for a batch created with blend = AF_BLEND_EXTERNAL: before every stage one
+ * launch computes s for all instances from their input states (the fused inference of
+ * af_mlp_indicator, tile by tile over the batch), then the blended stage reads it. The
+ * network is used in place (its later parameter updates take effect at the next stage)
+ * and must outlive the batch or be detached first. Waits for the batch's stream.
+ * AF_E_STATE for a batch created with another blend; af_batch_step and
+ * af_batch_autotune return AF_E_STATE while no network is attached. */
+af_status af_batch_set_mlp(af_batch* b, const af_mlp* net);
 
 /* Allocation-free total mass: *mass = cell_area * sum(ub_dev[0..ncells-1]) for a
  * caller-owned device array of cell averages, without any context and without

@@ -139,6 +139,7 @@ def lib():
         "af_mlp_train": [_V, _V, _V, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                          ctypes.c_ulonglong, F],
         "af_set_mlp": [_V, _V],
+        "af_batch_set_mlp": [_V, _V],
     }
     for name, args in msig.items():
         fn = getattr(L, name)
@@ -158,7 +159,7 @@ def exported_symbols():
             "af_batch_device_ptrs", "af_batch_step", "af_batch_sync", "af_batch_time", "af_batch_mass",
             "af_batch_bounds", "af_batch_stats", "af_mlp_create", "af_mlp_destroy", "af_mlp_set_params",
             "af_mlp_get_params", "af_mlp_features", "af_mlp_infer", "af_mlp_indicator", "af_mlp_grad",
-            "af_mlp_train", "af_set_mlp"]
+            "af_mlp_train", "af_set_mlp", "af_batch_set_mlp"]
 
 
 AF_MLP_NPARAM = 1793
@@ -223,6 +224,10 @@ def _bcheck(b, st):
     if st != AF_OK:
         msg = lib().af_batch_last_error(b).decode() if b else ""
         raise AfError(st, msg)
+
+
+def af_batch_set_mlp(b, net):
+    _bcheck(b, lib().af_batch_set_mlp(b, net))
 
 
 def af_batch_create(grids, fluxes, diffs, bounds, opts):

@@ -145,6 +145,11 @@ struct af_batch {
   // FP32-mixed without the blend: column-marching items (strips of stream_S rows)
   int stream_S = 32, total_items = 0, diff_uniform = -1, pme_e = 0;
   int* d_items = nullptr;
+  // the learned indicator (blend 2): the attached network, its 32 x 8 tiles over every
+  // instance and the per-cell indicator arrays of all instances
+  const af_mlp* mlp = nullptr;
+  int ind_total = 0;
+  double* d_s = nullptr;
   long long cells = 0;
   std::vector<BatchInst> h_inst;
   std::vector<af_grid> grids;
@@ -351,7 +356,12 @@ af_status build_work(af_batch* b) {
 
 af_status enqueue_step(af_batch* b) {
   BCK(b, launch_dt(b));
-  for (const auto& s : stages_of(b)) BCK(b, launch_stage(b, s));
+  for (const auto& s : stages_of(b)) {
+    // the learned blend: s of every instance from this stage's input first
+    if (b->blend == 2)
+      BCK(b, af::mlp_indicator_batch_launch(b->mlp, b->d_inst, b->n, b->ind_total, s.in, b->prec, b->stream));
+    BCK(b, launch_stage(b, s));
+  }
   return AF_OK;
 }
 
@@ -384,9 +394,10 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) return AF_E_UNSUPPORTED;
   if (opts->precision != AF_PREC_FP64 && opts->precision != AF_PREC_FP32_MIXED) return AF_E_ARG;
   if (opts->rk != AF_RK_SSP3 && opts->rk != AF_RK_SSP54) return AF_E_ARG;
-  // the plain smoothness blend is supported; the external (learned) indicator is not
-  if (opts->blend == AF_BLEND_EXTERNAL || opts->diffusion_form != AF_FORM_DC) return AF_E_UNSUPPORTED;
-  if (opts->blend != AF_BLEND_OFF && opts->blend != AF_BLEND_PLAIN) return AF_E_ARG;
+  // the plain blend, or the external indicator computed by a network attached with
+  // af_batch_set_mlp (a batch has no per-cell indicator input of its own)
+  if (opts->diffusion_form != AF_FORM_DC) return AF_E_UNSUPPORTED;
+  if (opts->blend != AF_BLEND_OFF && opts->blend != AF_BLEND_PLAIN && opts->blend != AF_BLEND_EXTERNAL) return AF_E_ARG;
   for (int k = 0; k < n; ++k) {
     if (grids[k].dim != 2 || grids[k].nx < 1 || grids[k].ny < 1) return AF_E_ARG;
     if (grids[k].bc != AF_BC_PERIODIC) return AF_E_UNSUPPORTED;
@@ -404,7 +415,7 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
   b->rk = opts->rk;
   b->nbuf = opts->rk == AF_RK_SSP54 ? 4 : 3;
   b->limiter = opts->limiter;
-  b->blend = opts->blend == AF_BLEND_PLAIN;
+  b->blend = opts->blend == AF_BLEND_PLAIN ? 1 : (opts->blend == AF_BLEND_EXTERNAL ? 2 : 0);
   b->gamma = opts->gamma;
   b->cfl = opts->cfl > 0.0 ? opts->cfl : 0.33 / 2;
   b->cfl_diff = opts->cfl_diff > 0.0 ? opts->cfl_diff
@@ -460,6 +471,23 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
       I.px[s] = p; p += al(c * ps);
       I.py[s] = p; p += al(c * ps);
     }
+    I.ind_begin = b->ind_total;
+    b->ind_total += ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
+  }
+  if (b->blend == 2) {
+    size_t stotal = 0;
+    for (int k = 0; k < n; ++k) stotal += al((size_t)grids[k].nx * grids[k].ny * 8);
+    if (cudaMalloc(&b->d_s, stotal) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(b->block);
+      delete b;
+      return AF_E_OOM;
+    }
+    unsigned char* q = (unsigned char*)b->d_s;
+    for (int k = 0; k < n; ++k) {
+      b->h_inst[k].s = (double*)q;
+      q += al((size_t)grids[k].nx * grids[k].ny * 8);
+    }
   }
   // the diffusion kind every instance shares (compiled into the column-marching stage)
   b->diff_uniform = b->h_inst[0].m.diff_kind;
@@ -505,6 +533,7 @@ af_status af_batch_destroy(af_batch* b) {
   if (b->stream) cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   cudaFree(b->block);
+  cudaFree(b->d_s);
   cudaFree(b->d_inst);
   cudaFree(b->d_work);
   cudaFree(b->d_items);
@@ -541,6 +570,18 @@ af_status af_batch_info(const af_batch* b, long long* cells, int* tiles, int* tx
   if (tiles) *tiles = b->total_tiles;
   if (tx) *tx = b->tx;
   if (ty) *ty = b->ty;
+  return AF_OK;
+}
+
+af_status af_batch_set_mlp(af_batch* b, const af_mlp* net) {
+  if (!b) return AF_E_ARG;
+  if (b->blend != 2) BFAIL(b, AF_E_STATE, "af_batch_set_mlp needs a batch created with blend = AF_BLEND_EXTERNAL");
+  cudaStreamSynchronize(b->stream);   // no step in flight uses the previous network
+  b->mlp = net;
+  if (b->graph) {   // the captured step holds the previous network's buffers
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
   return AF_OK;
 }
 
@@ -617,6 +658,7 @@ af_status af_batch_device_ptrs(af_batch* b, int i, void* ptrs[4], int dtype[2]) 
 
 af_status af_batch_step(af_batch* b, int nsteps) {
   if (!b || nsteps < 0) return AF_E_ARG;
+  if (b->blend == 2 && !b->mlp) BFAIL(b, AF_E_STATE, "blend with the external indicator needs af_batch_set_mlp");
   if (!b->graph) {
     cudaGraph_t g = nullptr;
     BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -693,6 +735,7 @@ af_status af_batch_stats(af_batch* b, long long* clamps, long long* errors, doub
 // and keep the fastest. The state is saved and restored around the trials.
 af_status af_batch_autotune(af_batch* b, int* tx, int* ty) {
   if (!b) return AF_E_ARG;
+  if (b->blend == 2 && !b->mlp) BFAIL(b, AF_E_STATE, "blend with the external indicator needs af_batch_set_mlp");
   BCK(b, cudaStreamSynchronize(b->stream));
   // snapshot U0 and the clocks so the trials leave no trace
   size_t bytes0 = 0;

@@ -19,6 +19,8 @@ struct BatchInst {
   float i6hf[2], i3h2f[2];       // the same in FP32
   int tile_begin, tiles_x;       // first work item of this instance, tiles along x
   int item_begin, bands;         // column-marching items: first item, bands of 28 columns
+  int ind_begin;                 // first 32 x 8 tile of the learned indicator's launch
+  double* s;                     // learned indicator per cell (blend with the network)
   double* ub[4];
   void* pv[4];
   void* px[4];
@@ -32,7 +34,8 @@ struct BatchStage {              // uniform over the batch for one launch
   int out[2], aidx[2], sg[2];
   double cA[2], cF[2], tcoef[2];
   int limiter;
-  int blend;                     // smoothness-indicator blend (Section 5.1.3), plain
+  int blend;                     // smoothness-indicator blend (Section 5.1.3): 0 off, 1 plain,
+                                 // 2 the learned indicator (BatchInst::s)
   double gamma;
 };
 
@@ -80,10 +83,10 @@ __device__ __forceinline__ void batch_stage_body(const BatchInst* __restrict__ i
       A.sg[o] = S.sg[o];
     }
     A.dt = I.dt;
-    A.s_ext = nullptr;
+    A.s_ext = I.s;
     A.limiter = S.limiter;
     A.blend = S.blend;
-    A.blend_external = 0;
+    A.blend_external = S.blend == 2;
     A.gamma = S.gamma;
     A.tol = I.tol;
     A.stats = stats;
@@ -125,5 +128,10 @@ cudaError_t batch_launch_blend(int prec, int flux, int tx, int ty, const BatchIn
 // the diffusion kind all instances share (pme_e its PME exponent), -1 if they differ.
 cudaError_t batch_launch_stream(int flux, int diff, int pme_e, const BatchInst* inst, const int* items, int total,
                                 const BatchStage& St, DevStats* stats, int S, cudaStream_t s);
+
+// The learned indicator (mlp.cu) of every instance's state buffer `in` into its array
+// s: `total` 32 x 8 tiles, instance k's from inst[k].ind_begin on; prec AF_PREC_*.
+cudaError_t mlp_indicator_batch_launch(const af_mlp* net, const BatchInst* inst, int n, int total, int in, int prec,
+                                       cudaStream_t s);
 
 }  // namespace af

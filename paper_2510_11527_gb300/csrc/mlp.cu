@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "af.h"
+#include "batch2d.cuh"
 #include "ctx.h"
 
 namespace {
@@ -204,12 +205,14 @@ __device__ __forceinline__ void net_rows(const NetFrags& F, const __nv_bfloat16 
 #define AF_INDICATOR_MIN_CTAS 3
 #endif
 
+// One 32 x 8 tile (cells i0 .. i0 + 31, j0 .. j0 + 7) of a periodic mesh: the patches
+// are gathered into shared memory, each warp runs the network on its row of 32 cells
+// and writes s. Called by all 256 threads of the CTA, which it leaves synchronised.
 template <class PT>
-__global__ void __launch_bounds__(256, AF_INDICATOR_MIN_CTAS) indicator_kernel(const double* __restrict__ ub, const PT* __restrict__ V,
-                                                           const PT* __restrict__ X, const PT* __restrict__ Y, int nx,
-                                                           int ny, const __nv_bfloat16* __restrict__ w1q,
-                                                           const __nv_bfloat16* __restrict__ w2q,
-                                                           const float* __restrict__ params, double* __restrict__ out) {
+__device__ __forceinline__ void indicator_tile(const NetFrags& F, const double* __restrict__ ub,
+                                               const PT* __restrict__ V, const PT* __restrict__ X,
+                                               const PT* __restrict__ Y, int nx, int ny, int i0, int j0,
+                                               double* __restrict__ out) {
   constexpr int UX = 36, UY = 12, PX = 33, PY = 9;
   constexpr int kPatchA[13] = {-1, 0, 1, -1, 0, 1, -1, 0, 1, -2, 2, 0, 0};
   constexpr int kPatchB[13] = {-1, -1, -1, 0, 0, 0, 1, 1, 1, 0, 0, -2, 2};
@@ -217,11 +220,7 @@ __global__ void __launch_bounds__(256, AF_INDICATOR_MIN_CTAS) indicator_kernel(c
   __shared__ float sV[PY][PX], sX[PY][PX], sY[PY][PX];
   __shared__ __align__(16) __nv_bfloat16 sx[8][32][40];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  NetFrags F;
-  load_frags(F, w1q, w2q, params, lane);
-  const int tiles_x = (nx + 31) / 32, tiles = tiles_x * ((ny + 7) / 8);
-  for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
-    const int i0 = (t % tiles_x) * 32, j0 = (t / tiles_x) * 8;
+  {
     for (int k = tid; k < UX * UY; k += 256) {
       const int bx = k % UX, by = k / UX;
       sU[by][bx] = af::to_stencil<float>(ub[(size_t)wrapm(j0 - 2 + by, ny) * nx + wrapm(i0 - 2 + bx, nx)]);
@@ -268,6 +267,43 @@ __global__ void __launch_bounds__(256, AF_INDICATOR_MIN_CTAS) indicator_kernel(c
       if (j < ny && i < nx) out[(size_t)j * nx + i] = af::f2d_exact(s);
     }
     __syncthreads();
+  }
+}
+
+template <class PT>
+__global__ void __launch_bounds__(256, AF_INDICATOR_MIN_CTAS) indicator_kernel(const double* __restrict__ ub, const PT* __restrict__ V,
+                                                           const PT* __restrict__ X, const PT* __restrict__ Y, int nx,
+                                                           int ny, const __nv_bfloat16* __restrict__ w1q,
+                                                           const __nv_bfloat16* __restrict__ w2q,
+                                                           const float* __restrict__ params, double* __restrict__ out) {
+  NetFrags F;
+  load_frags(F, w1q, w2q, params, threadIdx.x & 31);
+  const int tiles_x = (nx + 31) / 32, tiles = tiles_x * ((ny + 7) / 8);
+  for (int t = blockIdx.x; t < tiles; t += gridDim.x)
+    indicator_tile<PT>(F, ub, V, X, Y, nx, ny, (t % tiles_x) * 32, (t / tiles_x) * 8, out);
+}
+
+// The same over every instance of a batch (state buffer `in` of each, s into its
+// indicator array): the 32 x 8 tiles of instance k are numbered from inst[k].ind_begin
+// on, so a tile's instance is found by bisection.
+template <class PT>
+__global__ void __launch_bounds__(256, AF_INDICATOR_MIN_CTAS)
+    indicator_batch_kernel(const af::BatchInst* __restrict__ inst, int n, int total, int in,
+                           const __nv_bfloat16* __restrict__ w1q, const __nv_bfloat16* __restrict__ w2q,
+                           const float* __restrict__ params) {
+  NetFrags F;
+  load_frags(F, w1q, w2q, params, threadIdx.x & 31);
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    int lo = 0, hi = n - 1;   // the last instance whose first tile is <= w
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (inst[mid].ind_begin <= w) lo = mid;
+      else hi = mid - 1;
+    }
+    const af::BatchInst& I = inst[lo];
+    const int t = w - I.ind_begin, tiles_x = (I.nx + 31) / 32;
+    indicator_tile<PT>(F, I.ub[in], (const PT*)I.pv[in], (const PT*)I.px[in], (const PT*)I.py[in], I.nx, I.ny,
+                       (t % tiles_x) * 32, (t / tiles_x) * 8, I.s);
   }
 }
 
@@ -467,6 +503,17 @@ cudaError_t mlp_indicator_launch(const af_ctx* c, const af_mlp* net, int buf, do
     indicator_kernel<float><<<grid, 256, 0, c->stream>>>(c->ub[buf], (const float*)c->pv[buf],
                                                          (const float*)c->px[buf], (const float*)c->py[buf], c->nx,
                                                          c->ny, net->w1q, net->w2q, net->params, out);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_indicator_batch_launch(const af_mlp* net, const BatchInst* inst, int n, int total, int in, int prec,
+                                       cudaStream_t s) {
+  if (total < 1 || n < 1) return cudaErrorInvalidValue;
+  const int grid = (int)std::min<long long>(total, 152LL * AF_INDICATOR_MIN_CTAS);
+  if (prec == AF_PREC_FP64)
+    indicator_batch_kernel<double><<<grid, 256, 0, s>>>(inst, n, total, in, net->w1q, net->w2q, net->params);
+  else
+    indicator_batch_kernel<float><<<grid, 256, 0, s>>>(inst, n, total, in, net->w1q, net->w2q, net->params);
   return cudaGetLastError();
 }
 }  // namespace af

@@ -145,11 +145,28 @@ def test_batch_rejects_mixed_flux_kinds_and_blend():
     with pytest.raises(capi.AfError) as ei:
         capi.af_batch_create(*_structs([s1, s2], "fp64", 3))
     assert ei.value.status == capi.AF_E_ARG
+    # the external indicator comes from an attached network: none attached, no step
     g, f, d, b, o = _structs([s1], "fp64", 3)
-    o.blend = 2   # the external (learned) indicator is a single-mesh option
-    with pytest.raises(capi.AfError) as ei:
-        capi.af_batch_create(g, f, d, b, o)
-    assert ei.value.status == capi.AF_E_UNSUPPORTED
+    o.blend = 2
+    bt = capi.af_batch_create(g, f, d, b, o)
+    try:
+        for call in (lambda: capi.af_batch_step(bt, 1), lambda: capi.af_batch_autotune(bt)):
+            with pytest.raises(capi.AfError) as ei:
+                call()
+            assert ei.value.status == capi.AF_E_STATE
+    finally:
+        capi.af_batch_destroy(bt)
+    # a network needs a batch created for it
+    o.blend = 1
+    bt = capi.af_batch_create(g, f, d, b, o)
+    net = capi.af_mlp_create()
+    try:
+        with pytest.raises(capi.AfError) as ei:
+            capi.af_batch_set_mlp(bt, net)
+        assert ei.value.status == capi.AF_E_STATE
+    finally:
+        capi.af_batch_destroy(bt)
+        capi.af_mlp_destroy(net)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
@@ -190,6 +207,60 @@ def test_batch_plain_blend_matches_single_mesh_and_oracle(prec):
                 assert max(np.max(np.abs(x.reshape(r.shape) - r)) for x, r in zip(got, ref)) <= 1e-12
     finally:
         capi.af_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
+def test_batch_learned_blend_matches_single_mesh(prec):
+    """The learned indicator in the batch path: one launch per stage forms s for every
+    instance (uneven sizes, ragged 32 x 8 tiles) with the network, then the blended
+    stage reads it. Each instance agrees with a single-mesh context running the same
+    network (FP64 within 1e-12, FP32 within its stencils' rounding), the indicator is
+    the network's (the result differs from the plain blend's), and detaching the
+    network stops the batch."""
+    from paper_2510_11527_gb300 import Solver, capi
+    inst = _instances(count=5, seed=17, nmax=90)
+    specs = [s for s, _ in inst]
+    states = [[a.numpy() for a in ai.batch_state(s, m)] for s, m in inst]
+    net = capi.af_mlp_create()
+    capi.af_mlp_set_params(net, ai.mlp_init_params(6))
+    finals = {}
+    try:
+        for mode in (2, 1):
+            g, f, d, bd, o = _structs(specs, prec, 3)
+            o.blend = mode
+            b = capi.af_batch_create(g, f, d, bd, o)
+            try:
+                if mode == 2:
+                    capi.af_batch_set_mlp(b, net)
+                for i, (s, st) in enumerate(zip(specs, states)):
+                    capi.af_batch_set_state(b, i, s.cells, *st)
+                capi.af_batch_step(b, 2)
+                capi.af_batch_sync(b)
+                assert capi.af_batch_stats(b)["errors"] == 0
+                finals[mode] = [capi.af_batch_get_state(b, i, s.cells) for i, s in enumerate(specs)]
+                if mode == 2:
+                    capi.af_batch_set_mlp(b, None)
+                    with pytest.raises(capi.AfError) as ei:
+                        capi.af_batch_step(b, 1)
+                    assert ei.value.status == capi.AF_E_STATE
+            finally:
+                capi.af_batch_destroy(b)
+        tol = 1e-12 if prec == "fp64" else 2e-6
+        moved = 0.0
+        for i, (s, st) in enumerate(zip(specs, states)):
+            s.blend = "external"
+            with Solver(s, precision=prec, rk=3) as one:
+                capi.af_set_mlp(one.ctx, net)
+                one.set_state(st)
+                for _ in range(2):
+                    one.step(0.0)
+                want = one.get_state()
+            for x, y in zip(finals[2][i], want):
+                assert np.max(np.abs(x.reshape(y.shape) - y)) <= tol
+            moved = max(moved, float(np.max(np.abs(finals[2][i][0] - finals[1][i][0]))))
+        assert moved > 100 * tol
+    finally:
+        capi.af_mlp_destroy(net)
 
 
 def test_batch_cfl_interior_extrema_bl():
