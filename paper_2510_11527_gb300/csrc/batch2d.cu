@@ -142,7 +142,8 @@ struct af_batch {
   int n = 0, flux = 0, prec = AF_PREC_FP64, rk = AF_RK_SSP3, nbuf = 3, limiter = 1, blend = 0;
   double cfl = 0.165, cfl_diff = 0.0, gamma = 1.0;
   int tx = 32, ty = 8, total_tiles = 0;
-  // FP32-mixed without the blend: column-marching items (strips of stream_S rows)
+  // FP32-mixed without the blend: column-marching items (strips of stream_S rows,
+  // chosen in build_work)
   int stream_S = 32, total_items = 0, diff_uniform = -1, pme_e = 0;
   int* d_items = nullptr;
   // the learned indicator (blend 2): the attached network, its 32 x 8 tiles over every
@@ -328,7 +329,21 @@ af_status build_work(af_batch* b) {
     for (int t = 0; t < I.tiles_x * tiles_y; ++t) work.push_back(k);
   }
   b->total_tiles = (int)work.size();
-  // column-marching items of every instance (FP32-mixed without the blend)
+  // column-marching items of every instance (FP32-mixed without the blend). Strip
+  // height: the tallest of 128, 64, 32 rows that still gives every resident warp slot
+  // (SMs x 16 warps) at least 8 items -- each strip repeats a 4-row warm-up and its
+  // setup, so taller strips cost less per row (256 instances of 64^2..1024^2: S = 32
+  // 1.57e10, 64 1.77e10, 128 1.86e10 cell-stage/s)
+  {
+    long long rows = 0;
+    for (int k = 0; k < b->n; ++k)
+      rows += (long long)((b->h_inst[k].nx + af::BATCH_STREAM_BAND - 1) / af::BATCH_STREAM_BAND) * b->h_inst[k].ny;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    const long long want = 8LL * 16 * sms;
+    b->stream_S = rows / 128 >= want ? 128 : (rows / 64 >= want ? 64 : 32);
+  }
   std::vector<int> items;
   for (int k = 0; k < b->n; ++k) {
     BatchInst& I = b->h_inst[k];
