@@ -49,9 +49,9 @@ BYTES_PER_CELL_STAGE_1D = {"fp64": 42.67, "fp32_mixed": 32.0}
 # 3D (8 FP64 arrays per state): SSP-RK3 passes (2 + 3 + 3) / 3 per stage; and the
 # algorithmic flops of one limited forward-Euler evaluation per cell on the 3D
 # porous-medium workload (the oracle's count, pointwise functions evaluated once per
-# location as in the 2D count)
+# location as in the 2D count; f = 0, whose convection terms neither side forms)
 BYTES_PER_CELL_STAGE_3D = 170.67
-FLOPS_PER_CELL_STAGE_3D = 1895.56
+FLOPS_PER_CELL_STAGE_3D = 791.56
 # dram__bytes_read.sum + dram__bytes_write.sum of one stage launch (SSP-RK3 stage 2) from
 # the ncu captures summarised in profiles/stage2d_fp64_degenerate_burgers_1024.md and
 # profiles/stream2d_fp32mixed_degenerate_burgers_2048.md, keyed by (precision, n); null
@@ -627,8 +627,8 @@ def _form_pme3d(args, stream, peaks):
     gbs = BYTES_PER_CELL_STAGE_3D * cells / stage_s / 1e9
     out["roofline"] = {"bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                        "frac": round(tf / FP64_PEAK_TFLOPS, 4), "flops_per_cell_stage": FLOPS_PER_CELL_STAGE_3D,
-                       "flops_note": "the oracle's count includes the convection terms of f = 0 (exact zeros), "
-                                     "which the CUDA stage does not form: achieved is an upper bound",
+                       "flops_note": "pure diffusion (f = 0): the count holds the diffusion, limiter and update "
+                                     "operations; neither the oracle nor the CUDA stage forms the zero flux's terms",
                        "hbm_view": {"achieved_gbs": round(gbs, 1), "peak_gbs": peaks["hbm_gbs"],
                                     "frac": round(gbs / peaks["hbm_gbs"], 4),
                                     "bytes_per_cell_stage": BYTES_PER_CELL_STAGE_3D}}

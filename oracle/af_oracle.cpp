@@ -390,6 +390,14 @@ R line_residual(const R z[5], const R f[5], const R df[5], const R a[5], R h) {
   return -(Dp + Dm) + D2;
 }
 
+// The diffusion part of line_residual alone (f = 0): the compact fourth-order second
+// derivative of a, the same expression and order of operations.
+template <class R>
+R line_diffusion(const R a[5], R h) {
+  return (R(-1.0 / 3.0) * a[0] + R(16.0 / 3.0) * a[1] - R(10.0) * a[2] + R(16.0 / 3.0) * a[3] -
+          R(1.0 / 3.0) * a[4]) / (h * h);
+}
+
 // First-order point residual on the +-h/2 neighbours (reading for the blend's
 // low-order point scheme): -(2/h)[F(z0,z+) - F(z-,z0)] + (4/h^2)(a+ - 2 a0 + a-).
 template <class R>
@@ -604,6 +612,11 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
           const R* s_ext, R* ub_o, R* const* P_o) {
   const ao_problem& p = m.p;
   const int nk = 1 << d;
+  // f = 0 (pure diffusion): the convection terms of the high-order face fluxes, the
+  // point residuals and the low-order fluxes and states are identically zero and are
+  // not formed (the values are the same: x - 0 and -(0 + 0) + y are exact); the flop
+  // count then holds the pure-diffusion method's own operations
+  const bool conv = p.flux_kind != 0;
   int nn[3] = {1, 1, 1};
   for (int l = 0; l < d; ++l) nn[l] = n[l];
   const size_t N = (size_t)nn[0] * nn[1] * nn[2];
@@ -718,7 +731,7 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
         fp[l] += 1;
         int kp, km, k0;
         const size_t qp = at(fp, kp), qm = at(fm, km), q0 = at(f, k0);
-        fs = fs + wgt * Pf[kp][l][qp];   // face point at fine 2i + 1 along l
+        if (conv) fs = fs + wgt * Pf[kp][l][qp];   // face point at fine 2i + 1 along l
         R ahat = (-Pa[km][qm] + R(8.0) * Pa[k0][q0] - Pa[kp][qp]) / R(6.0);
         as = as + wgt * ahat;
         tot6 = tot;
@@ -749,7 +762,7 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
           df[t] = Pd[kt][l][qt];
           a[t] = Pa[kt][qt];
         }
-        RH[s][l][q] = line_residual<R>(z, fl, df, a, h[l]);
+        RH[s][l][q] = conv ? line_residual<R>(z, fl, df, a, h[l]) : line_diffusion<R>(a, h[l]);
       }
     }
 
@@ -770,12 +783,21 @@ void fend(const Model& m, int d, const int* n, const R* h, const R* ub, const R*
     ULp[l].resize(N);
     ULm[l].resize(N);
     for (size_t q = 0; q < N; ++q) {
+      if (!conv) {
+        FL[l][q] = R(0.0);
+        continue;
+      }
       size_t qp = nb(q, l, 1);
       R al = alpha_interval<R>(m, l, ub[q], ub[qp]);
       FL[l][q] = R(0.5) * (fU[l][q] + fU[l][qp]) - R(0.5) * al * (ub[qp] - ub[q]);
     }
     for (size_t q = 0; q < N; ++q) {
       size_t qp = nb(q, l, 1), qm = nb(q, l, -1);
+      if (!conv) {
+        ULp[l][q] = ub[q] + twod * nu[l] * (aU[qp] - aU[q]);
+        ULm[l][q] = ub[q] - twod * nu[l] * (aU[q] - aU[qm]);
+        continue;
+      }
       ULp[l][q] = ub[q] - twod * mu[l] * (FL[l][q] - fU[l][q]) + twod * nu[l] * (aU[qp] - aU[q]);
       ULm[l][q] = ub[q] - twod * mu[l] * (fU[l][q] - FL[l][qm]) - twod * nu[l] * (aU[q] - aU[qm]);
     }
