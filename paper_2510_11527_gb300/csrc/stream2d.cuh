@@ -654,15 +654,17 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, BK>()
 
 // ---- launch (host)
 
-// Strip height of the column-marching kernel: about four waves of 16 resident warps
-// per SM, at least 16 rows (the warm-up of a strip is 4 rows) and at most 64 (measured
-// on 1024^2 to 4096^2 meshes).
+// Strip height of the column-marching kernel: about two and a half waves of 16
+// resident warps per SM, at least 16 rows (the warm-up of a strip is 4 rows) and at
+// most 128. Measured stage times: 1024^2 S = 8/12/16: 0.0549/0.0544/0.0543 ms; 2048^2
+// S = 16/24/32/48: 0.1487/0.1451/0.1468/0.1494 ms; 4096^2 S = 62/96/128:
+// 0.477/0.471/0.508 ms.
 static int stream_strip(int nx, int ny) {
   const long long bands = (nx + STREAM_BAND - 1) / STREAM_BAND;
-  const long long target = 152LL * 16 * 4;
+  const long long target = 152LL * 16 * 5 / 2;
   long long S = (bands * ny + target - 1) / target;
   if (S < 16) S = 16;
-  if (S > 64) S = 64;
+  if (S > 128) S = 128;
   return (int)S;
 }
 
