@@ -451,11 +451,11 @@ __device__ __forceinline__ void k4_point(const DevModel& m, const StageArgs3D<T>
 }
 
 // One thread per cell: the average, then the 7 point kinds. MINB resident CTAs per SM:
-// the FP64 form leaves the registers to the compiler (it is bound by the FP64 unit);
-// the FP32-mixed form is bound by latency and takes 8 CTAs per SM at <= 64 registers
-// (porous medium 128^3, FP32-mixed stage: 1.24 ms with the compiler's 127 registers
-// and 4 CTAs per SM; 0.92 / 0.90 / 0.90 ms at 6 / 8 / 10 CTAs per SM; splitting a
-// cell's 8 values over 2, 4 or 8 threads measured 0.97, 1.09, 1.35 ms)
+// FP64 4 (the most its 46 KB of shared memory allow; 90-99 registers, none spilled;
+// porous medium 128^3 stage 2.59 ms at the compiler's 149 registers and 3 CTAs, 2.39 ms
+// at 4); FP32-mixed 8 at <= 64 registers (stage 1.24 ms with the compiler's 127
+// registers and 4 CTAs per SM; 0.92 / 0.90 / 0.90 ms at 6 / 8 / 10 CTAs per SM;
+// splitting a cell's 8 values over 2, 4 or 8 threads measured 0.97, 1.09, 1.35 ms)
 template <int FLUX, class T, int MINB>
 __global__ void __launch_bounds__(U3T, MINB) update3d_tile_kernel(const DevModel m, const StageArgs3D<T> A, int o) {
   const double dtv = *A.dt;
@@ -565,7 +565,7 @@ cudaError_t run3d(const DevModel& m, const StageArgs3D<T>& a, cudaStream_t s) {
   cellq3d_kernel<FLUX, T><<<(unsigned)tiles, U3T, 0, s>>>(m, a);
   for (int o = 0; o < a.nout; ++o) {
     limit3d_kernel<FLUX, T><<<grid, T3, 0, s>>>(m, a, o);
-    update3d_tile_kernel<FLUX, T, sizeof(T) == 4 ? 8 : 1><<<(unsigned)tiles, U3T, 0, s>>>(m, a, o);
+    update3d_tile_kernel<FLUX, T, sizeof(T) == 4 ? 8 : 4><<<(unsigned)tiles, U3T, 0, s>>>(m, a, o);
   }
   return cudaGetLastError();
 }
