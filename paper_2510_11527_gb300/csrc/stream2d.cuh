@@ -654,24 +654,27 @@ __global__ void __launch_bounds__(32 * STREAM_WPB, stream_min_blocks<FLUX, BK>()
 
 // ---- launch (host)
 
-// Strip height of the column-marching kernel: about two and a half waves of 16
-// resident warps per SM, at least 16 rows (the warm-up of a strip is 4 rows) and at
-// most 128. Measured stage times: 1024^2 S = 8/12/16: 0.0549/0.0544/0.0543 ms; 2048^2
-// S = 16/24/32/48: 0.1487/0.1451/0.1468/0.1494 ms; 4096^2 S = 62/96/128:
-// 0.477/0.471/0.508 ms.
-static int stream_strip(int nx, int ny) {
+// Strip height of the column-marching kernel, at least 16 rows (the warm-up of a strip
+// is 4 rows). At 16 resident warps per SM (4 CTAs): about two and a half waves, at most
+// 128 rows (measured stage times, degenerate Burgers: 1024^2 S = 8/12/16:
+// 0.0549/0.0544/0.0543 ms; 2048^2 S = 16/24/32/48: 0.1487/0.1451/0.1468/0.1494 ms;
+// 4096^2 S = 62/96/128: 0.477/0.471/0.508 ms). The heavier kernels at 12 warps per SM
+// (Buckley-Leverett, the blend) keep about four waves of 16 warps and at most 64 rows:
+// the blended Buckley-Leverett stage at 4096^2 lost 4 % at S = 100 (3.3 waves, the last
+// one partly filled) against S = 62.
+static int stream_strip(int nx, int ny, bool heavy) {
   const long long bands = (nx + STREAM_BAND - 1) / STREAM_BAND;
-  const long long target = 152LL * 16 * 5 / 2;
+  const long long target = heavy ? 152LL * 16 * 4 : 152LL * 16 * 5 / 2;
   long long S = (bands * ny + target - 1) / target;
   if (S < 16) S = 16;
-  if (S > 128) S = 128;
+  if (S > (heavy ? 64 : 128)) S = heavy ? 64 : 128;
   return (int)S;
 }
 
 // one launch per output of the stage
 template <int FLUX, int DIFF, int BK = 0>
 static cudaError_t stream2d_go(const DevModel& m, const StageArgs2D<float>& a, cudaStream_t s) {
-  const int S = stream_strip(a.nx, a.ny);
+  const int S = stream_strip(a.nx, a.ny, stream_min_blocks<FLUX, BK>() < 4);
   const int bands = (a.nx + STREAM_BAND - 1) / STREAM_BAND;
   const long long warps = (long long)bands * ((a.ny + S - 1) / S);
   const long long blocks = (warps + STREAM_WPB - 1) / STREAM_WPB;
