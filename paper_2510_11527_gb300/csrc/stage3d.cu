@@ -131,17 +131,16 @@ __global__ void __launch_bounds__(T3) centre3d_kernel(const StageArgs3D<T> A) {
   }
 }
 
-// low-order directional states of cell q along l (Lemma 5.1 with factor 2d = 6)
-// (q: the cell, qp / qm: its neighbour after / before it along l)
-template <int FLUX, class T>
-__device__ __forceinline__ T ulp3(const DevModel& m, const StageArgs3D<T>& A, size_t q, size_t qp, int l, T mu6, T nu6) {
-  const T u = to_stencil<T>(A.ub[q]), un = to_stencil<T>(A.ub[qp]);
-  return u - mu6 * (A.FL[l][q] - flux<FLUX, T>(m, l, u)) + nu6 * (apot<T>(m, un) - apot<T>(m, u));
+// low-order directional states of a cell along l (Lemma 5.1 with factor 2d = 6), from
+// its average u, f_l(u), a(u), the LLF flux of its face after (FLp) or before (FLm) and
+// a at its neighbour after (an) or before (am): each f and a is formed once per cell
+template <class T>
+__device__ __forceinline__ T ulp3(T u, T fu, T au, T FLp, T an, T mu6, T nu6) {
+  return u - mu6 * (FLp - fu) + nu6 * (an - au);
 }
-template <int FLUX, class T>
-__device__ __forceinline__ T ulm3(const DevModel& m, const StageArgs3D<T>& A, size_t q, size_t qm, int l, T mu6, T nu6) {
-  const T u = to_stencil<T>(A.ub[q]), um = to_stencil<T>(A.ub[qm]);
-  return u - mu6 * (flux<FLUX, T>(m, l, u) - A.FL[l][qm]) - nu6 * (apot<T>(m, u) - apot<T>(m, um));
+template <class T>
+__device__ __forceinline__ T ulm3(T u, T fu, T au, T FLm, T am, T mu6, T nu6) {
+  return u - mu6 * (fu - FLm) - nu6 * (au - am);
 }
 
 template <int FLUX, class T>
@@ -181,11 +180,16 @@ __global__ void __launch_bounds__(T3) limit3d_kernel(const DevModel m, const Sta
         const T mu6 = sK[l][0], nu6 = sK[l][1];
         const T k = sK[l][2], kd = sK[l][3];
         const T dF = fh - fl;
-        const T zp = ulp3<FLUX, T>(m, A, q, qp, l, mu6, nu6), zm = ulm3<FLUX, T>(m, A, qp, q, l, mu6, nu6);
+        // the cell (u), its neighbours after (up) and before (um) along l
+        const T up = to_stencil<T>(A.ub[qp]), um = to_stencil<T>(A.ub[qm]);
+        const T fu = flux<FLUX, T>(m, l, u), fup = flux<FLUX, T>(m, l, up), fum = flux<FLUX, T>(m, l, um);
+        const T aup = apot<T>(m, up), aum = apot<T>(m, um);
+        const T flm = A.FL[l][qm];
+        const T zp = ulp3<T>(u, fu, au, fl, aup, mu6, nu6), zm = ulm3<T>(up, fup, aup, fl, au, mu6, nu6);
         const T tcl = tmin(theta_fn<T>(zp, zp - k * dF, umin, umax), theta_fn<T>(zm, zm + k * dF, umin, umax));
         flim = is_one(tcl) ? fh : fl + tcl * dF;
         const T dA = ah - au;
-        const T p0 = ulp3<FLUX, T>(m, A, qm, q, l, mu6, nu6), q0 = ulm3<FLUX, T>(m, A, q, qm, l, mu6, nu6);
+        const T p0 = ulp3<T>(um, fum, aum, flm, au, mu6, nu6), q0 = ulm3<T>(u, fu, au, flm, aum, mu6, nu6);
         const T td = tmin(tmin(theta_fn<T>(p0, p0 + kd * dA, umin, umax), theta_fn<T>(zp, zp - kd * dA, umin, umax)),
                           tmin(theta_fn<T>(q0, q0 - kd * dA, umin, umax), theta_fn<T>(zm, zm + kd * dA, umin, umax)));
         alim = is_one(td) ? ah : au + td * dA;
