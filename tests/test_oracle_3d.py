@@ -173,3 +173,35 @@ def test_diffusion_symbol_radius():
     assert oracle.diffusion_spectral_radius(1, 8) == pytest.approx(16.0, rel=1e-12)
     assert oracle.diffusion_spectral_radius(2, 4) == pytest.approx(40.777, rel=1e-4)
     assert oracle.diffusion_spectral_radius(3, 4) == pytest.approx(63.335, rel=1e-4)
+
+
+@pytest.mark.parametrize("blend", ["off", "plain"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_zero_flux_skips_only_exact_zeros(blend, dim):
+    """With f = 0 the generic evaluation does not form the convection terms (the Simpson
+    face fluxes, the flux part of every 5-point line, the LLF fluxes and their share of
+    the low-order states). A linear flux with zero velocities forms all of them, every
+    one an exact zero: the two evaluations agree exactly, and the flop count of f = 0 is
+    smaller by those terms alone (the diffusion, limiter and update operations stay)."""
+    diff = ("pme", (2,))
+    if dim == 3:
+        sz, st = _rough3d(flux=("zero", ()), diff=diff, blend=blend)
+        sl = dataclasses.replace(sz, flux=("linear", (0.0, 0.0, 0.0)))
+    else:
+        sz = ai.Spec(dim=2, nx=9, ny=7, x0=0.0, x1=0.9, y0=0.0, y1=0.7, flux=("zero", ()), diff=diff, umin=0.0,
+                     umax=1.0, limiter=True, blend=blend)
+        sl = dataclasses.replace(sz, flux=("linear", (0.0, 0.0)))
+        st = _np(ai.random_state_2d(sz, 19))
+    tau = oracle.dt_cfl(sz, st[0])
+    fz = oracle.fe_generic(sz, st, tau) if dim == 2 else oracle.fe(sz, st, tau)
+    fl = oracle.fe_generic(sl, st, tau) if dim == 2 else oracle.fe(sl, st, tau)
+    for a, b in zip(fz, fl):
+        assert np.array_equal(a, b)
+    if dim == 3:
+        cz = oracle.flop_count(sz, st, tau)
+        cl = oracle.flop_count(sl, st, tau)
+        nz = sum(cz[k] for k in ("add", "mul", "div"))
+        nl = sum(cl[k] for k in ("add", "mul", "div"))
+        assert 0 < nz < nl
+        # per cell, at least the 21 lines' convection parts (each far above 10 operations)
+        assert (nl - nz) / st[0].size > 21 * 10
