@@ -23,7 +23,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.
 # Per-file flags: the column-marching kernel forms every face term in two places and
 # needs an arithmetic without compiler contraction (see csrc/stream2d_f32.cu).
 FILE_FLAGS = {"stream2d_f32.cu": ["-fmad=false"], "stream2d_blend_f32.cu": ["-fmad=false"],
-              "batch2d_stream.cu": ["-fmad=false"]}
+              "batch2d_stream.cu": ["-fmad=false"], "batch2d_stream_blend.cu": ["-fmad=false"]}
 
 
 def _sources():

@@ -219,6 +219,9 @@ cudaError_t launch_stage_shape(af_batch* b, const BatchStage& S) {
   if (sizeof(T) == 4 && !b->blend)
     return af::batch_launch_stream(b->flux, b->diff_uniform, b->pme_e, b->d_inst, b->d_items, b->total_items, S,
                                    b->d_stats, b->stream_S, b->stream);
+  if (sizeof(T) == 4)
+    return af::batch_launch_stream_blend(b->flux, b->blend, b->diff_uniform, b->d_inst, b->d_items, b->total_items,
+                                         S, b->d_stats, b->stream_S, b->stream);
   if (b->blend)
     return af::batch_launch_blend(b->prec, b->flux, b->tx, b->ty, b->d_inst, b->d_work, b->total_tiles, S,
                                   b->d_stats, b->stream);
@@ -331,7 +334,7 @@ af_status build_work(af_batch* b) {
   b->total_tiles = (int)work.size();
   // column-marching items of every instance (FP32-mixed without the blend). Strip
   // height: the tallest of 128, 64, 32 rows that still gives every resident warp slot
-  // (SMs x 16 warps) at least 8 items -- each strip repeats a 4-row warm-up and its
+  // (SMs x resident warps) at least 8 items -- each strip repeats a 4-row warm-up and its
   // setup, so taller strips cost less per row (256 instances of 64^2..1024^2: S = 32
   // 1.57e10, 64 1.77e10, 128 1.86e10 cell-stage/s)
   {
@@ -341,7 +344,9 @@ af_status build_work(af_batch* b) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
-    const long long want = 8LL * 16 * sms;
+    // resident warps per SM of the column-marching kernel: 12 for Buckley-Leverett and
+    // the blend (3 CTAs of 4 warps), else 16
+    const long long want = 8LL * ((b->blend || b->flux == AF_FLUX_BL) ? 12 : 16) * sms;
     b->stream_S = rows / 128 >= want ? 128 : (rows / 64 >= want ? 64 : 32);
   }
   std::vector<int> items;
@@ -372,9 +377,12 @@ af_status build_work(af_batch* b) {
 af_status enqueue_step(af_batch* b) {
   BCK(b, launch_dt(b));
   for (const auto& s : stages_of(b)) {
-    // the learned blend: s of every instance from this stage's input first
+    // the indicator of every instance from this stage's input first: learned, or the
+    // plain one for the FP32-mixed column-marching stage (the tile kernels form it)
     if (b->blend == 2)
       BCK(b, af::mlp_indicator_batch_launch(b->mlp, b->d_inst, b->n, b->ind_total, s.in, b->prec, b->stream));
+    else if (b->blend == 1 && b->prec == AF_PREC_FP32_MIXED)
+      BCK(b, af::batch_launch_blend_s(b->d_inst, b->n, b->ind_total, s.in, b->stream));
     BCK(b, launch_stage(b, s));
   }
   return AF_OK;
@@ -489,7 +497,10 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     I.ind_begin = b->ind_total;
     b->ind_total += ((g.nx + 31) / 32) * ((g.ny + 7) / 8);
   }
-  if (b->blend == 2) {
+  // indicator arrays: the learned one (one double per cell), or the plain one of the
+  // FP32-mixed column-marching stage (s_1, s_2 as FP32)
+  const bool plain32 = b->blend == 1 && b->prec == AF_PREC_FP32_MIXED;
+  if (b->blend == 2 || plain32) {
     size_t stotal = 0;
     for (int k = 0; k < n; ++k) stotal += al((size_t)grids[k].nx * grids[k].ny * 8);
     if (cudaMalloc(&b->d_s, stotal) != cudaSuccess) {
@@ -500,8 +511,14 @@ af_status af_batch_create(int n, const af_grid* grids, const af_flux* fluxes, co
     }
     unsigned char* q = (unsigned char*)b->d_s;
     for (int k = 0; k < n; ++k) {
-      b->h_inst[k].s = (double*)q;
-      q += al((size_t)grids[k].nx * grids[k].ny * 8);
+      const size_t c = (size_t)grids[k].nx * grids[k].ny;
+      if (plain32) {
+        b->h_inst[k].sb[0] = (float*)q;
+        b->h_inst[k].sb[1] = (float*)q + c;
+      } else {
+        b->h_inst[k].s = (double*)q;
+      }
+      q += al(c * 8);
     }
   }
   // the diffusion kind every instance shares (compiled into the column-marching stage)

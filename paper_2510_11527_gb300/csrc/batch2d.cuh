@@ -19,8 +19,9 @@ struct BatchInst {
   float i6hf[2], i3h2f[2];       // the same in FP32
   int tile_begin, tiles_x;       // first work item of this instance, tiles along x
   int item_begin, bands;         // column-marching items: first item, bands of 28 columns
-  int ind_begin;                 // first 32 x 8 tile of the learned indicator's launch
+  int ind_begin;                 // first 32 x 8 tile of the indicators' launches
   double* s;                     // learned indicator per cell (blend with the network)
+  float* sb[2];                  // plain indicator s_1, s_2 per cell (FP32-mixed blend)
   double* ub[4];
   void* pv[4];
   void* px[4];
@@ -128,6 +129,17 @@ cudaError_t batch_launch_blend(int prec, int flux, int tx, int ty, const BatchIn
 // the diffusion kind all instances share (pme_e its PME exponent), -1 if they differ.
 cudaError_t batch_launch_stream(int flux, int diff, int pme_e, const BatchInst* inst, const int* items, int total,
                                 const BatchStage& St, DevStats* stats, int S, cudaStream_t s);
+
+// The FP32-mixed stage with the blend on the column-marching kernel
+// (batch2d_stream_blend.cu): bk 1 the plain indicator (BatchInst::sb, formed first by
+// batch_launch_blend_s from the same input), bk 2 the learned one (BatchInst::s); diff
+// as for batch_launch_stream (AF_DIFF_CUBIC compiled in, any other kind read per
+// instance).
+cudaError_t batch_launch_stream_blend(int flux, int bk, int diff, const BatchInst* inst, const int* items, int total,
+                                      const BatchStage& St, DevStats* stats, int S, cudaStream_t s);
+// The plain indicator of every instance's state buffer `in` into its arrays sb: `total`
+// 32 x 8 tiles, instance k's from inst[k].ind_begin on.
+cudaError_t batch_launch_blend_s(const BatchInst* inst, int n, int total, int in, cudaStream_t s);
 
 // The learned indicator (mlp.cu) of every instance's state buffer `in` into its array
 // s: `total` 32 x 8 tiles, instance k's from inst[k].ind_begin on; prec AF_PREC_*.

@@ -6,50 +6,10 @@
 
 namespace af {
 
-// Plain smoothness indicator of Section 5.1.3 per cell, direction by direction
-// (Section 5.2): s~_l = |u_- - 2u + u_+| / (|u_-| + 2|u| + |u_+| + 1e-13) along l, then
-// s_l = (s~_{l,-1} + 4 s~_l + s~_{l,+1}) / 6, from the cell averages of the stage input
-// in the stencil precision (rounded as the stage kernel rounds them). One CTA per 32 x 8
-// tile: the averages of the tile and a +-2 halo are converted once in shared memory.
-constexpr int BS_TX = 32, BS_TY = 8, BS_H = 2, BS_BX = BS_TX + 2 * BS_H, BS_BY = BS_TY + 2 * BS_H;
-
 __global__ void __launch_bounds__(256) blend_s_kernel(const double* __restrict__ ub, int nx, int ny, double umid,
                                                       float* __restrict__ s1, float* __restrict__ s2) {
-  __shared__ float su[BS_BY][BS_BX];
-  __shared__ float st1[BS_TY][BS_TX + 2];   // s~_1 on columns -1 .. TX
-  __shared__ float st2[BS_TY + 2][BS_TX];   // s~_2 on rows -1 .. TY
   const int tiles_x = (nx + BS_TX - 1) / BS_TX;
-  const int i0 = (blockIdx.x % tiles_x) * BS_TX, j0 = (blockIdx.x / tiles_x) * BS_TY;
-  for (int q = threadIdx.x; q < BS_BX * BS_BY; q += blockDim.x) {
-    const int bx = q % BS_BX, by = q / BS_BX;
-    const int gi = wrapi(i0 - BS_H + bx, nx), gj = wrapi(j0 - BS_H + by, ny);
-    su[by][bx] = to_stencil_nb<float>(ub[(size_t)gj * nx + gi], umid);
-  }
-  __syncthreads();
-  // the quotient with the fast approximate division (2 ulp): the indicator only sets
-  // the blend weights, and the IEEE division cost this pass most of its time
-  auto stl = [](float a, float b, float c) {
-    return __fdividef(fabsf(a - 2.0f * b + c), fabsf(a) + 2.0f * fabsf(b) + fabsf(c) + 1e-13f);
-  };
-  for (int q = threadIdx.x; q < BS_TY * (BS_TX + 2); q += blockDim.x) {
-    const int x = q % (BS_TX + 2), y = q / (BS_TX + 2);
-    const int bx = x + BS_H - 1, by = y + BS_H;
-    st1[y][x] = stl(su[by][bx - 1], su[by][bx], su[by][bx + 1]);
-  }
-  for (int q = threadIdx.x; q < (BS_TY + 2) * BS_TX; q += blockDim.x) {
-    const int x = q % BS_TX, y = q / BS_TX;
-    const int bx = x + BS_H, by = y + BS_H - 1;
-    st2[y][x] = stl(su[by - 1][bx], su[by][bx], su[by + 1][bx]);
-  }
-  __syncthreads();
-  const int x = threadIdx.x % BS_TX, y = threadIdx.x / BS_TX;
-  const int gi = i0 + x, gj = j0 + y;
-  if (gi < nx && gj < ny) {
-    const float sixth = 1.0f / 6.0f;
-    const size_t g = (size_t)gj * nx + gi;
-    s1[g] = (st1[y][x] + 4.0f * st1[y][x + 1] + st1[y][x + 2]) * sixth;
-    s2[g] = (st2[y][x] + 4.0f * st2[y + 1][x] + st2[y + 2][x]) * sixth;
-  }
+  blend_s_tile(ub, nx, ny, umid, (blockIdx.x % tiles_x) * BS_TX, (blockIdx.x / tiles_x) * BS_TY, s1, s2);
 }
 
 // the diffusion kind: compiled in for the cubic potential (Buckley-Leverett), else the
