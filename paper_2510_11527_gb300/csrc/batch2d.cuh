@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(256, 6) batch_stage_kernel_f32occ6(const Batch
   batch_stage_body<FLUX, float, float, TX, TY, false>(inst, work_inst, total, S, stats);
 }
 
-// The blended stage kernels (instantiated in batch2d_blend.cu): one persistent launch
-// of `blocks` CTAs (0: the occupancy limit times the SM count) for tile shape tx x ty.
+// The blended FP64 stage kernels (instantiated in batch2d_blend.cu): one persistent
+// launch (the occupancy limit times the SM count) for tile shape tx x ty; prec must be
+// AF_PREC_FP64 (the FP32-mixed batch blends on the column-marching items).
 cudaError_t batch_launch_blend(int prec, int flux, int tx, int ty, const BatchInst* inst, const int* work, int total,
                                const BatchStage& S, DevStats* stats, cudaStream_t stream);
 

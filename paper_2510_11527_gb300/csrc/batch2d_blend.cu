@@ -1,6 +1,7 @@
-// Instantiations of the batched stage with the smoothness-indicator blend (Section
-// 5.1.3), kept in their own translation unit so that they compile in parallel with the
-// rest of the batch code.
+// Instantiations of the batched FP64 stage with the smoothness-indicator blend (Section
+// 5.1.3) on the tile kernel, kept in their own translation unit so that they compile in
+// parallel with the rest of the batch code. (The FP32-mixed batch runs the blend on the
+// column-marching items, batch2d_stream_blend.cu.)
 #include <algorithm>
 
 #include "batch2d.cuh"
@@ -53,8 +54,8 @@ cudaError_t flux(int fk, int tx, int ty, const BatchInst* inst, const int* work,
 
 cudaError_t batch_launch_blend(int prec, int fk, int tx, int ty, const BatchInst* inst, const int* work, int total,
                                const BatchStage& S, DevStats* stats, cudaStream_t stream) {
-  return prec == AF_PREC_FP64 ? flux<double>(fk, tx, ty, inst, work, total, S, stats, stream)
-                              : flux<float>(fk, tx, ty, inst, work, total, S, stats, stream);
+  if (prec != AF_PREC_FP64) return cudaErrorInvalidValue;
+  return flux<double>(fk, tx, ty, inst, work, total, S, stats, stream);
 }
 
 }  // namespace af
