@@ -172,8 +172,9 @@ def test_batch_rejects_mixed_flux_kinds_and_blend():
 @pytest.mark.parametrize("prec", ["fp64", "fp32_mixed"])
 def test_batch_plain_blend_matches_single_mesh_and_oracle(prec):
     """The smoothness-indicator blend (Section 5.1.3) in the batch path: instances of
-    uneven size with gamma = 1 agree with single-mesh contexts (FP64 within 1e-12, FP32
-    within its stencils' rounding) and, in FP64, with the oracle."""
+    uneven size with gamma = 1 agree with single-mesh contexts (FP64 within 1e-12; FP32-mixed
+    bit for bit: the batch runs the single mesh's column-marching blend) and, in FP64, with
+    the oracle."""
     from paper_2510_11527_gb300 import Solver, capi
     inst = _instances(count=5, seed=11, nmax=90)
     specs = []
@@ -197,7 +198,7 @@ def test_batch_plain_blend_matches_single_mesh_and_oracle(prec):
                 for _ in range(2):
                     one.step(0.0)
                 want = one.get_state()
-            tol = 1e-12 if prec == "fp64" else 2e-6
+            tol = 1e-12 if prec == "fp64" else 0.0   # FP32-mixed: the single mesh's column-marching arithmetic
             for x, y in zip(got, want):
                 assert np.max(np.abs(x.reshape(y.shape) - y)) <= tol
             if prec == "fp64":
@@ -214,7 +215,7 @@ def test_batch_learned_blend_matches_single_mesh(prec):
     """The learned indicator in the batch path: one launch per stage forms s for every
     instance (uneven sizes, ragged 32 x 8 tiles) with the network, then the blended
     stage reads it. Each instance agrees with a single-mesh context running the same
-    network (FP64 within 1e-12, FP32 within its stencils' rounding), the indicator is
+    network (FP64 within 1e-12, FP32-mixed bit for bit), the indicator is
     the network's (the result differs from the plain blend's), and detaching the
     network stops the batch."""
     from paper_2510_11527_gb300 import Solver, capi
@@ -245,7 +246,7 @@ def test_batch_learned_blend_matches_single_mesh(prec):
                     assert ei.value.status == capi.AF_E_STATE
             finally:
                 capi.af_batch_destroy(b)
-        tol = 1e-12 if prec == "fp64" else 2e-6
+        tol = 1e-12 if prec == "fp64" else 0.0   # FP32-mixed: the single mesh's column-marching arithmetic
         moved = 0.0
         for i, (s, st) in enumerate(zip(specs, states)):
             s.blend = "external"
@@ -258,7 +259,7 @@ def test_batch_learned_blend_matches_single_mesh(prec):
             for x, y in zip(finals[2][i], want):
                 assert np.max(np.abs(x.reshape(y.shape) - y)) <= tol
             moved = max(moved, float(np.max(np.abs(finals[2][i][0] - finals[1][i][0]))))
-        assert moved > 100 * tol
+        assert moved > 1e-10
     finally:
         capi.af_mlp_destroy(net)
 
